@@ -1,0 +1,346 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test checks the oracle against a fact that the paper or the mathematics
+fixes: published known-answer vectors of the generator, a library matrix
+exponential, the closed-form unmonitored evolution, a brute-force many-body
+state vector driven by the same draws, and exact invariants.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import lattice, observables, philox, trajectory
+from oracle.trajectory import HOMODYNE, PROJECTIVE, Params
+from tests import brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- generator
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_uniform_and_normal_draws():
+    u_sel, u_out = philox.measure_draws(seed=12345, traj_id=7, step=3, L=200000)
+    for u in (u_sel, u_out):
+        assert u.min() >= 0.0 and u.max() < 1.0
+        assert abs(u.mean() - 0.5) < 4 * np.sqrt(1 / 12 / u.size)
+        assert abs(u.var() - 1 / 12) < 0.002
+    assert abs(np.corrcoef(u_sel, u_out)[0, 1]) < 0.01
+    xi = philox.noise_normals(seed=12345, traj_id=7, step=3, L=200000)
+    assert abs(xi.mean()) < 4 / np.sqrt(xi.size)
+    assert abs(xi.var() - 1.0) < 0.015
+    assert abs(np.mean(xi ** 4) - 3.0) < 0.06          # Gaussian kurtosis
+    # distinct steps / trajectories / tags give distinct streams
+    a = philox.noise_normals(1, 0, 0, 64)
+    assert not np.allclose(a, philox.noise_normals(1, 0, 1, 64))
+    assert not np.allclose(a, philox.noise_normals(1, 1, 0, 64))
+    # 64-bit trajectory ids use the high counter bits
+    assert not np.allclose(philox.noise_normals(1, 5, 0, 64), philox.noise_normals(1, 5 + (1 << 32), 0, 64))
+
+
+# ---------------------------------------------------------------- propagator
+
+@pytest.mark.parametrize("Lx,Ly", [(2, 1), (3, 1), (8, 1), (17, 1), (64, 1), (4, 4), (4, 6), (6, 3)])
+def test_propagator_is_expm_of_hopping(Lx, Ly):
+    dt = 0.05
+    H = lattice.hopping_matrix(Lx, Ly, 1.0)
+    P = lattice.propagator(Lx, Ly, 1.0, dt)
+    ref = scipy.linalg.expm(-1j * dt * H)
+    assert np.max(np.abs(P - ref)) < 1e-13
+
+
+def test_hopping_matrix_bonds():
+    H = lattice.hopping_matrix(6, 1, 1.0)
+    assert H[0, 1] == 1.0 and H[0, 5] == 1.0 and H[0, 2] == 0.0 and np.allclose(H, H.T)
+    H2 = lattice.hopping_matrix(4, 3, 1.0)
+    # site (1, 2) = 9 neighbours (0,2)=8, (2,2)=10, (1,1)=5, (1,0)=1
+    assert sorted(np.nonzero(H2[9])[0].tolist()) == [1, 5, 8, 10]
+
+
+def test_propagator_unitary_and_semigroup():
+    P = lattice.propagator(32, 1, 1.0, 0.05)
+    assert np.max(np.abs(P @ P.conj().T - np.eye(32))) < 1e-14
+    P5 = lattice.propagator(32, 1, 1.0, 0.25)
+    assert np.max(np.abs(np.linalg.matrix_power(P, 5) - P5)) < 1e-13
+
+
+# ---------------------------------------------------------------- gamma = 0
+
+def _neel_density_closed_form(Lx, Ly, J, t):
+    """Unmonitored n_i(t) from the Neel / checkerboard start (derived in plane waves).
+
+    n_i(t) = 1/2 + 1/2 (-1)^{x+y} (1/L) sum_k cos(2 eps_k t), eps_k = 2J(cos kx + cos ky),
+    because eps_{k + (pi, pi)} = -eps_k.
+    """
+    kx = 2 * np.pi * np.arange(Lx) / Lx
+    if Ly == 1:
+        eps = 2 * J * np.cos(kx)
+        stag = (-1.0) ** np.arange(Lx)
+    else:
+        ky = 2 * np.pi * np.arange(Ly) / Ly
+        eps = (2 * J * (np.cos(kx)[None, :] + np.cos(ky)[:, None])).ravel()
+        stag = np.array([(-1.0) ** (x + y) for y in range(Ly) for x in range(Lx)])
+    return 0.5 + 0.5 * stag * np.mean(np.cos(2 * eps * t))
+
+
+@pytest.mark.parametrize("Lx,Ly,nsteps", [(64, 1, 200), (1024, 1, 30), (8, 6, 60)])
+def test_unmonitored_density_closed_form(Lx, Ly, nsteps):
+    prm = Params(Lx=Lx, Ly=Ly, gamma=0.0, protocol=PROJECTIVE, reorth_interval=10)
+    out = trajectory.run(prm, nsteps)
+    n = trajectory.occupations(out["U"])
+    ref = _neel_density_closed_form(Lx, Ly, 1.0, nsteps * prm.dt)
+    assert np.max(np.abs(n - ref)) < 1e-12
+    assert len(out["events"]) == 0
+
+
+# ---------------------------------------------------------------- brute force
+
+def _brute_setup(prm):
+    L = prm.L
+    occ = lattice.occupied_sites(prm.Lx, prm.Ly)
+    sec = brute.Sector(L, len(occ))
+    bonds = brute.ring_bonds(L) if prm.Ly == 1 else brute.torus_bonds(prm.Lx, prm.Ly)
+    E = brute.evolution_operator(sec, bonds, prm.J, prm.dt)
+    psi = np.zeros(sec.dim, dtype=np.complex128)
+    psi[sec.index[sum(1 << int(i) for i in occ)]] = 1.0
+    return sec, E, psi
+
+
+def _compare_projective(prm, nsteps, oracle_step=trajectory.step):
+    """Run oracle and brute force side by side; returns worst |C - conj(D)| and events."""
+    sec, E, psi = _brute_setup(prm)
+    U = lattice.initial_orbitals(prm.Lx, prm.Ly)
+    P = lattice.propagator(prm.Lx, prm.Ly, prm.J, prm.dt)
+    worst, all_events = 0.0, []
+    for s in range(nsteps):
+        U, events = oracle_step(U, P, prm, s)
+        psi = E @ psi
+        for (j, u, p, outcome) in events:
+            psi_try, w1 = sec.project(psi, j, 1)
+            assert abs(w1 - p) < 1e-11, (s, j, w1, p)
+            assert outcome == (1 if u < w1 else 0)
+            psi, _ = sec.project(psi, j, outcome)
+        all_events.extend(events)
+        D = sec.d_matrix(psi)
+        worst = max(worst, np.max(np.abs(observables.correlation(U) - np.conj(D))))
+    return worst, all_events, U, psi, sec
+
+
+@pytest.mark.parametrize("Lx,Ly,gamma,seed", [(8, 1, 2.0, 11), (10, 1, 1.0, 5), (4, 3, 3.0, 2)])
+def test_projective_matches_brute_force(Lx, Ly, gamma, seed):
+    prm = Params(Lx=Lx, Ly=Ly, gamma=gamma, protocol=PROJECTIVE, reorth_interval=3, seed=seed, traj_id=1)
+    worst, events, U, psi, sec = _compare_projective(prm, 40)
+    assert worst < 1e-12
+    outcomes = {e[3] for e in events}
+    assert len(events) >= 10 and outcomes == {0, 1}
+    # entropies of contiguous and non-contiguous subsystems vs Schmidt values
+    L = prm.L
+    for A in ([0, 1, 2], list(range(L // 2)), [0, 2, 5], [1, L - 1]):
+        assert abs(observables.entanglement_entropy(U, A) - sec.entropy(psi, A)) < 1e-11
+
+
+def _compare_homodyne(prm, nsteps, weight=trajectory.homodyne_weight):
+    sec, E, psi = _brute_setup(prm)
+    U = lattice.initial_orbitals(prm.Lx, prm.Ly)
+    P = lattice.propagator(prm.Lx, prm.Ly, prm.J, prm.dt)
+    worst = 0.0
+    for s in range(nsteps):
+        xi = philox.noise_normals(prm.seed, prm.traj_id, s, prm.L)
+        U = trajectory.orthonormalize(weight(P @ U, xi, prm.gamma, prm.dt))
+        psi = E @ psi
+        n = sec.occupation(psi)
+        m = np.sqrt(prm.gamma * prm.dt) * xi + (2 * n - 1) * prm.gamma * prm.dt
+        psi = sec.weight(psi, m)
+        worst = max(worst, np.max(np.abs(observables.correlation(U) - np.conj(sec.d_matrix(psi)))))
+    return worst, U, psi, sec
+
+
+@pytest.mark.parametrize("Lx,Ly,gamma", [(8, 1, 1.0), (10, 1, 0.3), (4, 2, 2.0)])
+def test_homodyne_matches_brute_force(Lx, Ly, gamma):
+    prm = Params(Lx=Lx, Ly=Ly, gamma=gamma, protocol=HOMODYNE, seed=99, traj_id=3)
+    worst, U, psi, sec = _compare_homodyne(prm, 30)
+    assert worst < 1e-12
+    # the oracle's own step() follows the same sequence
+    out = trajectory.run(prm, 30)
+    assert np.max(np.abs(observables.correlation(out["U"]) - observables.correlation(U))) < 1e-13
+    L = prm.L
+    A, B = [0, 1], [4, 5]
+    I_brute = sec.entropy(psi, A) + sec.entropy(psi, B) - sec.entropy(psi, A + B)
+    assert abs(observables.mutual_information(U, A, B) - I_brute) < 1e-11
+    assert abs(observables.entanglement_entropy(U, list(range(L // 2))) - sec.entropy(psi, list(range(L // 2)))) < 1e-11
+
+
+# ---------------------------------------------------------------- Eqs. (A1), (A2)
+
+def _random_state(L, N, seed):
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((L, N)) + 1j * rng.standard_normal((L, N))
+    return np.linalg.qr(Z)[0]
+
+
+def test_rank1_updates_equal_correlation_matrix_equations():
+    """The U-form updates reproduce Eq. (A1) (click) and Eq. (A2) with '+' (no click)."""
+    U = _random_state(12, 5, 0)
+    C = observables.correlation(U)
+    j = 4
+    p = C[j, j].real
+    # Eq. (A1): C'_ab = C_ab - C_aj C_jb / C_jj off row/column j, C'_jj = 1
+    C1 = C - np.outer(C[:, j], C[j, :]) / p
+    C1[j, :] = 0.0; C1[:, j] = 0.0; C1[j, j] = 1.0
+    U1 = trajectory.project_site(U, j, 1)
+    assert np.max(np.abs(observables.correlation(U1) - C1)) < 1e-13
+    # Eq. (A2) read with '+': C'_ab = C_ab + C_aj C_jb / (1 - C_jj), row/column j zero
+    C0 = C + np.outer(C[:, j], C[j, :]) / (1 - p)
+    C0[j, :] = 0.0; C0[:, j] = 0.0
+    U0 = trajectory.project_site(U, j, 0)
+    assert np.max(np.abs(observables.correlation(U0) - C0)) < 1e-13
+    # the sign printed in Eq. (A2) ('-') does not conserve the particle number
+    Cm = C - np.outer(C[:, j], C[j, :]) / (1 - p)
+    Cm[j, :] = 0.0; Cm[:, j] = 0.0
+    assert abs(np.trace(Cm).real - 5) > 1e-3
+    assert abs(np.trace(C0).real - 5) < 1e-12
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_invariants_along_a_projective_trajectory():
+    prm = Params(Lx=64, gamma=0.5, protocol=PROJECTIVE, reorth_interval=1, seed=3)
+    out = trajectory.run(prm, 60)
+    U = out["U"]
+    N = U.shape[1]
+    assert np.max(np.abs(U.conj().T @ U - np.eye(N))) < 1e-13
+    C = observables.correlation(U)
+    assert abs(np.trace(C).real - N) < 1e-12
+    assert np.max(np.abs(C @ C - C)) < 1e-13
+    A = list(range(20))
+    Abar = list(range(20, 64))
+    assert abs(observables.entanglement_entropy(U, A) - observables.entanglement_entropy(U, Abar)) < 1e-10
+    I = observables.mutual_information(U, list(range(10)), list(range(30, 40)))
+    assert I >= -1e-12
+    I_comp = observables.mutual_information(U, A, Abar)
+    assert abs(I_comp - 2 * observables.entanglement_entropy(U, A)) < 1e-10
+
+
+def test_neel_has_zero_entropy_and_click_makes_c_diagonal():
+    U0 = lattice.initial_orbitals(16)
+    assert observables.entanglement_entropy(U0, list(range(8))) == 0.0
+    U = _random_state(16, 8, 5)
+    U1 = trajectory.project_site(U, 3, 1)
+    C = observables.correlation(U1)
+    assert abs(C[3, 3] - 1) < 1e-13
+    assert np.max(np.abs(np.delete(C[3], 3))) < 1e-13
+    U0_ = trajectory.project_site(U, 3, 0)
+    assert np.max(np.abs(observables.correlation(U0_)[3])) < 1e-13
+
+
+def test_entropy_of_half_filled_random_state_matches_schmidt():
+    L, N = 10, 5
+    U = _random_state(L, N, 8)
+    sec = brute.Sector(L, N)
+    psi = sec.from_orbitals(U)
+    assert abs(np.linalg.norm(psi) - 1) < 1e-12
+    assert np.max(np.abs(observables.correlation(U) - np.conj(sec.d_matrix(psi)))) < 1e-13
+    for A in ([0, 1, 2, 3, 4], [0, 3, 7], [2, 9]):
+        assert abs(observables.entanglement_entropy(U, A) - sec.entropy(psi, A)) < 1e-11
+
+
+def test_binary_entropy_terms_edges():
+    f = observables.binary_entropy_terms(np.array([0.0, 1.0, 0.5, -1e-17, 1 + 1e-16]))
+    assert f[0] == 0 and f[1] == 0 and f[3] == 0 and f[4] == 0
+    assert abs(f[2] - np.log(0.5)) < 1e-15
+
+
+# ---------------------------------------------------------------- statistics
+
+def test_homodyne_occupation_is_a_martingale():
+    """With J = 0 the weight of Eq. (A4) leaves E[<n_i>] unchanged (Ito calculus)."""
+    L, N, T = 4, 2, 4000
+    rng = np.random.default_rng(1)
+    U_init = _random_state(L, N, 2)
+    n0 = trajectory.occupations(U_init)
+    acc = np.zeros(L)
+    for tr in range(T):
+        xi = philox.noise_normals(77, tr, 0, L)
+        U = trajectory.orthonormalize(trajectory.homodyne_weight(U_init, xi, 1.0, 0.05))
+        acc += trajectory.occupations(U)
+    drift = acc / T - n0
+    assert np.max(np.abs(drift)) < 4e-3          # MC error ~1e-3; a wrong drift term gives ~5e-2
+    del rng
+
+
+def test_projective_selection_frequency():
+    L, steps, gamma, dt = 512, 40, 1.0, 0.05
+    hits = 0
+    for s in range(steps):
+        u_sel, _ = philox.measure_draws(5, 0, s, L)
+        hits += int(np.sum(u_sel < 1 - np.exp(-gamma * dt)))
+    p = 1 - np.exp(-gamma * dt)
+    assert abs(hits / (L * steps) - p) < 4 * np.sqrt(p * (1 - p) / (L * steps))
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def _pin_fails(run):
+    """True when a brute-force comparison rejects the (planted) oracle."""
+    try:
+        worst = run()[0]
+    except AssertionError:
+        return True
+    return worst > 1e-6
+
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """Each plausible slip in the oracle fails one of the pins above."""
+    prm = Params(Lx=8, gamma=2.0, protocol=PROJECTIVE, reorth_interval=3, seed=11, traj_id=1)
+
+    # (a) a sign slip in the no-click orbital: (v + sqrt(p) e_j) instead of (v - sqrt(p) e_j)
+    good_project = trajectory.project_site
+
+    def bad_project(U, j, outcome):
+        if outcome == 1:
+            return good_project(U, j, 1)
+        x = U[j, :].copy(); p = float(np.real(np.vdot(x, x))); sp = np.sqrt(p)
+        v = (U @ np.conj(x)) / sp
+        ej = np.zeros(U.shape[0], complex); ej[j] = 1
+        return U + np.outer((v + sp * ej) / np.sqrt(1 - p) - v, x) / sp
+    monkeypatch.setattr(trajectory, "project_site", bad_project)
+    assert _pin_fails(lambda: _compare_projective(prm, 40))
+    monkeypatch.undo()
+
+    # (a') the Born weight read from the neighbouring row
+    def bad_measure(U, p_meas, u_sel, u_out, forced=None):
+        events = []
+        for j in np.nonzero(u_sel < p_meas)[0]:
+            j = int(j)
+            x = U[(j + 1) % U.shape[0], :]
+            p = min(max(float(np.real(np.vdot(x, x))), 0.0), 1.0)
+            outcome = 1 if u_out[j] < p else 0
+            events.append((j, float(u_out[j]), p, outcome))
+            U = trajectory.project_site(U, j, outcome)
+        return U, events
+    monkeypatch.setattr(trajectory, "projective_measurements", bad_measure)
+    assert _pin_fails(lambda: _compare_projective(prm, 40))
+    monkeypatch.undo()
+
+    # (b) propagation with P^dag (time running backwards)
+    def back_step(U, P, prm_, s):
+        return trajectory.step(U, P.conj().T, prm_, s)
+    assert _pin_fails(lambda: _compare_projective(prm, 20, oracle_step=back_step))
+
+    # (c) the QSD drift without the factor 2 on <n>
+    def bad_weight(U, xi, gamma, dt):
+        n = trajectory.occupations(U)
+        return np.exp(np.sqrt(gamma * dt) * xi + (n - 1.0) * gamma * dt)[:, None] * U
+    prm_h = Params(Lx=8, gamma=1.0, protocol=HOMODYNE, seed=99, traj_id=3)
+    assert _pin_fails(lambda: _compare_homodyne(prm_h, 10, weight=bad_weight))
