@@ -1,0 +1,176 @@
+/*
+ * fm.h -- C ABI of the GB300 library for monitored free-fermion trajectories
+ * (B. Fan, C. Yin, A. M. Garcia-Garcia, "Entanglement dynamics of monitored
+ * noninteracting fermions on graphics processing units", arXiv 2508.18468).
+ *
+ * What is computed.  A trajectory is the Slater determinant of App. A,
+ * |psi> = prod_k (sum_j U_jk c_j^dag)|vac>, with U an L x N matrix,
+ * U^dag U = 1, on a ring of L sites (Sec. II) or an Lx x Ly torus (Sec. IV),
+ * half filled, started from the Neel / checkerboard state (App. A).  One step
+ * t -> t + dt is
+ *   1. propagation U <- exp(-i H~ dt) U, H~_ij = J on nearest-neighbour bonds
+ *      (App. A; H of Sec. II), as a dense complex GEMM;
+ *   2. the measurement:
+ *      projective (App. A, Eqs. (A1), (A2)): every site is measured with
+ *        probability 1 - exp(-gamma dt), sites in ascending order, outcome 1
+ *        iff the uniform draw u < p_j = C_jj of the current state; a click
+ *        applies n_j, a no-click 1 - n_j (Eq. (A2) read with '+');
+ *      homodyne / QSD (App. A, Eq. (A4)): U <- exp(dW + (2<n> - 1) gamma dt) U
+ *        with dW_i = sqrt(gamma dt) xi_i, xi_i ~ N(0,1), <n_i> = sum_k |U_ik|^2;
+ *   3. re-orthonormalisation (App. A) by CholeskyQR2:
+ *      G = U^dag U, G = R^dag R, U <- U R^-1, twice.
+ * Observables: the entanglement entropy S_A = -sum f(lambda), f(x) =
+ * x ln x + (1-x) ln(1-x), lambda the eigenvalues of C_A = U_A U_A^dag
+ * (Sec. II), and the mutual information I = S_A + S_B - S_{A u B} (Sec. IV).
+ *
+ * Randomness.  Draws come from Philox4x32-10 (Salmon et al., SC'11) at
+ * counter (site, step, traj_id_lo, tag | traj_id_hi << 8), key (seed_lo,
+ * seed_hi); tag 1 = projective (u_select from words 0-1, u_outcome from words
+ * 2-3), tag 2 = homodyne (Box-Muller normal).  A uniform double is
+ * ((w_a >> 5) * 2^26 + (w_b >> 6)) * 2^-53.
+ *
+ * Conventions common to every call.
+ *  - Status codes only; nothing throws or aborts across the ABI.
+ *  - A CUDA, numeric or timeout error inside a state is sticky: later calls
+ *    on that state return FM_ESTATE.  Argument errors (FM_EINVAL) are not
+ *    sticky.  fm_last_error() tells what happened.
+ *  - Device memory: the caller allocates one device workspace of
+ *    fm_workspace_bytes() bytes and owns it; the library never allocates or
+ *    frees device memory on the stepping path and never frees caller memory.
+ *    The host-side fm_state object is allocated by fm_init_state and freed by
+ *    fm_destroy.
+ *  - Work is issued on the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  fm_step is asynchronous; calls
+ *    that return host values synchronise that stream.
+ *  - Matrices are column-major.  Site indices are 0-based; on the torus site
+ *    (x, y) has index x + Lx*y.  Entropies are in nats.
+ *  - U is exported as complex128 (interleaved re, im doubles).
+ */
+#ifndef FM_H
+#define FM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FM_OK = 0,
+  FM_EINVAL = 1,     /* bad argument (sizes, indices, overlapping A/B, ...) */
+  FM_ENOMEM = 2,     /* workspace smaller than fm_workspace_bytes() */
+  FM_ECUDA = 3,      /* a CUDA runtime / driver call failed */
+  FM_ENUMERIC = 4,   /* non-finite values or a non-positive Cholesky pivot */
+  FM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  FM_ESTATE = 6      /* the state holds an earlier (sticky) error */
+} fm_status;
+
+typedef enum { FM_PROJECTIVE = 0, FM_HOMODYNE = 1 } fm_protocol;
+
+/* FM_FP64: every step in float64 / complex128.
+ * FM_MIXED: U held as complex float32; the propagation, Gram and triangular
+ * products run on the tensor cores as split-fp16 products with float32
+ * accumulation; Cholesky pivots, entropies and eigenvalues in float64. */
+typedef enum { FM_FP64 = 0, FM_MIXED = 1 } fm_precision;
+
+typedef struct {
+  int32_t Lx, Ly;           /* lattice; Ly == 1 is the ring.  L = Lx*Ly even, N = L/2 */
+  int32_t batch;            /* trajectories advanced together, >= 1 */
+  int32_t protocol;         /* fm_protocol */
+  int32_t precision;        /* fm_precision */
+  int32_t reorth_interval;  /* >= 1.  Projective: CholeskyQR2 every k steps.
+                               Homodyne: first CholeskyQR pass every step, the
+                               second every k steps */
+  int32_t event_capacity;   /* projective outcome log entries kept (0 = no log) */
+  int32_t reserved;
+  double J, dt, gamma;      /* hopping, time step, monitoring rate (per site) */
+  uint64_t seed;            /* Philox key */
+  uint64_t traj_id;         /* trajectory b of the batch has id traj_id + b */
+} fm_params;
+
+/* One projective measurement: trajectory b of the batch, step index (t/dt
+ * before the step), site, the outcome draw u, Born probability p, outcome. */
+typedef struct {
+  int64_t step;
+  int32_t traj;
+  int32_t site;
+  double u;
+  double p;
+  int32_t outcome;
+  int32_t pad;
+} fm_event;
+
+typedef struct fm_state fm_state;
+
+/* Device bytes the state for *p needs; 0 if *p is invalid. */
+size_t fm_workspace_bytes(const fm_params* p);
+
+/* Build the propagator on the host (FP64 plane-wave sum, App. A), upload it,
+ * and put every trajectory in the Neel / checkerboard state at step 0.
+ * d_workspace: caller-owned device buffer of ws_bytes >= fm_workspace_bytes(p),
+ * 256-byte aligned.  cuda_stream: cudaStream_t or NULL.  Synchronises. */
+fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes,
+                        void* cuda_stream, fm_state** out);
+
+/* Advance every trajectory of the batch by nsteps >= 0 steps.  Asynchronous. */
+fm_status fm_step(fm_state* s, int32_t nsteps);
+
+/* Per-trajectory monitoring rates (host array of `batch` doubles >= 0). */
+fm_status fm_set_gammas(fm_state* s, const double* gammas);
+
+/* Restart trajectory b from the Neel state at step 0 with a new id and rate
+ * (continuous batching: a finished slot takes the next request). */
+fm_status fm_reset_trajectory(fm_state* s, int32_t b, uint64_t traj_id, double gamma);
+
+/* Steps trajectory b has taken since its (re)start. */
+fm_status fm_steps_done(fm_state* s, int32_t b, int64_t* out);
+
+/* S_A (nats) of trajectory b, A = host array of n distinct sites.  FP64
+ * Householder tridiagonalisation + bisection on the GPU.  Synchronises. */
+fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, double* S_out);
+
+/* I = S_A + S_B - S_{A u B} for trajectory b; A and B disjoint host arrays. */
+fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA,
+                         const int32_t* B, int32_t nB, double* I_out);
+
+/* U of trajectory b -> host complex128 array with leading dimension ld >= L. */
+fm_status fm_copy_U(fm_state* s, int32_t b, void* host_c128, int64_t ld);
+
+/* Overwrite U of trajectory b from host complex128 (checkpoint restore, tests). */
+fm_status fm_set_U(fm_state* s, int32_t b, const void* host_c128, int64_t ld);
+
+/* <n_i> = sum_k |U_ik|^2 of trajectory b -> host array of L doubles. */
+fm_status fm_occupations(fm_state* s, int32_t b, double* host_n);
+
+/* max_kl |(U^dag U - 1)_kl| of trajectory b over the columns k in `cols`
+ * (host array, 1 <= ncols <= min(N, 64) entries; all l), in float64 on the GPU. */
+fm_status fm_orthonormality_error(fm_state* s, int32_t b, const int32_t* cols, int32_t ncols,
+                                  double* err);
+
+/* Move up to `cap` logged projective events into host `out`, oldest first;
+ * *count = number written, *dropped = events lost to a full log since the
+ * last call.  Synchronises. */
+fm_status fm_take_events(fm_state* s, fm_event* out, int32_t cap, int32_t* count, int64_t* dropped);
+
+/* Checkpoint: U (as stored), step counters, rates and ids to / from a file.
+ * Philox is counter based, so a restored run continues bit-identically. */
+fm_status fm_save(fm_state* s, const char* path);
+fm_status fm_load(fm_state* s, const char* path);
+
+/* Launches of library kernels issued on this state since init. */
+int64_t fm_kernel_launches(const fm_state* s);
+
+/* Last error message of this state ("" if none); valid until the next call. */
+const char* fm_last_error(const fm_state* s);
+
+/* Free the host-side state (not the caller's workspace).  NULL is allowed. */
+void fm_destroy(fm_state* s);
+
+/* Library version string. */
+const char* fm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FM_H */

@@ -1,0 +1,275 @@
+// FP64 entanglement entropy of a Hermitian correlation block (Sec. II):
+// S = -sum_i f(lambda_i), f(x) = x ln x + (1-x) ln(1-x), lambda the eigenvalues
+// of the m x m Hermitian matrix M (C_A = U_A U_A^dag or U_A^dag U_A).
+//
+// Eigenvalues: Householder reduction to a real symmetric tridiagonal matrix
+// (reflectors H = I - tau v v^dag with v_0 = 1 and real beta, so that
+// H^dag x = beta e_1), then Sturm-sequence bisection, one eigenvalue per thread.
+// Everything is float64 and deterministic (fixed-order reductions).
+#include <float.h>
+#include <math.h>
+
+#include "kernels.h"
+
+namespace fm {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// fixed-order block sum for blockDim.x == 1024 (red: 33 doubles of shared memory)
+__device__ double bsum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  const double s = red[32];
+  __syncthreads();
+  return s;
+}
+
+// Reflector for x = M[k+1 .. m-1, k] (length n): beta, tau, v (v_0 = 1), by
+// the construction H^dag x = beta e_1, beta = -sign(Re x_0) |x|, tau = (beta - x_0)/beta,
+// v_i = x_i / (x_0 - beta).  Returns tau; writes v and beta.
+__device__ z64 reflector(const z64* x, int n, z64* v, double* beta_out, double* red, z64* sh) {
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) s += cabs2(x[i]);
+  const double xn2 = bsum(s, red);
+  if (threadIdx.x == 0) {
+    const z64 a = x[0];
+    z64 tau, scale;
+    double beta;
+    if (xn2 == 0.0 && a.im == 0.0) {
+      tau = cmk(0.0, 0.0);
+      beta = a.re;
+      scale = cmk(0.0, 0.0);
+    } else {
+      beta = -copysign(sqrt(cabs2(a) + xn2), a.re);
+      tau = cmk((beta - a.re) / beta, -a.im / beta);
+      // scale = 1 / (a - beta)
+      const z64 d = cmk(a.re - beta, a.im);
+      const double dd = cabs2(d);
+      scale = cmk(d.re / dd, -d.im / dd);
+    }
+    sh[0] = tau;
+    sh[1] = scale;
+    *beta_out = beta;
+  }
+  __syncthreads();
+  const z64 scale = sh[1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (i == 0) ? cmk(1.0, 0.0) : cmul(x[i], scale);
+  const z64 tau = sh[0];
+  __syncthreads();
+  return tau;
+}
+
+// ------------------------------------------------------------------ small m: one CTA
+// The whole reduction in one CTA of 1024 threads; the matrix stays in global
+// memory (L2 resident for the sizes this is used for).
+__global__ void __launch_bounds__(1024) tridiag_small_kernel(z64* M, int m, z64* vb, z64* wb, double* d, double* e) {
+  __shared__ double red[33];
+  __shared__ z64 sh[4];
+  __shared__ double sbeta;
+  for (int k = 0; k + 1 < m; ++k) {
+    const int n = m - k - 1;
+    z64* col = M + (k + 1) + (int64_t)k * m;
+    z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
+    const z64 tau = reflector(col, n, vb, &sbeta, red, sh);
+    if (threadIdx.x == 0) { d[k] = M[k + (int64_t)k * m].re; e[k] = sbeta; }
+    // p = M22 v ; s = v^dag p
+    double sr = 0.0, si = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      z64 acc = cmk(0.0, 0.0);
+      for (int j = 0; j < n; ++j) cfma(acc, M22[i + (int64_t)j * m], vb[j]);
+      wb[i] = acc;
+      const z64 t = cmul(cconj(vb[i]), acc);
+      sr += t.re; si += t.im;
+    }
+    const double s_re = bsum(sr, red);
+    const double s_im = bsum(si, red);
+    // w = tau p - (1/2)|tau|^2 s v
+    const double t2 = 0.5 * cabs2(tau);
+    const z64 cs = cmk(t2 * s_re, t2 * s_im);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) wb[i] = csub(cmul(tau, wb[i]), cmul(cs, vb[i]));
+    __syncthreads();
+    // M22 -= v w^dag + w v^dag
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const z64 vi = vb[i], wi = wb[i];
+      for (int j = 0; j < n; ++j) {
+        z64& a = M22[i + (int64_t)j * m];
+        a = csub(a, cadd(cmul(vi, cconj(wb[j])), cmul(wi, cconj(vb[j]))));
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d[m - 1] = M[(m - 1) + (int64_t)(m - 1) * m].re;
+}
+
+// ------------------------------------------------------------------ large m: per-column kernels
+__global__ void __launch_bounds__(1024) hh_reflector_kernel(z64* M, int m, int k, z64* vb, double* d, double* e,
+                                                            z64* tau_out) {
+  __shared__ double red[33];
+  __shared__ z64 sh[4];
+  __shared__ double sbeta;
+  const int n = m - k - 1;
+  const z64 tau = reflector(M + (k + 1) + (int64_t)k * m, n, vb, &sbeta, red, sh);
+  if (threadIdx.x == 0) {
+    d[k] = M[k + (int64_t)k * m].re;
+    e[k] = sbeta;
+    *tau_out = tau;
+  }
+}
+
+// partial[c][i] = sum_{j in chunk c} M22[i, j] v_j ; grid (ceil(n/32), nchunks), block (32, 8)
+__global__ void hh_matvec_kernel(const z64* __restrict__ M, int m, int k, const z64* __restrict__ vb,
+                                 z64* partial, int nchunks) {
+  const int n = m - k - 1;
+  const z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int per = FM_CEIL_DIV(n, nchunks);
+  const int j0 = blockIdx.y * per, j1 = min(n, j0 + per);
+  z64 acc = cmk(0.0, 0.0);
+  if (i < n)
+    for (int j = j0 + threadIdx.y; j < j1; j += 8) cfma(acc, M22[i + (int64_t)j * m], vb[j]);
+  __shared__ z64 red[8][33];
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    z64 s = cmk(0.0, 0.0);
+    for (int w = 0; w < 8; ++w) s = cadd(s, red[w][threadIdx.x]);
+    partial[(int64_t)blockIdx.y * n + i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(1024) hh_w_kernel(int m, int k, const z64* partial, int nchunks,
+                                                    const z64* vb, z64* wb, const z64* tau_in) {
+  __shared__ double red[33];
+  const int n = m - k - 1;
+  double sr = 0.0, si = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    z64 p = cmk(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) p = cadd(p, partial[(int64_t)c * n + i]);
+    wb[i] = p;
+    const z64 t = cmul(cconj(vb[i]), p);
+    sr += t.re; si += t.im;
+  }
+  const double s_re = bsum(sr, red);
+  const double s_im = bsum(si, red);
+  const z64 tau = *tau_in;
+  const double t2 = 0.5 * cabs2(tau);
+  const z64 cs = cmk(t2 * s_re, t2 * s_im);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) wb[i] = csub(cmul(tau, wb[i]), cmul(cs, vb[i]));
+}
+
+// M22 -= v w^dag + w v^dag, 2-D grid over (i, j)
+__global__ void hh_update_kernel(z64* M, int m, int k, const z64* __restrict__ vb, const z64* __restrict__ wb) {
+  const int n = m - k - 1;
+  z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const z64 vi = vb[i], wi = wb[i];
+  for (int j = blockIdx.y; j < n; j += gridDim.y) {
+    z64& a = M22[i + (int64_t)j * m];
+    a = csub(a, cadd(cmul(vi, cconj(wb[j])), cmul(wi, cconj(vb[j]))));
+  }
+}
+
+__global__ void last_diag_kernel(const z64* M, int m, double* d) { d[m - 1] = M[(m - 1) + (int64_t)(m - 1) * m].re; }
+
+// ------------------------------------------------------------------ bisection
+// count of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm / LDL^T inertia)
+__device__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++c;
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int m, double* lam) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  double lo = d[0], hi = d[0], emax2 = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i + 1 < m) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  const double span = fmax(fabs(lo), fabs(hi));
+  lo -= 2.0 * DBL_EPSILON * span + pivmin;
+  hi += 2.0 * DBL_EPSILON * span + pivmin;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 1e-18 + 2.0 * DBL_EPSILON * fabs(mid) || mid == lo || mid == hi) break;
+    if (sturm_count(d, e, m, mid, pivmin) > q) hi = mid;
+    else lo = mid;
+  }
+  lam[q] = 0.5 * (lo + hi);
+}
+
+// S = -sum f(clamp(lambda, 0, 1)), one CTA, fixed order
+__global__ void __launch_bounds__(1024) entropy_sum_kernel(const double* lam, int m, double* S) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    const double x = fmin(fmax(lam[q], 0.0), 1.0);
+    if (x > 0.0 && x < 1.0) s += x * log(x) + (1.0 - x) * log1p(-x);
+  }
+  const double tot = bsum(s, red);
+  if (threadIdx.x == 0) *S = -tot;
+}
+
+__global__ void one_by_one_kernel(const z64* M, double* d) { d[0] = M[0].re; }
+
+cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, z64* pbuf, double* partial_unused,
+                              double* d, double* e, double* lam, double* S, int* nlaunch) {
+  (void)partial_unused;
+  int launches = 0;
+  if (m <= 0) return cudaSuccess;
+  if (m == 1) {
+    one_by_one_kernel<<<1, 1, 0, st>>>(M, d);
+    ++launches;
+  } else if (m <= 256) {
+    tridiag_small_kernel<<<1, 1024, 0, st>>>(M, m, vb, wb, d, e);
+    ++launches;
+  } else {
+    z64* tau = pbuf;               // pbuf[0]: tau ; pbuf + 1: matvec partials (nchunks * m)
+    z64* partial = pbuf + 1;
+    for (int k = 0; k + 1 < m; ++k) {
+      const int n = m - k - 1;
+      hh_reflector_kernel<<<1, 1024, 0, st>>>(M, m, k, vb, d, e, tau);
+      const int rowblocks = FM_CEIL_DIV(n, 32);
+      const int nchunks = max(1, min(32, FM_CEIL_DIV(4 * 152, rowblocks)));
+      hh_matvec_kernel<<<dim3(rowblocks, nchunks), dim3(32, 8), 0, st>>>(M, m, k, vb, partial, nchunks);
+      hh_w_kernel<<<1, 1024, 0, st>>>(m, k, partial, nchunks, vb, wb, tau);
+      const int gy = max(1, min(n, FM_CEIL_DIV(8 * 152, FM_CEIL_DIV(n, 256))));
+      hh_update_kernel<<<dim3(FM_CEIL_DIV(n, 256), gy), 256, 0, st>>>(M, m, k, vb, wb);
+      launches += 4;
+    }
+    last_diag_kernel<<<1, 1, 0, st>>>(M, m, d);
+    ++launches;
+  }
+  bisect_kernel<<<FM_CEIL_DIV(m, 64), 64, 0, st>>>(d, e, m, lam);
+  entropy_sum_kernel<<<1, 1024, 0, st>>>(lam, m, S);
+  launches += 2;
+  if (nlaunch) *nlaunch += launches;
+  return cudaGetLastError();
+}
+
+}  // namespace fm

@@ -1,0 +1,720 @@
+// C ABI of the fm library: state, workspace plan, step orchestration.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "fm.h"
+#include "kernels.h"
+#include "mixed.h"
+
+using namespace fm;
+
+namespace {
+
+const int kCholNB = 32;        // Cholesky / triangular-inverse block
+const int kMaxChunks = 64;     // occupation partial sums
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+  size_t total = 0;
+  // offsets
+  size_t gamma, traj, step, status, occ, log_count, log, part, nocc, w, xbuf, vbuf;
+  size_t U, U2, P, G, R, T, Dinv, X;                  // FP64 path (G, R, T, Dinv, X also mixed)
+  size_t V, V2, Vh, Vl, Ah, Al, Th, Tl, aux;           // mixed path
+  size_t ee_vb, ee_wb, ee_pb, ee_d, ee_e, ee_lam, ee_S, ee_sites, ee_max;
+  size_t chk_cols, chk_G;                               // orthonormality check (<= 64 columns)
+  size_t mixed_extra;                                   // scratch owned by the mixed path
+  size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
+};
+
+bool valid_params(const fm_params* p, std::string* why) {
+  if (!p) { *why = "params is NULL"; return false; }
+  if (p->Lx < 2 || p->Ly < 1) { *why = "need Lx >= 2, Ly >= 1"; return false; }
+  const int64_t L = (int64_t)p->Lx * p->Ly;
+  if (L % 2) { *why = "L = Lx*Ly must be even (half filling)"; return false; }
+  if (p->Ly > 1 && (p->Lx % 2)) { *why = "torus needs even Lx for the checkerboard start"; return false; }
+  if (L > 65536) { *why = "L > 65536 not supported"; return false; }
+  if (p->batch < 1 || p->batch > 65535) { *why = "batch must be in [1, 65535]"; return false; }
+  if (p->protocol != FM_PROJECTIVE && p->protocol != FM_HOMODYNE) { *why = "bad protocol"; return false; }
+  if (p->precision != FM_FP64 && p->precision != FM_MIXED) { *why = "bad precision"; return false; }
+  if (p->reorth_interval < 1) { *why = "reorth_interval must be >= 1"; return false; }
+  if (p->event_capacity < 0) { *why = "event_capacity must be >= 0"; return false; }
+  if (!(p->dt > 0.0) || !isfinite(p->J) || !(p->gamma >= 0.0) || !isfinite(p->gamma)) {
+    *why = "need dt > 0, finite J, gamma >= 0";
+    return false;
+  }
+  if (p->precision == FM_MIXED) {
+    std::string w2;
+    if (!mixed_supported(p->Lx, p->Ly, p->batch, &w2)) { *why = w2; return false; }
+  }
+  return true;
+}
+
+Plan make_plan(const fm_params& p) {
+  Plan pl;
+  const int64_t L = (int64_t)p.Lx * p.Ly, N = L / 2, B = p.batch;
+  const int64_t nblk = (N + kCholNB - 1) / kCholNB;
+  pl.gamma = pl.take(B * 8);
+  pl.traj = pl.take(B * 8);
+  pl.step = pl.take(B * 8);
+  pl.status = pl.take(16);
+  pl.occ = pl.take(N * 4);
+  pl.log_count = pl.take(16);
+  pl.log = pl.take((size_t)p.event_capacity * sizeof(fm_event));
+  pl.part = pl.take(B * kMaxChunks * L * 8);
+  pl.nocc = pl.take(B * L * 8);
+  pl.w = pl.take(B * L * 8);
+  pl.xbuf = pl.take(B * N * 16);
+  pl.vbuf = pl.take(B * L * 16);
+  pl.G = pl.take(B * N * N * 16);
+  pl.R = pl.take(B * N * N * 16);
+  pl.T = pl.take(B * N * N * 16);
+  pl.Dinv = pl.take(B * nblk * kCholNB * kCholNB * 16);
+  pl.X = pl.take(B * N * kCholNB * 16);
+  pl.ee_vb = pl.take(N * 16);
+  pl.ee_wb = pl.take(N * 16);
+  pl.ee_pb = pl.take((1 + 32 * N) * 16);
+  pl.ee_d = pl.take(N * 8);
+  pl.ee_e = pl.take(N * 8);
+  pl.ee_lam = pl.take(N * 8);
+  pl.ee_S = pl.take(8);
+  pl.ee_max = pl.take(8);
+  pl.ee_sites = pl.take(L * 4);
+  pl.chk_cols = pl.take(L * std::min<int64_t>(N, 64) * 16);
+  pl.chk_G = pl.take(std::min<int64_t>(N, 64) * N * 16);
+  if (p.precision == FM_FP64) {
+    pl.U = pl.take(B * L * N * 16);
+    pl.U2 = pl.take(B * L * N * 16);
+    pl.P = pl.take(L * L * 16);
+    pl.aux = pl.U2;
+  } else {
+    pl.V = pl.take(B * 2 * L * N * 4);
+    pl.V2 = pl.take(B * 2 * L * N * 4);
+    pl.Vh = pl.take(B * 2 * L * N * 2);
+    pl.Vl = pl.take(B * 2 * L * N * 2);
+    pl.Ah = pl.take(4 * L * L * 2);
+    pl.Al = pl.take(4 * L * L * 2);
+    pl.Th = pl.take(B * 4 * N * N * 2);
+    pl.Tl = pl.take(B * 4 * N * N * 2);
+    pl.aux = pl.take(L * N * 16);
+    pl.mixed_extra = pl.take(mixed_scratch_bytes(p.Lx, p.Ly, p.batch));
+  }
+  return pl;
+}
+
+}  // namespace
+
+struct fm_state {
+  fm_params prm;
+  int Lx, Ly, L, N, B;
+  cudaStream_t st;
+  char* ws;
+  size_t ws_bytes;
+  Plan pl;
+  // common
+  double* gamma_d; uint64_t* traj_d; int64_t* step_d; int* status_d; int* occ_d;
+  unsigned long long* log_count_d; fm_event* log_d;
+  double *part_d, *nocc_d, *w_d;
+  void *xbuf_d, *vbuf_d;
+  z64 *G, *R, *T, *Dinv, *X;
+  // fp64
+  z64 *U, *U2, *P;
+  // mixed
+  float *V, *V2;
+  __half *Vh, *Vl, *Ah, *Al, *Th, *Tl;
+  z64* aux;
+  void* mixed_extra;
+  // EE
+  z64 *ee_vb, *ee_wb, *ee_pb;
+  double *ee_d, *ee_e, *ee_lam, *ee_S, *ee_max;
+  int* ee_sites;
+  z64 *chk_cols, *chk_G;
+  // host
+  std::vector<double> gamma_h;
+  std::vector<uint64_t> traj_h;
+  std::vector<int64_t> step_h;
+  int64_t global_steps;
+  int sticky;
+  std::string err;
+  int64_t launches;
+};
+
+namespace {
+
+// Record an error.  Device / numeric failures are sticky; argument errors are not.
+fm_status fail(fm_state* s, fm_status code, const std::string& msg) {
+  if (s && !s->sticky) {
+    s->err = msg;
+    if (code == FM_ECUDA || code == FM_ENUMERIC || code == FM_ETIMEOUT) s->sticky = code;
+  }
+  return code;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(s, FM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+#define CKL(call, n)                                                                             \
+  do {                                                                                           \
+    CK(call);                                                                                    \
+    s->launches += (n);                                                                          \
+  } while (0)
+
+// Read and clear the device status word; map to a sticky error.
+fm_status sync_and_check(fm_state* s) {
+  CK(cudaStreamSynchronize(s->st));
+  int st = 0;
+  CK(cudaMemcpy(&st, s->status_d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    int zero = 0;
+    CK(cudaMemcpy(s->status_d, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    if (st & FM_DEVERR_TIMEOUT) return fail(s, FM_ETIMEOUT, "a bounded device wait gave up");
+    if (st & FM_DEVERR_PIVOT) return fail(s, FM_ENUMERIC, "non-positive Cholesky pivot (U lost rank)");
+    if (st & FM_DEVERR_NONFINITE) return fail(s, FM_ENUMERIC, "non-finite values in U");
+    return fail(s, FM_ENUMERIC, "device error flag " + std::to_string(st));
+  }
+  return FM_OK;
+}
+
+// p[r] = (1/L) sum_m exp(2 pi i m r / L) exp(-2 i J dt cos(2 pi m / L)), the
+// angle index m*r reduced mod L exactly (plane-wave form of exp(-i H~ dt)).
+std::vector<z64> ring_row(int L, double J, double dt) {
+  std::vector<z64> out(L);
+  if (L == 1) { out[0].re = 1.0; out[0].im = 0.0; return out; }
+  std::vector<double> c(L), sn(L);
+  for (int q = 0; q < L; ++q) {
+    const double a = 2.0 * M_PI * (double)q / (double)L;
+    c[q] = cos(a);
+    sn[q] = sin(a);
+  }
+  std::vector<std::complex<double>> ph(L);
+  for (int m = 0; m < L; ++m) ph[m] = std::exp(std::complex<double>(0.0, -2.0 * J * dt * c[m]));
+  for (int r = 0; r < L; ++r) {
+    std::complex<double> acc(0.0, 0.0);
+    int64_t q = 0;
+    for (int m = 0; m < L; ++m) {
+      acc += std::complex<double>(c[q], sn[q]) * ph[m];
+      q += r;
+      if (q >= L) q -= L;
+    }
+    acc /= (double)L;
+    out[r].re = acc.real();
+    out[r].im = acc.imag();
+  }
+  return out;
+}
+
+std::vector<int> occupied(int Lx, int Ly) {
+  std::vector<int> occ;
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) {
+      const bool on = (Ly == 1) ? (x % 2 == 0) : ((x + y) % 2 == 0);
+      if (on) occ.push_back(x + Lx * y);
+    }
+  return occ;
+}
+
+fm_status check_state(fm_state* s) {
+  if (!s) return FM_EINVAL;
+  if (s->sticky) return FM_ESTATE;
+  return FM_OK;
+}
+
+// ------------------------------------------------------------------ FP64 CholeskyQR pass
+// G = U^dag U ; G = R^dag R (blocked, nb = 32) ; T = R^-1 ; U <- U T
+fm_status cholqr_f64(fm_state* s) {
+  const int L = s->L, N = s->N, B = s->B, nb = kCholNB;
+  const int nblk = (N + nb - 1) / nb;
+  const int64_t sNN = (int64_t)N * N, sLN = (int64_t)L * N, sD = (int64_t)nblk * nb * nb;
+  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0}, mone = {-1.0, 0.0};
+  CKL(zgemm<double>(s->st, N, N, L, OP_C, OP_N, one, s->U, L, sLN, s->U, L, sLN, zero, s->G, N, sNN, B,
+                    GEMM_UPPER_ONLY), 1);
+  for (int k = 0; k < N; k += nb) {
+    const int nbk = std::min(nb, N - k);
+    CKL(chol_diag_block(s->st, s->G, N, sNN, s->R, N, sNN, s->Dinv, sD, k, nb, nbk, B, s->status_d), 1);
+    const int rest = N - k - nbk;
+    if (rest > 0) {
+      z64* Dk = s->Dinv + (int64_t)(k / nb) * nb * nb;
+      CKL(zgemm<double>(s->st, nbk, rest, nbk, OP_C, OP_N, one, Dk, nb, sD, s->G + k + (int64_t)(k + nbk) * N, N,
+                        sNN, zero, s->R + k + (int64_t)(k + nbk) * N, N, sNN, B, 0), 1);
+      CKL(zgemm<double>(s->st, rest, rest, nbk, OP_C, OP_N, mone, s->R + k + (int64_t)(k + nbk) * N, N, sNN,
+                        s->R + k + (int64_t)(k + nbk) * N, N, sNN, one,
+                        s->G + (k + nbk) + (int64_t)(k + nbk) * N, N, sNN, B, GEMM_UPPER_ONLY), 1);
+    }
+  }
+  CKL(place_diag_blocks(s->st, s->Dinv, sD, s->T, N, sNN, N, nb, B), 1);
+  for (int j = 1; j < nblk; ++j) {
+    const int c0 = j * nb, nbj = std::min(nb, N - c0);
+    // X = T[0:c0, 0:c0] R[0:c0, c0:c0+nbj] ;  T[0:c0, c0:] = -X Dinv_j
+    CKL(zgemm<double>(s->st, c0, nbj, c0, OP_N, OP_N, one, s->T, N, sNN, s->R + (int64_t)c0 * N, N, sNN, zero,
+                      s->X, N, (int64_t)N * nb, B, GEMM_TRI_A_UPPER), 1);
+    CKL(zgemm<double>(s->st, c0, nbj, nbj, OP_N, OP_N, mone, s->X, N, (int64_t)N * nb,
+                      s->Dinv + (int64_t)j * nb * nb, nb, sD, zero, s->T + (int64_t)c0 * N, N, sNN, B, 0), 1);
+  }
+  CKL(zgemm<double>(s->st, L, N, N, OP_N, OP_N, one, s->U, L, sLN, s->T, N, sNN, zero, s->U2, L, sLN, B,
+                    GEMM_TRI_B_UPPER), 1);
+  std::swap(s->U, s->U2);
+  s->aux = s->U2;
+  return FM_OK;
+}
+
+fm_status step_f64(fm_state* s) {
+  const int L = s->L, N = s->N, B = s->B;
+  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  // 1. propagation, all trajectories in one product P [U_0 | U_1 | ...]
+  CKL(zgemm<double>(s->st, L, N * B, L, OP_N, OP_N, one, s->P, L, 0, s->U, L, 0, zero, s->U2, L, 0, 1, 0), 1);
+  std::swap(s->U, s->U2);
+  s->aux = s->U2;
+  const int64_t gstep = s->global_steps;
+  const int k = s->prm.reorth_interval;
+  if (s->prm.protocol == FM_HOMODYNE) {
+    const int nch = occupation_chunks(L, N, B);
+    CKL(rownorm_partials_z(s->st, s->U, L, N, B, s->part_d, nch), 1);
+    CKL(reduce_occupations(s->st, s->part_d, nch, L, B, s->nocc_d, s->w_d, s->gamma_d, s->prm.dt, s->traj_d,
+                           s->step_d, s->prm.seed), 1);
+    CKL(scale_rows_z(s->st, s->U, L, N, B, s->w_d), 1);
+    fm_status r = cholqr_f64(s);
+    if (r) return r;
+    if ((gstep + 1) % k == 0) {
+      r = cholqr_f64(s);
+      if (r) return r;
+    }
+  } else {
+    pm_args a;
+    a.U = s->U; a.L = L; a.N = N; a.batch = B; a.layout = 0;
+    a.gamma = s->gamma_d; a.dt = s->prm.dt; a.traj = s->traj_d; a.step = s->step_d; a.seed = s->prm.seed;
+    a.xbuf = s->xbuf_d; a.vbuf = s->vbuf_d;
+    a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
+    a.dev_status = s->status_d;
+    CKL(pm_measure(s->st, a), 1);
+    if ((gstep + 1) % k == 0) {
+      fm_status r = cholqr_f64(s);
+      if (r) return r;
+      r = cholqr_f64(s);
+      if (r) return r;
+    }
+  }
+  CKL(bump_steps(s->st, s->step_d, B), 1);
+  return FM_OK;
+}
+
+// gather rows `sites` of trajectory b into aux (n x N complex128)
+fm_status gather_rows(fm_state* s, int b, const int* d_sites, int n) {
+  if (s->prm.precision == FM_FP64) {
+    CKL(gather_rows_z(s->st, s->U + (int64_t)b * s->L * s->N, s->L, s->N, d_sites, n, s->aux), 1);
+  } else {
+    CKL(gather_rows_v(s->st, s->V + (int64_t)b * 2 * s->L * s->N, s->L, s->N, d_sites, n, s->aux), 1);
+  }
+  return FM_OK;
+}
+
+fm_status validate_sites(fm_state* s, const int32_t* sites, int32_t n) {
+  if (n < 0 || n > s->L || (n > 0 && !sites)) return fail(s, FM_EINVAL, "bad site list");
+  std::vector<char> seen(s->L, 0);
+  for (int i = 0; i < n; ++i) {
+    if (sites[i] < 0 || sites[i] >= s->L) return fail(s, FM_EINVAL, "site index out of range");
+    if (seen[sites[i]]) return fail(s, FM_EINVAL, "repeated site in subsystem");
+    seen[sites[i]] = 1;
+  }
+  return FM_OK;
+}
+
+// S_A of trajectory b; enqueues and synchronises.
+fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, double* S_out) {
+  if (n == 0) { *S_out = 0.0; return FM_OK; }
+  const int N = s->N;
+  CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  fm_status r = gather_rows(s, b, s->ee_sites, n);
+  if (r) return r;
+  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  const int m = std::min(n, N);
+  z64* M = s->G;  // scratch between steps
+  if (s->prm.precision == FM_MIXED && mixed_entropy_gram(s->st, s->aux, n, N, M)) {
+    s->launches += 1;
+  } else if (n <= N) {
+    CKL(zgemm<double>(s->st, n, n, N, OP_N, OP_C, one, s->aux, n, 0, s->aux, n, 0, zero, M, n, 0, 1, 0), 1);
+  } else {
+    CKL(zgemm<double>(s->st, N, N, n, OP_C, OP_N, one, s->aux, n, 0, s->aux, n, 0, zero, M, N, 0, 1, 0), 1);
+  }
+  int nl = 0;
+  CK(hermitian_entropy(s->st, M, m, s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e, s->ee_lam, s->ee_S,
+                       &nl));
+  s->launches += nl;
+  CK(cudaMemcpyAsync(S_out, s->ee_S, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+}  // namespace
+
+// =================================================================== public API
+extern "C" {
+
+const char* fm_version(void) { return "fm 0.1 (sm_103a)"; }
+
+size_t fm_workspace_bytes(const fm_params* p) {
+  std::string why;
+  if (!valid_params(p, &why)) return 0;
+  return make_plan(*p).total;
+}
+
+fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, void* cuda_stream, fm_state** out) {
+  if (!out) return FM_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (!valid_params(p, &why)) return FM_EINVAL;
+  Plan pl = make_plan(*p);
+  if (!d_workspace || ((uintptr_t)d_workspace & 255)) return FM_EINVAL;
+  if (ws_bytes < pl.total) return FM_ENOMEM;
+  fm_state* s = new fm_state();
+  s->prm = *p;
+  s->Lx = p->Lx; s->Ly = p->Ly; s->L = p->Lx * p->Ly; s->N = s->L / 2; s->B = p->batch;
+  s->st = (cudaStream_t)cuda_stream;
+  s->ws = (char*)d_workspace; s->ws_bytes = ws_bytes; s->pl = pl;
+  s->global_steps = 0; s->sticky = 0; s->launches = 0;
+  char* w = s->ws;
+  s->gamma_d = (double*)(w + pl.gamma); s->traj_d = (uint64_t*)(w + pl.traj); s->step_d = (int64_t*)(w + pl.step);
+  s->status_d = (int*)(w + pl.status); s->occ_d = (int*)(w + pl.occ);
+  s->log_count_d = (unsigned long long*)(w + pl.log_count); s->log_d = (fm_event*)(w + pl.log);
+  s->part_d = (double*)(w + pl.part); s->nocc_d = (double*)(w + pl.nocc); s->w_d = (double*)(w + pl.w);
+  s->xbuf_d = w + pl.xbuf; s->vbuf_d = w + pl.vbuf;
+  s->G = (z64*)(w + pl.G); s->R = (z64*)(w + pl.R); s->T = (z64*)(w + pl.T);
+  s->Dinv = (z64*)(w + pl.Dinv); s->X = (z64*)(w + pl.X);
+  s->ee_vb = (z64*)(w + pl.ee_vb); s->ee_wb = (z64*)(w + pl.ee_wb); s->ee_pb = (z64*)(w + pl.ee_pb);
+  s->ee_d = (double*)(w + pl.ee_d); s->ee_e = (double*)(w + pl.ee_e); s->ee_lam = (double*)(w + pl.ee_lam);
+  s->ee_S = (double*)(w + pl.ee_S); s->ee_max = (double*)(w + pl.ee_max); s->ee_sites = (int*)(w + pl.ee_sites);
+  s->chk_cols = (z64*)(w + pl.chk_cols); s->chk_G = (z64*)(w + pl.chk_G);
+  s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
+  s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
+  s->mixed_extra = nullptr;
+  if (p->precision == FM_FP64) {
+    s->U = (z64*)(w + pl.U); s->U2 = (z64*)(w + pl.U2); s->P = (z64*)(w + pl.P); s->aux = s->U2;
+  } else {
+    s->V = (float*)(w + pl.V); s->V2 = (float*)(w + pl.V2);
+    s->Vh = (__half*)(w + pl.Vh); s->Vl = (__half*)(w + pl.Vl);
+    s->Ah = (__half*)(w + pl.Ah); s->Al = (__half*)(w + pl.Al);
+    s->Th = (__half*)(w + pl.Th); s->Tl = (__half*)(w + pl.Tl);
+    s->aux = (z64*)(w + pl.aux); s->mixed_extra = w + pl.mixed_extra;
+  }
+  s->gamma_h.assign(s->B, p->gamma);
+  s->traj_h.resize(s->B);
+  for (int b = 0; b < s->B; ++b) s->traj_h[b] = p->traj_id + (uint64_t)b;
+  s->step_h.assign(s->B, 0);
+
+  fm_status r = FM_OK;
+  do {
+    // zero the whole workspace once: triangular factors rely on zero lower parts
+    if (cudaMemsetAsync(s->ws, 0, pl.total, s->st) != cudaSuccess) { r = fail(s, FM_ECUDA, "memset"); break; }
+    if (cudaMemcpyAsync(s->gamma_d, s->gamma_h.data(), 8 * s->B, cudaMemcpyHostToDevice, s->st) ||
+        cudaMemcpyAsync(s->traj_d, s->traj_h.data(), 8 * s->B, cudaMemcpyHostToDevice, s->st)) {
+      r = fail(s, FM_ECUDA, "upload");
+      break;
+    }
+    std::vector<int> occ = occupied(s->Lx, s->Ly);
+    if ((int)occ.size() != s->N) { r = fail(s, FM_EINVAL, "checkerboard does not half fill"); break; }
+    if (cudaMemcpyAsync(s->occ_d, occ.data(), 4 * s->N, cudaMemcpyHostToDevice, s->st)) {
+      r = fail(s, FM_ECUDA, "upload occ");
+      break;
+    }
+    std::vector<z64> px = ring_row(s->Lx, p->J, p->dt), py = ring_row(s->Ly, p->J, p->dt);
+    // stage the rows in the EE scratch (free until the first entropy call)
+    z64* dpx = s->ee_pb;
+    z64* dpy = s->ee_pb + s->Lx;
+    if (cudaMemcpyAsync(dpx, px.data(), 16 * s->Lx, cudaMemcpyHostToDevice, s->st) ||
+        cudaMemcpyAsync(dpy, py.data(), 16 * s->Ly, cudaMemcpyHostToDevice, s->st)) {
+      r = fail(s, FM_ECUDA, "upload propagator rows");
+      break;
+    }
+    if (p->precision == FM_FP64) {
+      if (expand_propagator_z(s->st, dpx, dpy, s->Lx, s->Ly, s->P) ||
+          neel_init_z(s->st, s->U, s->L, s->N, s->B, s->occ_d)) {
+        r = fail(s, FM_ECUDA, "init kernels");
+        break;
+      }
+      s->launches += 2;
+    } else {
+      if (expand_propagator_planes(s->st, dpx, dpy, s->Lx, s->Ly, s->Ah, s->Al) ||
+          neel_init_v(s->st, s->V, s->Vh, s->Vl, s->L, s->N, s->B, s->occ_d)) {
+        r = fail(s, FM_ECUDA, "init kernels");
+        break;
+      }
+      s->launches += 2;
+      std::string why2;
+      if (mixed_init(s->st, s->Lx, s->Ly, s->B, s->mixed_extra, &why2)) {
+        r = fail(s, FM_ECUDA, "mixed init: " + why2);
+        break;
+      }
+    }
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) { r = fail(s, FM_ECUDA, "init sync"); break; }
+  } while (0);
+  if (r != FM_OK) {
+    delete s;
+    return r;
+  }
+  *out = s;
+  return FM_OK;
+}
+
+fm_status fm_step(fm_state* s, int32_t nsteps) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (nsteps < 0) return fail(s, FM_EINVAL, "nsteps < 0");
+  for (int i = 0; i < nsteps; ++i) {
+    if (s->prm.precision == FM_FP64) r = step_f64(s);
+    else {
+      MixedCtx c = {s->st, s->Lx, s->Ly, s->L, s->N, s->B, s->prm.protocol, s->prm.reorth_interval,
+                    s->prm.dt, s->prm.seed, s->global_steps, s->V, s->V2, s->Vh, s->Vl, s->Ah, s->Al,
+                    s->Th, s->Tl, s->G, s->R, s->T, s->Dinv, s->X, s->gamma_d, s->traj_d, s->step_d,
+                    s->status_d, s->part_d, s->nocc_d, s->w_d, s->xbuf_d, s->vbuf_d, s->log_d,
+                    (int64_t*)s->log_count_d, s->prm.event_capacity, s->mixed_extra, 0, ""};
+      r = (fm_status)mixed_step(&c);
+      s->V = c.V; s->V2 = c.V2;
+      s->launches += c.launches;
+      if (r) r = fail(s, r, c.err);
+    }
+    if (r) return r;
+    s->global_steps += 1;
+    for (int b = 0; b < s->B; ++b) s->step_h[b] += 1;
+  }
+  return FM_OK;
+}
+
+fm_status fm_set_gammas(fm_state* s, const double* gammas) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!gammas) return fail(s, FM_EINVAL, "gammas is NULL");
+  for (int b = 0; b < s->B; ++b)
+    if (!(gammas[b] >= 0.0) || !isfinite(gammas[b])) return fail(s, FM_EINVAL, "gamma must be finite, >= 0");
+  for (int b = 0; b < s->B; ++b) s->gamma_h[b] = gammas[b];
+  CK(cudaMemcpyAsync(s->gamma_d, s->gamma_h.data(), 8 * s->B, cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return FM_OK;
+}
+
+fm_status fm_reset_trajectory(fm_state* s, int32_t b, uint64_t traj_id, double gamma) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (b < 0 || b >= s->B) return fail(s, FM_EINVAL, "trajectory index out of range");
+  if (!(gamma >= 0.0) || !isfinite(gamma)) return fail(s, FM_EINVAL, "gamma must be finite, >= 0");
+  CK(cudaStreamSynchronize(s->st));
+  s->gamma_h[b] = gamma;
+  s->traj_h[b] = traj_id;
+  s->step_h[b] = 0;
+  CK(cudaMemcpyAsync(s->gamma_d + b, &s->gamma_h[b], 8, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->traj_d + b, &s->traj_h[b], 8, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->step_d + b, &s->step_h[b], 8, cudaMemcpyHostToDevice, s->st));
+  if (s->prm.precision == FM_FP64) {
+    CKL(neel_init_z(s->st, s->U + (int64_t)b * s->L * s->N, s->L, s->N, 1, s->occ_d), 1);
+  } else {
+    const int64_t o = (int64_t)b * 2 * s->L * s->N;
+    CKL(neel_init_v(s->st, s->V + o, s->Vh + o, s->Vl + o, s->L, s->N, 1, s->occ_d), 1);
+  }
+  CK(cudaStreamSynchronize(s->st));
+  return FM_OK;
+}
+
+fm_status fm_steps_done(fm_state* s, int32_t b, int64_t* out) {
+  if (!s || !out) return FM_EINVAL;
+  if (b < 0 || b >= s->B) return fail(s, FM_EINVAL, "trajectory index out of range");
+  *out = s->step_h[b];
+  return FM_OK;
+}
+
+fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, double* S_out) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!S_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  r = validate_sites(s, sites, n);
+  if (r) return r;
+  return entropy_impl(s, b, sites, n, S_out);
+}
+
+fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA, const int32_t* B, int32_t nB,
+                         double* I_out) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!I_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  if ((r = validate_sites(s, A, nA)) || (r = validate_sites(s, B, nB))) return r;
+  std::vector<int32_t> AB(A, A + nA);
+  AB.insert(AB.end(), B, B + nB);
+  r = validate_sites(s, AB.data(), (int32_t)AB.size());
+  if (r) {
+    s->sticky = 0;
+    s->err.clear();
+    return fail(s, FM_EINVAL, "A and B overlap");
+  }
+  std::sort(AB.begin(), AB.end());
+  double SA, SB, SAB;
+  if ((r = entropy_impl(s, b, A, nA, &SA)) || (r = entropy_impl(s, b, B, nB, &SB)) ||
+      (r = entropy_impl(s, b, AB.data(), (int32_t)AB.size(), &SAB)))
+    return r;
+  *I_out = SA + SB - SAB;
+  return FM_OK;
+}
+
+fm_status fm_copy_U(fm_state* s, int32_t b, void* host_c128, int64_t ld) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (b < 0 || b >= s->B || !host_c128 || ld < s->L) return fail(s, FM_EINVAL, "bad copy_U arguments");
+  const z64* src;
+  if (s->prm.precision == FM_FP64) src = s->U + (int64_t)b * s->L * s->N;
+  else {
+    CKL(v_to_z(s->st, s->V + (int64_t)b * 2 * s->L * s->N, s->L, s->N, s->aux), 1);
+    src = s->aux;
+  }
+  CK(cudaMemcpy2DAsync(host_c128, ld * 16, src, (size_t)s->L * 16, (size_t)s->L * 16, s->N,
+                       cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+fm_status fm_set_U(fm_state* s, int32_t b, const void* host_c128, int64_t ld) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (b < 0 || b >= s->B || !host_c128 || ld < s->L) return fail(s, FM_EINVAL, "bad set_U arguments");
+  CK(cudaStreamSynchronize(s->st));
+  if (s->prm.precision == FM_FP64) {
+    CK(cudaMemcpy2DAsync(s->U + (int64_t)b * s->L * s->N, (size_t)s->L * 16, host_c128, ld * 16,
+                         (size_t)s->L * 16, s->N, cudaMemcpyHostToDevice, s->st));
+  } else {
+    CK(cudaMemcpy2DAsync(s->aux, (size_t)s->L * 16, host_c128, ld * 16, (size_t)s->L * 16, s->N,
+                         cudaMemcpyHostToDevice, s->st));
+    const int64_t o = (int64_t)b * 2 * s->L * s->N;
+    CKL(z_to_v(s->st, s->aux, s->L, s->N, s->V + o, s->Vh + o, s->Vl + o), 1);
+  }
+  return sync_and_check(s);
+}
+
+fm_status fm_occupations(fm_state* s, int32_t b, double* host_n) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (b < 0 || b >= s->B || !host_n) return fail(s, FM_EINVAL, "bad occupations arguments");
+  const int nch = occupation_chunks(s->L, s->N, 1);
+  if (s->prm.precision == FM_FP64) {
+    CKL(rownorm_partials_z(s->st, s->U + (int64_t)b * s->L * s->N, s->L, s->N, 1, s->part_d, nch), 1);
+  } else {
+    CKL(rownorm_partials_v(s->st, s->V + (int64_t)b * 2 * s->L * s->N, s->L, s->N, 1, s->part_d, nch), 1);
+  }
+  CKL(reduce_occupations(s->st, s->part_d, nch, s->L, 1, s->nocc_d, nullptr, s->gamma_d, s->prm.dt, s->traj_d,
+                         s->step_d, s->prm.seed), 1);
+  CK(cudaMemcpyAsync(host_n, s->nocc_d, 8 * s->L, cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+fm_status fm_orthonormality_error(fm_state* s, int32_t b, const int32_t* cols, int32_t ncols, double* err) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (b < 0 || b >= s->B || !err || ncols < 1 || ncols > std::min(s->N, 64) || !cols)
+    return fail(s, FM_EINVAL, "bad orthonormality arguments (1 <= ncols <= min(N, 64))");
+  for (int i = 0; i < ncols; ++i)
+    if (cols[i] < 0 || cols[i] >= s->N) return fail(s, FM_EINVAL, "column index out of range");
+  const int L = s->L, N = s->N;
+  // aux <- U_b as complex128 (L x N), then Gs = U[:, cols]^dag U (ncols x N) in R
+  const z64* U;
+  if (s->prm.precision == FM_FP64) U = s->U + (int64_t)b * L * N;
+  else {
+    CKL(v_to_z(s->st, s->V + (int64_t)b * 2 * L * N, L, N, s->aux), 1);
+    U = s->aux;
+  }
+  z64* Uc = s->chk_cols;
+  for (int i = 0; i < ncols; ++i)
+    CK(cudaMemcpyAsync(Uc + (int64_t)i * L, U + (int64_t)cols[i] * L, 16 * L, cudaMemcpyDeviceToDevice, s->st));
+  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  CKL(zgemm<double>(s->st, ncols, N, L, OP_C, OP_N, one, Uc, L, 0, U, L, 0, zero, s->chk_G, ncols, 0, 1, 0), 1);
+  CK(cudaMemcpyAsync(s->ee_sites, cols, 4 * ncols, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemsetAsync(s->ee_max, 0, 8, s->st));
+  CKL(max_abs_minus_identity(s->st, s->chk_G, ncols, N, s->ee_sites, s->ee_max), 1);
+  CK(cudaMemcpyAsync(err, s->ee_max, 8, cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+fm_status fm_take_events(fm_state* s, fm_event* out, int32_t cap, int32_t* count, int64_t* dropped) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!count || !dropped || cap < 0 || (cap > 0 && !out)) return fail(s, FM_EINVAL, "bad take_events arguments");
+  CK(cudaStreamSynchronize(s->st));
+  unsigned long long n = 0;
+  CK(cudaMemcpy(&n, s->log_count_d, 8, cudaMemcpyDeviceToHost));
+  const int64_t have = std::min<int64_t>((int64_t)n, s->prm.event_capacity);
+  const int64_t take = std::min<int64_t>(have, cap);
+  if (take > 0) CK(cudaMemcpy(out, s->log_d, take * sizeof(fm_event), cudaMemcpyDeviceToHost));
+  *count = (int32_t)take;
+  *dropped = (int64_t)n - take;
+  CK(cudaMemset(s->log_count_d, 0, 8));
+  return FM_OK;
+}
+
+fm_status fm_save(fm_state* s, const char* path) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!path) return fail(s, FM_EINVAL, "path is NULL");
+  CK(cudaStreamSynchronize(s->st));
+  const size_t ubytes = (s->prm.precision == FM_FP64) ? (size_t)s->B * s->L * s->N * 16
+                                                       : (size_t)s->B * 2 * s->L * s->N * 4;
+  std::vector<char> host(ubytes);
+  CK(cudaMemcpy(host.data(), s->prm.precision == FM_FP64 ? (void*)s->U : (void*)s->V, ubytes,
+                cudaMemcpyDeviceToHost));
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(s, FM_EINVAL, std::string("cannot open ") + path);
+  const char magic[8] = {'F', 'M', 'C', 'K', 'P', 'T', '0', '1'};
+  bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(&s->prm, sizeof(fm_params), 1, f) == 1 &&
+            fwrite(&s->global_steps, 8, 1, f) == 1 && fwrite(s->gamma_h.data(), 8, s->B, f) == (size_t)s->B &&
+            fwrite(s->traj_h.data(), 8, s->B, f) == (size_t)s->B &&
+            fwrite(s->step_h.data(), 8, s->B, f) == (size_t)s->B && fwrite(host.data(), 1, ubytes, f) == ubytes;
+  fclose(f);
+  if (!ok) return fail(s, FM_EINVAL, "short write");
+  return FM_OK;
+}
+
+fm_status fm_load(fm_state* s, const char* path) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!path) return fail(s, FM_EINVAL, "path is NULL");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(s, FM_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  fm_params p;
+  int64_t gsteps;
+  std::vector<double> g(s->B);
+  std::vector<uint64_t> t(s->B);
+  std::vector<int64_t> st(s->B);
+  const size_t ubytes = (s->prm.precision == FM_FP64) ? (size_t)s->B * s->L * s->N * 16
+                                                       : (size_t)s->B * 2 * s->L * s->N * 4;
+  std::vector<char> host(ubytes);
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "FMCKPT01", 8) == 0 &&
+            fread(&p, sizeof(fm_params), 1, f) == 1 && fread(&gsteps, 8, 1, f) == 1 &&
+            fread(g.data(), 8, s->B, f) == (size_t)s->B && fread(t.data(), 8, s->B, f) == (size_t)s->B &&
+            fread(st.data(), 8, s->B, f) == (size_t)s->B && fread(host.data(), 1, ubytes, f) == ubytes;
+  fclose(f);
+  if (!ok) return fail(s, FM_EINVAL, "bad or truncated checkpoint");
+  if (p.Lx != s->prm.Lx || p.Ly != s->prm.Ly || p.batch != s->prm.batch || p.precision != s->prm.precision ||
+      p.protocol != s->prm.protocol || p.seed != s->prm.seed || p.dt != s->prm.dt || p.J != s->prm.J)
+    return fail(s, FM_EINVAL, "checkpoint does not match this state's parameters");
+  CK(cudaStreamSynchronize(s->st));
+  s->gamma_h = g; s->traj_h = t; s->step_h = st; s->global_steps = gsteps;
+  CK(cudaMemcpy(s->gamma_d, g.data(), 8 * s->B, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->traj_d, t.data(), 8 * s->B, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->step_d, st.data(), 8 * s->B, cudaMemcpyHostToDevice));
+  if (s->prm.precision == FM_FP64) {
+    CK(cudaMemcpy(s->U, host.data(), ubytes, cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(s->V, host.data(), ubytes, cudaMemcpyHostToDevice));
+    CKL(split_planes(s->st, s->V, s->Vh, s->Vl, (int64_t)s->B * 2 * s->L * s->N), 1);
+  }
+  return sync_and_check(s);
+}
+
+int64_t fm_kernel_launches(const fm_state* s) { return s ? s->launches : 0; }
+
+const char* fm_last_error(const fm_state* s) { return s ? s->err.c_str() : "null state"; }
+
+void fm_destroy(fm_state* s) { delete s; }
+
+}  // extern "C"

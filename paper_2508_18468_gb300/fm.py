@@ -1,0 +1,216 @@
+"""Python binding of the fm C ABI (``include/fm.h``): argument marshalling only.
+
+Every step of a trajectory runs in ``libfm.so``.  PyTorch provides the device
+workspace and the CUDA stream.  Importing this module loads the library and
+raises if it is missing: there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfm.so")
+
+FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENUMERIC, FM_ETIMEOUT, FM_ESTATE = range(7)
+FM_PROJECTIVE, FM_HOMODYNE = 0, 1
+FM_FP64, FM_MIXED = 0, 1
+STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENUMERIC",
+                5: "FM_ETIMEOUT", 6: "FM_ESTATE"}
+
+
+class fm_params(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("protocol", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reorth_interval", ctypes.c_int32), ("event_capacity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("J", ctypes.c_double), ("dt", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64), ("traj_id", ctypes.c_uint64)]
+
+
+class fm_event(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("traj", ctypes.c_int32), ("site", ctypes.c_int32),
+                ("u", ctypes.c_double), ("p", ctypes.c_double), ("outcome", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class FmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libfm.so is not built (run __graft_entry__.build()); "
+                          "this package has no non-CUDA fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, i32, i64, u64, dbl, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, \
+        ctypes.c_double, ctypes.c_size_t
+    sigs = {
+        "fm_workspace_bytes": (sz, [P(fm_params)]),
+        "fm_init_state": (i32, [P(fm_params), vp, sz, vp, P(vp)]),
+        "fm_step": (i32, [vp, i32]),
+        "fm_set_gammas": (i32, [vp, P(dbl)]),
+        "fm_reset_trajectory": (i32, [vp, i32, u64, dbl]),
+        "fm_steps_done": (i32, [vp, i32, P(i64)]),
+        "fm_entropy": (i32, [vp, i32, P(i32), i32, P(dbl)]),
+        "fm_mutual_info": (i32, [vp, i32, P(i32), i32, P(i32), i32, P(dbl)]),
+        "fm_copy_U": (i32, [vp, i32, vp, i64]),
+        "fm_set_U": (i32, [vp, i32, vp, i64]),
+        "fm_occupations": (i32, [vp, i32, P(dbl)]),
+        "fm_orthonormality_error": (i32, [vp, i32, P(i32), i32, P(dbl)]),
+        "fm_take_events": (i32, [vp, P(fm_event), i32, P(i32), P(i64)]),
+        "fm_save": (i32, [vp, ctypes.c_char_p]),
+        "fm_load": (i32, [vp, ctypes.c_char_p]),
+        "fm_kernel_launches": (i64, [vp]),
+        "fm_last_error": (ctypes.c_char_p, [vp]),
+        "fm_destroy": (None, [vp]),
+        "fm_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _i32_array(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.int32).ravel())
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def make_params(Lx, Ly=1, batch=1, protocol=FM_PROJECTIVE, precision=FM_FP64, reorth_interval=1,
+                event_capacity=0, J=1.0, dt=0.05, gamma=0.5, seed=0, traj_id=0):
+    return fm_params(Lx=Lx, Ly=Ly, batch=batch, protocol=protocol, precision=precision,
+                     reorth_interval=reorth_interval, event_capacity=event_capacity, reserved=0,
+                     J=J, dt=dt, gamma=gamma, seed=seed, traj_id=traj_id)
+
+
+def fm_workspace_bytes(params):
+    return int(lib.fm_workspace_bytes(ctypes.byref(params)))
+
+
+def fm_version():
+    return lib.fm_version().decode()
+
+
+class Trajectories:
+    """A batch of trajectories held on the GPU (one ``fm_state``).
+
+    The device workspace is a torch uint8 tensor owned by this object; work is
+    issued on the torch stream current at construction.
+    """
+
+    def __init__(self, params, device="cuda", stream=None):
+        import torch
+        self.params = params
+        self.L = params.Lx * params.Ly
+        self.N = self.L // 2
+        self.batch = params.batch
+        nbytes = fm_workspace_bytes(params)
+        if nbytes == 0:
+            raise FmError(FM_EINVAL, "invalid parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.workspace.device)
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        code = lib.fm_init_state(ctypes.byref(params), ctypes.c_void_p(self.workspace.data_ptr()),
+                                 ctypes.c_size_t(nbytes), ctypes.c_void_p(stream.cuda_stream),
+                                 ctypes.byref(handle))
+        if code != FM_OK:
+            raise FmError(code, "fm_init_state failed")
+        self._h = handle
+
+    # -- marshalling helpers
+    def _check(self, code):
+        if code != FM_OK:
+            raise FmError(code, lib.fm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI, same names without the prefix
+    def step(self, nsteps=1):
+        self._check(lib.fm_step(self._h, int(nsteps)))
+
+    def set_gammas(self, gammas):
+        g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64))
+        assert g.size == self.batch
+        self._check(lib.fm_set_gammas(self._h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def reset_trajectory(self, b, traj_id, gamma):
+        self._check(lib.fm_reset_trajectory(self._h, int(b), int(traj_id), float(gamma)))
+
+    def steps_done(self, b=0):
+        out = ctypes.c_int64()
+        self._check(lib.fm_steps_done(self._h, int(b), ctypes.byref(out)))
+        return out.value
+
+    def entropy(self, sites, b=0):
+        a, p = _i32_array(sites)
+        out = ctypes.c_double()
+        self._check(lib.fm_entropy(self._h, int(b), p, int(a.size), ctypes.byref(out)))
+        return out.value
+
+    def mutual_info(self, A, B, b=0):
+        a, pa = _i32_array(A)
+        c, pb = _i32_array(B)
+        out = ctypes.c_double()
+        self._check(lib.fm_mutual_info(self._h, int(b), pa, int(a.size), pb, int(c.size), ctypes.byref(out)))
+        return out.value
+
+    def copy_U(self, b=0):
+        U = np.empty((self.L, self.N), dtype=np.complex128, order="F")
+        self._check(lib.fm_copy_U(self._h, int(b), ctypes.c_void_p(U.ctypes.data), self.L))
+        return U
+
+    def set_U(self, U, b=0):
+        U = np.asfortranarray(np.asarray(U, dtype=np.complex128))
+        assert U.shape == (self.L, self.N)
+        self._check(lib.fm_set_U(self._h, int(b), ctypes.c_void_p(U.ctypes.data), self.L))
+
+    def occupations(self, b=0):
+        n = np.empty(self.L, dtype=np.float64)
+        self._check(lib.fm_occupations(self._h, int(b), n.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return n
+
+    def orthonormality_error(self, cols, b=0):
+        a, p = _i32_array(cols)
+        out = ctypes.c_double()
+        self._check(lib.fm_orthonormality_error(self._h, int(b), p, int(a.size), ctypes.byref(out)))
+        return out.value
+
+    def take_events(self, cap=1 << 20):
+        buf = (fm_event * cap)()
+        count = ctypes.c_int32()
+        dropped = ctypes.c_int64()
+        self._check(lib.fm_take_events(self._h, buf, cap, ctypes.byref(count), ctypes.byref(dropped)))
+        ev = [(buf[i].traj, buf[i].step, buf[i].site, buf[i].u, buf[i].p, buf[i].outcome)
+              for i in range(count.value)]
+        return ev, dropped.value
+
+    def save(self, path):
+        self._check(lib.fm_save(self._h, str(path).encode()))
+
+    def load(self, path):
+        self._check(lib.fm_load(self._h, str(path).encode()))
+
+    @property
+    def kernel_launches(self):
+        return int(lib.fm_kernel_launches(self._h))
+
+    def last_error(self):
+        return lib.fm_last_error(self._h).decode()

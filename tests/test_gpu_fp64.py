@@ -1,0 +1,215 @@
+"""All-FP64 GPU path vs the FP64 oracle, element by element (needs a GB300).
+
+Bars (FP64 mode): max |C_gpu - C_oracle| <= 1e-10 with C = U U^dag, entropy
+relative error <= 1e-9 (relative to max(S, 1 nat)), projective outcomes and
+their uniform draws bit-identical.
+"""
+import numpy as np
+import pytest
+
+from oracle import lattice, observables, philox, trajectory
+from oracle.trajectory import HOMODYNE, PROJECTIVE, Params
+
+pytestmark = pytest.mark.gpu
+
+C_TOL = 1e-10
+S_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def fm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_18468_gb300 import build
+    build.build()
+    from paper_2508_18468_gb300 import fm as mod
+    return mod
+
+
+def pair(fm, Lx, Ly=1, gamma=0.5, protocol=PROJECTIVE, batch=1, seed=1, traj_id=0, reorth=1, events=0,
+         precision=0):
+    po = Params(Lx=Lx, Ly=Ly, gamma=gamma, protocol=protocol, reorth_interval=reorth, seed=seed, traj_id=traj_id)
+    pg = fm.make_params(Lx, Ly, batch=batch, protocol=protocol, precision=precision, reorth_interval=reorth,
+                        event_capacity=events, gamma=gamma, seed=seed, traj_id=traj_id)
+    return po, fm.Trajectories(pg)
+
+
+def cdiff(Ua, Ub):
+    return float(np.max(np.abs(observables.correlation(Ua) - observables.correlation(Ub))))
+
+
+def srel(a, b):
+    return abs(a - b) / max(abs(b), 1.0)
+
+
+def test_projective_draws_and_outcomes_bit_exact(fm):
+    po, g = pair(fm, 64, gamma=2.0, events=100000, seed=77, traj_id=3)
+    g.step(20)
+    ev, dropped = g.take_events()
+    ref = trajectory.run(po, 20)
+    assert dropped == 0
+    got = sorted((e[1], e[2], e[3], e[5]) for e in ev)          # (step, site, u, outcome)
+    exp = sorted((s, j, u, o) for (s, j, u, p, o) in ref["events"])
+    assert [(a, b, d) for a, b, c, d in got] == [(a, b, d) for a, b, c, d in exp]
+    assert all(a[2] == b[2] for a, b in zip(got, exp))           # uniforms bit-identical
+    # Born weights agree to rounding
+    pg = {(e[1], e[2]): e[4] for e in ev}
+    for (s, j, u, p, o) in ref["events"]:
+        assert abs(pg[(s, j)] - p) < 1e-12
+    # the selection is exactly the oracle's u_select < 1 - exp(-gamma dt)
+    for s in range(20):
+        us, _ = philox.measure_draws(77, 3, s, 64)
+        sel = set(np.nonzero(us < 1 - np.exp(-2.0 * 0.05))[0].tolist())
+        assert sel == {e[2] for e in ev if e[1] == s}
+
+
+def test_ring64_projective_200_steps(fm):
+    """Projective ring L = 64, gamma = 0.5, reorth every step, half-chain EE every 10 steps."""
+    po, g = pair(fm, 64, gamma=0.5, seed=0x2508184681, events=100000)
+    half = list(range(32))
+    ref = trajectory.run(po, 200, ee_every=10, ee_sites=half)
+    ee = []
+    for k in range(20):
+        g.step(10)
+        ee.append(g.entropy(half))
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    for (done, s_ref), s in zip(ref["ee"], ee):
+        assert srel(s, s_ref) <= S_TOL, (done, s, s_ref)
+    ev, _ = g.take_events()
+    assert sorted((e[1], e[2], e[5]) for e in ev) == sorted((s, j, o) for (s, j, u, p, o) in ref["events"])
+
+
+@pytest.mark.parametrize("gamma,reorth", [(1.0, 1), (0.3, 2)])
+def test_ring64_homodyne(fm, gamma, reorth):
+    po, g = pair(fm, 64, gamma=gamma, protocol=HOMODYNE, seed=11, traj_id=2, reorth=reorth)
+    ref = trajectory.run(po, 100)
+    g.step(100)
+    U = g.copy_U()
+    assert cdiff(U, ref["U"]) <= C_TOL
+    half = list(range(32))
+    assert srel(g.entropy(half), observables.entanglement_entropy(ref["U"], half)) <= S_TOL
+
+
+@pytest.mark.parametrize("protocol,gamma", [(PROJECTIVE, 1.5), (HOMODYNE, 1.0)])
+def test_torus_8x6(fm, protocol, gamma):
+    po, g = pair(fm, 8, 6, gamma=gamma, protocol=protocol, seed=5)
+    ref = trajectory.run(po, 40)
+    g.step(40)
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    strip = [x + 8 * y for y in range(6) for x in range(4)]
+    assert srel(g.entropy(strip), observables.entanglement_entropy(ref["U"], strip)) <= S_TOL
+
+
+def test_batch_with_per_trajectory_rates(fm):
+    gam = [0.2, 1.0, 3.0]
+    _, g = pair(fm, 32, batch=3, protocol=PROJECTIVE, seed=9, traj_id=5)
+    g.set_gammas(gam)
+    g.step(30)
+    for b in range(3):
+        po = Params(Lx=32, gamma=gam[b], protocol=PROJECTIVE, seed=9, traj_id=5 + b)
+        ref = trajectory.run(po, 30)
+        assert cdiff(g.copy_U(b), ref["U"]) <= C_TOL
+
+
+@pytest.mark.parametrize("Lx", [2, 6, 70, 130])
+@pytest.mark.parametrize("protocol", [PROJECTIVE, HOMODYNE])
+def test_ragged_sizes(fm, Lx, protocol):
+    po, g = pair(fm, Lx, gamma=1.0, protocol=protocol, seed=3)
+    ref = trajectory.run(po, 15)
+    g.step(15)
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    A = list(range(Lx // 2))
+    assert srel(g.entropy(A), observables.entanglement_entropy(ref["U"], A)) <= S_TOL
+
+
+def test_unmonitored_ring1024_closed_form(fm):
+    _, g = pair(fm, 1024, gamma=0.0, reorth=8)
+    g.step(40)
+    n = g.occupations()
+    k = 2 * np.pi * np.arange(1024) / 1024
+    ref = 0.5 + 0.5 * (-1.0) ** np.arange(1024) * np.mean(np.cos(4.0 * 40 * 0.05 * np.cos(k)))
+    assert np.max(np.abs(n - ref)) < 1e-12
+
+
+def test_ring1024_projective_short(fm):
+    po, g = pair(fm, 1024, gamma=2.0, seed=0x2508184682, traj_id=1)
+    ref = trajectory.run(po, 6)
+    g.step(6)
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    for ell in (128, 256, 512):
+        A = list(range(ell))
+        assert srel(g.entropy(A), observables.entanglement_entropy(ref["U"], A)) <= S_TOL
+
+
+def test_entropy_edge_cases(fm):
+    po, g = pair(fm, 48, gamma=0.8, protocol=HOMODYNE, seed=21)
+    g.step(25)
+    ref = trajectory.run(po, 25)["U"]
+    assert g.entropy([]) == 0.0
+    assert abs(g.entropy(list(range(48)))) < 1e-10               # pure state
+    A = [0, 3, 4, 17, 30]
+    Abar = [i for i in range(48) if i not in A]
+    assert abs(g.entropy(A) - g.entropy(Abar)) < 1e-10
+    assert srel(g.entropy(A), observables.entanglement_entropy(ref, A)) <= S_TOL
+    assert srel(g.entropy(Abar), observables.entanglement_entropy(ref, Abar)) <= S_TOL
+
+
+def test_mutual_info_vs_oracle(fm):
+    po, g = pair(fm, 8, 6, gamma=1.0, protocol=HOMODYNE, seed=4)
+    g.step(20)
+    ref = trajectory.run(po, 20)["U"]
+    A = [0, 1, 8, 9]
+    B = [4, 5, 12, 13]
+    I = g.mutual_info(A, B)
+    assert abs(I - observables.mutual_information(ref, A, B)) <= 1e-9
+    with pytest.raises(fm.FmError):
+        g.mutual_info(A, [1, 2])
+    g.step(1)                                                       # argument errors are not sticky
+
+
+def test_checkpoint_resume_is_bitwise(fm, tmp_path):
+    _, g1 = pair(fm, 40, gamma=1.0, protocol=HOMODYNE, seed=8)
+    g1.step(20)
+    _, g2 = pair(fm, 40, gamma=1.0, protocol=HOMODYNE, seed=8)
+    g2.step(10)
+    g2.save(tmp_path / "ck.bin")
+    _, g3 = pair(fm, 40, gamma=1.0, protocol=HOMODYNE, seed=8)
+    g3.load(tmp_path / "ck.bin")
+    g3.step(10)
+    assert np.array_equal(g1.copy_U(), g3.copy_U())
+    assert g3.steps_done() == 20
+
+
+def test_reset_trajectory_matches_fresh_run(fm):
+    _, g = pair(fm, 32, batch=2, gamma=1.0, protocol=PROJECTIVE, seed=12, traj_id=0)
+    g.step(7)
+    g.reset_trajectory(1, traj_id=40, gamma=0.5)
+    g.step(9)
+    assert g.steps_done(1) == 9 and g.steps_done(0) == 16
+    ref = trajectory.run(Params(Lx=32, gamma=0.5, protocol=PROJECTIVE, seed=12, traj_id=40), 9)
+    assert cdiff(g.copy_U(1), ref["U"]) <= C_TOL
+
+
+def test_orthonormality_and_invariants(fm):
+    _, g = pair(fm, 96, gamma=1.0, protocol=HOMODYNE, seed=6)
+    g.step(30)
+    assert g.orthonormality_error(list(range(0, 48, 3))) < 1e-13
+    U = g.copy_U()
+    C = observables.correlation(U)
+    assert abs(np.trace(C).real - 48) < 1e-11
+    assert np.max(np.abs(C @ C - C)) < 1e-12
+
+
+def test_invalid_arguments_are_rejected(fm):
+    _, g = pair(fm, 16)
+    with pytest.raises(fm.FmError):
+        g.entropy([0, 0])
+    with pytest.raises(fm.FmError):
+        g.entropy([16])
+    with pytest.raises(fm.FmError):
+        g.step(-1)
+    with pytest.raises(fm.FmError):
+        g.orthonormality_error([99])
+    g.step(2)
+    assert g.steps_done() == 2
