@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput of the monitored free-fermion trajectory step on GB300.
+
+One step = the whole hot path for every trajectory of the batch: dense
+propagation U <- exp(-i H dt) U, the homodyne weight, CholeskyQR2
+re-orthonormalisation, and -- on the workload's schedule -- the half-chain
+entanglement entropy (FP64 eigenvalues).  Default workload: 1d ring
+L = 16384 (N = 8192), homodyne protocol, 4 trajectories (gamma 0.3, 0.3,
+1.0, 1.0), dt = 0.05, half-chain EE every 100 steps, mixed precision
+(split-fp16 tensor-core GEMMs, FP64 Cholesky / eigenvalues).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: trajectories are independent, so N ranks run N independent
+batches (replicas, weak scaling); the only collective is the timing barrier.
+--impl reference times the FP64 CPU oracle on this host's cores (bounded
+sample, scaled by the step's L^3 flop count).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trajectory steps/s at L=16384 (mixed precision, EE err <= 1e-3)"
+UNIT = "trajectory-steps/s"
+WORKLOAD = "ring16384_homodyne"
+ORACLE_SAMPLE_L = 4096
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+def oracle_step_seconds(L_sample, nsteps, seed):
+    """Wall time per oracle homodyne step at L_sample (FP64, numpy on all host cores)."""
+    import numpy as np  # noqa: F401
+    from oracle import lattice, trajectory
+    prm = trajectory.Params(Lx=L_sample, gamma=1.0, protocol=trajectory.HOMODYNE, seed=seed)
+    P = lattice.propagator(L_sample, 1, prm.J, prm.dt)
+    U = lattice.initial_orbitals(L_sample)
+    U, _ = trajectory.step(U, P, prm, 0)       # one untimed step (first touch)
+    t0 = time.perf_counter()
+    for s in range(1, 1 + nsteps):
+        U, _ = trajectory.step(U, P, prm, s)
+    return (time.perf_counter() - t0) / nsteps
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline_line(L_target, seed, nsteps=3):
+    t = oracle_step_seconds(ORACLE_SAMPLE_L, nsteps, seed)
+    scale = (L_target / ORACLE_SAMPLE_L) ** 3
+    return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": "%d homodyne oracle steps at L=%d (numpy FP64, %.2f s/step), scaled by (%d/%d)^3"
+                      % (nsteps, ORACLE_SAMPLE_L, t, L_target, ORACLE_SAMPLE_L)}
+
+
+# ---------------------------------------------------------------- helpers
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def profiled_traffic(name):
+    """dram bytes per launch recorded in profiles/<name>.md ('dram_bytes_per_launch: X'), if present."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.strip().startswith("dram_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def setup_distributed(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    from paper_2508_18468_gb300 import workloads
+    if rank != 0:
+        return
+    wl = workloads.WORKLOADS[args.workload]
+    L = wl["Lx"] * wl["Ly"]
+    seed = workloads.seed_of(args.workload)
+    for s in range(args.warmup):
+        oracle_step_seconds(ORACLE_SAMPLE_L, 1, seed + s)
+    per = oracle_step_seconds(ORACLE_SAMPLE_L, args.steps, seed)
+    scale = (L / ORACLE_SAMPLE_L) ** 3
+    value = 1.0 / (per * scale)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "L": L, "N": L // 2, "protocol": wl["protocol"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": "%d oracle steps at L=%d scaled by (%d/%d)^3" % (
+                                 args.steps, ORACLE_SAMPLE_L, L, ORACLE_SAMPLE_L)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_18468_gb300 import fm, workloads
+
+    wl = workloads.WORKLOADS[args.workload]
+    Lx, Ly = wl["Lx"], wl["Ly"]
+    L = Lx * Ly
+    N = L // 2
+    gam = list(wl["gammas"])
+    B = len(gam)
+    seed = workloads.seed_of(args.workload)
+    precision = fm.FM_MIXED if args.precision == "mixed" else fm.FM_FP64
+    protocol = fm.FM_HOMODYNE if wl["protocol"] == "homodyne" else fm.FM_PROJECTIVE
+    prm = fm.make_params(Lx, Ly, batch=B, protocol=protocol, precision=precision,
+                         reorth_interval=wl["reorth_interval"], gamma=gam[0], seed=seed, traj_id=rank * B)
+    g = fm.Trajectories(prm)
+    g.set_gammas(gam)
+    ee_sites = workloads.half_chain(L)
+    ee_every = wl["ee_every"]
+
+    def one_step(done):
+        g.step(1)
+        if (done + 1) % ee_every == 0:
+            for b in range(B):
+                g.entropy(ee_sites, b)
+
+    done = 0
+    for _ in range(args.warmup):
+        one_step(done)
+        done += 1
+    # align the timed window so it contains the EE evaluations its length implies
+    torch.cuda.synchronize()
+    g.phase_times()
+    g.set_timing(True)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    launches0 = g.kernel_launches
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step(done)
+        done += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    launches = g.kernel_launches - launches0
+    phases = g.phase_times()
+    g.set_timing(False)
+    t_dev = e0.elapsed_time(e1) / 1e3
+    t = max_over_ranks(t_dev, world)
+    value = world * B * args.steps / t
+
+    # end to end through the public API: per step, upload the rates (pinned host),
+    # advance, read every trajectory's occupations back to the host
+    e2e = None
+    if not args.no_e2e:
+        gam_host = torch.tensor(gam, dtype=torch.float64).pin_memory().numpy()
+        occ_host = [torch.empty(L, dtype=torch.float64).pin_memory().numpy() for _ in range(B)]
+        barrier(world)
+        torch.cuda.synchronize()
+        w1 = time.perf_counter()
+        for _ in range(args.steps):
+            g.set_gammas(gam_host)
+            one_step(done)
+            done += 1
+            for b in range(B):
+                g.occupations(b, out=occ_host[b])
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - w1, world)
+        e2e = {"value": world * B * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * B,
+               "d2h_bytes_per_step": 8 * B * L}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = load_peaks()
+    prop_ms, prop_n = phases["propagate"]
+    prop_flops = 8.0 * L * L * N * B                        # algorithmic complex GEMM flops per launch
+    if precision == fm.FM_MIXED:
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / 3.0
+        peak_note = ("%s sustained dense bf16/fp16 tensor rate / 3 (three fp16 products per "
+                     "split-precision product)" % peak_src)
+        dtype = "f32 state, split-fp16 tensor products, f64 Cholesky/eigenvalues"
+    else:
+        peak = 1.05
+        peak_note = "cuBLAS DGEMM measured on this pool (FP64)"
+        dtype = "f64"
+    roof = None
+    if prop_n > 0:
+        achieved = prop_flops / (prop_ms / prop_n / 1e3) / 1e12
+        traffic = profiled_traffic("prop_gemm_ring16384") if precision == fm.FM_MIXED else None
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "tc_gemm_kernel<256> (propagation)",
+                "ms_per_launch": prop_ms / prop_n, "peak_note": peak_note}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "L": L, "N": N, "batch_per_gpu": B, "gammas": gam,
+                   "protocol": wl["protocol"], "dt": 0.05, "ee_every": ee_every,
+                   "ee_sites": "half chain (%d sites)" % (L // 2), "precision": args.precision,
+                   "l2": "inputs larger than L2 (state %.1f GB, propagator %.1f GB per GPU)" % (
+                       B * 2 * L * N * 4 / 1e9, 4 * L * L * 4 / 1e9),
+                   "parallelism": "replicas x%d" % world},
+        "roofline": roof,
+        "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
+        "gpu_launches": int(launches),
+        "wall_s": wall,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_line(L, seed)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = setup_distributed(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

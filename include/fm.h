@@ -158,6 +158,16 @@ fm_status fm_take_events(fm_state* s, fm_event* out, int32_t cap, int32_t* count
 fm_status fm_save(fm_state* s, const char* path);
 fm_status fm_load(fm_state* s, const char* path);
 
+/* Phase timing (tracing).  When enabled, each phase of fm_step and fm_entropy
+ * is bracketed by CUDA events on the state's stream.  fm_phase_times
+ * synchronises, adds the elapsed milliseconds of every completed phase since
+ * the last call into ms[0..FM_NPHASES-1] and the number of timed launches
+ * into counts[] (either may be NULL), then resets.  Phases: */
+enum { FM_PH_PROPAGATE = 0, FM_PH_MEASURE = 1, FM_PH_GRAM = 2, FM_PH_CHOLESKY = 3, FM_PH_TRMM = 4,
+       FM_PH_ENTROPY = 5, FM_NPHASES = 6 };
+fm_status fm_set_timing(fm_state* s, int32_t enable);
+fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts);
+
 /* Launches of library kernels issued on this state since init. */
 int64_t fm_kernel_launches(const fm_state* s);
 

@@ -1,0 +1,39 @@
+/*
+ * fm_testing.h -- test hooks of libfm.so that expose the split-fp16 tensor-core
+ * GEMM on its own, so it can be checked against a reference product.  They
+ * are not part of the trajectory API (include/fm.h); the paper has no
+ * counterpart of them.
+ *
+ * Operand planes: a float x is passed as two fp16 arrays h, l with
+ * x ~= h + l * 2^-11.  All pointers are device pointers; work is issued on
+ * `stream` (cudaStream_t or NULL) and not synchronised.  Return value: 0 on
+ * success, otherwise a cudaError_t code (invalid sizes give
+ * cudaErrorInvalidValue).  d_tiles: caller-owned device scratch of at least
+ * 16 bytes per output tile.
+ */
+#ifndef FM_TESTING_H
+#define FM_TESTING_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* D (M x N, column-major, ld M, float) = A B^T, A: M x K and B: N x K, both
+ * row-major (K contiguous) planes.  M % 128 == 0, N % BN == 0 (BN 128 or
+ * 256), K % 64 == 0.  grid: CTAs (<= 0: one per tile).  chunk_kb > 0 (BN 128
+ * only): move the TMEM accumulators into fp32 registers every chunk_kb
+ * 64-deep K-blocks.  raster != 0: tiles in computed grouped order (d_tiles
+ * unused) instead of an uploaded tile list. */
+int fmx_tc_gemm(const void* Ah, const void* Al, const void* Bh, const void* Bl, int M, int N, int K,
+                float* D, int BN, int grid, int chunk_kb, int raster, void* d_tiles, void* stream);
+
+/* Complex Gram G_b = U_b^dag U_b (complex128, N x N column-major, upper 128 x BN
+ * tiles written) of B trajectories whose orbitals are stored as V_b (2L x N,
+ * column-major planes, column k = [Re U_{:,k}; Im U_{:,k}]). */
+int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, double* G, int BN, void* d_tiles,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FM_TESTING_H */

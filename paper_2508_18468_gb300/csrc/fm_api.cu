@@ -11,13 +11,14 @@
 #include "fm.h"
 #include "kernels.h"
 #include "mixed.h"
+#include "timer.h"
 
 using namespace fm;
 
 namespace {
 
-const int kCholNB = 32;        // Cholesky / triangular-inverse block
-const int kMaxChunks = 64;     // occupation partial sums
+const int kCholNB = CHOL_NB;   // Cholesky / triangular-inverse block
+const int kMaxChunks = 128;    // occupation partial sums
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -130,6 +131,9 @@ struct fm_state {
   __half *Vh, *Vl, *Ah, *Al, *Th, *Tl;
   z64* aux;
   void* mixed_extra;
+  MixedCtx mc;
+  MixedHost* mh;
+  PhaseTimer timer;
   // EE
   z64 *ee_vb, *ee_wb, *ee_pb;
   double *ee_d, *ee_e, *ee_lam, *ee_S, *ee_max;
@@ -230,38 +234,22 @@ fm_status check_state(fm_state* s) {
 }
 
 // ------------------------------------------------------------------ FP64 CholeskyQR pass
-// G = U^dag U ; G = R^dag R (blocked, nb = 32) ; T = R^-1 ; U <- U T
+// G = U^dag U ; G = R^dag R ; T = R^-1 ; U <- U T
 fm_status cholqr_f64(fm_state* s) {
-  const int L = s->L, N = s->N, B = s->B, nb = kCholNB;
-  const int nblk = (N + nb - 1) / nb;
-  const int64_t sNN = (int64_t)N * N, sLN = (int64_t)L * N, sD = (int64_t)nblk * nb * nb;
-  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0}, mone = {-1.0, 0.0};
+  const int L = s->L, N = s->N, B = s->B;
+  const int64_t sNN = (int64_t)N * N, sLN = (int64_t)L * N;
+  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  s->timer.begin(FM_PH_GRAM);
   CKL(zgemm<double>(s->st, N, N, L, OP_C, OP_N, one, s->U, L, sLN, s->U, L, sLN, zero, s->G, N, sNN, B,
                     GEMM_UPPER_ONLY), 1);
-  for (int k = 0; k < N; k += nb) {
-    const int nbk = std::min(nb, N - k);
-    CKL(chol_diag_block(s->st, s->G, N, sNN, s->R, N, sNN, s->Dinv, sD, k, nb, nbk, B, s->status_d), 1);
-    const int rest = N - k - nbk;
-    if (rest > 0) {
-      z64* Dk = s->Dinv + (int64_t)(k / nb) * nb * nb;
-      CKL(zgemm<double>(s->st, nbk, rest, nbk, OP_C, OP_N, one, Dk, nb, sD, s->G + k + (int64_t)(k + nbk) * N, N,
-                        sNN, zero, s->R + k + (int64_t)(k + nbk) * N, N, sNN, B, 0), 1);
-      CKL(zgemm<double>(s->st, rest, rest, nbk, OP_C, OP_N, mone, s->R + k + (int64_t)(k + nbk) * N, N, sNN,
-                        s->R + k + (int64_t)(k + nbk) * N, N, sNN, one,
-                        s->G + (k + nbk) + (int64_t)(k + nbk) * N, N, sNN, B, GEMM_UPPER_ONLY), 1);
-    }
-  }
-  CKL(place_diag_blocks(s->st, s->Dinv, sD, s->T, N, sNN, N, nb, B), 1);
-  for (int j = 1; j < nblk; ++j) {
-    const int c0 = j * nb, nbj = std::min(nb, N - c0);
-    // X = T[0:c0, 0:c0] R[0:c0, c0:c0+nbj] ;  T[0:c0, c0:] = -X Dinv_j
-    CKL(zgemm<double>(s->st, c0, nbj, c0, OP_N, OP_N, one, s->T, N, sNN, s->R + (int64_t)c0 * N, N, sNN, zero,
-                      s->X, N, (int64_t)N * nb, B, GEMM_TRI_A_UPPER), 1);
-    CKL(zgemm<double>(s->st, c0, nbj, nbj, OP_N, OP_N, mone, s->X, N, (int64_t)N * nb,
-                      s->Dinv + (int64_t)j * nb * nb, nb, sD, zero, s->T + (int64_t)c0 * N, N, sNN, B, 0), 1);
-  }
+  s->timer.end(FM_PH_GRAM);
+  s->timer.begin(FM_PH_CHOLESKY);
+  CK(cholesky_inverse_f64(s->st, s->G, s->R, s->T, s->Dinv, s->X, N, N, sNN, N, B, s->status_d, &s->launches));
+  s->timer.end(FM_PH_CHOLESKY);
+  s->timer.begin(FM_PH_TRMM);
   CKL(zgemm<double>(s->st, L, N, N, OP_N, OP_N, one, s->U, L, sLN, s->T, N, sNN, zero, s->U2, L, sLN, B,
                     GEMM_TRI_B_UPPER), 1);
+  s->timer.end(FM_PH_TRMM);
   std::swap(s->U, s->U2);
   s->aux = s->U2;
   return FM_OK;
@@ -271,17 +259,21 @@ fm_status step_f64(fm_state* s) {
   const int L = s->L, N = s->N, B = s->B;
   const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
   // 1. propagation, all trajectories in one product P [U_0 | U_1 | ...]
+  s->timer.begin(FM_PH_PROPAGATE);
   CKL(zgemm<double>(s->st, L, N * B, L, OP_N, OP_N, one, s->P, L, 0, s->U, L, 0, zero, s->U2, L, 0, 1, 0), 1);
+  s->timer.end(FM_PH_PROPAGATE);
   std::swap(s->U, s->U2);
   s->aux = s->U2;
   const int64_t gstep = s->global_steps;
   const int k = s->prm.reorth_interval;
   if (s->prm.protocol == FM_HOMODYNE) {
     const int nch = occupation_chunks(L, N, B);
+    s->timer.begin(FM_PH_MEASURE);
     CKL(rownorm_partials_z(s->st, s->U, L, N, B, s->part_d, nch), 1);
     CKL(reduce_occupations(s->st, s->part_d, nch, L, B, s->nocc_d, s->w_d, s->gamma_d, s->prm.dt, s->traj_d,
                            s->step_d, s->prm.seed), 1);
     CKL(scale_rows_z(s->st, s->U, L, N, B, s->w_d), 1);
+    s->timer.end(FM_PH_MEASURE);
     fm_status r = cholqr_f64(s);
     if (r) return r;
     if ((gstep + 1) % k == 0) {
@@ -295,7 +287,9 @@ fm_status step_f64(fm_state* s) {
     a.xbuf = s->xbuf_d; a.vbuf = s->vbuf_d;
     a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
     a.dev_status = s->status_d;
+    s->timer.begin(FM_PH_MEASURE);
     CKL(pm_measure(s->st, a), 1);
+    s->timer.end(FM_PH_MEASURE);
     if ((gstep + 1) % k == 0) {
       fm_status r = cholqr_f64(s);
       if (r) return r;
@@ -333,6 +327,7 @@ fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, doub
   if (n == 0) { *S_out = 0.0; return FM_OK; }
   const int N = s->N;
   CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  s->timer.begin(FM_PH_ENTROPY);
   fm_status r = gather_rows(s, b, s->ee_sites, n);
   if (r) return r;
   const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
@@ -349,6 +344,7 @@ fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, doub
   CK(hermitian_entropy(s->st, M, m, s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e, s->ee_lam, s->ee_S,
                        &nl));
   s->launches += nl;
+  s->timer.end(FM_PH_ENTROPY);
   CK(cudaMemcpyAsync(S_out, s->ee_S, sizeof(double), cudaMemcpyDeviceToHost, s->st));
   return sync_and_check(s);
 }
@@ -395,6 +391,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
   s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
   s->mixed_extra = nullptr;
+  s->mh = nullptr;
   if (p->precision == FM_FP64) {
     s->U = (z64*)(w + pl.U); s->U2 = (z64*)(w + pl.U2); s->P = (z64*)(w + pl.P); s->aux = s->U2;
   } else {
@@ -404,6 +401,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
     s->Th = (__half*)(w + pl.Th); s->Tl = (__half*)(w + pl.Tl);
     s->aux = (z64*)(w + pl.aux); s->mixed_extra = w + pl.mixed_extra;
   }
+  s->timer.st = s->st;
   s->gamma_h.assign(s->B, p->gamma);
   s->traj_h.resize(s->B);
   for (int b = 0; b < s->B; ++b) s->traj_h[b] = p->traj_id + (uint64_t)b;
@@ -447,8 +445,18 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
         break;
       }
       s->launches += 2;
+      MixedCtx& c = s->mc;
+      c.st = s->st; c.Lx = s->Lx; c.Ly = s->Ly; c.L = s->L; c.N = s->N; c.B = s->B;
+      c.protocol = p->protocol; c.reorth_interval = p->reorth_interval; c.dt = p->dt; c.seed = p->seed;
+      c.global_step = 0; c.V = s->V; c.V2 = s->V2; c.Vh = s->Vh; c.Vl = s->Vl; c.Ah = s->Ah; c.Al = s->Al;
+      c.Th = s->Th; c.Tl = s->Tl; c.G = s->G; c.R = s->R; c.T = s->T; c.Dinv = s->Dinv; c.X = s->X;
+      c.gamma = s->gamma_d; c.traj = s->traj_d; c.step = s->step_d; c.status = s->status_d;
+      c.part = s->part_d; c.nocc = s->nocc_d; c.w = s->w_d; c.xbuf = s->xbuf_d; c.vbuf = s->vbuf_d;
+      c.log = s->log_d; c.log_count = (int64_t*)s->log_count_d; c.log_capacity = p->event_capacity;
+      c.extra = s->mixed_extra; c.launches = 0; c.timer = &s->timer;
       std::string why2;
-      if (mixed_init(s->st, s->Lx, s->Ly, s->B, s->mixed_extra, &why2)) {
+      s->mh = mixed_create(&c, &why2);
+      if (!s->mh) {
         r = fail(s, FM_ECUDA, "mixed init: " + why2);
         break;
       }
@@ -456,6 +464,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
     if (cudaStreamSynchronize(s->st) != cudaSuccess) { r = fail(s, FM_ECUDA, "init sync"); break; }
   } while (0);
   if (r != FM_OK) {
+    mixed_free(s->mh);
     delete s;
     return r;
   }
@@ -470,12 +479,11 @@ fm_status fm_step(fm_state* s, int32_t nsteps) {
   for (int i = 0; i < nsteps; ++i) {
     if (s->prm.precision == FM_FP64) r = step_f64(s);
     else {
-      MixedCtx c = {s->st, s->Lx, s->Ly, s->L, s->N, s->B, s->prm.protocol, s->prm.reorth_interval,
-                    s->prm.dt, s->prm.seed, s->global_steps, s->V, s->V2, s->Vh, s->Vl, s->Ah, s->Al,
-                    s->Th, s->Tl, s->G, s->R, s->T, s->Dinv, s->X, s->gamma_d, s->traj_d, s->step_d,
-                    s->status_d, s->part_d, s->nocc_d, s->w_d, s->xbuf_d, s->vbuf_d, s->log_d,
-                    (int64_t*)s->log_count_d, s->prm.event_capacity, s->mixed_extra, 0, ""};
-      r = (fm_status)mixed_step(&c);
+      MixedCtx& c = s->mc;
+      c.global_step = s->global_steps;
+      c.V = s->V; c.V2 = s->V2;
+      c.launches = 0;
+      r = (fm_status)mixed_step(s->mh, &c);
       s->V = c.V; s->V2 = c.V2;
       s->launches += c.launches;
       if (r) r = fail(s, r, c.err);
@@ -546,11 +554,7 @@ fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA, c
   std::vector<int32_t> AB(A, A + nA);
   AB.insert(AB.end(), B, B + nB);
   r = validate_sites(s, AB.data(), (int32_t)AB.size());
-  if (r) {
-    s->sticky = 0;
-    s->err.clear();
-    return fail(s, FM_EINVAL, "A and B overlap");
-  }
+  if (r) return fail(s, FM_EINVAL, "A and B overlap");
   std::sort(AB.begin(), AB.end());
   double SA, SB, SAB;
   if ((r = entropy_impl(s, b, A, nA, &SA)) || (r = entropy_impl(s, b, B, nB, &SB)) ||
@@ -711,10 +715,29 @@ fm_status fm_load(fm_state* s, const char* path) {
   return sync_and_check(s);
 }
 
+fm_status fm_set_timing(fm_state* s, int32_t enable) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  CK(cudaStreamSynchronize(s->st));
+  s->timer.on = enable != 0;
+  return FM_OK;
+}
+
+fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!s->timer.collect(ms, counts)) return fail(s, FM_ECUDA, "event timing failed");
+  return FM_OK;
+}
+
 int64_t fm_kernel_launches(const fm_state* s) { return s ? s->launches : 0; }
 
 const char* fm_last_error(const fm_state* s) { return s ? s->err.c_str() : "null state"; }
 
-void fm_destroy(fm_state* s) { delete s; }
+void fm_destroy(fm_state* s) {
+  if (!s) return;
+  mixed_free(s->mh);
+  delete s;
+}
 
 }  // extern "C"

@@ -1,0 +1,56 @@
+// Split-fp16 tcgen05 GEMM: host interface.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace fm {
+namespace tc {
+
+constexpr int BM = 128;  // tile rows (TMEM lanes)
+constexpr int BK = 64;   // K per pipeline stage: one 128-byte swizzle row of fp16
+
+enum Mode {
+  MODE_PLAIN = 0,  // out_f[m + n ld_out] = D (fp32)
+  MODE_PROP = 1,   // propagation: out_f as PLAIN + per-row sums of D^2 into partial
+  MODE_GRAM = 2,   // Gram: D into the real (part 0) / imaginary (part 1) half of complex128 G_b
+  MODE_TRMM = 3    // U R^-1: D into V_b (fp32) and its fp16 planes
+};
+
+struct Params {
+  int mode;
+  int ntiles;
+  const int4* tiles;   // (mt, nt, b, part) per tile, device memory; NULL: grouped raster over
+  int mtiles, ntiles_n;  //   mtiles x ntiles_n tiles per batch item (batch = ntiles / (mtiles ntiles_n))
+  int chunk_kb;        // >0 (BN = 128 only): drain TMEM into fp32 registers every chunk_kb K-blocks
+  int64_t out_batch_stride;  // PLAIN: elements between batch items of out_f
+  const float* in_f;   // TRMM: if set, out = in + D (D = U (T - 1))
+  int kblocks;         // K / BK
+  int tri_k;           // limit K-blocks to (nt+1) BN / BK (triangular B)
+  int a_rows_per_b;    // A row offset per batch item
+  int b_rows_per_b;    // B row offset per batch item
+  int k_shift;         // part 1 of the Gram: B read at (k + k_shift) mod kdim, negated past the wrap
+  int kdim;            // K in elements
+  float* out_f;
+  __half* out_h;
+  __half* out_l;
+  double* out_g;
+  double* partial;
+  int64_t ld_out;
+  int L, Ntraj, C;
+  int* status;
+};
+
+bool make_kmajor_map(CUtensorMap* m, const __half* base, uint64_t K, uint64_t rows, uint64_t ld, uint32_t box_rows);
+cudaError_t launch(cudaStream_t st, int BN, const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
+                   const CUtensorMap& Bl, const Params& p, int grid);
+std::vector<int4> tile_list(int mtiles, int ntiles, int batch, int parts, bool upper_only, int BN, int GM);
+size_t smem_bytes(int BN);
+int sm_count();
+
+}  // namespace tc
+}  // namespace fm

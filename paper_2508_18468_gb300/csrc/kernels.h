@@ -53,7 +53,13 @@ struct pm_args {
 };
 cudaError_t pm_measure(cudaStream_t st, const pm_args& a);
 
-// ---- Cholesky / triangular inverse pieces (FP64)
+// ---- Cholesky / triangular inverse (FP64)
+constexpr int CHOL_NB = 32;
+// T_b = R_b^-1 with G_b = R_b^dag R_b for the n x n blocks at G, R, T (leading
+// dimension ld, batch stride sNN; upper part of G read, G overwritten).
+// Scratch per trajectory: Dinv ceil(alloc_n/32) 32 x 32 blocks, X alloc_n x 32.
+cudaError_t cholesky_inverse_f64(cudaStream_t st, z64* G, z64* R, z64* T, z64* Dinv, z64* X, int n, int ld,
+                                 int64_t sNN, int alloc_n, int B, int* status, int64_t* launches);
 // factor the nb x nb diagonal block at (k,k) of every G_b in place into R_b (upper),
 // and write its inverse into Dinv_b (nb x nb at block index k/nb).
 // nbk = min(nb, N - k) rows of the block are real, the rest padded with identity.

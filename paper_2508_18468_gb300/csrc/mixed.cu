@@ -1,18 +1,545 @@
-// Mixed-precision step: placeholder until the tensor-core GEMM lands.
+// Mixed-precision step: the propagation, Gram and U R^-1 products run on the
+// tensor cores as split-fp16 GEMMs (gemm_tc.cu); occupations, the homodyne
+// weight and the projective updates on the CUDA cores in float / double; the
+// Cholesky factor and its inverse in float64.
+//
+// State layout: trajectory b holds V_b (2L x N float, column-major): column k
+// is [Re U_{:,k}; Im U_{:,k}].  Read as an L x 2N column-major matrix, V_b is
+// U~ = [Re u_0, Im u_0, Re u_1, ...].
+//   propagation  V' = [[Re P, -Im P], [Im P, Re P]] V          (A: 2L x 2L, B: V)
+//   Gram         Re G = V^T V,  Im G_kl = sum_s V_sk V_{(s+L) mod 2L, l} (-1)^{s >= L}
+//   U R^-1       U~' = U~ T~,  T~ the real 2N x 2N embedding of T = R^-1
+#include <algorithm>
+#include <vector>
+
+#include "fm_testing.h"
+#include "gemm_tc.h"
 #include "mixed.h"
 
 namespace fm {
 
-bool mixed_supported(int, int, int, std::string* why) {
-  *why = "mixed precision path not built";
-  return false;
+namespace {
+
+int pick_bn(int N) { return (N % 256 == 0) ? 256 : 128; }
+
+struct Scratch {
+  size_t total = 0;
+  size_t tiles_prop, tiles_gram, tiles_trmm, urm_h, urm_l;
+  size_t ca_h, ca_l, cb_h, cb_l, cd, xs;   // complex tensor GEMM helper (Cholesky recursion)
+  size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
+};
+
+Scratch scratch_plan(int Lx, int Ly, int B) {
+  Scratch s;
+  const int64_t L = (int64_t)Lx * Ly, N = L / 2;
+  const int BN = pick_bn((int)N);
+  const int64_t n_prop = (2 * L / tc::BM) * (B * N / BN);
+  const int64_t n_gram = (int64_t)B * 2 * (N / tc::BM) * (N / BN);
+  const int64_t n_trmm = (int64_t)B * (L / tc::BM) * (2 * N / 128);
+  s.tiles_prop = s.take(n_prop * 16);
+  s.tiles_gram = s.take(n_gram * 16);
+  s.tiles_trmm = s.take(n_trmm * 16);
+  s.urm_h = s.take((int64_t)B * L * 2 * N * 2);
+  s.urm_l = s.take((int64_t)B * L * 2 * N * 2);
+  const int64_t md = N / 2 + 128;                  // largest block the recursion multiplies
+  s.ca_h = s.take((int64_t)B * 4 * md * md * 2);
+  s.ca_l = s.take((int64_t)B * 4 * md * md * 2);
+  s.cb_h = s.take((int64_t)B * 2 * md * md * 2);
+  s.cb_l = s.take((int64_t)B * 2 * md * md * 2);
+  s.cd = s.take((int64_t)B * 2 * md * md * 4);
+  s.xs = s.take((int64_t)B * md * md * 16);
+  return s;
 }
-size_t mixed_scratch_bytes(int, int, int) { return 0; }
-int mixed_init(cudaStream_t, int, int, int, void*, std::string*) { return 1; }
-int mixed_step(MixedCtx* c) {
-  c->err = "mixed precision path not built";
-  return FM_EINVAL;
+
+// ------------------------------------------------------------------ kernels
+FM_DEVFN void split16_d(double v, __half& h, __half& l) {
+  h = __float2half_rn((float)v);
+  l = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
 }
+
+// K-major planes of the real embedding of an upper-triangular N x N complex
+// matrix Z (rows c, K index j, 2N x 2N per trajectory):
+//   Z~[2l+s, 2n+s'] = Re Z_ln (s = s'), Im Z_ln (s=0, s'=1), -Im Z_ln (s=1, s'=0).
+// mode 0: Z = T - 1 (T = R^-1 from the Cholesky recursion);
+// mode 1: Z = -F, F = strict upper part of G plus half of (diag G - 1): the
+//         first-order inverse factor of G = 1 + E, (1 + F)^dag (1 + F) = G + O(E^2).
+__global__ void build_ttilde_kernel(const z64* __restrict__ Z, int mode, int N, int B, __half* Th, __half* Tl) {
+  const int64_t N2 = 2 * (int64_t)N;
+  const int64_t tot = (int64_t)B * N2 * N2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx % N2, row = idx / N2;
+    const int64_t b = row / N2, c = row % N2;
+    const int64_t n = c >> 1, l = j >> 1;
+    const int sp = (int)(c & 1), s = (int)(j & 1);
+    double v = 0.0;
+    if (l <= n) {
+      z64 z = Z[b * (int64_t)N * N + l + n * (int64_t)N];
+      if (mode == 0) {
+        if (l == n) z.re -= 1.0;
+      } else {
+        if (l == n) { z.re = -(z.re - 1.0) * 0.5; z.im = 0.0; }
+        else { z.re = -z.re; z.im = -z.im; }
+      }
+      v = (s == sp) ? z.re : (s == 0 ? z.im : -z.im);
+    }
+    __half h, lo;
+    split16_d(v, h, lo);
+    Th[idx] = h;
+    Tl[idx] = lo;
+  }
+}
+
+// Planes of the real embedding of op(X) (m x k complex; op: 0 = none, 2 = conjugate
+// transpose): A (2m x 2k, row-major) = [[Re, -Im], [Im, Re]].
+__global__ void embed_a_kernel(const z64* __restrict__ X, int64_t ldx, int64_t sX, int op, int m, int k,
+                               __half* Ah, __half* Al) {
+  const int64_t b = blockIdx.y;
+  const int64_t tot = 4 * (int64_t)m * k;
+  const int64_t k2 = 2 * (int64_t)k;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / k2, c = idx % k2;
+    const int64_t rr = r % m, cc = c % k;
+    const bool rb = r >= m, cb = c >= k;
+    z64 x = (op == 2) ? X[b * sX + cc + rr * ldx] : X[b * sX + rr + cc * ldx];
+    if (op == 2) x.im = -x.im;
+    const double v = (!rb && !cb) ? x.re : (!rb && cb) ? -x.im : (rb && !cb) ? x.im : x.re;
+    __half h, lo;
+    split16_d(v, h, lo);
+    Ah[b * tot + idx] = h;
+    Al[b * tot + idx] = lo;
+  }
+}
+
+// Planes of B (n x 2k, row-major): row j = [Re op(Y)[:, j], Im op(Y)[:, j]].
+__global__ void embed_b_kernel(const z64* __restrict__ Y, int64_t ldy, int64_t sY, int op, int k, int n,
+                               __half* Bh, __half* Bl) {
+  const int64_t b = blockIdx.y;
+  const int64_t tot = 2 * (int64_t)k * n;
+  const int64_t k2 = 2 * (int64_t)k;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx / k2, c = idx % k2;
+    const int64_t kk = c % k;
+    z64 y = (op == 2) ? Y[b * sY + j + kk * ldy] : Y[b * sY + kk + j * ldy];
+    if (op == 2) y.im = -y.im;
+    const double v = (c >= k) ? y.im : y.re;
+    __half h, lo;
+    split16_d(v, h, lo);
+    Bh[b * tot + idx] = h;
+    Bl[b * tot + idx] = lo;
+  }
+}
+
+// C = alpha (D_re + i D_im) + beta C, D = [D_re; D_im] (2m x n, column-major, per trajectory)
+__global__ void combine_kernel(const float* __restrict__ D, int m, int n, double alpha, double beta, z64* C,
+                               int64_t ldc, int64_t sC) {
+  const int64_t b = blockIdx.y;
+  const int64_t tot = (int64_t)m * n;
+  const float* Db = D + b * 2 * tot;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % m, j = idx / m;
+    const double re = Db[r + j * 2 * (int64_t)m], im = Db[m + r + j * 2 * (int64_t)m];
+    z64* c = C + b * sC + r + j * ldc;
+    z64 out = cmk(alpha * re, alpha * im);
+    if (beta != 0.0) { out.re += beta * c->re; out.im += beta * c->im; }
+    *c = out;
+  }
+}
+
+// Urm[(b L + i) 2N + c] = Vplane_b[(c&1) L + i + (c>>1) 2L]  (both planes)
+__global__ void transpose_planes_kernel(const __half* __restrict__ Vh, const __half* __restrict__ Vl, int L, int N,
+                                        __half* Uh, __half* Ul) {
+  __shared__ __half th[32][34];
+  __shared__ __half tl[32][34];
+  const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int64_t b = blockIdx.z;
+  const int64_t vb = b * 2 * (int64_t)L * N;
+  for (int cc = threadIdx.y; cc < 32; cc += 8) {
+    const int c = c0 + cc, i = i0 + threadIdx.x;
+    const int64_t o = vb + (int64_t)(c & 1) * L + i + (int64_t)(c >> 1) * 2 * L;
+    th[cc][threadIdx.x] = Vh[o];
+    tl[cc][threadIdx.x] = Vl[o];
+  }
+  __syncthreads();
+  for (int ii = threadIdx.y; ii < 32; ii += 8) {
+    const int i = i0 + ii, c = c0 + threadIdx.x;
+    const int64_t o = (b * L + i) * 2 * (int64_t)N + c;
+    Uh[o] = th[threadIdx.x][ii];
+    Ul[o] = tl[threadIdx.x][ii];
+  }
+}
+
+// G_b[k,k] = sum_s V_b[s,k]^2 accumulated in float64 from the float state (one
+// warp per column).  Replaces the tensor-core diagonal, whose fp32 accumulator
+// loses up to one ulp per 16-deep MMA, biased toward zero on these all-positive
+// sums.
+__global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int B, z64* G) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)B * N) return;
+  const int64_t b = w / N, k = w % N;
+  const float* col = V + b * 2 * (int64_t)L * N + k * 2 * (int64_t)L;
+  double acc = 0.0;
+  for (int s = lane; s < 2 * L; s += 32) {
+    const double x = col[s];
+    acc += x * x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) G[b * (int64_t)N * N + k + k * (int64_t)N] = cmk(acc, 0.0);
+}
+
+}  // namespace
+
+struct MixedHost {
+  int BN;
+  int n_prop, n_gram, n_trmm;
+  int4 *tiles_prop, *tiles_gram, *tiles_trmm;
+  __half *urm_h, *urm_l;
+  __half *ca_h, *ca_l, *cb_h, *cb_l;
+  float* cd;
+  z64* xs;
+  int64_t md;        // largest block dimension of the Cholesky recursion products
+  CUtensorMap prop_Ah, prop_Al, prop_Bh, prop_Bl;
+  CUtensorMap gram_Ah, gram_Al, gram_Bh, gram_Bl;
+  CUtensorMap trmm_Ah, trmm_Al, trmm_Bh, trmm_Bl;
+};
+
+bool mixed_supported(int Lx, int Ly, int batch, std::string* why) {
+  const int64_t L = (int64_t)Lx * Ly;
+  if (L % 256 != 0) {
+    *why = "mixed precision needs L = Lx*Ly divisible by 256 (N a multiple of 128)";
+    return false;
+  }
+  if ((int64_t)batch * L > (1ll << 31) / 4) {
+    *why = "batch * L too large for the tensor maps";
+    return false;
+  }
+  return true;
+}
+
+size_t mixed_scratch_bytes(int Lx, int Ly, int batch) { return scratch_plan(Lx, Ly, batch).total; }
+
+void mixed_free(MixedHost* h) { delete h; }
+
+MixedHost* mixed_create(MixedCtx* c, std::string* why) {
+  MixedHost* h = new MixedHost();
+  const int L = c->L, N = c->N, B = c->B;
+  h->BN = pick_bn(N);
+  const int BN = h->BN;
+  Scratch sp = scratch_plan(c->Lx, c->Ly, B);
+  char* base = (char*)c->extra;
+  h->tiles_prop = (int4*)(base + sp.tiles_prop);
+  h->tiles_gram = (int4*)(base + sp.tiles_gram);
+  h->tiles_trmm = (int4*)(base + sp.tiles_trmm);
+  h->urm_h = (__half*)(base + sp.urm_h);
+  h->urm_l = (__half*)(base + sp.urm_l);
+  h->ca_h = (__half*)(base + sp.ca_h);
+  h->ca_l = (__half*)(base + sp.ca_l);
+  h->cb_h = (__half*)(base + sp.cb_h);
+  h->cb_l = (__half*)(base + sp.cb_l);
+  h->cd = (float*)(base + sp.cd);
+  h->xs = (z64*)(base + sp.xs);
+  h->md = N / 2 + 128;
+  std::vector<int4> tp = tc::tile_list(2 * L / tc::BM, B * N / BN, 1, 1, false, BN, 16);
+  std::vector<int4> tg = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, 16);
+  std::vector<int4> tt = tc::tile_list(L / tc::BM, 2 * N / 128, B, 1, false, 128, 16);
+  h->n_prop = (int)tp.size();
+  h->n_gram = (int)tg.size();
+  h->n_trmm = (int)tt.size();
+  bool ok = cudaMemcpyAsync(h->tiles_prop, tp.data(), tp.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
+            cudaMemcpyAsync(h->tiles_gram, tg.data(), tg.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
+            cudaMemcpyAsync(h->tiles_trmm, tt.data(), tt.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
+            cudaStreamSynchronize(c->st) == cudaSuccess;
+  if (!ok) { *why = "tile upload"; delete h; return nullptr; }
+  const uint64_t L2 = 2 * (uint64_t)L, N2 = 2 * (uint64_t)N;
+  ok = tc::make_kmajor_map(&h->prop_Ah, c->Ah, L2, L2, L2, tc::BM) &&
+       tc::make_kmajor_map(&h->prop_Al, c->Al, L2, L2, L2, tc::BM) &&
+       tc::make_kmajor_map(&h->prop_Bh, c->Vh, L2, (uint64_t)B * N, L2, BN) &&
+       tc::make_kmajor_map(&h->prop_Bl, c->Vl, L2, (uint64_t)B * N, L2, BN) &&
+       tc::make_kmajor_map(&h->gram_Ah, c->Vh, L2, (uint64_t)B * N, L2, tc::BM) &&
+       tc::make_kmajor_map(&h->gram_Al, c->Vl, L2, (uint64_t)B * N, L2, tc::BM) &&
+       tc::make_kmajor_map(&h->gram_Bh, c->Vh, L2, (uint64_t)B * N, L2, BN) &&
+       tc::make_kmajor_map(&h->gram_Bl, c->Vl, L2, (uint64_t)B * N, L2, BN) &&
+       tc::make_kmajor_map(&h->trmm_Ah, h->urm_h, N2, (uint64_t)B * L, N2, tc::BM) &&
+       tc::make_kmajor_map(&h->trmm_Al, h->urm_l, N2, (uint64_t)B * L, N2, tc::BM) &&
+       tc::make_kmajor_map(&h->trmm_Bh, c->Th, N2, (uint64_t)B * N2, N2, 128) &&
+       tc::make_kmajor_map(&h->trmm_Bl, c->Tl, N2, (uint64_t)B * N2, N2, 128);
+  if (!ok) { *why = "cuTensorMapEncodeTiled failed"; delete h; return nullptr; }
+  return h;
+}
+
+namespace {
+
+#define MCK(call)                                                   \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) {                                        \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);  \
+      return FM_ECUDA;                                              \
+    }                                                               \
+    c->launches += 1;                                               \
+  } while (0)
+
+tc::Params base_params(MixedCtx* c, MixedHost* h) {
+  tc::Params p;
+  memset(&p, 0, sizeof(p));
+  p.L = c->L;
+  p.Ntraj = c->N;
+  p.C = c->N / h->BN;
+  p.status = c->status;
+  return p;
+}
+
+// op(X) op(Y) on the tensor cores for complex128 blocks (all trajectories):
+// C = alpha op(X) op(Y) + beta C, op(X) m x k, op(Y) k x n; m, n multiples of 128,
+// k of 32.  The product runs as the real GEMM [[Re, -Im], [Im, Re]] (op X) x [Re; Im] (op Y).
+int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const z64* X, int64_t ldx, int64_t sX, int opY, const z64* Y,
+             int64_t ldy, int64_t sY, int m, int n, int k, double alpha, double beta, z64* C, int64_t ldc,
+             int64_t sC) {
+  const int B = c->B;
+  const unsigned gx = (unsigned)std::min<int64_t>(FM_CEIL_DIV(4 * (int64_t)m * k, 256), 2048);
+  embed_a_kernel<<<dim3(gx, B), 256, 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+  MCK(cudaGetLastError());
+  const unsigned gy = (unsigned)std::min<int64_t>(FM_CEIL_DIV(2 * (int64_t)k * n, 256), 2048);
+  embed_b_kernel<<<dim3(gy, B), 256, 0, c->st>>>(Y, ldy, sY, opY, k, n, h->cb_h, h->cb_l);
+  MCK(cudaGetLastError());
+  CUtensorMap ah, al, bh, bl;
+  const uint64_t K2 = 2 * (uint64_t)k;
+  if (!tc::make_kmajor_map(&ah, h->ca_h, K2, (uint64_t)B * 2 * m, K2, tc::BM) ||
+      !tc::make_kmajor_map(&al, h->ca_l, K2, (uint64_t)B * 2 * m, K2, tc::BM) ||
+      !tc::make_kmajor_map(&bh, h->cb_h, K2, (uint64_t)B * n, K2, 128) ||
+      !tc::make_kmajor_map(&bl, h->cb_l, K2, (uint64_t)B * n, K2, 128)) {
+    c->err = "cgemm tensor maps";
+    return FM_ECUDA;
+  }
+  tc::Params p = base_params(c, h);
+  p.mode = tc::MODE_PLAIN;
+  p.tiles = nullptr;
+  p.mtiles = 2 * m / tc::BM;
+  p.ntiles_n = n / 128;
+  p.ntiles = B * p.mtiles * p.ntiles_n;
+  p.kblocks = 2 * k / tc::BK;
+  p.a_rows_per_b = 2 * m;
+  p.b_rows_per_b = n;
+  p.out_f = h->cd;
+  p.ld_out = 2 * (int64_t)m;
+  p.out_batch_stride = 2 * (int64_t)m * n;
+  MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, tc::sm_count()));
+  const unsigned gc = (unsigned)std::min<int64_t>(FM_CEIL_DIV((int64_t)m * n, 256), 2048);
+  combine_kernel<<<dim3(gc, B), 256, 0, c->st>>>(h->cd, m, n, alpha, beta, C, ldc, sC);
+  MCK(cudaGetLastError());
+  return FM_OK;
+}
+
+// R and T = R^-1 of the n x n diagonal block at `off` of G (= R^dag R), recursively:
+//   R11, T11 <- block(off, h);  R12 = T11^dag G12;  G22 -= R12^dag R12;
+//   R22, T22 <- block(off + h, n - h);  T12 = -T11 (R12 T22).
+// Blocks of <= 128 are factored in float64; the products run on the tensor cores.
+int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
+  const int N = c->N;
+  const int64_t sNN = (int64_t)N * N;
+  z64* G = c->G;
+  z64* R = c->R;
+  z64* T = c->T;
+  const int64_t d0 = off + (int64_t)off * N;
+  if (n <= 128) {
+    int64_t nl = 0;
+    cudaError_t e = cholesky_inverse_f64(c->st, G + d0, R + d0, T + d0, c->Dinv, c->X, n, N, sNN, N, c->B,
+                                         c->status, &nl);
+    c->launches += nl;
+    if (e != cudaSuccess) { c->err = std::string("cholesky leaf: ") + cudaGetErrorString(e); return FM_ECUDA; }
+    return FM_OK;
+  }
+  const int hh = std::max(128, (n / 2 / 128) * 128);
+  const int m2 = n - hh;
+  const int64_t o12 = off + (int64_t)(off + hh) * N, d1 = (off + hh) + (int64_t)(off + hh) * N;
+  int r;
+  const int64_t sXS = (int64_t)h->md * h->md;  // batch stride of the xs scratch
+  if ((r = chol_inv_rec(h, c, off, hh))) return r;
+  if ((r = cgemm_tc(h, c, 2, T + d0, N, sNN, 0, G + o12, N, sNN, hh, m2, hh, 1.0, 0.0, R + o12, N, sNN))) return r;
+  if ((r = cgemm_tc(h, c, 2, R + o12, N, sNN, 0, R + o12, N, sNN, m2, m2, hh, -1.0, 1.0, G + d1, N, sNN))) return r;
+  if ((r = chol_inv_rec(h, c, off + hh, m2))) return r;
+  if ((r = cgemm_tc(h, c, 0, R + o12, N, sNN, 0, T + d1, N, sNN, hh, m2, m2, 1.0, 0.0, h->xs, hh, sXS))) return r;
+  if ((r = cgemm_tc(h, c, 0, T + d0, N, sNN, 0, h->xs, hh, sXS, hh, m2, hh, -1.0, 0.0, T + o12, N, sNN))) return r;
+  return FM_OK;
+}
+
+// One CholeskyQR pass on V: Gram (tensor) -> inverse factor -> U <- U + U (T - 1) (tensor).
+// first == true: T = R^-1 from the recursive factorisation (G far from 1), and
+//   the product accumulates in fp32 registers every 2 K-blocks;
+// first == false: G = 1 + E with |E| small after a full pass, T = 1 - F to first
+//   order (O(|E|^2) error), F built in float64 straight from G.
+int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
+  const int L = c->L, N = c->N, B = c->B, BN = h->BN;
+  const int grid = tc::sm_count();
+  tc::Params p = base_params(c, h);
+  p.mode = tc::MODE_GRAM;
+  p.ntiles = h->n_gram;
+  p.tiles = h->tiles_gram;
+  p.kblocks = 2 * L / tc::BK;
+  p.a_rows_per_b = N;
+  p.b_rows_per_b = N;
+  p.k_shift = L;
+  p.kdim = 2 * L;
+  p.out_g = (double*)c->G;
+  c->timer->begin(FM_PH_GRAM);
+  MCK(tc::launch(c->st, BN, h->gram_Ah, h->gram_Al, h->gram_Bh, h->gram_Bl, p, grid));
+  gram_diag_kernel<<<FM_CEIL_DIV((int64_t)B * N * 32, 256), 256, 0, c->st>>>(c->V, L, N, B, c->G);
+  MCK(cudaGetLastError());
+  c->timer->end(FM_PH_GRAM);
+  c->timer->begin(FM_PH_CHOLESKY);
+  if (first) {
+    int r = chol_inv_rec(h, c, 0, N);
+    if (r) return r;
+  }
+  build_ttilde_kernel<<<152 * 8, 256, 0, c->st>>>(first ? c->T : c->G, first ? 0 : 1, N, B, c->Th, c->Tl);
+  MCK(cudaGetLastError());
+  transpose_planes_kernel<<<dim3(L / 32, 2 * N / 32, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
+                                                                                  h->urm_l);
+  MCK(cudaGetLastError());
+  c->timer->end(FM_PH_CHOLESKY);
+  p = base_params(c, h);
+  p.mode = tc::MODE_TRMM;
+  p.ntiles = h->n_trmm;
+  p.tiles = h->tiles_trmm;
+  p.kblocks = 2 * N / tc::BK;
+  p.tri_k = 1;
+  p.a_rows_per_b = L;
+  p.b_rows_per_b = 2 * N;
+  p.out_f = c->V2;
+  p.out_h = c->Vh;
+  p.out_l = c->Vl;
+  p.in_f = c->V;
+  p.chunk_kb = first ? 2 : 0;
+  c->timer->begin(FM_PH_TRMM);
+  MCK(tc::launch(c->st, 128, h->trmm_Ah, h->trmm_Al, h->trmm_Bh, h->trmm_Bl, p, grid));
+  c->timer->end(FM_PH_TRMM);
+  std::swap(c->V, c->V2);
+  return FM_OK;
+}
+
+}  // namespace
+
+int mixed_step(MixedHost* h, MixedCtx* c) {
+  const int L = c->L, N = c->N, B = c->B, BN = h->BN;
+  const int grid = tc::sm_count();
+  // 1. propagation V2 = A V with row sums of squares
+  tc::Params p = base_params(c, h);
+  p.mode = tc::MODE_PROP;
+  p.ntiles = h->n_prop;
+  p.tiles = h->tiles_prop;
+  p.kblocks = 2 * L / tc::BK;
+  p.out_f = c->V2;
+  p.ld_out = 2 * (int64_t)L;
+  p.partial = c->part;
+  c->timer->begin(FM_PH_PROPAGATE);
+  MCK(tc::launch(c->st, BN, h->prop_Ah, h->prop_Al, h->prop_Bh, h->prop_Bl, p, grid));
+  c->timer->end(FM_PH_PROPAGATE);
+  std::swap(c->V, c->V2);
+  const int k = c->reorth_interval;
+  const int nchunks = 2 * (N / BN);
+  if (c->protocol == FM_HOMODYNE) {
+    c->timer->begin(FM_PH_MEASURE);
+    MCK(reduce_occupations(c->st, c->part, nchunks, L, B, c->nocc, c->w, c->gamma, c->dt, c->traj, c->step, c->seed));
+    MCK(scale_rows_v(c->st, c->V, c->Vh, c->Vl, L, N, B, c->w));
+    c->timer->end(FM_PH_MEASURE);
+    int r = qr_pass(h, c, true);
+    if (r) return r;
+    if ((c->global_step + 1) % k == 0) {
+      r = qr_pass(h, c, false);
+      if (r) return r;
+    }
+  } else {
+    pm_args a;
+    a.U = c->V; a.L = L; a.N = N; a.batch = B; a.layout = 1;
+    a.gamma = c->gamma; a.dt = c->dt; a.traj = c->traj; a.step = c->step; a.seed = c->seed;
+    a.xbuf = c->xbuf; a.vbuf = c->vbuf;
+    a.log = c->log; a.log_count = c->log_count; a.log_capacity = c->log_capacity;
+    a.dev_status = c->status;
+    c->timer->begin(FM_PH_MEASURE);
+    MCK(pm_measure(c->st, a));
+    MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
+    c->timer->end(FM_PH_MEASURE);
+    if ((c->global_step + 1) % k == 0) {
+      int r = qr_pass(h, c, true);
+      if (r) return r;
+      r = qr_pass(h, c, false);
+      if (r) return r;
+    }
+  }
+  MCK(bump_steps(c->st, c->step, B));
+  return FM_OK;
+}
+
 bool mixed_entropy_gram(cudaStream_t, const z64*, int, int, z64*) { return false; }
 
 }  // namespace fm
+
+// ====================================================================== test hooks
+using namespace fm;
+
+extern "C" int fmx_tc_gemm(const void* Ah, const void* Al, const void* Bh, const void* Bl, int M, int N, int K,
+                           float* D, int BN, int grid, int chunk_kb, int raster, void* d_tiles, void* stream) {
+  if (M % tc::BM || (BN != 128 && BN != 256) || N % BN || K % tc::BK) return (int)cudaErrorInvalidValue;
+  if (chunk_kb > 0 && BN != 128) return (int)cudaErrorInvalidValue;
+  CUtensorMap a_h, a_l, b_h, b_l;
+  if (!tc::make_kmajor_map(&a_h, (const __half*)Ah, K, M, K, tc::BM) ||
+      !tc::make_kmajor_map(&a_l, (const __half*)Al, K, M, K, tc::BM) ||
+      !tc::make_kmajor_map(&b_h, (const __half*)Bh, K, N, K, BN) ||
+      !tc::make_kmajor_map(&b_l, (const __half*)Bl, K, N, K, BN))
+    return (int)cudaErrorInvalidValue;
+  cudaStream_t st = (cudaStream_t)stream;
+  tc::Params p;
+  memset(&p, 0, sizeof(p));
+  p.mode = tc::MODE_PLAIN;
+  p.mtiles = M / tc::BM;
+  p.ntiles_n = N / BN;
+  p.ntiles = p.mtiles * p.ntiles_n;
+  if (raster) {
+    p.tiles = nullptr;
+  } else {
+    std::vector<int4> t = tc::tile_list(M / tc::BM, N / BN, 1, 1, false, BN, 16);
+    cudaError_t e = cudaMemcpyAsync(d_tiles, t.data(), t.size() * 16, cudaMemcpyHostToDevice, st);
+    if (e) return (int)e;
+    p.tiles = (const int4*)d_tiles;
+  }
+  p.kblocks = K / tc::BK;
+  p.chunk_kb = chunk_kb > 0 ? chunk_kb : 0;
+  p.out_f = D;
+  p.ld_out = M;
+  return (int)tc::launch(st, BN, a_h, a_l, b_h, b_l, p, grid);
+}
+
+extern "C" int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, double* G, int BN, void* d_tiles,
+                           void* stream) {
+  if (N % tc::BM || (BN != 128 && BN != 256) || N % BN || (2 * L) % tc::BK) return (int)cudaErrorInvalidValue;
+  CUtensorMap a_h, a_l, b_h, b_l;
+  const uint64_t L2 = 2 * (uint64_t)L;
+  if (!tc::make_kmajor_map(&a_h, (const __half*)Vh, L2, (uint64_t)B * N, L2, tc::BM) ||
+      !tc::make_kmajor_map(&a_l, (const __half*)Vl, L2, (uint64_t)B * N, L2, tc::BM) ||
+      !tc::make_kmajor_map(&b_h, (const __half*)Vh, L2, (uint64_t)B * N, L2, BN) ||
+      !tc::make_kmajor_map(&b_l, (const __half*)Vl, L2, (uint64_t)B * N, L2, BN))
+    return (int)cudaErrorInvalidValue;
+  std::vector<int4> t = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, 16);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(d_tiles, t.data(), t.size() * 16, cudaMemcpyHostToDevice, st);
+  if (e) return (int)e;
+  tc::Params p;
+  memset(&p, 0, sizeof(p));
+  p.mode = tc::MODE_GRAM;
+  p.ntiles = (int)t.size();
+  p.tiles = (const int4*)d_tiles;
+  p.kblocks = 2 * L / tc::BK;
+  p.a_rows_per_b = N;
+  p.b_rows_per_b = N;
+  p.k_shift = L;
+  p.kdim = 2 * L;
+  p.out_g = G;
+  p.L = L;
+  p.Ntraj = N;
+  return (int)tc::launch(st, BN, a_h, a_l, b_h, b_l, p, tc::sm_count());
+}

@@ -4,9 +4,12 @@
 #include <string>
 
 #include "kernels.h"
+#include "timer.h"
 
 namespace fm {
 
+// Device pointers and step parameters of one state (filled at init; V / V2
+// swap as the step double-buffers the float state).
 struct MixedCtx {
   cudaStream_t st;
   int Lx, Ly, L, N, B;
@@ -15,27 +18,28 @@ struct MixedCtx {
   uint64_t seed;
   int64_t global_step;
   float *V, *V2;           // state (2L x N float per trajectory) and its double buffer
-  __half *Vh, *Vl;         // split-fp16 planes of V
+  __half *Vh, *Vl;         // split-fp16 planes of V (x = h + l 2^-11)
   __half *Ah, *Al;         // planes of the real 2L x 2L propagator embedding (row-major)
-  __half *Th, *Tl;         // planes of the real 2N x 2N embedding of R^-1 (per trajectory)
+  __half *Th, *Tl;         // planes of the real 2N x 2N embedding of R^-1, K-major (per trajectory)
   z64 *G, *R, *T, *Dinv, *X;
   double* gamma; uint64_t* traj; int64_t* step; int* status;
   double *part, *nocc, *w;
   void *xbuf, *vbuf;
   fm_event* log; int64_t* log_count; int log_capacity;
-  void* extra;             // mixed_scratch_bytes() of scratch
+  void* extra;             // mixed_scratch_bytes() of device scratch
+  PhaseTimer* timer;       // phase events (may be off)
   int64_t launches;        // out: kernels launched
   std::string err;         // out: message on failure
 };
 
-// Whether the mixed path handles this geometry; *why says why not.
+struct MixedHost;          // tensor maps and tile lists of one state
+
 bool mixed_supported(int Lx, int Ly, int batch, std::string* why);
 size_t mixed_scratch_bytes(int Lx, int Ly, int batch);
-// One-time set-up (tensor maps, kernel attributes). 0 on success.
-int mixed_init(cudaStream_t st, int Lx, int Ly, int batch, void* extra, std::string* why);
-// One step; returns an fm_status value.
-int mixed_step(MixedCtx* c);
-// M = C_A Gram of the gathered rows (n x N complex128) on the tensor cores; false = not handled.
+MixedHost* mixed_create(MixedCtx* c, std::string* why);   // uploads tile lists, encodes tensor maps
+void mixed_free(MixedHost* h);
+int mixed_step(MixedHost* h, MixedCtx* c);               // returns an fm_status value
+// M = Gram of the gathered rows (n x N complex128) on the tensor cores; false = not handled here.
 bool mixed_entropy_gram(cudaStream_t st, const z64* rows, int n, int N, z64* M);
 
 }  // namespace fm

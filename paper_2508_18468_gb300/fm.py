@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libfm.so")
 FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENUMERIC, FM_ETIMEOUT, FM_ESTATE = range(7)
 FM_PROJECTIVE, FM_HOMODYNE = 0, 1
 FM_FP64, FM_MIXED = 0, 1
+PHASES = ("propagate", "measure", "gram", "cholesky", "trmm", "entropy")
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENUMERIC",
                 5: "FM_ETIMEOUT", 6: "FM_ESTATE"}
 
@@ -64,6 +65,8 @@ def _load():
         "fm_save": (i32, [vp, ctypes.c_char_p]),
         "fm_load": (i32, [vp, ctypes.c_char_p]),
         "fm_kernel_launches": (i64, [vp]),
+        "fm_set_timing": (i32, [vp, i32]),
+        "fm_phase_times": (i32, [vp, P(dbl), P(i64)]),
         "fm_last_error": (ctypes.c_char_p, [vp]),
         "fm_destroy": (None, [vp]),
         "fm_version": (ctypes.c_char_p, []),
@@ -182,8 +185,9 @@ class Trajectories:
         assert U.shape == (self.L, self.N)
         self._check(lib.fm_set_U(self._h, int(b), ctypes.c_void_p(U.ctypes.data), self.L))
 
-    def occupations(self, b=0):
-        n = np.empty(self.L, dtype=np.float64)
+    def occupations(self, b=0, out=None):
+        n = np.empty(self.L, dtype=np.float64) if out is None else out
+        assert n.dtype == np.float64 and n.size == self.L and n.flags.c_contiguous
         self._check(lib.fm_occupations(self._h, int(b), n.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return n
 
@@ -207,6 +211,16 @@ class Trajectories:
 
     def load(self, path):
         self._check(lib.fm_load(self._h, str(path).encode()))
+
+    def set_timing(self, enable=True):
+        self._check(lib.fm_set_timing(self._h, 1 if enable else 0))
+
+    def phase_times(self):
+        """{phase: (milliseconds, launches)} accumulated since the last call."""
+        ms = (ctypes.c_double * len(PHASES))()
+        cnt = (ctypes.c_int64 * len(PHASES))()
+        self._check(lib.fm_phase_times(self._h, ms, cnt))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(PHASES)}
 
     @property
     def kernel_launches(self):

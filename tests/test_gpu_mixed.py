@@ -1,0 +1,132 @@
+"""Mixed-precision (split-fp16 tensor-core) path vs the FP64 oracle (needs a GB300).
+
+Tolerances come from the arithmetic: the float32 state (2^-24), split-fp16
+products (2^-22) and fp32 tensor-core accumulation (about 2^-24 per 16-deep
+update on the banded propagation sums) give a per-step error in C = U U^dag
+of at most ~2e-6, so after n steps max|dC| <= 2e-6 n.  The entropy bar is the
+method's: relative error <= 1e-3; orthonormality <= 1e-6 after a full
+CholeskyQR2 step.
+"""
+import numpy as np
+import pytest
+
+from oracle import observables, trajectory
+from oracle.trajectory import HOMODYNE, PROJECTIVE, Params
+
+pytestmark = pytest.mark.gpu
+
+PER_STEP_C = 2e-6
+S_REL = 1e-3
+ORTHO = 1e-6
+
+
+@pytest.fixture(scope="module")
+def fm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_18468_gb300 import build
+    build.build()
+    from paper_2508_18468_gb300 import fm as mod
+    return mod
+
+
+def mixed(fm, Lx, Ly=1, **kw):
+    return fm.Trajectories(fm.make_params(Lx, Ly, precision=fm.FM_MIXED, **kw))
+
+
+def cdiff(Ua, Ub):
+    return float(np.max(np.abs(observables.correlation(Ua) - observables.correlation(Ub))))
+
+
+def srel(a, b):
+    return abs(a - b) / max(abs(b), 1.0)
+
+
+@pytest.mark.parametrize("gamma,reorth", [(1.0, 1), (0.3, 1), (1.0, 4)])
+def test_homodyne_ring256(fm, gamma, reorth):
+    n = 48
+    g = mixed(fm, 256, protocol=fm.FM_HOMODYNE, gamma=gamma, seed=31, reorth_interval=reorth)
+    g.step(n)
+    ref = trajectory.run(Params(Lx=256, gamma=gamma, protocol=HOMODYNE, seed=31), n)["U"]
+    U = g.copy_U()
+    dc = cdiff(U, ref)
+    half = list(range(128))
+    S, S_ref = g.entropy(half), observables.entanglement_entropy(ref, half)
+    ortho = g.orthonormality_error(list(range(0, 128, 4)))
+    print("homodyne L=256 gamma=%g reorth=%d: max|dC|=%.2e  S=%.6f S_ref=%.6f rel=%.2e  ortho=%.2e"
+          % (gamma, reorth, dc, S, S_ref, srel(S, S_ref), ortho))
+    assert dc <= PER_STEP_C * n
+    assert srel(S, S_ref) <= S_REL
+    assert ortho <= ORTHO
+
+
+def test_projective_ring256(fm):
+    n = 40
+    g = mixed(fm, 256, protocol=fm.FM_PROJECTIVE, gamma=1.0, seed=44, event_capacity=100000)
+    g.step(n)
+    ref = trajectory.run(Params(Lx=256, gamma=1.0, protocol=PROJECTIVE, seed=44), n)
+    ev, _ = g.take_events()
+    got = sorted((e[1], e[2], e[5]) for e in ev)
+    exp = sorted((s, j, o) for (s, j, u, p, o) in ref["events"])
+    margins = [abs(u - p) for (s, j, u, p, o) in ref["events"]]
+    # outcomes agree unless a draw sits within the mixed precision of its Born weight
+    if got != exp:
+        assert min(margins) < 1e-4, "outcome mismatch away from a near tie"
+        pytest.skip("near tie between draw and Born weight; replay not exercised here")
+    dc = cdiff(g.copy_U(), ref["U"])
+    half = list(range(128))
+    S, S_ref = g.entropy(half), observables.entanglement_entropy(ref["U"], half)
+    print("projective L=256: events=%d max|dC|=%.2e S rel=%.2e" % (len(ev), dc, srel(S, S_ref)))
+    assert dc <= PER_STEP_C * n
+    assert srel(S, S_ref) <= S_REL
+
+
+def test_homodyne_torus_16x16(fm):
+    n = 30
+    g = mixed(fm, 16, 16, protocol=fm.FM_HOMODYNE, gamma=1.5, seed=7)
+    g.step(n)
+    ref = trajectory.run(Params(Lx=16, Ly=16, gamma=1.5, protocol=HOMODYNE, seed=7), n)["U"]
+    assert cdiff(g.copy_U(), ref) <= PER_STEP_C * n
+    A = [x + 16 * y for y in range(4) for x in range(4)]
+    B = [x + 16 * y for y in range(4) for x in range(8, 12)]
+    I, I_ref = g.mutual_info(A, B), observables.mutual_information(ref, A, B)
+    print("torus 16x16: I=%.6f I_ref=%.6f" % (I, I_ref))
+    assert abs(I - I_ref) <= S_REL * max(1.0, abs(I_ref))
+
+
+def test_batch_of_three_with_rates(fm):
+    n = 20
+    gam = [0.3, 1.0, 2.0]
+    g = mixed(fm, 512, batch=3, protocol=fm.FM_HOMODYNE, seed=5, traj_id=10)
+    g.set_gammas(gam)
+    g.step(n)
+    for b in range(3):
+        ref = trajectory.run(Params(Lx=512, gamma=gam[b], protocol=HOMODYNE, seed=5, traj_id=10 + b), n)["U"]
+        assert cdiff(g.copy_U(b), ref) <= PER_STEP_C * n
+
+
+def test_unmonitored_ring1024_closed_form(fm):
+    n = 40
+    g = mixed(fm, 1024, protocol=fm.FM_PROJECTIVE, gamma=0.0, reorth_interval=1)
+    g.step(n)
+    occ = g.occupations()
+    k = 2 * np.pi * np.arange(1024) / 1024
+    ref = 0.5 + 0.5 * (-1.0) ** np.arange(1024) * np.mean(np.cos(4.0 * n * 0.05 * np.cos(k)))
+    err = float(np.max(np.abs(occ - ref)))
+    print("unmonitored L=1024 mixed: max|dn|=%.2e" % err)
+    assert err <= PER_STEP_C * n
+
+
+def test_mixed_against_fp64_gpu_ring2048(fm):
+    n = 12
+    kw = dict(protocol=fm.FM_HOMODYNE, gamma=0.5, seed=9)
+    gm = mixed(fm, 2048, **kw)
+    gd = fm.Trajectories(fm.make_params(2048, precision=fm.FM_FP64, **kw))
+    gm.step(n)
+    gd.step(n)
+    half = list(range(1024))
+    Sm, Sd = gm.entropy(half), gd.entropy(half)
+    print("L=2048 mixed vs fp64 GPU: S=%.8f vs %.8f rel=%.2e" % (Sm, Sd, srel(Sm, Sd)))
+    assert srel(Sm, Sd) <= S_REL
+    assert gm.orthonormality_error(list(range(0, 1024, 16))) <= ORTHO
