@@ -1,6 +1,6 @@
 """Summarise an ncu launch list (``--metrics gpu__time_duration.sum --csv``) per kernel.
 
-Usage: python profiles/summarize_launches.py <launches.csv>
+Usage: python -m paper_2508_18468_gb300.profiling <launches.csv>
 Prints launches, total time and share of every kernel, largest first.
 """
 import collections
