@@ -168,6 +168,32 @@ enum { FM_PH_PROPAGATE = 0, FM_PH_MEASURE = 1, FM_PH_GRAM = 2, FM_PH_CHOLESKY = 
 fm_status fm_set_timing(fm_state* s, int32_t enable);
 fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts);
 
+/* Limits of fm_entropy_noalloc. */
+#define FM_NOALLOC_MAX_SITES 1024
+#define FM_NOALLOC_MAX_N 512
+
+/* S_A (nats) of a Slater determinant held by the caller, computed without
+ * allocating any device memory.  The paper has no counterpart of this call: it
+ * serves callers that cannot call cudaMalloc, such as an application whose own
+ * memory pool already holds nearly all of the device memory, or a loop that
+ * must not pay the device-wide synchronisation that freeing memory implies.
+ *   d_U    device complex128 U, L x N column-major (ld = L), read only;
+ *   sites  host array of n distinct site indices in [0, L);
+ *   d_S    device double receiving S_A;
+ *   cuda_stream  cudaStream_t or NULL; the call is asynchronous on it.
+ * Limits: n <= FM_NOALLOC_MAX_SITES, N <= FM_NOALLOC_MAX_N, L <= 65536;
+ * larger sizes return FM_EINVAL without touching the GPU.  The scratch is one
+ * fixed array of about 13 MB in the library's static device memory that every
+ * GPU loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Each call writes every scratch word it
+ * reads, so nothing carries over from the previous call.  The same FP64
+ * Householder + bisection method as fm_entropy. */
+fm_status fm_entropy_noalloc(const void* d_U, int32_t L, int32_t N, const int32_t* sites, int32_t n,
+                             double* d_S, void* cuda_stream);
+
 /* Launches of library kernels issued on this state since init. */
 int64_t fm_kernel_launches(const fm_state* s);
 

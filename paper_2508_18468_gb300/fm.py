@@ -70,6 +70,7 @@ def _load():
         "fm_last_error": (ctypes.c_char_p, [vp]),
         "fm_destroy": (None, [vp]),
         "fm_version": (ctypes.c_char_p, []),
+        "fm_entropy_noalloc": (i32, [vp, i32, i32, P(i32), i32, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -99,6 +100,17 @@ def fm_workspace_bytes(params):
 
 def fm_version():
     return lib.fm_version().decode()
+
+
+def fm_entropy_noalloc(d_U, L, N, sites, d_S, stream=None):
+    """S_A of a device complex128 U (L x N, column-major) into the device double d_S; no allocation.
+
+    d_U and d_S are device pointers (ints); stream a cudaStream_t handle or None.
+    Returns the status code.
+    """
+    a, p = _i32_array(sites)
+    return int(lib.fm_entropy_noalloc(ctypes.c_void_p(d_U), int(L), int(N), p, int(a.size), ctypes.c_void_p(d_S),
+                                      ctypes.c_void_p(stream)))
 
 
 class Trajectories:
