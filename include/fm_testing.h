@@ -27,10 +27,10 @@ extern "C" {
 int fmx_tc_gemm(const void* Ah, const void* Al, const void* Bh, const void* Bl, int M, int N, int K,
                 float* D, int BN, int grid, int chunk_kb, int raster, void* d_tiles, void* stream);
 
-/* Complex Gram G_b = U_b^dag U_b (complex128, N x N column-major, upper 128 x BN
+/* Complex Gram G_b = U_b^dag U_b (complex64, N x N column-major, upper 128 x BN
  * tiles written) of B trajectories whose orbitals are stored as V_b (2L x N,
  * column-major planes, column k = [Re U_{:,k}; Im U_{:,k}]). */
-int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, double* G, int BN, void* d_tiles,
+int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, float* G, int BN, void* d_tiles,
                 void* stream);
 
 #ifdef __cplusplus

@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(1024) tridiag_small_kernel(z64* M, int m, z64*
 }
 
 // ------------------------------------------------------------------ large m: per-column kernels
+// Only the lower triangle (i >= j) of the trailing block is read and updated.
 __global__ void __launch_bounds__(1024) hh_reflector_kernel(z64* M, int m, int k, z64* vb, double* d, double* e,
                                                             z64* tau_out) {
   __shared__ double red[33];
@@ -129,55 +130,122 @@ __global__ void __launch_bounds__(1024) hh_reflector_kernel(z64* M, int m, int k
   }
 }
 
-// partial[c][i] = sum_{j in chunk c} M22[i, j] v_j ; grid (ceil(n/32), nchunks), block (32, 8)
-__global__ void hh_matvec_kernel(const z64* __restrict__ M, int m, int k, const z64* __restrict__ vb,
-                                 z64* partial, int nchunks) {
+constexpr int HT = 64;  // tile of the Hermitian matrix-vector product
+
+// p = M22 v from the lower triangle: tile (I, J), J <= I, adds sum_j M_ij v_j to
+// prow[J][i] and sum_{i > j} conj(M_ij) v_i to pcol[I][j].  The tile is staged in
+// shared memory (column stride HT + 1) and read once with a row mapping (thread:
+// row tid % 64, 16 columns) and once with a column mapping (thread: column
+// tid % 64, 16 rows); no shuffles.
+__global__ void __launch_bounds__(256) hemv_lower_kernel(const z64* __restrict__ M, int m, int k,
+                                                         const z64* __restrict__ vb, z64* prow, z64* pcol) {
   const int n = m - k - 1;
   const z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int per = FM_CEIL_DIV(n, nchunks);
-  const int j0 = blockIdx.y * per, j1 = min(n, j0 + per);
-  z64 acc = cmk(0.0, 0.0);
-  if (i < n)
-    for (int j = j0 + threadIdx.y; j < j1; j += 8) cfma(acc, M22[i + (int64_t)j * m], vb[j]);
-  __shared__ z64 red[8][33];
-  red[threadIdx.y][threadIdx.x] = acc;
+  // decode lower tile t = I (I+1)/2 + J
+  const int t = blockIdx.x;
+  int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  while (I * (I + 1) / 2 > t) --I;
+  const int J = t - I * (I + 1) / 2;
+  extern __shared__ z64 tile[];             // HT columns of HT + 1
+  __shared__ z64 vi_s[HT], vj_s[HT];
+  __shared__ z64 red_s[4][HT + 1];
+  const int lo = threadIdx.x % HT, q = threadIdx.x / HT;
+  for (int cc = q; cc < HT; cc += 4) {
+    const int i = I * HT + lo, j = J * HT + cc;
+    z64 a = cmk(0.0, 0.0);
+    if (i < n && j < n && j <= i) a = M22[i + (int64_t)j * m];
+    tile[cc * (HT + 1) + lo] = a;            // zero above the diagonal and outside
+  }
+  if (threadIdx.x < HT) {
+    const int ii = I * HT + threadIdx.x, jj = J * HT + threadIdx.x;
+    vi_s[threadIdx.x] = ii < n ? vb[ii] : cmk(0.0, 0.0);
+    vj_s[threadIdx.x] = jj < n ? vb[jj] : cmk(0.0, 0.0);
+  }
   __syncthreads();
-  if (threadIdx.y == 0 && i < n) {
-    z64 s = cmk(0.0, 0.0);
-    for (int w = 0; w < 8; ++w) s = cadd(s, red[w][threadIdx.x]);
-    partial[(int64_t)blockIdx.y * n + i] = s;
+  // rows: sum_j M_ij v_j (diagonal included)
+  z64 acc = cmk(0.0, 0.0);
+  for (int cc = q; cc < HT; cc += 4) cfma(acc, tile[cc * (HT + 1) + lo], vj_s[cc]);
+  red_s[q][lo] = acc;
+  __syncthreads();
+  if (threadIdx.x < HT) {
+    const int ii = I * HT + threadIdx.x;
+    z64 s2 = cadd(cadd(red_s[0][threadIdx.x], red_s[1][threadIdx.x]), cadd(red_s[2][threadIdx.x], red_s[3][threadIdx.x]));
+    if (ii < n) prow[(int64_t)J * n + ii] = s2;
+  }
+  __syncthreads();
+  // columns: sum_{i > j} conj(M_ij) v_i (strictly lower; on the diagonal tile skip i == j)
+  acc = cmk(0.0, 0.0);
+  const bool diag_tile = (I == J);
+  for (int rr = q; rr < HT; rr += 4) {
+    if (diag_tile && rr <= lo) continue;
+    cfma(acc, cconj(tile[lo * (HT + 1) + rr]), vi_s[rr]);
+  }
+  red_s[q][lo] = acc;
+  __syncthreads();
+  if (threadIdx.x < HT) {
+    const int jj = J * HT + threadIdx.x;
+    z64 s2 = cadd(cadd(red_s[0][threadIdx.x], red_s[1][threadIdx.x]), cadd(red_s[2][threadIdx.x], red_s[3][threadIdx.x]));
+    if (jj < n) pcol[(int64_t)I * n + jj] = s2;
   }
 }
 
-__global__ void __launch_bounds__(1024) hh_w_kernel(int m, int k, const z64* partial, int nchunks,
-                                                    const z64* vb, z64* wb, const z64* tau_in) {
-  __shared__ double red[33];
+// p_i = sum_{J <= I(i)} prow[J][i] + sum_{I >= J(i)} pcol[I][i]; also partial v^dag p per block
+__global__ void hemv_reduce_kernel(int m, int k, const z64* __restrict__ prow, const z64* __restrict__ pcol,
+                                   const z64* __restrict__ vb, z64* p, z64* sdot) {
   const int n = m - k - 1;
+  const int nb = FM_CEIL_DIV(n, HT);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double sr = 0.0, si = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    z64 p = cmk(0.0, 0.0);
-    for (int c = 0; c < nchunks; ++c) p = cadd(p, partial[(int64_t)c * n + i]);
-    wb[i] = p;
-    const z64 t = cmul(cconj(vb[i]), p);
-    sr += t.re; si += t.im;
+  if (i < n) {
+    const int Ii = i / HT;
+    z64 acc = cmk(0.0, 0.0);
+    for (int J = 0; J <= Ii; ++J) acc = cadd(acc, prow[(int64_t)J * n + i]);
+    for (int I = Ii; I < nb; ++I) acc = cadd(acc, pcol[(int64_t)I * n + i]);
+    p[i] = acc;
+    const z64 t = cmul(cconj(vb[i]), acc);
+    sr = t.re; si = t.im;
   }
-  const double s_re = bsum(sr, red);
-  const double s_im = bsum(si, red);
+  __shared__ double red_r[8], red_i[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red_r[threadIdx.x >> 5] = sr; red_i[threadIdx.x >> 5] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red_r[w]; b += red_i[w]; }
+    sdot[blockIdx.x] = cmk(a, b);
+  }
+}
+
+// w = tau p - (1/2)|tau|^2 (v^dag p) v, v^dag p from the per-block partials (fixed order)
+__global__ void hh_w_kernel(int m, int k, const z64* __restrict__ p, const z64* __restrict__ sdot, int nsd,
+                            const z64* __restrict__ vb, z64* wb, const z64* tau_in) {
+  const int n = m - k - 1;
+  __shared__ z64 s_sh;
+  if (threadIdx.x == 0) {
+    z64 s = cmk(0.0, 0.0);
+    for (int b = 0; b < nsd; ++b) s = cadd(s, sdot[b]);
+    s_sh = s;
+  }
+  __syncthreads();
   const z64 tau = *tau_in;
   const double t2 = 0.5 * cabs2(tau);
-  const z64 cs = cmk(t2 * s_re, t2 * s_im);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) wb[i] = csub(cmul(tau, wb[i]), cmul(cs, vb[i]));
+  const z64 cs = cmk(t2 * s_sh.re, t2 * s_sh.im);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    wb[i] = csub(cmul(tau, p[i]), cmul(cs, vb[i]));
 }
 
-// M22 -= v w^dag + w v^dag, 2-D grid over (i, j)
-__global__ void hh_update_kernel(z64* M, int m, int k, const z64* __restrict__ vb, const z64* __restrict__ wb) {
+// M22 -= v w^dag + w v^dag on the lower triangle (i >= j); block (256 rows) x columns
+__global__ void her2_lower_kernel(z64* M, int m, int k, const z64* __restrict__ vb, const z64* __restrict__ wb) {
   const int n = m - k - 1;
   z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const z64 vi = vb[i], wi = wb[i];
-  for (int j = blockIdx.y; j < n; j += gridDim.y) {
+  for (int j = blockIdx.y; j <= i; j += gridDim.y) {
     z64& a = M22[i + (int64_t)j * m];
     a = csub(a, cadd(cmul(vi, cconj(wb[j])), cmul(wi, cconj(vb[j]))));
   }
@@ -237,6 +305,11 @@ __global__ void __launch_bounds__(1024) entropy_sum_kernel(const double* lam, in
 
 __global__ void one_by_one_kernel(const z64* M, double* d) { d[0] = M[0].re; }
 
+int64_t hermitian_entropy_pbuf(int m) {
+  const int64_t nbm = FM_CEIL_DIV(m, HT);
+  return 1 + 2 * nbm * m + m + m / 256 + 2;
+}
+
 cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, z64* pbuf, double* partial_unused,
                               double* d, double* e, double* lam, double* S, int* nlaunch) {
   (void)partial_unused;
@@ -249,18 +322,31 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, 
     tridiag_small_kernel<<<1, 1024, 0, st>>>(M, m, vb, wb, d, e);
     ++launches;
   } else {
-    z64* tau = pbuf;               // pbuf[0]: tau ; pbuf + 1: matvec partials (nchunks * m)
-    z64* partial = pbuf + 1;
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t ce = cudaFuncSetAttribute(hemv_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(HT * (HT + 1) * sizeof(z64)));
+      if (ce != cudaSuccess) return ce;
+      configured = true;
+    }
+    // pbuf layout: [tau][prow: nb*m][pcol: nb*m][p: m][sdot: m/256 + 1]
+    const int nbm = FM_CEIL_DIV(m, HT);
+    z64* tau = pbuf;
+    z64* prow = pbuf + 1;
+    z64* pcol = prow + (int64_t)nbm * m;
+    z64* p = pcol + (int64_t)nbm * m;
+    z64* sdot = p + m;
     for (int k = 0; k + 1 < m; ++k) {
       const int n = m - k - 1;
+      const int nb = FM_CEIL_DIV(n, HT);
       hh_reflector_kernel<<<1, 1024, 0, st>>>(M, m, k, vb, d, e, tau);
-      const int rowblocks = FM_CEIL_DIV(n, 32);
-      const int nchunks = max(1, min(32, FM_CEIL_DIV(4 * 152, rowblocks)));
-      hh_matvec_kernel<<<dim3(rowblocks, nchunks), dim3(32, 8), 0, st>>>(M, m, k, vb, partial, nchunks);
-      hh_w_kernel<<<1, 1024, 0, st>>>(m, k, partial, nchunks, vb, wb, tau);
-      const int gy = max(1, min(n, FM_CEIL_DIV(8 * 152, FM_CEIL_DIV(n, 256))));
-      hh_update_kernel<<<dim3(FM_CEIL_DIV(n, 256), gy), 256, 0, st>>>(M, m, k, vb, wb);
-      launches += 4;
+      hemv_lower_kernel<<<nb * (nb + 1) / 2, 256, HT * (HT + 1) * sizeof(z64), st>>>(M, m, k, vb, prow, pcol);
+      const int rb = FM_CEIL_DIV(n, 256);
+      hemv_reduce_kernel<<<rb, 256, 0, st>>>(m, k, prow, pcol, vb, p, sdot);
+      hh_w_kernel<<<FM_CEIL_DIV(n, 256), 256, 0, st>>>(m, k, p, sdot, rb, vb, wb, tau);
+      const int gy = max(1, min(n, FM_CEIL_DIV(8 * 152, rb)));
+      her2_lower_kernel<<<dim3(rb, gy), 256, 0, st>>>(M, m, k, vb, wb);
+      launches += 5;
     }
     last_diag_kernel<<<1, 1, 0, st>>>(M, m, d);
     ++launches;

@@ -80,7 +80,7 @@ Plan make_plan(const fm_params& p) {
   pl.X = pl.take(B * N * kCholNB * 16);
   pl.ee_vb = pl.take(N * 16);
   pl.ee_wb = pl.take(N * 16);
-  pl.ee_pb = pl.take((1 + 32 * N) * 16);
+  pl.ee_pb = pl.take(std::max<int64_t>(hermitian_entropy_pbuf((int)N), 1 + 32 * N) * 16);
   pl.ee_d = pl.take(N * 8);
   pl.ee_e = pl.take(N * 8);
   pl.ee_lam = pl.take(N * 8);
@@ -244,7 +244,7 @@ fm_status cholqr_f64(fm_state* s) {
                     GEMM_UPPER_ONLY), 1);
   s->timer.end(FM_PH_GRAM);
   s->timer.begin(FM_PH_CHOLESKY);
-  CK(cholesky_inverse_f64(s->st, s->G, s->R, s->T, s->Dinv, s->X, N, N, sNN, N, B, s->status_d, &s->launches));
+  CK(cholesky_inverse<double>(s->st, s->G, s->R, s->T, s->Dinv, s->X, N, N, sNN, N, B, s->status_d, &s->launches));
   s->timer.end(FM_PH_CHOLESKY);
   s->timer.begin(FM_PH_TRMM);
   CKL(zgemm<double>(s->st, L, N, N, OP_N, OP_N, one, s->U, L, sLN, s->T, N, sNN, zero, s->U2, L, sLN, B,
@@ -336,9 +336,11 @@ fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, doub
   if (s->prm.precision == FM_MIXED && mixed_entropy_gram(s->st, s->aux, n, N, M)) {
     s->launches += 1;
   } else if (n <= N) {
-    CKL(zgemm<double>(s->st, n, n, N, OP_N, OP_C, one, s->aux, n, 0, s->aux, n, 0, zero, M, n, 0, 1, 0), 1);
+    const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
+    CKL(zgemm<double>(s->st, n, n, N, OP_N, OP_C, one, s->aux, n, 0, s->aux, n, 0, zero, M, n, 0, 1, fl), 1);
   } else {
-    CKL(zgemm<double>(s->st, N, N, n, OP_C, OP_N, one, s->aux, n, 0, s->aux, n, 0, zero, M, N, 0, 1, 0), 1);
+    const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
+    CKL(zgemm<double>(s->st, N, N, n, OP_C, OP_N, one, s->aux, n, 0, s->aux, n, 0, zero, M, N, 0, 1, fl), 1);
   }
   int nl = 0;
   CK(hermitian_entropy(s->st, M, m, s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e, s->ee_lam, s->ee_S,

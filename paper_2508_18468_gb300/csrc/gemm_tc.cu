@@ -78,11 +78,11 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
       rowsum += (double)d[j] * (double)d[j];
     }
   } else if (MODE == MODE_GRAM) {
-    // complex128 G_b[k1 + k2 N], real or imaginary part
-    double* out = p.out_g + 2 * ((int64_t)ti.b * p.Ntraj * p.Ntraj + (int64_t)(m0 + r) +
+    // complex64 G_b[k1 + k2 N], real or imaginary part
+    float* out = p.out_gf + 2 * ((int64_t)ti.b * p.Ntraj * p.Ntraj + (int64_t)(m0 + r) +
                                  (int64_t)(n0 + c0) * p.Ntraj) + ti.part;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.Ntraj] = (double)d[j];
+    for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.Ntraj] = d[j];
   } else {  // MODE_TRMM: column c of the L x 2N view -> V_b[(c&1) L + i + (c>>1) 2L]
     const int64_t base = (int64_t)ti.b * 2 * p.L * p.Ntraj + (m0 + r);
 #pragma unroll

@@ -17,7 +17,7 @@ constexpr int BK = 64;   // K per pipeline stage: one 128-byte swizzle row of fp
 enum Mode {
   MODE_PLAIN = 0,  // out_f[m + n ld_out] = D (fp32)
   MODE_PROP = 1,   // propagation: out_f as PLAIN + per-row sums of D^2 into partial
-  MODE_GRAM = 2,   // Gram: D into the real (part 0) / imaginary (part 1) half of complex128 G_b
+  MODE_GRAM = 2,   // Gram: D into the real (part 0) / imaginary (part 1) half of complex64 G_b
   MODE_TRMM = 3    // U R^-1: D into V_b (fp32) and its fp16 planes
 };
 
@@ -38,7 +38,7 @@ struct Params {
   float* out_f;
   __half* out_h;
   __half* out_l;
-  double* out_g;
+  float* out_gf;       // GRAM: complex64 G_b (interleaved re, im)
   double* partial;
   int64_t ld_out;
   int L, Ntraj, C;

@@ -12,7 +12,7 @@ namespace fm {
 // op codes for the CUDA-core complex GEMM
 enum { OP_N = 0, OP_T = 1, OP_C = 2 };
 // flags
-enum { GEMM_UPPER_ONLY = 1, GEMM_TRI_A_UPPER = 2, GEMM_TRI_B_UPPER = 4 };
+enum { GEMM_UPPER_ONLY = 1, GEMM_TRI_A_UPPER = 2, GEMM_TRI_B_UPPER = 4, GEMM_LOWER_ONLY = 8 };
 
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b], column-major complex, T = double or float.
 // beta == 0 does not read C.
@@ -53,21 +53,23 @@ struct pm_args {
 };
 cudaError_t pm_measure(cudaStream_t st, const pm_args& a);
 
-// ---- Cholesky / triangular inverse (FP64)
+// ---- Cholesky / triangular inverse (T = double or float)
 constexpr int CHOL_NB = 32;
-// T_b = R_b^-1 with G_b = R_b^dag R_b for the n x n blocks at G, R, T (leading
+// T_b = R_b^-1 with G_b = R_b^dag R_b for the n x n blocks at G, R, Tm (leading
 // dimension ld, batch stride sNN; upper part of G read, G overwritten).
 // Scratch per trajectory: Dinv ceil(alloc_n/32) 32 x 32 blocks, X alloc_n x 32.
-cudaError_t cholesky_inverse_f64(cudaStream_t st, z64* G, z64* R, z64* T, z64* Dinv, z64* X, int n, int ld,
-                                 int64_t sNN, int alloc_n, int B, int* status, int64_t* launches);
-// factor the nb x nb diagonal block at (k,k) of every G_b in place into R_b (upper),
-// and write its inverse into Dinv_b (nb x nb at block index k/nb).
-// nbk = min(nb, N - k) rows of the block are real, the rest padded with identity.
-cudaError_t chol_diag_block(cudaStream_t st, const z64* G, int64_t ldg, int64_t sG, z64* R, int64_t ldr,
-                            int64_t sR, z64* Dinv, int64_t sD, int k, int nb, int nbk, int batch,
-                            int* dev_status);
-// T_b = block-diagonal of Dinv_b, zero elsewhere (N x N)
-cudaError_t place_diag_blocks(cudaStream_t st, const z64* Dinv, int64_t sD, z64* T, int64_t ldt, int64_t sT,
+template <typename T>
+cudaError_t cholesky_inverse(cudaStream_t st, cplx<T>* G, cplx<T>* R, cplx<T>* Tm, cplx<T>* Dinv, cplx<T>* X, int n,
+                             int ld, int64_t sNN, int alloc_n, int B, int* status, int64_t* launches);
+// factor the nb x nb diagonal block at (k,k) of every G_b into R_b (upper) and
+// write its inverse into Dinv_b (nb x nb at block index k/nb); nbk = min(nb, n - k)
+// rows are real, the rest padded with identity.
+template <typename T>
+cudaError_t chol_diag_block(cudaStream_t st, const cplx<T>* G, int64_t ldg, int64_t sG, cplx<T>* R, int64_t ldr,
+                            int64_t sR, cplx<T>* Dinv, int64_t sD, int k, int nb, int nbk, int batch, int* status);
+// Tm_b = block-diagonal of Dinv_b, zero elsewhere (N x N)
+template <typename T>
+cudaError_t place_diag_blocks(cudaStream_t st, const cplx<T>* Dinv, int64_t sD, cplx<T>* Tm, int64_t ldt, int64_t sT,
                               int N, int nb, int batch);
 cudaError_t zero_lower(cudaStream_t st, z64* R, int64_t ldr, int64_t sR, int N, int batch);
 
@@ -90,9 +92,15 @@ cudaError_t max_abs_minus_identity(cudaStream_t st, const z64* G, int ncols, int
 cudaError_t check_finite_z(cudaStream_t st, const z64* X, int64_t n, int* dev_status);
 
 // ---- eigenvalues / entropy (FP64)
-// in: Hermitian m x m matrix M (column-major, overwritten); out: S = -sum f(lambda)
+// in: Hermitian m x m matrix M (column-major, overwritten; for m > 256 only its
+// lower triangle is read); out: S = -sum f(lambda).  pbuf: 1 + 2 * ceil(m/64) * m + m
+// complex entries of scratch.
 cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vbuf, z64* wbuf, z64* pbuf,
                               double* partial, double* d, double* e, double* lam, double* S_dev,
                               int* nlaunch);
+// size of pbuf (complex entries) hermitian_entropy needs for an m x m matrix
+int64_t hermitian_entropy_pbuf(int m);
+// the lower triangle alone is enough for this m
+inline bool hermitian_entropy_lower_only(int m) { return m > 256; }
 
 }  // namespace fm

@@ -2,6 +2,8 @@
 // the all-FP64 path, occupations and the homodyne weight, the projective
 // measurement, Cholesky pieces, and layout conversions.
 #include <float.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "kernels.h"
@@ -26,6 +28,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA
   C += bz * sC;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if ((flags & GEMM_UPPER_ONLY) && m0 > n0 + BN - 1) return;
+  if ((flags & GEMM_LOWER_ONLY) && n0 > m0 + BM - 1) return;
   int kbeg = 0, kend = K;
   if (flags & GEMM_TRI_A_UPPER) kbeg = (m0 / BK) * BK;
   if (flags & GEMM_TRI_B_UPPER) kend = min(K, n0 + BN);
@@ -221,26 +224,36 @@ FM_DEVFN void split16(float x, __half& h, __half& l) {
   l = __float2half_rn((x - __half2float(h)) * 2048.0f);
 }
 
-__global__ void scale_rows_v_kernel(float* V, __half* Vh, __half* Vl, int L, int N, int batch,
+// rows: blockIdx.x * 256 + tid of the 2L rows; columns: 8 consecutive of the B*N
+// (N is a multiple of 8 on this path, so a group never spans two trajectories).
+__global__ void scale_rows_v_kernel(float* V, __half* Vh, __half* Vl, int L, int N, int64_t ngroups,
                                     const double* __restrict__ w) {
-  const int64_t tot = (int64_t)2 * L * N * batch;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx % (2 * L);
-    const int64_t b = idx / ((int64_t)2 * L * N);
-    const float s = (float)w[b * L + (r % L)];
-    const float x = V[idx] * s;
-    V[idx] = x;
-    __half h, l;
-    split16(x, h, l);
-    Vh[idx] = h;
-    Vl[idx] = l;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= 2 * L) return;
+  const int64_t L2 = 2 * (int64_t)L;
+  for (int64_t g = blockIdx.y; g < ngroups; g += gridDim.y) {
+    const int64_t c0 = g * 8;
+    const int64_t b = c0 / N;
+    const float s = (float)w[b * L + (r < L ? r : r - L)];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t idx = r + (c0 + q) * L2;
+      const float x = V[idx] * s;
+      V[idx] = x;
+      __half h, l;
+      split16(x, h, l);
+      Vh[idx] = h;
+      Vl[idx] = l;
+    }
   }
 }
 
 cudaError_t scale_rows_v(cudaStream_t st, float* V, __half* Vh, __half* Vl, int L, int N, int batch,
                          const double* w) {
-  scale_rows_v_kernel<<<152 * 8, 256, 0, st>>>(V, Vh, Vl, L, N, batch, w);
+  if (N % 8) return cudaErrorInvalidValue;
+  const int64_t ngroups = (int64_t)batch * N / 8;
+  dim3 grid(FM_CEIL_DIV(2 * L, 256), (unsigned)std::min<int64_t>(ngroups, 65535));
+  scale_rows_v_kernel<<<grid, 256, 0, st>>>(V, Vh, Vl, L, N, ngroups, w);
   return cudaGetLastError();
 }
 
@@ -400,78 +413,88 @@ cudaError_t pm_measure(cudaStream_t st, const pm_args& a) {
   return cudaGetLastError();
 }
 
-// =================================================================== Cholesky pieces (FP64)
+// =================================================================== Cholesky pieces
 // One CTA (32 x 32 threads) per trajectory: upper Cholesky of the nbk x nbk
 // diagonal block at (k,k) of G (right-looking), written into R, and its
 // triangular inverse into Dinv (nb x nb, column-major, block index k/nb).
-__global__ void __launch_bounds__(1024) chol_diag_kernel(const z64* __restrict__ G, int64_t ldg, int64_t sG,
-                                                         z64* R, int64_t ldr, int64_t sR, z64* Dinv,
+template <typename T>
+__global__ void __launch_bounds__(1024) chol_diag_kernel(const cplx<T>* __restrict__ G, int64_t ldg, int64_t sG,
+                                                         cplx<T>* R, int64_t ldr, int64_t sR, cplx<T>* Dinv,
                                                          int64_t sD, int k, int nb, int nbk, int* status) {
   const int64_t b = blockIdx.x;
   G += b * sG;
   R += b * sR;
   Dinv += b * sD + (int64_t)(k / nb) * nb * nb;
-  __shared__ z64 A[32][33];
-  __shared__ z64 X[32][33];
+  __shared__ cplx<T> A[32][33];
+  __shared__ cplx<T> X[32][33];
   const int r = threadIdx.x / 32, c = threadIdx.x % 32;
   if (r < nbk && c < nbk) A[r][c] = G[(k + r) + (int64_t)(k + c) * ldg];
-  else A[r][c] = cmk(r == c ? 1.0 : 0.0, 0.0);
+  else A[r][c] = cmk<T>(r == c ? (T)1 : (T)0, (T)0);
   __syncthreads();
   for (int j = 0; j < nbk; ++j) {
     if (threadIdx.x == 0) {
-      double d = A[j][j].re;
-      if (!(d > 0.0) || !isfinite(d)) { atomicOr(status, FM_DEVERR_PIVOT); d = 1.0; }
-      A[j][j] = cmk(sqrt(d), 0.0);
+      T d = A[j][j].re;
+      if (!(d > (T)0) || !isfinite(d)) { atomicOr(status, FM_DEVERR_PIVOT); d = (T)1; }
+      A[j][j] = cmk<T>(sqrt(d), (T)0);
     }
     __syncthreads();
-    if (r == j && c > j) A[j][c] = cscale(A[j][c], 1.0 / A[j][j].re);
+    if (r == j && c > j) A[j][c] = cscale(A[j][c], (T)1 / A[j][j].re);
     __syncthreads();
     if (r > j && c >= r) A[r][c] = csub(A[r][c], cmul(cconj(A[j][r]), A[j][c]));
     __syncthreads();
   }
-  if (r < nbk && c < nbk) R[(k + r) + (int64_t)(k + c) * ldr] = (r <= c) ? A[r][c] : cmk(0.0, 0.0);
+  if (r < nbk && c < nbk) R[(k + r) + (int64_t)(k + c) * ldr] = (r <= c) ? A[r][c] : cmk<T>((T)0, (T)0);
   // inverse of the upper-triangular block, one column per thread
   if (threadIdx.x < 32) {
     const int cc = threadIdx.x;
     for (int i = 31; i >= 0; --i) {
-      if (i > cc) { X[i][cc] = cmk(0.0, 0.0); continue; }
-      z64 s = cmk(i == cc ? 1.0 : 0.0, 0.0);
+      if (i > cc) { X[i][cc] = cmk<T>((T)0, (T)0); continue; }
+      cplx<T> s = cmk<T>(i == cc ? (T)1 : (T)0, (T)0);
       for (int l = i + 1; l <= cc; ++l) s = csub(s, cmul(A[i][l], X[l][cc]));
-      X[i][cc] = cscale(s, 1.0 / A[i][i].re);
+      X[i][cc] = cscale(s, (T)1 / A[i][i].re);
     }
   }
   __syncthreads();
-  if (r < nb && c < nb) Dinv[r + (int64_t)c * nb] = (r < nbk && c < nbk) ? X[r][c] : cmk(0.0, 0.0);
+  if (r < nb && c < nb) Dinv[r + (int64_t)c * nb] = (r < nbk && c < nbk) ? X[r][c] : cmk<T>((T)0, (T)0);
 }
 
-cudaError_t chol_diag_block(cudaStream_t st, const z64* G, int64_t ldg, int64_t sG, z64* R, int64_t ldr,
-                            int64_t sR, z64* Dinv, int64_t sD, int k, int nb, int nbk, int batch, int* status) {
-  chol_diag_kernel<<<batch, 1024, 0, st>>>(G, ldg, sG, R, ldr, sR, Dinv, sD, k, nb, nbk, status);
+template <typename T>
+cudaError_t chol_diag_block(cudaStream_t st, const cplx<T>* G, int64_t ldg, int64_t sG, cplx<T>* R, int64_t ldr,
+                            int64_t sR, cplx<T>* Dinv, int64_t sD, int k, int nb, int nbk, int batch, int* status) {
+  chol_diag_kernel<T><<<batch, 1024, 0, st>>>(G, ldg, sG, R, ldr, sR, Dinv, sD, k, nb, nbk, status);
   return cudaGetLastError();
 }
+template cudaError_t chol_diag_block<double>(cudaStream_t, const z64*, int64_t, int64_t, z64*, int64_t, int64_t, z64*,
+                                             int64_t, int, int, int, int, int*);
+template cudaError_t chol_diag_block<float>(cudaStream_t, const c32*, int64_t, int64_t, c32*, int64_t, int64_t, c32*,
+                                            int64_t, int, int, int, int, int*);
 
-__global__ void place_diag_blocks_kernel(const z64* __restrict__ Dinv, int64_t sD, z64* T, int64_t ldt,
+template <typename T>
+__global__ void place_diag_blocks_kernel(const cplx<T>* __restrict__ Dinv, int64_t sD, cplx<T>* Tm, int64_t ldt,
                                          int64_t sT, int N, int nb) {
   const int64_t b = blockIdx.y;
   const int64_t tot = (int64_t)N * N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % N), j = (int)(idx / N);
-    z64 v = cmk(0.0, 0.0);
+    cplx<T> v = cmk<T>((T)0, (T)0);
     if (i / nb == j / nb) {
       const int blk = i / nb;
       v = Dinv[b * sD + (int64_t)blk * nb * nb + (i % nb) + (int64_t)(j % nb) * nb];
     }
-    T[b * sT + i + (int64_t)j * ldt] = v;
+    Tm[b * sT + i + (int64_t)j * ldt] = v;
   }
 }
 
-cudaError_t place_diag_blocks(cudaStream_t st, const z64* Dinv, int64_t sD, z64* T, int64_t ldt, int64_t sT, int N,
-                              int nb, int batch) {
-  dim3 grid(min(FM_CEIL_DIV((int64_t)N * N, 256), (int64_t)2048), batch);
-  place_diag_blocks_kernel<<<grid, 256, 0, st>>>(Dinv, sD, T, ldt, sT, N, nb);
+template <typename T>
+cudaError_t place_diag_blocks(cudaStream_t st, const cplx<T>* Dinv, int64_t sD, cplx<T>* Tm, int64_t ldt, int64_t sT,
+                              int N, int nb, int batch) {
+  dim3 grid((unsigned)min(FM_CEIL_DIV((int64_t)N * N, 256), (int64_t)2048), batch);
+  place_diag_blocks_kernel<T><<<grid, 256, 0, st>>>(Dinv, sD, Tm, ldt, sT, N, nb);
   return cudaGetLastError();
 }
+template cudaError_t place_diag_blocks<double>(cudaStream_t, const z64*, int64_t, z64*, int64_t, int64_t, int, int, int);
+template cudaError_t place_diag_blocks<float>(cudaStream_t, const c32*, int64_t, c32*, int64_t, int64_t, int, int, int);
 
 __global__ void zero_lower_kernel(z64* R, int64_t ldr, int64_t sR, int N) {
   const int64_t b = blockIdx.y;

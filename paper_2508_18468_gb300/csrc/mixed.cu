@@ -26,6 +26,7 @@ struct Scratch {
   size_t total = 0;
   size_t tiles_prop, tiles_gram, tiles_trmm, urm_h, urm_l;
   size_t ca_h, ca_l, cb_h, cb_l, cd, xs;   // complex tensor GEMM helper (Cholesky recursion)
+  size_t gf, rf, tf, dinvf, xf, diag;     // complex64 Gram / factor / inverse, FP64 Gram diagonal
   size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
 };
 
@@ -47,23 +48,32 @@ Scratch scratch_plan(int Lx, int Ly, int B) {
   s.cb_h = s.take((int64_t)B * 2 * md * md * 2);
   s.cb_l = s.take((int64_t)B * 2 * md * md * 2);
   s.cd = s.take((int64_t)B * 2 * md * md * 4);
-  s.xs = s.take((int64_t)B * md * md * 16);
+  s.xs = s.take((int64_t)B * md * md * 8);
+  s.gf = s.take((int64_t)B * N * N * 8);
+  s.rf = s.take((int64_t)B * N * N * 8);
+  s.tf = s.take((int64_t)B * N * N * 8);
+  s.dinvf = s.take((int64_t)B * ((N + 31) / 32) * 32 * 32 * 8);
+  s.xf = s.take((int64_t)B * N * 32 * 8);
+  s.diag = s.take((int64_t)B * N * 8);
   return s;
 }
 
 // ------------------------------------------------------------------ kernels
-FM_DEVFN void split16_d(double v, __half& h, __half& l) {
-  h = __float2half_rn((float)v);
-  l = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
+
+FM_DEVFN void split16_f(float v, __half& h, __half& l) {
+  h = __float2half_rn(v);
+  l = __float2half_rn((v - __half2float(h)) * 2048.0f);
 }
 
 // K-major planes of the real embedding of an upper-triangular N x N complex
 // matrix Z (rows c, K index j, 2N x 2N per trajectory):
 //   Z~[2l+s, 2n+s'] = Re Z_ln (s = s'), Im Z_ln (s=0, s'=1), -Im Z_ln (s=1, s'=0).
 // mode 0: Z = T - 1 (T = R^-1 from the Cholesky recursion);
-// mode 1: Z = -F, F = strict upper part of G plus half of (diag G - 1): the
-//         first-order inverse factor of G = 1 + E, (1 + F)^dag (1 + F) = G + O(E^2).
-__global__ void build_ttilde_kernel(const z64* __restrict__ Z, int mode, int N, int B, __half* Th, __half* Tl) {
+// mode 1: Z = -F, F = strict upper part of G plus half of (diag G - 1) (the
+//         diagonal taken from the float64 Gram diagonal): the first-order
+//         inverse factor of G = 1 + E, (1 + F)^dag (1 + F) = G + O(E^2).
+__global__ void build_ttilde_kernel(const c32* __restrict__ Z, const double* __restrict__ diag, int mode, int N,
+                                    int B, __half* Th, __half* Tl) {
   const int64_t N2 = 2 * (int64_t)N;
   const int64_t tot = (int64_t)B * N2 * N2;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
@@ -72,19 +82,22 @@ __global__ void build_ttilde_kernel(const z64* __restrict__ Z, int mode, int N, 
     const int64_t b = row / N2, c = row % N2;
     const int64_t n = c >> 1, l = j >> 1;
     const int sp = (int)(c & 1), s = (int)(j & 1);
-    double v = 0.0;
+    float v = 0.0f;
     if (l <= n) {
-      z64 z = Z[b * (int64_t)N * N + l + n * (int64_t)N];
+      c32 z = Z[b * (int64_t)N * N + l + n * (int64_t)N];
       if (mode == 0) {
-        if (l == n) z.re -= 1.0;
+        if (l == n) z.re -= 1.0f;
+      } else if (l == n) {
+        z.re = (float)(-(diag[b * N + n] - 1.0) * 0.5);
+        z.im = 0.0f;
       } else {
-        if (l == n) { z.re = -(z.re - 1.0) * 0.5; z.im = 0.0; }
-        else { z.re = -z.re; z.im = -z.im; }
+        z.re = -z.re;
+        z.im = -z.im;
       }
       v = (s == sp) ? z.re : (s == 0 ? z.im : -z.im);
     }
     __half h, lo;
-    split16_d(v, h, lo);
+    split16_f(v, h, lo);
     Th[idx] = h;
     Tl[idx] = lo;
   }
@@ -92,7 +105,7 @@ __global__ void build_ttilde_kernel(const z64* __restrict__ Z, int mode, int N, 
 
 // Planes of the real embedding of op(X) (m x k complex; op: 0 = none, 2 = conjugate
 // transpose): A (2m x 2k, row-major) = [[Re, -Im], [Im, Re]].
-__global__ void embed_a_kernel(const z64* __restrict__ X, int64_t ldx, int64_t sX, int op, int m, int k,
+__global__ void embed_a_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op, int m, int k,
                                __half* Ah, __half* Al) {
   const int64_t b = blockIdx.y;
   const int64_t tot = 4 * (int64_t)m * k;
@@ -102,18 +115,18 @@ __global__ void embed_a_kernel(const z64* __restrict__ X, int64_t ldx, int64_t s
     const int64_t r = idx / k2, c = idx % k2;
     const int64_t rr = r % m, cc = c % k;
     const bool rb = r >= m, cb = c >= k;
-    z64 x = (op == 2) ? X[b * sX + cc + rr * ldx] : X[b * sX + rr + cc * ldx];
+    c32 x = (op == 2) ? X[b * sX + cc + rr * ldx] : X[b * sX + rr + cc * ldx];
     if (op == 2) x.im = -x.im;
-    const double v = (!rb && !cb) ? x.re : (!rb && cb) ? -x.im : (rb && !cb) ? x.im : x.re;
+    const float v = (!rb && !cb) ? x.re : (!rb && cb) ? -x.im : (rb && !cb) ? x.im : x.re;
     __half h, lo;
-    split16_d(v, h, lo);
+    split16_f(v, h, lo);
     Ah[b * tot + idx] = h;
     Al[b * tot + idx] = lo;
   }
 }
 
 // Planes of B (n x 2k, row-major): row j = [Re op(Y)[:, j], Im op(Y)[:, j]].
-__global__ void embed_b_kernel(const z64* __restrict__ Y, int64_t ldy, int64_t sY, int op, int k, int n,
+__global__ void embed_b_kernel(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int op, int k, int n,
                                __half* Bh, __half* Bl) {
   const int64_t b = blockIdx.y;
   const int64_t tot = 2 * (int64_t)k * n;
@@ -122,18 +135,18 @@ __global__ void embed_b_kernel(const z64* __restrict__ Y, int64_t ldy, int64_t s
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = idx / k2, c = idx % k2;
     const int64_t kk = c % k;
-    z64 y = (op == 2) ? Y[b * sY + j + kk * ldy] : Y[b * sY + kk + j * ldy];
+    c32 y = (op == 2) ? Y[b * sY + j + kk * ldy] : Y[b * sY + kk + j * ldy];
     if (op == 2) y.im = -y.im;
-    const double v = (c >= k) ? y.im : y.re;
+    const float v = (c >= k) ? y.im : y.re;
     __half h, lo;
-    split16_d(v, h, lo);
+    split16_f(v, h, lo);
     Bh[b * tot + idx] = h;
     Bl[b * tot + idx] = lo;
   }
 }
 
 // C = alpha (D_re + i D_im) + beta C, D = [D_re; D_im] (2m x n, column-major, per trajectory)
-__global__ void combine_kernel(const float* __restrict__ D, int m, int n, double alpha, double beta, z64* C,
+__global__ void combine_kernel(const float* __restrict__ D, int m, int n, float alpha, float beta, c32* C,
                                int64_t ldc, int64_t sC) {
   const int64_t b = blockIdx.y;
   const int64_t tot = (int64_t)m * n;
@@ -141,10 +154,10 @@ __global__ void combine_kernel(const float* __restrict__ D, int m, int n, double
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = idx % m, j = idx / m;
-    const double re = Db[r + j * 2 * (int64_t)m], im = Db[m + r + j * 2 * (int64_t)m];
-    z64* c = C + b * sC + r + j * ldc;
-    z64 out = cmk(alpha * re, alpha * im);
-    if (beta != 0.0) { out.re += beta * c->re; out.im += beta * c->im; }
+    const float re = Db[r + j * 2 * (int64_t)m], im = Db[m + r + j * 2 * (int64_t)m];
+    c32* c = C + b * sC + r + j * ldc;
+    c32 out = cmk(alpha * re, alpha * im);
+    if (beta != 0.0f) { out.re += beta * c->re; out.im += beta * c->im; }
     *c = out;
   }
 }
@@ -172,24 +185,35 @@ __global__ void transpose_planes_kernel(const __half* __restrict__ Vh, const __h
   }
 }
 
-// G_b[k,k] = sum_s V_b[s,k]^2 accumulated in float64 from the float state (one
-// warp per column).  Replaces the tensor-core diagonal, whose fp32 accumulator
-// loses up to one ulp per 16-deep MMA, biased toward zero on these all-positive
-// sums.
-__global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int B, z64* G) {
+// diag_b[k] = sum_s V_b[s,k]^2 (float64: 16-term float partial sums added into a
+// double) and the same value on the diagonal of the complex64 Gram.  Replaces
+// the tensor-core diagonal, whose fp32 accumulator loses up to one ulp per
+// 16-deep MMA, biased toward zero on these all-positive sums.
+__global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int B, double* diag, c32* G) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)B * N) return;
   const int64_t b = w / N, k = w % N;
   const float* col = V + b * 2 * (int64_t)L * N + k * 2 * (int64_t)L;
   double acc = 0.0;
-  for (int s = lane; s < 2 * L; s += 32) {
-    const double x = col[s];
-    acc += x * x;
+  for (int s0 = 0; s0 < 2 * L; s0 += 32 * 16) {
+    float part = 0.0f;
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+      const int s = s0 + q * 32 + lane;
+      if (s < 2 * L) {
+        const float x = col[s];
+        part = fmaf(x, x, part);
+      }
+    }
+    acc += (double)part;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) G[b * (int64_t)N * N + k + k * (int64_t)N] = cmk(acc, 0.0);
+  if (lane == 0) {
+    diag[b * N + k] = acc;
+    G[b * (int64_t)N * N + k + k * (int64_t)N] = cmk((float)acc, 0.0f);
+  }
 }
 
 }  // namespace
@@ -201,8 +225,10 @@ struct MixedHost {
   __half *urm_h, *urm_l;
   __half *ca_h, *ca_l, *cb_h, *cb_l;
   float* cd;
-  z64* xs;
+  c32* xs;
   int64_t md;        // largest block dimension of the Cholesky recursion products
+  c32 *gf, *rf, *tf, *dinvf, *xf;
+  double* diag;
   CUtensorMap prop_Ah, prop_Al, prop_Bh, prop_Bl;
   CUtensorMap gram_Ah, gram_Al, gram_Bh, gram_Bl;
   CUtensorMap trmm_Ah, trmm_Al, trmm_Bh, trmm_Bl;
@@ -242,8 +268,14 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   h->cb_h = (__half*)(base + sp.cb_h);
   h->cb_l = (__half*)(base + sp.cb_l);
   h->cd = (float*)(base + sp.cd);
-  h->xs = (z64*)(base + sp.xs);
+  h->xs = (c32*)(base + sp.xs);
   h->md = N / 2 + 128;
+  h->gf = (c32*)(base + sp.gf);
+  h->rf = (c32*)(base + sp.rf);
+  h->tf = (c32*)(base + sp.tf);
+  h->dinvf = (c32*)(base + sp.dinvf);
+  h->xf = (c32*)(base + sp.xf);
+  h->diag = (double*)(base + sp.diag);
   std::vector<int4> tp = tc::tile_list(2 * L / tc::BM, B * N / BN, 1, 1, false, BN, 16);
   std::vector<int4> tg = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, 16);
   std::vector<int4> tt = tc::tile_list(L / tc::BM, 2 * N / 128, B, 1, false, 128, 16);
@@ -294,11 +326,11 @@ tc::Params base_params(MixedCtx* c, MixedHost* h) {
   return p;
 }
 
-// op(X) op(Y) on the tensor cores for complex128 blocks (all trajectories):
+// op(X) op(Y) on the tensor cores for complex64 blocks (all trajectories):
 // C = alpha op(X) op(Y) + beta C, op(X) m x k, op(Y) k x n; m, n multiples of 128,
 // k of 32.  The product runs as the real GEMM [[Re, -Im], [Im, Re]] (op X) x [Re; Im] (op Y).
-int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const z64* X, int64_t ldx, int64_t sX, int opY, const z64* Y,
-             int64_t ldy, int64_t sY, int m, int n, int k, double alpha, double beta, z64* C, int64_t ldc,
+int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int64_t sX, int opY, const c32* Y,
+             int64_t ldy, int64_t sY, int m, int n, int k, float alpha, float beta, c32* C, int64_t ldc,
              int64_t sC) {
   const int B = c->B;
   const unsigned gx = (unsigned)std::min<int64_t>(FM_CEIL_DIV(4 * (int64_t)m * k, 256), 2048);
@@ -335,21 +367,23 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const z64* X, int64_t ldx, int6
   return FM_OK;
 }
 
-// R and T = R^-1 of the n x n diagonal block at `off` of G (= R^dag R), recursively:
+// R and T = R^-1 of the n x n diagonal block at `off` of G (= R^dag R), recursively,
+// on the complex64 copies (the first pass only needs its factor to bring U within
+// reach of the second, float64-factored pass):
 //   R11, T11 <- block(off, h);  R12 = T11^dag G12;  G22 -= R12^dag R12;
 //   R22, T22 <- block(off + h, n - h);  T12 = -T11 (R12 T22).
-// Blocks of <= 128 are factored in float64; the products run on the tensor cores.
+// Blocks of <= 128 are factored on the CUDA cores; the products run on the tensor cores.
 int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   const int N = c->N;
   const int64_t sNN = (int64_t)N * N;
-  z64* G = c->G;
-  z64* R = c->R;
-  z64* T = c->T;
+  c32* G = h->gf;
+  c32* R = h->rf;
+  c32* T = h->tf;
   const int64_t d0 = off + (int64_t)off * N;
   if (n <= 128) {
     int64_t nl = 0;
-    cudaError_t e = cholesky_inverse_f64(c->st, G + d0, R + d0, T + d0, c->Dinv, c->X, n, N, sNN, N, c->B,
-                                         c->status, &nl);
+    cudaError_t e = cholesky_inverse<float>(c->st, G + d0, R + d0, T + d0, h->dinvf, h->xf, n, N, sNN, N, c->B,
+                                            c->status, &nl);
     c->launches += nl;
     if (e != cudaSuccess) { c->err = std::string("cholesky leaf: ") + cudaGetErrorString(e); return FM_ECUDA; }
     return FM_OK;
@@ -360,11 +394,11 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   int r;
   const int64_t sXS = (int64_t)h->md * h->md;  // batch stride of the xs scratch
   if ((r = chol_inv_rec(h, c, off, hh))) return r;
-  if ((r = cgemm_tc(h, c, 2, T + d0, N, sNN, 0, G + o12, N, sNN, hh, m2, hh, 1.0, 0.0, R + o12, N, sNN))) return r;
-  if ((r = cgemm_tc(h, c, 2, R + o12, N, sNN, 0, R + o12, N, sNN, m2, m2, hh, -1.0, 1.0, G + d1, N, sNN))) return r;
+  if ((r = cgemm_tc(h, c, 2, T + d0, N, sNN, 0, G + o12, N, sNN, hh, m2, hh, 1.f, 0.f, R + o12, N, sNN))) return r;
+  if ((r = cgemm_tc(h, c, 2, R + o12, N, sNN, 0, R + o12, N, sNN, m2, m2, hh, -1.f, 1.f, G + d1, N, sNN))) return r;
   if ((r = chol_inv_rec(h, c, off + hh, m2))) return r;
-  if ((r = cgemm_tc(h, c, 0, R + o12, N, sNN, 0, T + d1, N, sNN, hh, m2, m2, 1.0, 0.0, h->xs, hh, sXS))) return r;
-  if ((r = cgemm_tc(h, c, 0, T + d0, N, sNN, 0, h->xs, hh, sXS, hh, m2, hh, -1.0, 0.0, T + o12, N, sNN))) return r;
+  if ((r = cgemm_tc(h, c, 0, R + o12, N, sNN, 0, T + d1, N, sNN, hh, m2, m2, 1.f, 0.f, h->xs, hh, sXS))) return r;
+  if ((r = cgemm_tc(h, c, 0, T + d0, N, sNN, 0, h->xs, hh, sXS, hh, m2, hh, -1.f, 0.f, T + o12, N, sNN))) return r;
   return FM_OK;
 }
 
@@ -372,7 +406,7 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
 // first == true: T = R^-1 from the recursive factorisation (G far from 1), and
 //   the product accumulates in fp32 registers every 2 K-blocks;
 // first == false: G = 1 + E with |E| small after a full pass, T = 1 - F to first
-//   order (O(|E|^2) error), F built in float64 straight from G.
+//   order (O(|E|^2) error), F built from G with its float64 diagonal.
 int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
   const int L = c->L, N = c->N, B = c->B, BN = h->BN;
   const int grid = tc::sm_count();
@@ -385,10 +419,10 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
   p.b_rows_per_b = N;
   p.k_shift = L;
   p.kdim = 2 * L;
-  p.out_g = (double*)c->G;
+  p.out_gf = (float*)h->gf;
   c->timer->begin(FM_PH_GRAM);
   MCK(tc::launch(c->st, BN, h->gram_Ah, h->gram_Al, h->gram_Bh, h->gram_Bl, p, grid));
-  gram_diag_kernel<<<FM_CEIL_DIV((int64_t)B * N * 32, 256), 256, 0, c->st>>>(c->V, L, N, B, c->G);
+  gram_diag_kernel<<<FM_CEIL_DIV((int64_t)B * N * 32, 256), 256, 0, c->st>>>(c->V, L, N, B, h->diag, h->gf);
   MCK(cudaGetLastError());
   c->timer->end(FM_PH_GRAM);
   c->timer->begin(FM_PH_CHOLESKY);
@@ -396,7 +430,8 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
     int r = chol_inv_rec(h, c, 0, N);
     if (r) return r;
   }
-  build_ttilde_kernel<<<152 * 8, 256, 0, c->st>>>(first ? c->T : c->G, first ? 0 : 1, N, B, c->Th, c->Tl);
+  build_ttilde_kernel<<<152 * 8, 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag, first ? 0 : 1, N, B, c->Th,
+                                                  c->Tl);
   MCK(cudaGetLastError());
   transpose_planes_kernel<<<dim3(L / 32, 2 * N / 32, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
                                                                                   h->urm_l);
@@ -514,7 +549,7 @@ extern "C" int fmx_tc_gemm(const void* Ah, const void* Al, const void* Bh, const
   return (int)tc::launch(st, BN, a_h, a_l, b_h, b_l, p, grid);
 }
 
-extern "C" int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, double* G, int BN, void* d_tiles,
+extern "C" int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, float* G, int BN, void* d_tiles,
                            void* stream) {
   if (N % tc::BM || (BN != 128 && BN != 256) || N % BN || (2 * L) % tc::BK) return (int)cudaErrorInvalidValue;
   CUtensorMap a_h, a_l, b_h, b_l;
@@ -538,7 +573,7 @@ extern "C" int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, 
   p.b_rows_per_b = N;
   p.k_shift = L;
   p.kdim = 2 * L;
-  p.out_g = G;
+  p.out_gf = G;
   p.L = L;
   p.Ntraj = N;
   return (int)tc::launch(st, BN, a_h, a_l, b_h, b_l, p, tc::sm_count());
