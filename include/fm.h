@@ -158,6 +158,14 @@ fm_status fm_take_events(fm_state* s, fm_event* out, int32_t cap, int32_t* count
 fm_status fm_save(fm_state* s, const char* path);
 fm_status fm_load(fm_state* s, const char* path);
 
+/* CUDA graphs.  When enabled, fm_step replays captured graphs of whole step
+ * periods (2 * reorth_interval steps, started at a multiple of the period;
+ * the remaining steps run eagerly), removing per-kernel launch overhead.
+ * The first replay captures the graph (on a library-owned stream) and
+ * synchronises.  Results are bit-identical to eager stepping.  Phase timing
+ * is not recorded inside graphs. */
+fm_status fm_set_graphs(fm_state* s, int32_t enable);
+
 /* Phase timing (tracing).  When enabled, each phase of fm_step and fm_entropy
  * is bracketed by CUDA events on the state's stream.  fm_phase_times
  * synchronises, adds the elapsed milliseconds of every completed phase since

@@ -134,6 +134,12 @@ struct fm_state {
   MixedCtx mc;
   MixedHost* mh;
   PhaseTimer timer;
+  // CUDA graph of one step period
+  bool graphs_on;
+  cudaStream_t cap_st;
+  cudaGraphExec_t graph_exec;
+  int graph_period;
+  int64_t graph_launch_count;
   // EE
   z64 *ee_vb, *ee_wb, *ee_pb;
   double *ee_d, *ee_e, *ee_lam, *ee_S, *ee_max;
@@ -351,6 +357,70 @@ fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, doub
   return sync_and_check(s);
 }
 
+// one eager step of the whole batch on s->st
+fm_status step_once(fm_state* s) {
+  fm_status r;
+  if (s->prm.precision == FM_FP64) r = step_f64(s);
+  else {
+    MixedCtx& c = s->mc;
+    c.st = s->st;
+    c.global_step = s->global_steps;
+    c.V = s->V; c.V2 = s->V2;
+    c.launches = 0;
+    r = (fm_status)mixed_step(s->mh, &c);
+    s->V = c.V; s->V2 = c.V2;
+    s->launches += c.launches;
+    if (r) r = fail(s, r, c.err);
+  }
+  if (r) return r;
+  s->global_steps += 1;
+  for (int b = 0; b < s->B; ++b) s->step_h[b] += 1;
+  return FM_OK;
+}
+
+// Capture one period of steps into s->graph_exec (state pointers return to
+// their starting buffers after a period, so the graph can be replayed).
+fm_status capture_period(fm_state* s) {
+  const int P = s->graph_period;
+  if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(s->st));
+  cudaStream_t user = s->st;
+  const int64_t g0 = s->global_steps;
+  const int64_t l0 = s->launches;
+  std::vector<int64_t> steps0 = s->step_h;
+  z64* U0 = s->U;
+  float* V0 = s->V;
+  const bool timing = s->timer.on;
+  s->timer.on = false;
+  s->st = s->cap_st;
+  s->timer.st = s->cap_st;
+  fm_status r = FM_OK;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    r = fail(s, FM_ECUDA, "cudaStreamBeginCapture");
+  } else {
+    for (int i = 0; i < P && r == FM_OK; ++i) r = step_once(s);
+    cudaError_t e = cudaStreamEndCapture(s->cap_st, &graph);
+    if (r == FM_OK && e != cudaSuccess) r = fail(s, FM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+  }
+  s->st = user;
+  s->timer.st = user;
+  s->timer.on = timing;
+  if (s->prm.precision != FM_FP64) s->mc.st = user;
+  // capturing did not execute anything: restore the host bookkeeping
+  const int64_t per_period = s->launches - l0;
+  s->global_steps = g0;
+  s->step_h = steps0;
+  s->launches = l0;
+  if (r == FM_OK && (s->U != U0 || s->V != V0)) r = fail(s, FM_ECUDA, "graph period does not return the state buffers");
+  if (r == FM_OK) {
+    if (cudaGraphInstantiate(&s->graph_exec, graph, 0) != cudaSuccess) r = fail(s, FM_ECUDA, "cudaGraphInstantiate");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  s->graph_launch_count = per_period;
+  return r;
+}
+
 }  // namespace
 
 // =================================================================== public API
@@ -378,6 +448,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->st = (cudaStream_t)cuda_stream;
   s->ws = (char*)d_workspace; s->ws_bytes = ws_bytes; s->pl = pl;
   s->global_steps = 0; s->sticky = 0; s->launches = 0;
+  s->graphs_on = false; s->cap_st = nullptr; s->graph_exec = nullptr; s->graph_period = 0;
   char* w = s->ws;
   s->gamma_d = (double*)(w + pl.gamma); s->traj_d = (uint64_t*)(w + pl.traj); s->step_d = (int64_t*)(w + pl.step);
   s->status_d = (int*)(w + pl.status); s->occ_d = (int*)(w + pl.occ);
@@ -478,22 +549,32 @@ fm_status fm_step(fm_state* s, int32_t nsteps) {
   fm_status r = check_state(s);
   if (r) return r;
   if (nsteps < 0) return fail(s, FM_EINVAL, "nsteps < 0");
-  for (int i = 0; i < nsteps; ++i) {
-    if (s->prm.precision == FM_FP64) r = step_f64(s);
-    else {
-      MixedCtx& c = s->mc;
-      c.global_step = s->global_steps;
-      c.V = s->V; c.V2 = s->V2;
-      c.launches = 0;
-      r = (fm_status)mixed_step(s->mh, &c);
-      s->V = c.V; s->V2 = c.V2;
-      s->launches += c.launches;
-      if (r) r = fail(s, r, c.err);
+  int i = 0;
+  if (s->graphs_on) {
+    const int P = s->graph_period;
+    while (i < nsteps && (s->global_steps % P) != 0) {
+      if ((r = step_once(s))) return r;
+      ++i;
     }
-    if (r) return r;
-    s->global_steps += 1;
-    for (int b = 0; b < s->B; ++b) s->step_h[b] += 1;
+    while (nsteps - i >= P) {
+      if (!s->graph_exec && (r = capture_period(s))) return r;
+      CK(cudaGraphLaunch(s->graph_exec, s->st));
+      s->launches += s->graph_launch_count;
+      s->global_steps += P;
+      for (int b = 0; b < s->B; ++b) s->step_h[b] += P;
+      i += P;
+    }
   }
+  for (; i < nsteps; ++i)
+    if ((r = step_once(s))) return r;
+  return FM_OK;
+}
+
+fm_status fm_set_graphs(fm_state* s, int32_t enable) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  s->graphs_on = enable != 0;
+  s->graph_period = 2 * s->prm.reorth_interval;
   return FM_OK;
 }
 
@@ -738,6 +819,8 @@ const char* fm_last_error(const fm_state* s) { return s ? s->err.c_str() : "null
 
 void fm_destroy(fm_state* s) {
   if (!s) return;
+  if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+  if (s->cap_st) cudaStreamDestroy(s->cap_st);
   mixed_free(s->mh);
   delete s;
 }

@@ -341,15 +341,32 @@ bool make_kmajor_map(CUtensorMap* m, const __half* base, uint64_t K, uint64_t ro
 size_t smem_bytes(int BN) { return BN == 256 ? Cfg<256, 0>::SMEM_BYTES : Cfg<128, 0>::SMEM_BYTES; }
 
 template <int BN, int CH, int MODE>
+static cudaError_t set_smem() {
+  return cudaFuncSetAttribute(tc_gemm_kernel<BN, CH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Cfg<BN, CH>::SMEM_BYTES);
+}
+
+// Shared-memory opt-in of every instantiation, done once before any launch (so
+// that no attribute call falls inside a stream capture).
+cudaError_t configure_all() {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaSuccess) return done;
+  cudaError_t e;
+  if ((e = set_smem<256, 0, MODE_PLAIN>()) || (e = set_smem<128, 0, MODE_PLAIN>()) ||
+      (e = set_smem<128, 1, MODE_PLAIN>()) || (e = set_smem<256, 0, MODE_PROP>()) ||
+      (e = set_smem<128, 0, MODE_PROP>()) || (e = set_smem<256, 0, MODE_GRAM>()) ||
+      (e = set_smem<128, 0, MODE_GRAM>()) || (e = set_smem<128, 1, MODE_TRMM>()) ||
+      (e = set_smem<128, 0, MODE_TRMM>()))
+    return e;
+  done = cudaSuccess;
+  return done;
+}
+
+template <int BN, int CH, int MODE>
 static cudaError_t launch_one(cudaStream_t st, const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
                               const CUtensorMap& Bl, const Params& p, int grid) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, CH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<BN, CH>::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = configure_all();
+  if (e != cudaSuccess) return e;
   tc_gemm_kernel<BN, CH, MODE><<<grid, 256, Cfg<BN, CH>::SMEM_BYTES, st>>>(Ah, Al, Bh, Bl, p);
   return cudaGetLastError();
 }

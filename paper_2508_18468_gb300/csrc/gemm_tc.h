@@ -50,6 +50,8 @@ cudaError_t launch(cudaStream_t st, int BN, const CUtensorMap& Ah, const CUtenso
                    const CUtensorMap& Bl, const Params& p, int grid);
 std::vector<int4> tile_list(int mtiles, int ntiles, int batch, int parts, bool upper_only, int BN, int GM);
 size_t smem_bytes(int BN);
+// shared-memory opt-in of every kernel instantiation (idempotent)
+cudaError_t configure_all();
 int sm_count();
 
 }  // namespace tc

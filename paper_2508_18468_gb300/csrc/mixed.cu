@@ -252,6 +252,10 @@ size_t mixed_scratch_bytes(int Lx, int Ly, int batch) { return scratch_plan(Lx, 
 void mixed_free(MixedHost* h) { delete h; }
 
 MixedHost* mixed_create(MixedCtx* c, std::string* why) {
+  if (tc::configure_all() != cudaSuccess) {
+    *why = "kernel attributes";
+    return nullptr;
+  }
   MixedHost* h = new MixedHost();
   const int L = c->L, N = c->N, B = c->B;
   h->BN = pick_bn(N);

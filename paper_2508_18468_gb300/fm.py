@@ -66,6 +66,7 @@ def _load():
         "fm_load": (i32, [vp, ctypes.c_char_p]),
         "fm_kernel_launches": (i64, [vp]),
         "fm_set_timing": (i32, [vp, i32]),
+        "fm_set_graphs": (i32, [vp, i32]),
         "fm_phase_times": (i32, [vp, P(dbl), P(i64)]),
         "fm_last_error": (ctypes.c_char_p, [vp]),
         "fm_destroy": (None, [vp]),
@@ -223,6 +224,9 @@ class Trajectories:
 
     def load(self, path):
         self._check(lib.fm_load(self._h, str(path).encode()))
+
+    def set_graphs(self, enable=True):
+        self._check(lib.fm_set_graphs(self._h, 1 if enable else 0))
 
     def set_timing(self, enable=True):
         self._check(lib.fm_set_timing(self._h, 1 if enable else 0))

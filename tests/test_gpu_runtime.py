@@ -1,0 +1,55 @@
+"""Runtime features on the GPU: CUDA-graph stepping and the continuous-batching server.
+
+Graph replay must reproduce eager stepping bit for bit, and a request's result
+must not depend on the requests it is batched with (each slot's arithmetic is
+independent of the others), so both are checked for exact equality.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_18468_gb300 import build
+    build.build()
+    from paper_2508_18468_gb300 import fm as mod
+    return mod
+
+
+@pytest.mark.parametrize("precision,protocol,L,reorth", [(0, 1, 64, 1), (0, 0, 64, 2), (1, 1, 256, 1),
+                                                          (1, 0, 512, 3)])
+def test_graph_replay_equals_eager(fm, precision, protocol, L, reorth):
+    kw = dict(batch=2, protocol=protocol, precision=precision, reorth_interval=reorth, gamma=1.0, seed=4)
+    a = fm.Trajectories(fm.make_params(L, **kw))
+    b = fm.Trajectories(fm.make_params(L, **kw))
+    b.set_graphs(True)
+    a.step(3)
+    b.step(3)            # one eager step to align, then one graph period, ...
+    a.step(11)
+    b.step(11)           # ... several replays and an eager remainder
+    for t in range(2):
+        assert np.array_equal(a.copy_U(t), b.copy_U(t))
+    assert a.steps_done(1) == b.steps_done(1) == 14
+    assert b.kernel_launches > 0
+
+
+def test_served_mix_equals_each_request_alone(fm):
+    from paper_2508_18468_gb300 import serve
+    kinds = [(256, "homodyne"), (512, "projective"), (256, "projective")]
+    reqs = [serve.Request(rid=i, L=kinds[i % 3][0], protocol=kinds[i % 3][1], gamma=0.3 + 0.2 * i,
+                          traj_id=100 + i, steps=12 + 2 * (i % 2)) for i in range(7)]
+    srv = serve.Server(slots=2, memory_budget=8 << 30)
+    res, st = srv.run(reqs, realtime=False)
+    assert sorted(r.rid for r in res) == list(range(7))
+    assert st["step_latency_ms_p99"] >= st["step_latency_ms_p50"] > 0
+    for r in res:
+        q = reqs[r.rid]
+        alone = serve.Server(slots=1, memory_budget=8 << 30)
+        (ra,), _ = alone.run([serve.Request(rid=0, L=q.L, protocol=q.protocol, gamma=q.gamma, traj_id=q.traj_id,
+                                            steps=q.steps)], realtime=False)
+        assert ra.S == r.S, (q, ra.S, r.S)

@@ -1,0 +1,102 @@
+"""Scheduling logic of the continuous-batching server, on the CPU with fake groups."""
+import contextlib
+
+import pytest
+
+pytest.importorskip("torch")
+from paper_2508_18468_gb300 import serve  # noqa: E402
+
+
+class FakeGroup:
+    """Same interface as serve.Group; 'computes' S = rid + steps / 1000."""
+    live = []
+
+    def __init__(self, L, protocol, slots, precision, seed, reorth_interval, graphs=True):
+        self.L, self.protocol, self.slots = L, protocol, slots
+        self.bytes = L * slots
+        self.period = 2 * reorth_interval if graphs else 1
+        self.free = list(range(slots))[::-1]
+        self.active = {}
+        self.closed = False
+        self.admitted = 0
+        FakeGroup.live.append(self)
+
+    def stream_context(self):
+        return contextlib.nullcontext()
+
+    def synchronize(self):
+        pass
+
+    def close(self):
+        self.closed = True
+
+    def admit(self, req, now):
+        assert req.L == self.L and req.protocol == self.protocol
+        b = self.free.pop()
+        self.active[b] = serve._Slot(req=req, done=0, admitted=now)
+        self.admitted += 1
+
+    tick_steps = serve.Group.tick_steps
+    launch_steps_real = serve.Group.launch_steps
+
+    def launch_steps(self, n):
+        for sl in self.active.values():
+            sl.done += n
+
+    def harvest(self, now):
+        out = []
+        for b in [b for b, sl in self.active.items() if sl.done >= sl.req.steps]:
+            sl = self.active.pop(b)
+            out.append(serve.Result(rid=sl.req.rid, S=sl.req.rid + sl.done / 1000.0, steps=sl.done,
+                                    admitted=sl.admitted, finished=now, group=(self.L, self.protocol)))
+            self.free.append(b)
+        return out
+
+
+def size_of(L, protocol, slots, precision, reorth_interval):
+    return L * slots
+
+
+def make_requests(n, steps=10):
+    kinds = [(256, "homodyne"), (512, "projective"), (256, "projective"), (1024, "homodyne")]
+    return [serve.Request(rid=i, L=kinds[i % 4][0], protocol=kinds[i % 4][1], gamma=0.5, traj_id=i,
+                          steps=steps + (i % 3), arrival=0.0) for i in range(n)]
+
+
+def test_every_request_answered_once_with_exact_steps():
+    FakeGroup.live = []
+    srv = serve.Server(memory_budget=1 << 40, slots=3, group_factory=FakeGroup, size_of=size_of)
+    reqs = make_requests(20)
+    res, st = srv.run(reqs, realtime=False)
+    assert sorted(r.rid for r in res) == list(range(20))
+    for r in res:
+        assert r.steps == reqs[r.rid].steps            # ticks are clipped to the finishing request
+        assert r.group == (reqs[r.rid].L, reqs[r.rid].protocol)
+    assert st["requests"] == 20
+    assert st["trajectory_steps"] == sum(q.steps for q in reqs)
+    # slots are reused: 4 groups of 3 slots served 20 requests
+    assert len(FakeGroup.live) == 4 and sum(g.admitted for g in FakeGroup.live) == 20
+
+
+def test_memory_budget_is_respected_and_idle_groups_are_evicted():
+    FakeGroup.live = []
+    budget = 1024 * 2            # room for one group of two 1024-site slots, or a few smaller ones
+    srv = serve.Server(memory_budget=budget, slots=2, group_factory=FakeGroup, size_of=size_of)
+    used_max = [0]
+    orig = srv._group_for
+
+    def tracking(req):
+        g = orig(req)
+        used_max[0] = max(used_max[0], srv.used)
+        return g
+    srv._group_for = tracking
+    res, _ = srv.run(make_requests(16), realtime=False)
+    assert len(res) == 16
+    assert used_max[0] <= budget
+    assert any(g.closed for g in FakeGroup.live)       # groups were evicted to make room
+
+
+def test_request_larger_than_budget_is_reported():
+    srv = serve.Server(memory_budget=10, slots=2, group_factory=FakeGroup, size_of=size_of)
+    with pytest.raises(RuntimeError):
+        srv.run(make_requests(1), realtime=False)
