@@ -130,6 +130,18 @@ fm_status fm_steps_done(fm_state* s, int32_t b, int64_t* out);
  * Householder tridiagonalisation + bisection on the GPU.  Synchronises. */
 fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, double* S_out);
 
+/* Asynchronous S_A of trajectory b at the current point of the step sequence.
+ * The rows of A are copied out of the state on a library-owned stream (the
+ * caller's stream waits only for that copy), and the FP64 eigen-solve runs
+ * there while later fm_step calls proceed, so the two overlap on the GPU.
+ * *ticket identifies the result for fm_entropy_wait.  Up to 64 results may be
+ * outstanding; a 65th call first waits for the oldest.  Results live in a
+ * small pinned host buffer the state allocates on first use. */
+fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t n, int64_t* ticket);
+
+/* Block until the entropy of `ticket` is ready and return it. */
+fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out);
+
 /* I = S_A + S_B - S_{A u B} for trajectory b; A and B disjoint host arrays. */
 fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA,
                          const int32_t* B, int32_t nB, double* I_out);

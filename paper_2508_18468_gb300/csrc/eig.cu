@@ -20,7 +20,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// fixed-order block sum for blockDim.x == 1024 (red: 33 doubles of shared memory)
+// fixed-order block sum for blockDim.x a multiple of 32, <= 1024 (red: 33 doubles of shared memory)
 __device__ double bsum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   v = warp_sum(v);
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(1024) tridiag_small_kernel(z64* M, int m, z64*
 
 // ------------------------------------------------------------------ large m: per-column kernels
 // Only the lower triangle (i >= j) of the trailing block is read and updated.
-__global__ void __launch_bounds__(1024) hh_reflector_kernel(z64* M, int m, int k, z64* vb, double* d, double* e,
-                                                            z64* tau_out) {
+__global__ void __launch_bounds__(256) hh_reflector_kernel(z64* M, int m, int k, z64* vb, double* d, double* e,
+                                                           z64* tau_out) {
   __shared__ double red[33];
   __shared__ z64 sh[4];
   __shared__ double sbeta;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(1024) hh_reflector_kernel(z64* M, int m, int k
   }
 }
 
-constexpr int HT = 64;  // tile of the Hermitian matrix-vector product
+constexpr int HT = EIG_TILE;  // tile of the Hermitian matrix-vector product (17 KB of shared memory)
 
 // p = M22 v from the lower triangle: tile (I, J), J <= I, adds sum_j M_ij v_j to
 // prow[J][i] and sum_{i > j} conj(M_ij) v_i to pcol[I][j].  The tile is staged in
@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(256) hemv_lower_kernel(const z64* __restrict__
   while (I * (I + 1) / 2 > t) --I;
   const int J = t - I * (I + 1) / 2;
   extern __shared__ z64 tile[];             // HT columns of HT + 1
+  constexpr int NQ = 256 / HT;               // phases
   __shared__ z64 vi_s[HT], vj_s[HT];
-  __shared__ z64 red_s[4][HT + 1];
+  __shared__ z64 red_s[NQ][HT + 1];
   const int lo = threadIdx.x % HT, q = threadIdx.x / HT;
-  for (int cc = q; cc < HT; cc += 4) {
+  for (int cc = q; cc < HT; cc += NQ) {
     const int i = I * HT + lo, j = J * HT + cc;
     z64 a = cmk(0.0, 0.0);
     if (i < n && j < n && j <= i) a = M22[i + (int64_t)j * m];
@@ -165,19 +166,20 @@ __global__ void __launch_bounds__(256) hemv_lower_kernel(const z64* __restrict__
   __syncthreads();
   // rows: sum_j M_ij v_j (diagonal included)
   z64 acc = cmk(0.0, 0.0);
-  for (int cc = q; cc < HT; cc += 4) cfma(acc, tile[cc * (HT + 1) + lo], vj_s[cc]);
+  for (int cc = q; cc < HT; cc += NQ) cfma(acc, tile[cc * (HT + 1) + lo], vj_s[cc]);
   red_s[q][lo] = acc;
   __syncthreads();
   if (threadIdx.x < HT) {
     const int ii = I * HT + threadIdx.x;
-    z64 s2 = cadd(cadd(red_s[0][threadIdx.x], red_s[1][threadIdx.x]), cadd(red_s[2][threadIdx.x], red_s[3][threadIdx.x]));
+    z64 s2 = cmk(0.0, 0.0);
+    for (int qq = 0; qq < NQ; ++qq) s2 = cadd(s2, red_s[qq][threadIdx.x]);
     if (ii < n) prow[(int64_t)J * n + ii] = s2;
   }
   __syncthreads();
   // columns: sum_{i > j} conj(M_ij) v_i (strictly lower; on the diagonal tile skip i == j)
   acc = cmk(0.0, 0.0);
   const bool diag_tile = (I == J);
-  for (int rr = q; rr < HT; rr += 4) {
+  for (int rr = q; rr < HT; rr += NQ) {
     if (diag_tile && rr <= lo) continue;
     cfma(acc, cconj(tile[lo * (HT + 1) + rr]), vi_s[rr]);
   }
@@ -185,7 +187,8 @@ __global__ void __launch_bounds__(256) hemv_lower_kernel(const z64* __restrict__
   __syncthreads();
   if (threadIdx.x < HT) {
     const int jj = J * HT + threadIdx.x;
-    z64 s2 = cadd(cadd(red_s[0][threadIdx.x], red_s[1][threadIdx.x]), cadd(red_s[2][threadIdx.x], red_s[3][threadIdx.x]));
+    z64 s2 = cmk(0.0, 0.0);
+    for (int qq = 0; qq < NQ; ++qq) s2 = cadd(s2, red_s[qq][threadIdx.x]);
     if (jj < n) pcol[(int64_t)I * n + jj] = s2;
   }
 }
@@ -305,10 +308,7 @@ __global__ void __launch_bounds__(1024) entropy_sum_kernel(const double* lam, in
 
 __global__ void one_by_one_kernel(const z64* M, double* d) { d[0] = M[0].re; }
 
-int64_t hermitian_entropy_pbuf(int m) {
-  const int64_t nbm = FM_CEIL_DIV(m, HT);
-  return 1 + 2 * nbm * m + m + m / 256 + 2;
-}
+
 
 cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, z64* pbuf, double* partial_unused,
                               double* d, double* e, double* lam, double* S, int* nlaunch) {
@@ -339,7 +339,7 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, 
     for (int k = 0; k + 1 < m; ++k) {
       const int n = m - k - 1;
       const int nb = FM_CEIL_DIV(n, HT);
-      hh_reflector_kernel<<<1, 1024, 0, st>>>(M, m, k, vb, d, e, tau);
+      hh_reflector_kernel<<<1, 256, 0, st>>>(M, m, k, vb, d, e, tau);
       hemv_lower_kernel<<<nb * (nb + 1) / 2, 256, HT * (HT + 1) * sizeof(z64), st>>>(M, m, k, vb, prow, pcol);
       const int rb = FM_CEIL_DIV(n, 256);
       hemv_reduce_kernel<<<rb, 256, 0, st>>>(m, k, prow, pcol, vb, p, sdot);

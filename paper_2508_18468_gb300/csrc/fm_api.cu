@@ -19,6 +19,7 @@ namespace {
 
 const int kCholNB = CHOL_NB;   // Cholesky / triangular-inverse block
 const int kMaxChunks = 128;    // occupation partial sums
+const int kAsyncSlots = 64;    // outstanding asynchronous entropies
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -30,6 +31,7 @@ struct Plan {
   size_t V, V2, Vh, Vl, Ah, Al, Th, Tl, aux;           // mixed path
   size_t ee_vb, ee_wb, ee_pb, ee_d, ee_e, ee_lam, ee_S, ee_sites, ee_max;
   size_t chk_cols, chk_G;                               // orthonormality check (<= 64 columns)
+  size_t ea_M, ea_rows, ea_sites, ea_S;                 // asynchronous entropy
   size_t mixed_extra;                                   // scratch owned by the mixed path
   size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
 };
@@ -89,6 +91,10 @@ Plan make_plan(const fm_params& p) {
   pl.ee_sites = pl.take(L * 4);
   pl.chk_cols = pl.take(L * std::min<int64_t>(N, 64) * 16);
   pl.chk_G = pl.take(std::min<int64_t>(N, 64) * N * 16);
+  pl.ea_M = pl.take(N * N * 16);
+  pl.ea_rows = pl.take(L * N * 16);
+  pl.ea_sites = pl.take(L * 4);
+  pl.ea_S = pl.take(kAsyncSlots * 8);
   if (p.precision == FM_FP64) {
     pl.U = pl.take(B * L * N * 16);
     pl.U2 = pl.take(B * L * N * 16);
@@ -145,6 +151,15 @@ struct fm_state {
   double *ee_d, *ee_e, *ee_lam, *ee_S, *ee_max;
   int* ee_sites;
   z64 *chk_cols, *chk_G;
+  // asynchronous entropy
+  z64 *ea_M, *ea_rows;
+  int* ea_sites;
+  double* ea_S;
+  cudaStream_t ea_st;
+  cudaEvent_t ea_state_ev, ea_gather_ev;
+  cudaEvent_t ea_done[kAsyncSlots];
+  double* ea_host;            // pinned, kAsyncSlots doubles
+  int64_t ea_next;            // next ticket
   // host
   std::vector<double> gamma_h;
   std::vector<uint64_t> traj_h;
@@ -331,6 +346,7 @@ fm_status validate_sites(fm_state* s, const int32_t* sites, int32_t n) {
 // S_A of trajectory b; enqueues and synchronises.
 fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, double* S_out) {
   if (n == 0) { *S_out = 0.0; return FM_OK; }
+  if (s->ea_st) CK(cudaStreamSynchronize(s->ea_st));   // shared eigen-solver scratch
   const int N = s->N;
   CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   s->timer.begin(FM_PH_ENTROPY);
@@ -421,6 +437,64 @@ fm_status capture_period(fm_state* s) {
   return r;
 }
 
+// ------------------------------------------------------------------ asynchronous entropy
+fm_status ea_setup(fm_state* s) {
+  if (s->ea_st) return FM_OK;
+  CK(cudaStreamCreateWithFlags(&s->ea_st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->ea_state_ev, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ea_gather_ev, cudaEventDisableTiming));
+  for (int i = 0; i < kAsyncSlots; ++i) CK(cudaEventCreateWithFlags(&s->ea_done[i], cudaEventDisableTiming));
+  CK(cudaHostAlloc((void**)&s->ea_host, kAsyncSlots * sizeof(double), cudaHostAllocDefault));
+  return FM_OK;
+}
+
+fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n, int64_t* ticket) {
+  fm_status r = ea_setup(s);
+  if (r) return r;
+  const int64_t t = s->ea_next;
+  const int slot = (int)(t % kAsyncSlots);
+  if (t >= kAsyncSlots) CK(cudaEventSynchronize(s->ea_done[slot]));    // slot reuse
+  cudaStream_t st = s->ea_st;
+  const int N = s->N, L = s->L;
+  // the state as queued so far on the caller's stream
+  CK(cudaEventRecord(s->ea_state_ev, s->st));
+  CK(cudaStreamWaitEvent(st, s->ea_state_ev, 0));
+  if (n == 0) {
+    CK(cudaMemsetAsync(s->ea_S + slot, 0, sizeof(double), st));
+  } else {
+    CK(cudaMemcpyAsync(s->ea_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    if (s->prm.precision == FM_FP64) {
+      CKL(gather_rows_z(st, s->U + (int64_t)b * L * N, L, N, s->ea_sites, n, s->ea_rows), 1);
+    } else {
+      CKL(gather_rows_v(st, s->V + (int64_t)b * 2 * L * N, L, N, s->ea_sites, n, s->ea_rows), 1);
+    }
+  }
+  // the caller's stream may overwrite the state only after the rows are out
+  CK(cudaEventRecord(s->ea_gather_ev, st));
+  CK(cudaStreamWaitEvent(s->st, s->ea_gather_ev, 0));
+  if (n > 0) {
+    const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+    const int m = std::min(n, N);
+    const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
+    if (n <= N) {
+      CKL(zgemm<double>(st, n, n, N, OP_N, OP_C, one, s->ea_rows, n, 0, s->ea_rows, n, 0, zero, s->ea_M, n, 0, 1, fl),
+          1);
+    } else {
+      CKL(zgemm<double>(st, N, N, n, OP_C, OP_N, one, s->ea_rows, n, 0, s->ea_rows, n, 0, zero, s->ea_M, N, 0, 1, fl),
+          1);
+    }
+    int nl = 0;
+    CK(hermitian_entropy(st, s->ea_M, m, s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e, s->ee_lam,
+                         s->ea_S + slot, &nl));
+    s->launches += nl;
+  }
+  CK(cudaMemcpyAsync(s->ea_host + slot, s->ea_S + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(s->ea_done[slot], st));
+  s->ea_next = t + 1;
+  *ticket = t;
+  return FM_OK;
+}
+
 }  // namespace
 
 // =================================================================== public API
@@ -461,6 +535,10 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ee_d = (double*)(w + pl.ee_d); s->ee_e = (double*)(w + pl.ee_e); s->ee_lam = (double*)(w + pl.ee_lam);
   s->ee_S = (double*)(w + pl.ee_S); s->ee_max = (double*)(w + pl.ee_max); s->ee_sites = (int*)(w + pl.ee_sites);
   s->chk_cols = (z64*)(w + pl.chk_cols); s->chk_G = (z64*)(w + pl.chk_G);
+  s->ea_M = (z64*)(w + pl.ea_M); s->ea_rows = (z64*)(w + pl.ea_rows);
+  s->ea_sites = (int*)(w + pl.ea_sites); s->ea_S = (double*)(w + pl.ea_S);
+  s->ea_st = nullptr; s->ea_state_ev = s->ea_gather_ev = nullptr; s->ea_host = nullptr; s->ea_next = 0;
+  for (int i = 0; i < kAsyncSlots; ++i) s->ea_done[i] = nullptr;
   s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
   s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
   s->mixed_extra = nullptr;
@@ -626,6 +704,26 @@ fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, do
   r = validate_sites(s, sites, n);
   if (r) return r;
   return entropy_impl(s, b, sites, n, S_out);
+}
+
+fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t n, int64_t* ticket) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!ticket || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or ticket");
+  r = validate_sites(s, sites, n);
+  if (r) return r;
+  return entropy_async_impl(s, b, sites, n, ticket);
+}
+
+fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!S_out || ticket < 0 || ticket >= s->ea_next || ticket < s->ea_next - kAsyncSlots)
+    return fail(s, FM_EINVAL, "unknown or expired ticket");
+  const int slot = (int)(ticket % kAsyncSlots);
+  CK(cudaEventSynchronize(s->ea_done[slot]));
+  *S_out = s->ea_host[slot];
+  return sync_and_check(s);
 }
 
 fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA, const int32_t* B, int32_t nB,
@@ -819,6 +917,14 @@ const char* fm_last_error(const fm_state* s) { return s ? s->err.c_str() : "null
 
 void fm_destroy(fm_state* s) {
   if (!s) return;
+  if (s->ea_st) {
+    cudaStreamSynchronize(s->ea_st);
+    cudaStreamDestroy(s->ea_st);
+    cudaEventDestroy(s->ea_state_ev);
+    cudaEventDestroy(s->ea_gather_ev);
+    for (int i = 0; i < kAsyncSlots; ++i) cudaEventDestroy(s->ea_done[i]);
+    cudaFreeHost(s->ea_host);
+  }
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   mixed_free(s->mh);

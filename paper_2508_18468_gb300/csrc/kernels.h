@@ -99,7 +99,10 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vbuf, z64* wb
                               double* partial, double* d, double* e, double* lam, double* S_dev,
                               int* nlaunch);
 // size of pbuf (complex entries) hermitian_entropy needs for an m x m matrix
-int64_t hermitian_entropy_pbuf(int m);
+constexpr int EIG_TILE = 32;
+constexpr int64_t hermitian_entropy_pbuf(int m) {
+  return 1 + 2 * (int64_t)((m + EIG_TILE - 1) / EIG_TILE) * m + m + m / 256 + 2;
+}
 // the lower triangle alone is enough for this m
 inline bool hermitian_entropy_lower_only(int m) { return m > 256; }
 

@@ -23,7 +23,7 @@ constexpr size_t kMOff = kRowsOff + al((size_t)kMaxRows * kMaxN * 16);
 constexpr size_t kVbOff = kMOff + al((size_t)kMaxM * kMaxM * 16);
 constexpr size_t kWbOff = kVbOff + al((size_t)kMaxM * 16);
 constexpr size_t kPbOff = kWbOff + al((size_t)kMaxM * 16);
-constexpr size_t kDOff = kPbOff + al((size_t)(1 + 32 * kMaxM) * 16);
+constexpr size_t kDOff = kPbOff + al((size_t)fm::hermitian_entropy_pbuf(kMaxM) * 16);
 constexpr size_t kEOff = kDOff + al((size_t)kMaxM * 8);
 constexpr size_t kLamOff = kEOff + al((size_t)kMaxM * 8);
 constexpr size_t kSitesOff = kLamOff + al((size_t)kMaxM * 8);

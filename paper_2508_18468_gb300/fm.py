@@ -57,6 +57,8 @@ def _load():
         "fm_steps_done": (i32, [vp, i32, P(i64)]),
         "fm_entropy": (i32, [vp, i32, P(i32), i32, P(dbl)]),
         "fm_mutual_info": (i32, [vp, i32, P(i32), i32, P(i32), i32, P(dbl)]),
+        "fm_entropy_async": (i32, [vp, i32, P(i32), i32, P(i64)]),
+        "fm_entropy_wait": (i32, [vp, i64, P(dbl)]),
         "fm_copy_U": (i32, [vp, i32, vp, i64]),
         "fm_set_U": (i32, [vp, i32, vp, i64]),
         "fm_occupations": (i32, [vp, i32, P(dbl)]),
@@ -179,6 +181,18 @@ class Trajectories:
         a, p = _i32_array(sites)
         out = ctypes.c_double()
         self._check(lib.fm_entropy(self._h, int(b), p, int(a.size), ctypes.byref(out)))
+        return out.value
+
+    def entropy_async(self, sites, b=0):
+        """Start S_A of trajectory b at this point of the step sequence; returns a ticket."""
+        a, p = _i32_array(sites)
+        t = ctypes.c_int64()
+        self._check(lib.fm_entropy_async(self._h, int(b), p, int(a.size), ctypes.byref(t)))
+        return t.value
+
+    def entropy_wait(self, ticket):
+        out = ctypes.c_double()
+        self._check(lib.fm_entropy_wait(self._h, int(ticket), ctypes.byref(out)))
         return out.value
 
     def mutual_info(self, A, B, b=0):

@@ -53,3 +53,24 @@ def test_served_mix_equals_each_request_alone(fm):
         (ra,), _ = alone.run([serve.Request(rid=0, L=q.L, protocol=q.protocol, gamma=q.gamma, traj_id=q.traj_id,
                                             steps=q.steps)], realtime=False)
         assert ra.S == r.S, (q, ra.S, r.S)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_async_entropy_sees_the_state_when_requested(fm, precision):
+    L = 512 if precision else 96
+    kw = dict(batch=2, protocol=1, precision=precision, gamma=0.7, seed=21)
+    a = fm.Trajectories(fm.make_params(L, **kw))
+    b = fm.Trajectories(fm.make_params(L, **kw))
+    half = list(range(L // 2))
+    a.step(5)
+    b.step(5)
+    t0 = a.entropy_async(half, 0)
+    t1 = a.entropy_async(list(range(0, L, 3)), 1)
+    a.step(7)                                   # the state moves on while the solves run
+    ref0 = b.entropy(half, 0)
+    ref1 = b.entropy(list(range(0, L, 3)), 1)
+    assert a.entropy_wait(t0) == ref0
+    assert a.entropy_wait(t1) == ref1
+    b.step(7)
+    assert np.array_equal(a.copy_U(1), b.copy_U(1))
+    assert a.entropy(half, 1) == b.entropy(half, 1)

@@ -43,6 +43,18 @@ def test_noalloc_entropy_matches_fm_entropy():
         got, ref = dS.item(), g.entropy(sites)
         assert abs(got - ref) <= S_TOL * max(1.0, abs(ref)), (sites[:4], got, ref)
 
+    # the largest eigenproblem size takes the multi-kernel reduction path (m > 256)
+    g2 = fm.Trajectories(fm.make_params(1024, protocol=fm.FM_PROJECTIVE, precision=fm.FM_FP64, gamma=1.0,
+                                        seed=14))
+    g2.step(6)
+    dU2 = torch.from_numpy(np.ascontiguousarray(g2.copy_U().T)).to("cuda")
+    sites2 = list(range(0, 1024, 3))[:300]
+    rc = fm.fm_entropy_noalloc(dU2.data_ptr(), 1024, 512, sites2, dS.data_ptr(), stream)
+    assert rc == fm.FM_OK
+    torch.cuda.synchronize()
+    got, ref = dS.item(), g2.entropy(sites2)
+    assert abs(got - ref) <= S_TOL * max(1.0, abs(ref)), (got, ref)
+
     # sizes beyond the fixed scratch, and bad site lists, are refused up front
     assert fm.fm_entropy_noalloc(dU.data_ptr(), L, N, [0, 0], dS.data_ptr(), stream) == fm.FM_EINVAL
     assert fm.fm_entropy_noalloc(dU.data_ptr(), L, N, [L], dS.data_ptr(), stream) == fm.FM_EINVAL
