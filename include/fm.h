@@ -175,7 +175,9 @@ fm_status fm_load(fm_state* s, const char* path);
  * the remaining steps run eagerly), removing per-kernel launch overhead.
  * The first replay captures the graph (on a library-owned stream) and
  * synchronises.  Results are bit-identical to eager stepping.  Phase timing
- * is not recorded inside graphs. */
+ * is not recorded inside graphs.  Projective states whose measurements run as
+ * grid-wide per-event kernels (few trajectories or L > 2048: the per-step
+ * event count is read back to size the launches) always step eagerly. */
 fm_status fm_set_graphs(fm_state* s, int32_t enable);
 
 /* Phase timing (tracing).  When enabled, each phase of fm_step and fm_entropy

@@ -32,6 +32,7 @@ struct Plan {
   size_t ee_vb, ee_wb, ee_pb, ee_d, ee_e, ee_lam, ee_S, ee_sites, ee_max;
   size_t chk_cols, chk_G;                               // orthonormality check (<= 64 columns)
   size_t ea_M, ea_rows, ea_sites, ea_S;                 // asynchronous entropy
+  size_t pmw;                                           // grid-wide projective update
   size_t mixed_extra;                                   // scratch owned by the mixed path
   size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
 };
@@ -95,6 +96,7 @@ Plan make_plan(const fm_params& p) {
   pl.ea_rows = pl.take(L * N * 16);
   pl.ea_sites = pl.take(L * 4);
   pl.ea_S = pl.take(kAsyncSlots * 8);
+  pl.pmw = pl.take(pm_wide_scratch_bytes((int)L, (int)B));
   if (p.precision == FM_FP64) {
     pl.U = pl.take(B * L * N * 16);
     pl.U2 = pl.take(B * L * N * 16);
@@ -159,6 +161,7 @@ struct fm_state {
   cudaEvent_t ea_state_ev, ea_gather_ev;
   cudaEvent_t ea_done[kAsyncSlots];
   double* ea_host;            // pinned, kAsyncSlots doubles
+  void* pmw;                  // grid-wide projective update scratch
   int64_t ea_next;            // next ticket
   // host
   std::vector<double> gamma_h;
@@ -309,7 +312,8 @@ fm_status step_f64(fm_state* s) {
     a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
     a.dev_status = s->status_d;
     s->timer.begin(FM_PH_MEASURE);
-    CKL(pm_measure(s->st, a), 1);
+    if (pm_use_wide(L, N, B)) CK(pm_measure_wide(s->st, a, s->pmw, &s->launches));
+    else CKL(pm_measure(s->st, a), 1);
     s->timer.end(FM_PH_MEASURE);
     if ((gstep + 1) % k == 0) {
       fm_status r = cholqr_f64(s);
@@ -538,6 +542,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ea_M = (z64*)(w + pl.ea_M); s->ea_rows = (z64*)(w + pl.ea_rows);
   s->ea_sites = (int*)(w + pl.ea_sites); s->ea_S = (double*)(w + pl.ea_S);
   s->ea_st = nullptr; s->ea_state_ev = s->ea_gather_ev = nullptr; s->ea_host = nullptr; s->ea_next = 0;
+  s->pmw = w + pl.pmw;
   for (int i = 0; i < kAsyncSlots; ++i) s->ea_done[i] = nullptr;
   s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
   s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
@@ -604,7 +609,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       c.gamma = s->gamma_d; c.traj = s->traj_d; c.step = s->step_d; c.status = s->status_d;
       c.part = s->part_d; c.nocc = s->nocc_d; c.w = s->w_d; c.xbuf = s->xbuf_d; c.vbuf = s->vbuf_d;
       c.log = s->log_d; c.log_count = (int64_t*)s->log_count_d; c.log_capacity = p->event_capacity;
-      c.extra = s->mixed_extra; c.launches = 0; c.timer = &s->timer;
+      c.extra = s->mixed_extra; c.launches = 0; c.timer = &s->timer; c.pmw = s->pmw;
       std::string why2;
       s->mh = mixed_create(&c, &why2);
       if (!s->mh) {
@@ -628,7 +633,8 @@ fm_status fm_step(fm_state* s, int32_t nsteps) {
   if (r) return r;
   if (nsteps < 0) return fail(s, FM_EINVAL, "nsteps < 0");
   int i = 0;
-  if (s->graphs_on) {
+  const bool graph_ok = !(s->prm.protocol == FM_PROJECTIVE && pm_use_wide(s->L, s->N, s->B));
+  if (s->graphs_on && graph_ok) {
     const int P = s->graph_period;
     while (i < nsteps && (s->global_steps % P) != 0) {
       if ((r = step_once(s))) return r;

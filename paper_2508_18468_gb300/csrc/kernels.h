@@ -52,6 +52,12 @@ struct pm_args {
   int* dev_status;
 };
 cudaError_t pm_measure(cudaStream_t st, const pm_args& a);
+// the same measurements as grid-wide kernels per event, all trajectories at once
+// (reads the per-trajectory event counts back to the host: synchronises the stream)
+cudaError_t pm_measure_wide(cudaStream_t st, const pm_args& a, void* scratch, int64_t* launches);
+size_t pm_wide_scratch_bytes(int L, int B);
+// which of the two projective paths suits this shape
+bool pm_use_wide(int L, int N, int B);
 
 // ---- Cholesky / triangular inverse (T = double or float)
 constexpr int CHOL_NB = 32;

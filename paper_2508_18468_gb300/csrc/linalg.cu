@@ -4,6 +4,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <vector>
 #include <math.h>
 
 #include "kernels.h"
@@ -412,6 +413,195 @@ cudaError_t pm_measure(cudaStream_t st, const pm_args& a) {
   else pm_kernel<float, 1><<<a.batch, 1024, 0, st>>>(a);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------ projective update, GPU-wide per event
+// For lattices whose per-event passes are too large for one CTA: the sites of a
+// step are selected first (list per trajectory, ascending), then every event e
+// runs as three grid-wide kernels over all trajectories at once: the row x_j and
+// its Born weight with the outcome (one CTA per trajectory), v = U x^dag / sqrt(p),
+// and the rank-1 update U <- U + (v_new - v) x / sqrt(p).
+struct PmEvent {
+  double p, sp, inv_s1;
+  int site, outcome, active, pad;
+};
+
+__global__ void __launch_bounds__(1024) pm_select_kernel(const double* gamma, double dt, const uint64_t* traj,
+                                                         const int64_t* step, uint64_t seed, int L, int* list,
+                                                         double* ulist, int* count) {
+  const int b = blockIdx.x;
+  const double pmeas = 1.0 - exp(-gamma[b] * dt);
+  __shared__ int warp_cnt[33];
+  __shared__ int base_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) base_sh = 0;
+  __syncthreads();
+  for (int base = 0; base < L; base += 1024) {
+    const int j = base + tid;
+    bool sel = false;
+    double uo = 0.0;
+    if (j < L) {
+      philox_out o = fm_draw(seed, traj[b], step[b], j, FM_TAG_MEASURE);
+      sel = fm_u53(o.w[0], o.w[1]) < pmeas;
+      uo = fm_u53(o.w[2], o.w[3]);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0) warp_cnt[warp] = __popc(bal);
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int w = 0; w < 32; ++w) { int c = warp_cnt[w]; warp_cnt[w] = acc; acc += c; }
+      warp_cnt[32] = acc;
+    }
+    __syncthreads();
+    if (sel) {
+      const int pos = base_sh + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
+      list[(int64_t)b * L + pos] = j;
+      ulist[(int64_t)b * L + pos] = uo;
+    }
+    __syncthreads();
+    if (tid == 0) base_sh += warp_cnt[32];
+    __syncthreads();
+  }
+  if (tid == 0) count[b] = base_sh;
+}
+
+template <typename T, int LAYOUT>
+__global__ void __launch_bounds__(1024) pm_row_kernel(void* Ub, int L, int N, int e, const int* list,
+                                                      const double* ulist, const int* count, const int64_t* step,
+                                                      void* xbuf, PmEvent* ev, fm_event* log,
+                                                      unsigned long long* log_count, int log_capacity) {
+  const int b = blockIdx.x;
+  __shared__ double red[33];
+  uacc<T, LAYOUT> u;
+  u.init(Ub, b, L, N);
+  cplx<T>* xb = (cplx<T>*)xbuf + (int64_t)b * N;
+  const bool has = e < count[b];
+  const int js = has ? list[(int64_t)b * L + e] : 0;
+  double ps = 0.0;
+  if (has)
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      const cplx<T> x = u.ld(js, k);
+      xb[k] = x;
+      ps += (double)x.re * x.re + (double)x.im * x.im;
+    }
+  double p = block_sum_1024(ps, red);
+  if (threadIdx.x == 0) {
+    PmEvent r;
+    r.site = js;
+    r.active = 0;
+    r.outcome = 0;
+    r.p = r.sp = r.inv_s1 = 0.0;
+    r.pad = 0;
+    if (has) {
+      p = fmin(fmax(p, 0.0), 1.0);
+      const double uu = ulist[(int64_t)b * L + e];
+      r.outcome = (uu < p) ? 1 : 0;
+      r.p = p;
+      r.sp = sqrt(p);
+      r.inv_s1 = r.outcome ? 0.0 : 1.0 / sqrt(1.0 - p);
+      r.active = (p >= 1e-300) ? 1 : 0;
+      if (log && log_capacity > 0) {
+        const unsigned long long slot = atomicAdd(log_count, 1ull);
+        if (slot < (unsigned long long)log_capacity) {
+          fm_event le;
+          le.step = step[b]; le.traj = b; le.site = js; le.u = uu; le.p = p; le.outcome = r.outcome; le.pad = 0;
+          log[slot] = le;
+        }
+      }
+    }
+    ev[b] = r;
+  }
+}
+
+// v_i = sum_k U_ik conj(x_k) / sqrt(p); block (32 rows, 8 column phases), grid (ceil(L/32), 1, B)
+template <typename T, int LAYOUT>
+__global__ void pm_gemv_kernel(void* Ub, int L, int N, const void* xbuf, const PmEvent* ev, void* vbuf) {
+  const int b = blockIdx.z;
+  const PmEvent r = ev[b];
+  if (!r.active) return;
+  uacc<T, LAYOUT> u;
+  u.init(Ub, b, L, N);
+  const cplx<T>* xb = (const cplx<T>*)xbuf + (int64_t)b * N;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  cplx<T> acc = cmk<T>(0, 0);
+  if (i < L)
+    for (int k = threadIdx.y; k < N; k += 8) cfma(acc, u.ld(i, k), cconj(xb[k]));
+  __shared__ cplx<T> red[8][33];
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < L) {
+    cplx<T> s = cmk<T>(0, 0);
+    for (int w = 0; w < 8; ++w) s = cadd(s, red[w][threadIdx.x]);
+    ((cplx<T>*)vbuf)[(int64_t)b * L + i] = cscale(s, (T)(1.0 / r.sp));
+  }
+}
+
+// U_ik += (v_new_i - v_i) x_k / sqrt(p); grid (ceil(L/256), column chunks, B)
+template <typename T, int LAYOUT>
+__global__ void pm_update_kernel(void* Ub, int L, int N, int kchunk, const void* xbuf, const PmEvent* ev,
+                                 const void* vbuf) {
+  const int b = blockIdx.z;
+  const PmEvent r = ev[b];
+  if (!r.active) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  uacc<T, LAYOUT> u;
+  u.init(Ub, b, L, N);
+  const cplx<T>* xb = (const cplx<T>*)xbuf + (int64_t)b * N;
+  const cplx<T> v = ((const cplx<T>*)vbuf)[(int64_t)b * L + i];
+  cplx<T> vn;
+  if (r.outcome) vn = cmk<T>(i == r.site ? (T)1 : (T)0, (T)0);
+  else vn = cscale(cmk<T>(v.re - (i == r.site ? (T)r.sp : (T)0), v.im), (T)r.inv_s1);
+  const cplx<T> d = cscale(csub(vn, v), (T)(1.0 / r.sp));
+  const int k0 = blockIdx.y * kchunk, k1 = min(N, k0 + kchunk);
+  for (int k = k0; k < k1; ++k) u.add(i, k, cmul(d, xb[k]));
+}
+
+cudaError_t pm_measure_wide(cudaStream_t st, const pm_args& a, void* scratch, int64_t* launches) {
+  // scratch: list (B*L int), ulist (B*L double), count (B int), events (B PmEvent)
+  char* s = (char*)scratch;
+  int* list = (int*)s;
+  s += (((int64_t)a.batch * a.L * 4) + 255) & ~(int64_t)255;
+  double* ulist = (double*)s;
+  s += (((int64_t)a.batch * a.L * 8) + 255) & ~(int64_t)255;
+  int* count = (int*)s;
+  s += (((int64_t)a.batch * 4) + 255) & ~(int64_t)255;
+  PmEvent* ev = (PmEvent*)s;
+  pm_select_kernel<<<a.batch, 1024, 0, st>>>(a.gamma, a.dt, a.traj, a.step, a.seed, a.L, list, ulist, count);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  ++*launches;
+  std::vector<int> hc(a.batch);
+  if ((e = cudaMemcpyAsync(hc.data(), count, 4 * a.batch, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  int emax = 0;
+  for (int c : hc) emax = std::max(emax, c);
+  const int kchunk = std::max(32, FM_CEIL_DIV(a.N, std::max(1, (4 * 152) / std::max(1, FM_CEIL_DIV(a.L, 256) * a.batch))));
+  const dim3 g_gemv(FM_CEIL_DIV(a.L, 32), 1, a.batch), g_upd(FM_CEIL_DIV(a.L, 256), FM_CEIL_DIV(a.N, kchunk), a.batch);
+  for (int ev_i = 0; ev_i < emax; ++ev_i) {
+    if (a.layout == 0) {
+      pm_row_kernel<double, 0><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, ev_i, list, ulist, count, a.step, a.xbuf, ev,
+                                                         a.log, (unsigned long long*)a.log_count, a.log_capacity);
+      pm_gemv_kernel<double, 0><<<g_gemv, dim3(32, 8), 0, st>>>(a.U, a.L, a.N, a.xbuf, ev, a.vbuf);
+      pm_update_kernel<double, 0><<<g_upd, 256, 0, st>>>(a.U, a.L, a.N, kchunk, a.xbuf, ev, a.vbuf);
+    } else {
+      pm_row_kernel<float, 1><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, ev_i, list, ulist, count, a.step, a.xbuf, ev,
+                                                        a.log, (unsigned long long*)a.log_count, a.log_capacity);
+      pm_gemv_kernel<float, 1><<<g_gemv, dim3(32, 8), 0, st>>>(a.U, a.L, a.N, a.xbuf, ev, a.vbuf);
+      pm_update_kernel<float, 1><<<g_upd, 256, 0, st>>>(a.U, a.L, a.N, kchunk, a.xbuf, ev, a.vbuf);
+    }
+    if ((e = cudaGetLastError())) return e;
+    *launches += 3;
+  }
+  return cudaSuccess;
+}
+
+size_t pm_wide_scratch_bytes(int L, int B) {
+  auto al = [](int64_t x) { return (x + 255) & ~(int64_t)255; };
+  return al((int64_t)B * L * 4) + al((int64_t)B * L * 8) + al((int64_t)B * 4) + al((int64_t)B * sizeof(PmEvent));
+}
+
+bool pm_use_wide(int L, int N, int B) { return !(B >= 64 && L <= 2048); }
 
 // =================================================================== Cholesky pieces
 // One CTA (32 x 32 threads) per trajectory: upper Cholesky of the nbk x nbk

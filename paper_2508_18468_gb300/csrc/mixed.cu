@@ -500,7 +500,12 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     a.log = c->log; a.log_count = c->log_count; a.log_capacity = c->log_capacity;
     a.dev_status = c->status;
     c->timer->begin(FM_PH_MEASURE);
-    MCK(pm_measure(c->st, a));
+    if (pm_use_wide(L, N, B)) {
+      cudaError_t e = pm_measure_wide(c->st, a, c->pmw, &c->launches);
+      if (e != cudaSuccess) { c->err = std::string("projective update: ") + cudaGetErrorString(e); return FM_ECUDA; }
+    } else {
+      MCK(pm_measure(c->st, a));
+    }
     MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
     c->timer->end(FM_PH_MEASURE);
     if ((c->global_step + 1) % k == 0) {

@@ -28,6 +28,7 @@ struct MixedCtx {
   fm_event* log; int64_t* log_count; int log_capacity;
   void* extra;             // mixed_scratch_bytes() of device scratch
   PhaseTimer* timer;       // phase events (may be off)
+  void* pmw;               // scratch of the grid-wide projective update
   int64_t launches;        // out: kernels launched
   std::string err;         // out: message on failure
 };

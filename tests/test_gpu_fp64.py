@@ -213,3 +213,12 @@ def test_invalid_arguments_are_rejected(fm):
         g.orthonormality_error([99])
     g.step(2)
     assert g.steps_done() == 2
+
+
+def test_large_batch_uses_one_cta_per_trajectory_path(fm):
+    """64 trajectories take the one-CTA-per-trajectory projective kernel."""
+    _, g = pair(fm, 32, batch=64, protocol=PROJECTIVE, gamma=2.0, seed=17, traj_id=0)
+    g.step(12)
+    for b in (0, 31, 63):
+        ref = trajectory.run(Params(Lx=32, gamma=2.0, protocol=PROJECTIVE, seed=17, traj_id=b), 12)
+        assert cdiff(g.copy_U(b), ref["U"]) <= C_TOL

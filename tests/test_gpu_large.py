@@ -1,0 +1,73 @@
+"""Full-size checks in the launch configuration the benchmark uses (needs a GB300).
+
+The oracle cannot follow an L = 16384 ring or a 160 x 160 torus for long, so
+these check what holds at any size: the unmonitored closed form, U^dag U = 1,
+Tr C = N, measured sites ending the step with n_j in {0, 1}, and 0 <= MI.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_18468_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_18468_gb300 import build
+    build.build()
+    from paper_2508_18468_gb300 import fm as mod
+    return mod
+
+
+def test_ring16384_unmonitored_closed_form(fm):
+    L, n = 16384, 20
+    g = fm.Trajectories(fm.make_params(L, protocol=fm.FM_PROJECTIVE, precision=fm.FM_MIXED, gamma=0.0))
+    g.step(n)
+    occ = g.occupations()
+    k = 2 * np.pi * np.arange(L) / L
+    ref = 0.5 + 0.5 * (-1.0) ** np.arange(L) * np.mean(np.cos(4.0 * n * 0.05 * np.cos(k)))
+    assert np.max(np.abs(occ - ref)) <= 2e-6 * n
+
+
+def test_ring16384_homodyne_invariants(fm):
+    L = 16384
+    wl = workloads.WORKLOADS["ring16384_homodyne"]
+    g = fm.Trajectories(fm.make_params(L, batch=4, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED,
+                                       seed=workloads.seed_of("ring16384_homodyne")))
+    g.set_gammas(wl["gammas"])
+    g.step(3)
+    for b in range(4):
+        assert g.orthonormality_error(list(range(b, L // 2, 131))[:64], b) <= 1e-6
+        occ = g.occupations(b)
+        assert abs(occ.sum() - L // 2) <= 1e-6 * L
+        assert occ.min() >= -1e-6 and occ.max() <= 1 + 1e-6
+
+
+def test_torus160_projective_step_invariants(fm):
+    Lx = 160
+    L = Lx * Lx
+    g = fm.Trajectories(fm.make_params(Lx, Lx, protocol=fm.FM_PROJECTIVE, precision=fm.FM_MIXED, gamma=2.0,
+                                       seed=workloads.seed_of("torus160_both"), event_capacity=1 << 16))
+    g.step(1)
+    ev, dropped = g.take_events()
+    assert dropped == 0 and len(ev) > 1500             # about 0.095 L measurements per step
+    occ = g.occupations()
+    measured = np.array(sorted({e[2] for e in ev}))
+    dist = np.minimum(np.abs(occ[measured]), np.abs(occ[measured] - 1.0))
+    assert dist.max() <= 1e-5
+    assert abs(occ.sum() - L // 2) <= 1e-6 * L
+    assert g.orthonormality_error(list(range(0, L // 2, 211))[:64]) <= 1e-6
+
+
+def test_torus160_homodyne_mutual_information(fm):
+    g = fm.Trajectories(fm.make_params(160, 160, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED, gamma=1.0,
+                                       seed=workloads.seed_of("torus160_both")))
+    g.step(4)
+    A, B, _ = workloads.torus_blocks()
+    I = g.mutual_info(A, B)
+    assert I >= -1e-9
+    assert g.orthonormality_error(list(range(0, 12800, 199))[:64]) <= 1e-6
