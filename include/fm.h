@@ -83,11 +83,22 @@ typedef struct {
                                Homodyne: first CholeskyQR pass every step, the
                                second every k steps */
   int32_t event_capacity;   /* projective outcome log entries kept (0 = no log) */
-  int32_t reserved;
+  int32_t tile_config;      /* mixed precision only, 0 = defaults; see FM_TILE_* (fm_autotune picks it) */
   double J, dt, gamma;      /* hopping, time step, monitoring rate (per site) */
   uint64_t seed;            /* Philox key */
   uint64_t traj_id;         /* trajectory b of the batch has id traj_id + b */
 } fm_params;
+
+/* fm_params.tile_config of the mixed-precision path: bits 0-1 the output tile
+ * width of the propagation and Gram products (0 automatic: 256 when N is a
+ * multiple of 256, else 128; 1: 128; 2: 256, needs N % 256 == 0); bits 2-4 g
+ * the height of the tile raster groups, 2^(g+1) row tiles (0: 16).  Any other
+ * bit set is FM_EINVAL.  Results do not depend on it beyond float rounding
+ * order inside a tile (none: each output is one fixed-order sum per tile). */
+#define FM_TILE_BN_AUTO 0
+#define FM_TILE_BN_128 1
+#define FM_TILE_BN_256 2
+#define FM_TILE_GROUP(g) ((g) << 2)
 
 /* One projective measurement: trajectory b of the batch, step index (t/dt
  * before the step), site, the outcome draw u, Born probability p, outcome. */
@@ -131,12 +142,19 @@ fm_status fm_steps_done(fm_state* s, int32_t b, int64_t* out);
 fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, double* S_out);
 
 /* Asynchronous S_A of trajectory b at the current point of the step sequence.
- * The rows of A are copied out of the state on a library-owned stream (the
- * caller's stream waits only for that copy), and the FP64 eigen-solve runs
- * there while later fm_step calls proceed, so the two overlap on the GPU.
+ * The rows of A are gathered and C_A is formed on the caller's stream, in
+ * order with the steps (one of 4 C_A buffers of the workspace); the FP64
+ * eigen-solve (Householder tridiagonalisation, about 5 launches per row of
+ * C_A) is issued by a library-owned host thread onto a low-priority stream.
+ * From the first call on, fm_step runs its kernels on a high-priority stream
+ * ordered after and before the caller's stream by events, so later steps
+ * proceed while the eigen-solve fills what their kernels leave of each SM.
  * *ticket identifies the result for fm_entropy_wait.  Up to 64 results may be
- * outstanding; a 65th call first waits for the oldest.  Results live in a
- * small pinned host buffer the state allocates on first use. */
+ * outstanding (a 65th call first waits for the oldest); a 5th call while 4
+ * eigen-solves are still queued makes the caller's stream wait for the
+ * oldest to release its C_A buffer.  Results live in a small pinned host
+ * buffer the state allocates on first use.  A launch error of the library
+ * thread is reported by fm_entropy_wait (FM_ECUDA, sticky). */
 fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t n, int64_t* ticket);
 
 /* Block until the entropy of `ticket` is ready and return it. */
@@ -189,6 +207,34 @@ enum { FM_PH_PROPAGATE = 0, FM_PH_MEASURE = 1, FM_PH_GRAM = 2, FM_PH_CHOLESKY = 
        FM_PH_ENTROPY = 5, FM_NPHASES = 6 };
 fm_status fm_set_timing(fm_state* s, int32_t enable);
 fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts);
+
+/* Result of fm_autotune. */
+typedef struct {
+  int32_t tile_config;      /* best fm_params.tile_config */
+  int32_t reorth_interval;  /* best fm_params.reorth_interval */
+  double ms_per_step;       /* its device time per step of the whole batch */
+  double ortho_err;         /* its largest max|U^dag U - 1| seen on the checked steps */
+  int32_t tried;            /* configurations timed */
+  int32_t rejected;         /* of which over the orthonormality tolerance */
+} fm_tuning;
+
+/* Pick tile_config and reorth_interval for the workload *p by measurement
+ * (the re-orthonormalisation interval of App. A is a free parameter of the
+ * method; the tile shape is not part of it).  One state of *p is built in the
+ * caller's workspace (ws_bytes >= fm_workspace_bytes(p), any tile_config);
+ * for every candidate -- tile width 128 / 256 (mixed precision; 256 only when
+ * N % 256 == 0) x raster groups of 8 / 16 / 32 row tiles x reorth_interval
+ * 1, 2, 4, ... <= max_reorth -- the trajectories restart from the Neel state,
+ * run 2 * reorth_interval warm-up steps, then `steps` timed steps (rounded up
+ * to a whole number of 2 * reorth_interval; CUDA events on the stream, CUDA
+ * graphs when use_graphs != 0), then 2 * reorth_interval single steps after
+ * each of which max|U^dag U - 1| over 64 sampled columns of the first and
+ * last trajectory is measured.  The fastest candidate whose error stays
+ * <= ortho_tol wins; if none does, the fastest with reorth_interval = 1.
+ * Synchronises; the workspace holds nothing useful afterwards. */
+fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, void* cuda_stream,
+                      int32_t steps, int32_t max_reorth, double ortho_tol, int32_t use_graphs,
+                      fm_tuning* out);
 
 /* Limits of fm_entropy_noalloc. */
 #define FM_NOALLOC_MAX_SITES 1024

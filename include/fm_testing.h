@@ -1,8 +1,9 @@
 /*
- * fm_testing.h -- test hooks of libfm.so that expose the split-fp16 tensor-core
- * GEMM on its own, so it can be checked against a reference product.  They
- * are not part of the trajectory API (include/fm.h); the paper has no
- * counterpart of them.
+ * fm_testing.h -- test hooks of libfm.so that expose the tensor-core products
+ * on their own (the split-fp16 GEMM and the exact-product Gram of the
+ * entropy), so they can be checked against reference products.  They are not
+ * part of the trajectory API (include/fm.h); the paper has no counterpart of
+ * them.
  *
  * Operand planes: a float x is passed as two fp16 arrays h, l with
  * x ~= h + l * 2^-11.  All pointers are device pointers; work is issued on
@@ -32,6 +33,16 @@ int fmx_tc_gemm(const void* Ah, const void* Al, const void* Bh, const void* Bl, 
  * column-major planes, column k = [Re U_{:,k}; Im U_{:,k}]). */
 int fmx_tc_gram(const void* Vh, const void* Vl, int L, int N, int B, float* G, int BN, void* d_tiles,
                 void* stream);
+
+/* Device scratch bytes fmx_exact_gram needs for blocks with up to nmax rows. */
+unsigned long long fmx_exact_gram_scratch_bytes(int nmax, int N);
+
+/* M (m x m complex128, column-major, m = min(n, N); lower triangle written)
+ * = X X^dag (n <= N) or X^T conj(X) (n > N) for the n x N complex128 block X
+ * (column-major, ld n) whose entries are floats; exact for the 28-bit
+ * truncation of every row of [Re | Im] relative to its largest entry.  The
+ * same routine the mixed-precision entropy uses for m > 256. */
+int fmx_exact_gram(const void* X, int n, int N, void* M, void* d_scratch, void* stream);
 
 #ifdef __cplusplus
 }

@@ -322,13 +322,7 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, 
     tridiag_small_kernel<<<1, 1024, 0, st>>>(M, m, vb, wb, d, e);
     ++launches;
   } else {
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t ce = cudaFuncSetAttribute(hemv_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(HT * (HT + 1) * sizeof(z64)));
-      if (ce != cudaSuccess) return ce;
-      configured = true;
-    }
+    static_assert(HT * (HT + 1) * sizeof(z64) <= 48 * 1024, "hemv tile must not need a shared-memory opt-in");
     // pbuf layout: [tau][prow: nb*m][pcol: nb*m][p: m][sdot: m/256 + 1]
     const int nbm = FM_CEIL_DIV(m, HT);
     z64* tau = pbuf;

@@ -4,8 +4,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <complex>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fm.h"
@@ -20,6 +25,7 @@ namespace {
 const int kCholNB = CHOL_NB;   // Cholesky / triangular-inverse block
 const int kMaxChunks = 128;    // occupation partial sums
 const int kAsyncSlots = 64;    // outstanding asynchronous entropies
+const int kEaRing = 4;         // C_A buffers of the asynchronous entropies
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -31,8 +37,9 @@ struct Plan {
   size_t V, V2, Vh, Vl, Ah, Al, Th, Tl, aux;           // mixed path
   size_t ee_vb, ee_wb, ee_pb, ee_d, ee_e, ee_lam, ee_S, ee_sites, ee_max;
   size_t chk_cols, chk_G;                               // orthonormality check (<= 64 columns)
-  size_t ea_M, ea_rows, ea_sites, ea_S;                 // asynchronous entropy
+  size_t ea_M, ea_vb, ea_wb, ea_pb, ea_d, ea_e, ea_lam, ea_S;   // asynchronous entropy
   size_t pmw;                                           // grid-wide projective update
+  size_t xg;                                            // exact-product Gram of C_A (mixed)
   size_t mixed_extra;                                   // scratch owned by the mixed path
   size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
 };
@@ -55,7 +62,7 @@ bool valid_params(const fm_params* p, std::string* why) {
   }
   if (p->precision == FM_MIXED) {
     std::string w2;
-    if (!mixed_supported(p->Lx, p->Ly, p->batch, &w2)) { *why = w2; return false; }
+    if (!mixed_supported(p->Lx, p->Ly, p->batch, p->tile_config, &w2)) { *why = w2; return false; }
   }
   return true;
 }
@@ -92,9 +99,13 @@ Plan make_plan(const fm_params& p) {
   pl.ee_sites = pl.take(L * 4);
   pl.chk_cols = pl.take(L * std::min<int64_t>(N, 64) * 16);
   pl.chk_G = pl.take(std::min<int64_t>(N, 64) * N * 16);
-  pl.ea_M = pl.take(N * N * 16);
-  pl.ea_rows = pl.take(L * N * 16);
-  pl.ea_sites = pl.take(L * 4);
+  pl.ea_M = pl.take(kEaRing * N * N * 16);
+  pl.ea_vb = pl.take(N * 16);
+  pl.ea_wb = pl.take(N * 16);
+  pl.ea_pb = pl.take(hermitian_entropy_pbuf((int)N) * 16);
+  pl.ea_d = pl.take(N * 8);
+  pl.ea_e = pl.take(N * 8);
+  pl.ea_lam = pl.take(N * 8);
   pl.ea_S = pl.take(kAsyncSlots * 8);
   pl.pmw = pl.take(pm_wide_scratch_bytes((int)L, (int)B));
   if (p.precision == FM_FP64) {
@@ -113,6 +124,7 @@ Plan make_plan(const fm_params& p) {
     pl.Tl = pl.take(B * 4 * N * N * 2);
     pl.aux = pl.take(L * N * 16);
     pl.mixed_extra = pl.take(mixed_scratch_bytes(p.Lx, p.Ly, p.batch));
+    pl.xg = pl.take(exact_gram_scratch_bytes((int)L, (int)N));
   }
   return pl;
 }
@@ -139,6 +151,7 @@ struct fm_state {
   __half *Vh, *Vl, *Ah, *Al, *Th, *Tl;
   z64* aux;
   void* mixed_extra;
+  void* xg;                  // exact-product Gram scratch (mixed precision)
   MixedCtx mc;
   MixedHost* mh;
   PhaseTimer timer;
@@ -153,16 +166,34 @@ struct fm_state {
   double *ee_d, *ee_e, *ee_lam, *ee_S, *ee_max;
   int* ee_sites;
   z64 *chk_cols, *chk_G;
-  // asynchronous entropy
-  z64 *ea_M, *ea_rows;
-  int* ea_sites;
-  double* ea_S;
-  cudaStream_t ea_st;
-  cudaEvent_t ea_state_ev, ea_gather_ev;
+  // Asynchronous entropy.  The caller's thread gathers the rows of A and
+  // forms C_A on the caller's stream (into one of kEaRing buffers); a library
+  // thread issues the eigen-solver launches (about 5 per row of C_A) on a
+  // low-priority stream.  Steps then run on a high-priority stream bridged to
+  // the caller's by events, so the FP64 eigen-solve fills what the steps'
+  // kernels leave of each SM and the caller's thread never waits on the
+  // launch queue.
+  int dev;
+  z64* ea_M;                  // kEaRing x N x N
+  z64 *ea_vb, *ea_wb, *ea_pb;
+  double *ea_d, *ea_e, *ea_lam, *ea_S;
+  cudaStream_t ea_st, hp_st;
+  cudaEvent_t hp_in, hp_out;
+  cudaEvent_t ea_M_ready[kEaRing], ea_M_free[kEaRing];
   cudaEvent_t ea_done[kAsyncSlots];
   double* ea_host;            // pinned, kAsyncSlots doubles
   void* pmw;                  // grid-wide projective update scratch
   int64_t ea_next;            // next ticket
+  struct EaJob { int64_t t; int slot, ring, m; };
+  std::thread ea_thread;
+  std::mutex ea_mu;
+  std::condition_variable ea_cv;
+  std::deque<EaJob> ea_q;
+  int64_t ea_issued;          // tickets whose launches are all enqueued (in ticket order)
+  bool ea_stop;
+  bool ea_failed;
+  std::string ea_errmsg;
+  std::atomic<int64_t> ea_launches;
   // host
   std::vector<double> gamma_h;
   std::vector<uint64_t> traj_h;
@@ -347,30 +378,38 @@ fm_status validate_sites(fm_state* s, const int32_t* sites, int32_t n) {
   return FM_OK;
 }
 
-// S_A of trajectory b; enqueues and synchronises.
+// C_A (or U_A^dag U_A when n > N, the same nonzero spectrum) from the n
+// gathered rows in s->aux into M on stream st; only the lower triangle when
+// the eigen-solver reads only that.  Mixed precision (float state): exact
+// digit products on the tensor cores for the large blocks; FP64 otherwise.
+fm_status form_correlation(fm_state* s, cudaStream_t st, int n, z64* M) {
+  const int N = s->N;
+  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  const int m = std::min(n, N);
+  const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
+  if (s->prm.precision == FM_MIXED && hermitian_entropy_lower_only(m)) {
+    CK(exact_gram(st, s->aux, n, N, M, s->xg, s->status_d, &s->launches));
+  } else if (n <= N) {
+    CKL(zgemm<double>(st, n, n, N, OP_N, OP_C, one, s->aux, n, 0, s->aux, n, 0, zero, M, n, 0, 1, fl), 1);
+  } else {
+    CKL(zgemm<double>(st, N, N, n, OP_C, OP_N, one, s->aux, n, 0, s->aux, n, 0, zero, M, N, 0, 1, fl), 1);
+  }
+  return FM_OK;
+}
+
+// S_A of trajectory b; enqueues and synchronises.  Uses its own scratch, so
+// asynchronous entropies still in flight are not disturbed.
 fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, double* S_out) {
   if (n == 0) { *S_out = 0.0; return FM_OK; }
-  if (s->ea_st) CK(cudaStreamSynchronize(s->ea_st));   // shared eigen-solver scratch
-  const int N = s->N;
   CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   s->timer.begin(FM_PH_ENTROPY);
   fm_status r = gather_rows(s, b, s->ee_sites, n);
   if (r) return r;
-  const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
-  const int m = std::min(n, N);
   z64* M = s->G;  // scratch between steps
-  if (s->prm.precision == FM_MIXED && mixed_entropy_gram(s->st, s->aux, n, N, M)) {
-    s->launches += 1;
-  } else if (n <= N) {
-    const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
-    CKL(zgemm<double>(s->st, n, n, N, OP_N, OP_C, one, s->aux, n, 0, s->aux, n, 0, zero, M, n, 0, 1, fl), 1);
-  } else {
-    const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
-    CKL(zgemm<double>(s->st, N, N, n, OP_C, OP_N, one, s->aux, n, 0, s->aux, n, 0, zero, M, N, 0, 1, fl), 1);
-  }
+  if ((r = form_correlation(s, s->st, n, M))) return r;
   int nl = 0;
-  CK(hermitian_entropy(s->st, M, m, s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e, s->ee_lam, s->ee_S,
-                       &nl));
+  CK(hermitian_entropy(s->st, M, std::min(n, s->N), s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e,
+                       s->ee_lam, s->ee_S, &nl));
   s->launches += nl;
   s->timer.end(FM_PH_ENTROPY);
   CK(cudaMemcpyAsync(S_out, s->ee_S, sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -441,59 +480,172 @@ fm_status capture_period(fm_state* s) {
   return r;
 }
 
+// nsteps steps on s->st: eager up to the next period boundary, then whole
+// periods as CUDA-graph replays when graphs are on, eager for the rest
+fm_status step_many(fm_state* s, int32_t nsteps) {
+  fm_status r;
+  int i = 0;
+  const bool graph_ok = !(s->prm.protocol == FM_PROJECTIVE && pm_use_wide(s->L, s->N, s->B));
+  if (s->graphs_on && graph_ok) {
+    const int P = s->graph_period;
+    while (i < nsteps && (s->global_steps % P) != 0) {
+      if ((r = step_once(s))) return r;
+      ++i;
+    }
+    while (nsteps - i >= P) {
+      if (!s->graph_exec && (r = capture_period(s))) return r;
+      CK(cudaGraphLaunch(s->graph_exec, s->st));
+      s->launches += s->graph_launch_count;
+      s->global_steps += P;
+      for (int b = 0; b < s->B; ++b) s->step_h[b] += P;
+      i += P;
+    }
+  }
+  for (; i < nsteps; ++i)
+    if ((r = step_once(s))) return r;
+  return FM_OK;
+}
+
+// Re-target the state to another tile configuration and reorth interval and
+// put every trajectory back in the Neel state at step 0 (the autotuner's loop).
+fm_status retune(fm_state* s, int tile_config, int reorth) {
+  CK(cudaStreamSynchronize(s->st));
+  if (s->graph_exec) {
+    cudaGraphExecDestroy(s->graph_exec);
+    s->graph_exec = nullptr;
+  }
+  s->prm.tile_config = tile_config;
+  s->prm.reorth_interval = reorth;
+  s->graph_period = 2 * reorth;
+  const int L = s->L, N = s->N, B = s->B;
+  if (s->prm.precision == FM_FP64) {
+    CKL(neel_init_z(s->st, s->U, L, N, B, s->occ_d), 1);
+  } else {
+    mixed_free(s->mh);
+    s->mh = nullptr;
+    s->mc.tile_config = tile_config;
+    s->mc.reorth_interval = reorth;
+    s->mc.st = s->st;
+    std::string why;
+    s->mh = mixed_create(&s->mc, &why);
+    if (!s->mh) return fail(s, FM_ECUDA, "mixed re-init: " + why);
+    CKL(neel_init_v(s->st, s->V, s->Vh, s->Vl, L, N, B, s->occ_d), 1);
+  }
+  s->global_steps = 0;
+  for (int b = 0; b < B; ++b) s->step_h[b] = 0;
+  CK(cudaMemsetAsync(s->step_d, 0, 8 * (size_t)B, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return FM_OK;
+}
+
 // ------------------------------------------------------------------ asynchronous entropy
+// The library thread: for each job, wait for its C_A, run the eigen-solver on
+// ea_st, copy S to the pinned slot and record the slot's event.  Launch errors
+// are kept for fm_entropy_wait (the state's error fields belong to the caller).
+void ea_worker(fm_state* s) {
+  cudaSetDevice(s->dev);
+  for (;;) {
+    fm_state::EaJob j;
+    {
+      std::unique_lock<std::mutex> lk(s->ea_mu);
+      s->ea_cv.wait(lk, [s] { return s->ea_stop || !s->ea_q.empty(); });
+      if (s->ea_q.empty()) return;          // stop requested and nothing left
+      j = s->ea_q.front();
+      s->ea_q.pop_front();
+    }
+    cudaError_t e = cudaStreamWaitEvent(s->ea_st, s->ea_M_ready[j.ring], 0);
+    const char* what = "cudaStreamWaitEvent";
+    if (e == cudaSuccess) {
+      if (j.m == 0) {
+        e = cudaMemsetAsync(s->ea_S + j.slot, 0, sizeof(double), s->ea_st);
+        what = "cudaMemsetAsync";
+      } else {
+        int nl = 0;
+        e = hermitian_entropy(s->ea_st, s->ea_M + (int64_t)j.ring * s->N * s->N, j.m, s->ea_vb, s->ea_wb, s->ea_pb,
+                              nullptr, s->ea_d, s->ea_e, s->ea_lam, s->ea_S + j.slot, &nl);
+        s->ea_launches += nl;
+        what = "eigen-solver launch";
+      }
+    }
+    if (e == cudaSuccess) {
+      e = cudaMemcpyAsync(s->ea_host + j.slot, s->ea_S + j.slot, sizeof(double), cudaMemcpyDeviceToHost, s->ea_st);
+      what = "cudaMemcpyAsync";
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s->ea_M_free[j.ring], s->ea_st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ea_done[j.slot], s->ea_st);
+    std::lock_guard<std::mutex> lk(s->ea_mu);
+    if (e != cudaSuccess && !s->ea_failed) {
+      s->ea_failed = true;
+      s->ea_errmsg = std::string("asynchronous entropy: ") + what + ": " + cudaGetErrorString(e);
+    }
+    s->ea_issued = j.t + 1;
+    s->ea_cv.notify_all();
+  }
+}
+
 fm_status ea_setup(fm_state* s) {
   if (s->ea_st) return FM_OK;
-  CK(cudaStreamCreateWithFlags(&s->ea_st, cudaStreamNonBlocking));
-  CK(cudaEventCreateWithFlags(&s->ea_state_ev, cudaEventDisableTiming));
-  CK(cudaEventCreateWithFlags(&s->ea_gather_ev, cudaEventDisableTiming));
+  int least = 0, greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  CK(cudaStreamCreateWithPriority(&s->ea_st, cudaStreamNonBlocking, least));
+  CK(cudaStreamCreateWithPriority(&s->hp_st, cudaStreamNonBlocking, greatest));
+  CK(cudaEventCreateWithFlags(&s->hp_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->hp_out, cudaEventDisableTiming));
+  for (int i = 0; i < kEaRing; ++i) {
+    CK(cudaEventCreateWithFlags(&s->ea_M_ready[i], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&s->ea_M_free[i], cudaEventDisableTiming));
+  }
   for (int i = 0; i < kAsyncSlots; ++i) CK(cudaEventCreateWithFlags(&s->ea_done[i], cudaEventDisableTiming));
   CK(cudaHostAlloc((void**)&s->ea_host, kAsyncSlots * sizeof(double), cudaHostAllocDefault));
+  s->ea_stop = false;
+  s->ea_thread = std::thread(ea_worker, s);
+  return FM_OK;
+}
+
+// Block until the library thread has enqueued everything of tickets < t.
+void ea_wait_issued(fm_state* s, int64_t t) {
+  std::unique_lock<std::mutex> lk(s->ea_mu);
+  s->ea_cv.wait(lk, [s, t] { return s->ea_issued >= t; });
+}
+
+fm_status ea_check(fm_state* s) {
+  std::lock_guard<std::mutex> lk(s->ea_mu);
+  if (s->ea_failed) return fail(s, FM_ECUDA, s->ea_errmsg);
   return FM_OK;
 }
 
 fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n, int64_t* ticket) {
   fm_status r = ea_setup(s);
   if (r) return r;
+  if ((r = ea_check(s))) return r;
   const int64_t t = s->ea_next;
   const int slot = (int)(t % kAsyncSlots);
-  if (t >= kAsyncSlots) CK(cudaEventSynchronize(s->ea_done[slot]));    // slot reuse
-  cudaStream_t st = s->ea_st;
-  const int N = s->N, L = s->L;
-  // the state as queued so far on the caller's stream
-  CK(cudaEventRecord(s->ea_state_ev, s->st));
-  CK(cudaStreamWaitEvent(st, s->ea_state_ev, 0));
-  if (n == 0) {
-    CK(cudaMemsetAsync(s->ea_S + slot, 0, sizeof(double), st));
-  } else {
-    CK(cudaMemcpyAsync(s->ea_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, st));
-    if (s->prm.precision == FM_FP64) {
-      CKL(gather_rows_z(st, s->U + (int64_t)b * L * N, L, N, s->ea_sites, n, s->ea_rows), 1);
-    } else {
-      CKL(gather_rows_v(st, s->V + (int64_t)b * 2 * L * N, L, N, s->ea_sites, n, s->ea_rows), 1);
-    }
+  const int ring = (int)(t % kEaRing);
+  const int N = s->N;
+  const int m = std::min(n, N);
+  if (t >= kAsyncSlots) {                                   // slot reuse: the oldest result must be back
+    ea_wait_issued(s, t - kAsyncSlots + 1);
+    CK(cudaEventSynchronize(s->ea_done[slot]));
   }
-  // the caller's stream may overwrite the state only after the rows are out
-  CK(cudaEventRecord(s->ea_gather_ev, st));
-  CK(cudaStreamWaitEvent(s->st, s->ea_gather_ev, 0));
-  if (n > 0) {
-    const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
-    const int m = std::min(n, N);
-    const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
-    if (n <= N) {
-      CKL(zgemm<double>(st, n, n, N, OP_N, OP_C, one, s->ea_rows, n, 0, s->ea_rows, n, 0, zero, s->ea_M, n, 0, 1, fl),
-          1);
-    } else {
-      CKL(zgemm<double>(st, N, N, n, OP_C, OP_N, one, s->ea_rows, n, 0, s->ea_rows, n, 0, zero, s->ea_M, N, 0, 1, fl),
-          1);
+  z64* M = s->ea_M + (int64_t)ring * N * N;
+  if (m > 0) {
+    // C_A buffer reuse: the eigen-solve of ticket t - kEaRing must be queued before
+    // the caller's stream may wait for it to release the buffer
+    if (t >= kEaRing) {
+      ea_wait_issued(s, t - kEaRing + 1);
+      CK(cudaStreamWaitEvent(s->st, s->ea_M_free[ring], 0));
     }
-    int nl = 0;
-    CK(hermitian_entropy(st, s->ea_M, m, s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e, s->ee_lam,
-                         s->ea_S + slot, &nl));
-    s->launches += nl;
+    // rows of A and C_A, in order with the steps on the caller's stream
+    CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+    if ((r = gather_rows(s, b, s->ee_sites, n))) return r;
+    if ((r = form_correlation(s, s->st, n, M))) return r;
   }
-  CK(cudaMemcpyAsync(s->ea_host + slot, s->ea_S + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaEventRecord(s->ea_done[slot], st));
+  CK(cudaEventRecord(s->ea_M_ready[ring], s->st));
+  {
+    std::lock_guard<std::mutex> lk(s->ea_mu);
+    s->ea_q.push_back(fm_state::EaJob{t, slot, ring, m});
+  }
+  s->ea_cv.notify_all();
   s->ea_next = t + 1;
   *ticket = t;
   return FM_OK;
@@ -539,14 +691,20 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ee_d = (double*)(w + pl.ee_d); s->ee_e = (double*)(w + pl.ee_e); s->ee_lam = (double*)(w + pl.ee_lam);
   s->ee_S = (double*)(w + pl.ee_S); s->ee_max = (double*)(w + pl.ee_max); s->ee_sites = (int*)(w + pl.ee_sites);
   s->chk_cols = (z64*)(w + pl.chk_cols); s->chk_G = (z64*)(w + pl.chk_G);
-  s->ea_M = (z64*)(w + pl.ea_M); s->ea_rows = (z64*)(w + pl.ea_rows);
-  s->ea_sites = (int*)(w + pl.ea_sites); s->ea_S = (double*)(w + pl.ea_S);
-  s->ea_st = nullptr; s->ea_state_ev = s->ea_gather_ev = nullptr; s->ea_host = nullptr; s->ea_next = 0;
+  s->ea_M = (z64*)(w + pl.ea_M);
+  s->ea_vb = (z64*)(w + pl.ea_vb); s->ea_wb = (z64*)(w + pl.ea_wb); s->ea_pb = (z64*)(w + pl.ea_pb);
+  s->ea_d = (double*)(w + pl.ea_d); s->ea_e = (double*)(w + pl.ea_e); s->ea_lam = (double*)(w + pl.ea_lam);
+  s->ea_S = (double*)(w + pl.ea_S);
+  s->ea_st = s->hp_st = nullptr; s->hp_in = s->hp_out = nullptr; s->ea_host = nullptr; s->ea_next = 0;
+  for (int i = 0; i < kEaRing; ++i) s->ea_M_ready[i] = s->ea_M_free[i] = nullptr;
+  s->ea_issued = 0; s->ea_stop = false; s->ea_failed = false; s->ea_launches = 0;
+  if (cudaGetDevice(&s->dev) != cudaSuccess) { delete s; return FM_ECUDA; }
   s->pmw = w + pl.pmw;
   for (int i = 0; i < kAsyncSlots; ++i) s->ea_done[i] = nullptr;
   s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
   s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
   s->mixed_extra = nullptr;
+  s->xg = nullptr;
   s->mh = nullptr;
   if (p->precision == FM_FP64) {
     s->U = (z64*)(w + pl.U); s->U2 = (z64*)(w + pl.U2); s->P = (z64*)(w + pl.P); s->aux = s->U2;
@@ -555,7 +713,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
     s->Vh = (__half*)(w + pl.Vh); s->Vl = (__half*)(w + pl.Vl);
     s->Ah = (__half*)(w + pl.Ah); s->Al = (__half*)(w + pl.Al);
     s->Th = (__half*)(w + pl.Th); s->Tl = (__half*)(w + pl.Tl);
-    s->aux = (z64*)(w + pl.aux); s->mixed_extra = w + pl.mixed_extra;
+    s->aux = (z64*)(w + pl.aux); s->mixed_extra = w + pl.mixed_extra; s->xg = w + pl.xg;
   }
   s->timer.st = s->st;
   s->gamma_h.assign(s->B, p->gamma);
@@ -604,6 +762,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       MixedCtx& c = s->mc;
       c.st = s->st; c.Lx = s->Lx; c.Ly = s->Ly; c.L = s->L; c.N = s->N; c.B = s->B;
       c.protocol = p->protocol; c.reorth_interval = p->reorth_interval; c.dt = p->dt; c.seed = p->seed;
+      c.tile_config = p->tile_config;
       c.global_step = 0; c.V = s->V; c.V2 = s->V2; c.Vh = s->Vh; c.Vl = s->Vl; c.Ah = s->Ah; c.Al = s->Al;
       c.Th = s->Th; c.Tl = s->Tl; c.G = s->G; c.R = s->R; c.T = s->T; c.Dinv = s->Dinv; c.X = s->X;
       c.gamma = s->gamma_d; c.traj = s->traj_d; c.step = s->step_d; c.status = s->status_d;
@@ -632,26 +791,27 @@ fm_status fm_step(fm_state* s, int32_t nsteps) {
   fm_status r = check_state(s);
   if (r) return r;
   if (nsteps < 0) return fail(s, FM_EINVAL, "nsteps < 0");
-  int i = 0;
-  const bool graph_ok = !(s->prm.protocol == FM_PROJECTIVE && pm_use_wide(s->L, s->N, s->B));
-  if (s->graphs_on && graph_ok) {
-    const int P = s->graph_period;
-    while (i < nsteps && (s->global_steps % P) != 0) {
-      if ((r = step_once(s))) return r;
-      ++i;
-    }
-    while (nsteps - i >= P) {
-      if (!s->graph_exec && (r = capture_period(s))) return r;
-      CK(cudaGraphLaunch(s->graph_exec, s->st));
-      s->launches += s->graph_launch_count;
-      s->global_steps += P;
-      for (int b = 0; b < s->B; ++b) s->step_h[b] += P;
-      i += P;
-    }
+  if (nsteps == 0) return FM_OK;
+  // once asynchronous entropies exist, the steps run on the high-priority
+  // stream, ordered after and before the caller's stream by two events
+  cudaStream_t user = s->st;
+  const bool bridge = s->hp_st != nullptr;
+  if (bridge) {
+    CK(cudaEventRecord(s->hp_in, user));
+    CK(cudaStreamWaitEvent(s->hp_st, s->hp_in, 0));
+    s->st = s->hp_st;
+    s->timer.st = s->hp_st;
   }
-  for (; i < nsteps; ++i)
-    if ((r = step_once(s))) return r;
-  return FM_OK;
+  r = step_many(s, nsteps);
+  if (bridge) {
+    s->st = user;
+    s->timer.st = user;
+    if (s->prm.precision != FM_FP64) s->mc.st = user;
+    cudaError_t e = cudaEventRecord(s->hp_out, s->hp_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, s->hp_out, 0);
+    if (e != cudaSuccess && r == FM_OK) r = fail(s, FM_ECUDA, std::string("step stream bridge: ") + cudaGetErrorString(e));
+  }
+  return r;
 }
 
 fm_status fm_set_graphs(fm_state* s, int32_t enable) {
@@ -727,6 +887,8 @@ fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out) {
   if (!S_out || ticket < 0 || ticket >= s->ea_next || ticket < s->ea_next - kAsyncSlots)
     return fail(s, FM_EINVAL, "unknown or expired ticket");
   const int slot = (int)(ticket % kAsyncSlots);
+  ea_wait_issued(s, ticket + 1);
+  if ((r = ea_check(s))) return r;
   CK(cudaEventSynchronize(s->ea_done[slot]));
   *S_out = s->ea_host[slot];
   return sync_and_check(s);
@@ -917,17 +1079,102 @@ fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts) {
   return FM_OK;
 }
 
-int64_t fm_kernel_launches(const fm_state* s) { return s ? s->launches : 0; }
+fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, void* cuda_stream, int32_t steps,
+                      int32_t max_reorth, double ortho_tol, int32_t use_graphs, fm_tuning* out) {
+  if (!p || !out || steps < 1 || max_reorth < 1 || !(ortho_tol > 0.0)) return FM_EINVAL;
+  fm_params p0 = *p;
+  p0.tile_config = 0;
+  p0.reorth_interval = 1;
+  fm_state* s = nullptr;
+  fm_status r = fm_init_state(&p0, d_workspace, ws_bytes, cuda_stream, &s);
+  if (r) return r;
+  const bool mixed = p->precision == FM_MIXED;
+  std::vector<int> tiles;
+  if (mixed) {
+    for (int bn : {1, 2}) {
+      if (bn == 2 && s->N % 256) continue;
+      for (int g : {2, 3, 4}) tiles.push_back(bn | (g << 2));
+    }
+  } else {
+    tiles.push_back(0);
+  }
+  std::vector<int> cols;
+  for (int i = 0; i < std::min(s->N, 64); ++i) cols.push_back((int)((int64_t)i * s->N / std::min(s->N, 64)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fm_tuning best{0, 1, 0.0, 0.0, 0, 0}, best1{0, 1, 0.0, 0.0, 0, 0};
+  bool have = false, have1 = false;
+  int tried = 0, rejected = 0;
+  do {
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { r = FM_ECUDA; break; }
+    for (int k = 1; k <= max_reorth && r == FM_OK; k *= 2)
+      for (int tc : tiles) {
+        if ((r = retune(s, tc, k))) break;
+        if ((r = fm_set_graphs(s, use_graphs ? 1 : 0))) break;
+        const int period = 2 * k;
+        const int nt = ((steps + period - 1) / period) * period;
+        if ((r = fm_step(s, period))) break;                     // warm-up (and graph capture)
+        if (cudaEventRecord(e0, s->st) != cudaSuccess) { r = fail(s, FM_ECUDA, "event"); break; }
+        if ((r = fm_step(s, nt))) break;
+        if (cudaEventRecord(e1, s->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          r = fail(s, FM_ECUDA, "event");
+          break;
+        }
+        if ((r = sync_and_check(s))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double worst = 0.0;
+        for (int i = 0; i < period && r == FM_OK; ++i) {
+          if ((r = fm_step(s, 1))) break;
+          for (int b : {0, s->B - 1}) {
+            double e = 0.0;
+            if ((r = fm_orthonormality_error(s, b, cols.data(), (int)cols.size(), &e))) break;
+            worst = std::max(worst, e);
+          }
+        }
+        if (r) break;
+        fm_tuning cand{tc, k, (double)ms / nt, worst, 0, 0};
+        ++tried;
+        if (k == 1 && (!have1 || cand.ms_per_step < best1.ms_per_step)) { best1 = cand; have1 = true; }
+        if (worst <= ortho_tol) {
+          if (!have || cand.ms_per_step < best.ms_per_step) { best = cand; have = true; }
+        } else {
+          ++rejected;
+        }
+      }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  fm_destroy(s);
+  if (r) return r;
+  *out = have ? best : best1;
+  out->tried = tried;
+  out->rejected = rejected;
+  return FM_OK;
+}
+
+int64_t fm_kernel_launches(const fm_state* s) { return s ? s->launches + s->ea_launches.load() : 0; }
 
 const char* fm_last_error(const fm_state* s) { return s ? s->err.c_str() : "null state"; }
 
 void fm_destroy(fm_state* s) {
   if (!s) return;
   if (s->ea_st) {
+    {
+      std::lock_guard<std::mutex> lk(s->ea_mu);
+      s->ea_stop = true;
+    }
+    s->ea_cv.notify_all();
+    if (s->ea_thread.joinable()) s->ea_thread.join();   // the thread drains its queue first
     cudaStreamSynchronize(s->ea_st);
+    cudaStreamSynchronize(s->hp_st);
     cudaStreamDestroy(s->ea_st);
-    cudaEventDestroy(s->ea_state_ev);
-    cudaEventDestroy(s->ea_gather_ev);
+    cudaStreamDestroy(s->hp_st);
+    cudaEventDestroy(s->hp_in);
+    cudaEventDestroy(s->hp_out);
+    for (int i = 0; i < kEaRing; ++i) {
+      cudaEventDestroy(s->ea_M_ready[i]);
+      cudaEventDestroy(s->ea_M_free[i]);
+    }
     for (int i = 0; i < kAsyncSlots; ++i) cudaEventDestroy(s->ea_done[i]);
     cudaFreeHost(s->ea_host);
   }

@@ -29,7 +29,9 @@ struct Cfg {
   static constexpr uint32_t A_BYTES = BM * BK * 2;
   static constexpr uint32_t B_BYTES = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int NBUF = CHUNKED ? 2 : 1;       // TMEM accumulator sets
+  // TMEM accumulator sets: two (the epilogue of one tile or chunk overlaps the
+  // MMAs of the next) whenever both fit in the 512 columns
+  static constexpr int NBUF = (CHUNKED || BN <= 128) ? 2 : 1;
   static constexpr uint32_t TMEM_COLS = (NBUF * 2 * BN <= 256) ? 256 : 512;
   static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   static_assert(NBUF * 2 * BN <= 512, "TMEM holds 512 columns");
@@ -275,13 +277,13 @@ __global__ void __launch_bounds__(256, 1)
           emit<BN, MODE>(p, ti, r, c0, d, rowsum);
         }
       } else {
-        const int buf = 0;
-        const uint32_t bpar = cbuf & 1u;
+        const int buf = (int)(cbuf % C::NBUF);
+        const uint32_t bpar = (cbuf / C::NBUF) & 1u;
         if (!mbar_wait(&tmem_full[buf], bpar, abort_flag)) { ok = false; break; }
         tc_fence_after();
         for (int c0 = 0; c0 < BN; c0 += 32) {
           uint32_t a0[32], a1[32];
-          const uint32_t tl = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0;
+          const uint32_t tl = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * 2 * BN) + (uint32_t)c0;
           tmem_ld32(tl, a0);
           tmem_ld32(tl + BN, a1);
           tmem_wait_ld();
@@ -356,7 +358,7 @@ cudaError_t configure_all() {
       (e = set_smem<128, 1, MODE_PLAIN>()) || (e = set_smem<256, 0, MODE_PROP>()) ||
       (e = set_smem<128, 0, MODE_PROP>()) || (e = set_smem<256, 0, MODE_GRAM>()) ||
       (e = set_smem<128, 0, MODE_GRAM>()) || (e = set_smem<128, 1, MODE_TRMM>()) ||
-      (e = set_smem<128, 0, MODE_TRMM>()))
+      (e = set_smem<128, 0, MODE_TRMM>()) || (e = set_smem<256, 0, MODE_TRMM>()))
     return e;
   done = cudaSuccess;
   return done;
@@ -393,9 +395,9 @@ cudaError_t launch(cudaStream_t st, int BN, const CUtensorMap& Ah, const CUtenso
       return BN == 256 ? launch_one<256, 0, MODE_GRAM>(st, Ah, Al, Bh, Bl, p, grid)
                        : launch_one<128, 0, MODE_GRAM>(st, Ah, Al, Bh, Bl, p, grid);
     case MODE_TRMM:
-      if (BN != 128) return cudaErrorInvalidValue;
-      return ch ? launch_one<128, 1, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid)
-                : launch_one<128, 0, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid);
+      if (ch) return launch_one<128, 1, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid);
+      return BN == 256 ? launch_one<256, 0, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid)
+                       : launch_one<128, 0, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid);
   }
   return cudaErrorInvalidValue;
 }

@@ -112,4 +112,14 @@ constexpr int64_t hermitian_entropy_pbuf(int m) {
 // the lower triangle alone is enough for this m
 inline bool hermitian_entropy_lower_only(int m) { return m > 256; }
 
+// ---- exact-product Gram of a float-valued block on the tensor cores (gram_exact.cu)
+// X: n x N complex128 block (column-major, ld = n) whose entries are floats.
+// M (m x m, m = min(n, N), column-major): lower triangle of X X^dag (n <= N)
+// or of X^T conj(X) (n > N), exact for the 28-bit truncation of every row of
+// [Re | Im] relative to its largest entry.  scratch: exact_gram_scratch_bytes(nmax, N)
+// device bytes, n <= nmax.  Five launches on st.
+size_t exact_gram_scratch_bytes(int nmax, int N);
+cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void* scratch, int* status,
+                       int64_t* launches);
+
 }  // namespace fm

@@ -20,11 +20,21 @@ namespace fm {
 
 namespace {
 
-int pick_bn(int N) { return (N % 256 == 0) ? 256 : 128; }
+// tile width of the propagation and Gram products, raster group height (fm.h, FM_TILE_*)
+int pick_bn(int N, int tile_config) {
+  const int c = tile_config & 3;
+  if (c == 1) return 128;
+  if (c == 2) return 256;
+  return (N % 256 == 0) ? 256 : 128;
+}
+int pick_gm(int tile_config) {
+  const int g = (tile_config >> 2) & 7;
+  return g ? (1 << (g + 1)) : 16;
+}
 
 struct Scratch {
   size_t total = 0;
-  size_t tiles_prop, tiles_gram, tiles_trmm, urm_h, urm_l;
+  size_t tiles_prop, tiles_gram, tiles_trmm, tiles_trmm2, urm_h, urm_l;
   size_t ca_h, ca_l, cb_h, cb_l, cd, xs;   // complex tensor GEMM helper (Cholesky recursion)
   size_t gf, rf, tf, dinvf, xf, diag;     // complex64 Gram / factor / inverse, FP64 Gram diagonal
   size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
@@ -33,13 +43,14 @@ struct Scratch {
 Scratch scratch_plan(int Lx, int Ly, int B) {
   Scratch s;
   const int64_t L = (int64_t)Lx * Ly, N = L / 2;
-  const int BN = pick_bn((int)N);
+  const int BN = 128;                              // the longer tile lists of either width
   const int64_t n_prop = (2 * L / tc::BM) * (B * N / BN);
   const int64_t n_gram = (int64_t)B * 2 * (N / tc::BM) * (N / BN);
   const int64_t n_trmm = (int64_t)B * (L / tc::BM) * (2 * N / 128);
   s.tiles_prop = s.take(n_prop * 16);
   s.tiles_gram = s.take(n_gram * 16);
   s.tiles_trmm = s.take(n_trmm * 16);
+  s.tiles_trmm2 = s.take(n_trmm / 2 * 16);        // second pass: 256-wide tiles
   s.urm_h = s.take((int64_t)B * L * 2 * N * 2);
   s.urm_l = s.take((int64_t)B * L * 2 * N * 2);
   const int64_t md = N / 2 + 128;                  // largest block the recursion multiplies
@@ -220,8 +231,8 @@ __global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int 
 
 struct MixedHost {
   int BN;
-  int n_prop, n_gram, n_trmm;
-  int4 *tiles_prop, *tiles_gram, *tiles_trmm;
+  int n_prop, n_gram, n_trmm, n_trmm2;
+  int4 *tiles_prop, *tiles_gram, *tiles_trmm, *tiles_trmm2;
   __half *urm_h, *urm_l;
   __half *ca_h, *ca_l, *cb_h, *cb_l;
   float* cd;
@@ -232,12 +243,21 @@ struct MixedHost {
   CUtensorMap prop_Ah, prop_Al, prop_Bh, prop_Bl;
   CUtensorMap gram_Ah, gram_Al, gram_Bh, gram_Bl;
   CUtensorMap trmm_Ah, trmm_Al, trmm_Bh, trmm_Bl;
+  CUtensorMap trmm2_Bh, trmm2_Bl;   // 256-row boxes of the factor planes (second pass)
 };
 
-bool mixed_supported(int Lx, int Ly, int batch, std::string* why) {
+bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* why) {
   const int64_t L = (int64_t)Lx * Ly;
   if (L % 256 != 0) {
     *why = "mixed precision needs L = Lx*Ly divisible by 256 (N a multiple of 128)";
+    return false;
+  }
+  if ((tile_config & ~0x1f) || (tile_config & 3) == 3) {
+    *why = "unknown tile_config bits";
+    return false;
+  }
+  if ((tile_config & 3) == 2 && (L / 2) % 256 != 0) {
+    *why = "tile width 256 needs N a multiple of 256";
     return false;
   }
   if ((int64_t)batch * L > (1ll << 31) / 4) {
@@ -258,13 +278,15 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   }
   MixedHost* h = new MixedHost();
   const int L = c->L, N = c->N, B = c->B;
-  h->BN = pick_bn(N);
+  h->BN = pick_bn(N, c->tile_config);
   const int BN = h->BN;
+  const int GM = pick_gm(c->tile_config);
   Scratch sp = scratch_plan(c->Lx, c->Ly, B);
   char* base = (char*)c->extra;
   h->tiles_prop = (int4*)(base + sp.tiles_prop);
   h->tiles_gram = (int4*)(base + sp.tiles_gram);
   h->tiles_trmm = (int4*)(base + sp.tiles_trmm);
+  h->tiles_trmm2 = (int4*)(base + sp.tiles_trmm2);
   h->urm_h = (__half*)(base + sp.urm_h);
   h->urm_l = (__half*)(base + sp.urm_l);
   h->ca_h = (__half*)(base + sp.ca_h);
@@ -280,15 +302,19 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   h->dinvf = (c32*)(base + sp.dinvf);
   h->xf = (c32*)(base + sp.xf);
   h->diag = (double*)(base + sp.diag);
-  std::vector<int4> tp = tc::tile_list(2 * L / tc::BM, B * N / BN, 1, 1, false, BN, 16);
-  std::vector<int4> tg = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, 16);
-  std::vector<int4> tt = tc::tile_list(L / tc::BM, 2 * N / 128, B, 1, false, 128, 16);
+  std::vector<int4> tp = tc::tile_list(2 * L / tc::BM, B * N / BN, 1, 1, false, BN, GM);
+  std::vector<int4> tg = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, GM);
+  std::vector<int4> tt = tc::tile_list(L / tc::BM, 2 * N / 128, B, 1, false, 128, GM);
+  std::vector<int4> tt2 = tc::tile_list(L / tc::BM, 2 * N / 256, B, 1, false, 256, GM);
   h->n_prop = (int)tp.size();
   h->n_gram = (int)tg.size();
   h->n_trmm = (int)tt.size();
+  h->n_trmm2 = (int)tt2.size();
   bool ok = cudaMemcpyAsync(h->tiles_prop, tp.data(), tp.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
             cudaMemcpyAsync(h->tiles_gram, tg.data(), tg.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
             cudaMemcpyAsync(h->tiles_trmm, tt.data(), tt.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
+            cudaMemcpyAsync(h->tiles_trmm2, tt2.data(), tt2.size() * 16, cudaMemcpyHostToDevice, c->st) ==
+                cudaSuccess &&
             cudaStreamSynchronize(c->st) == cudaSuccess;
   if (!ok) { *why = "tile upload"; delete h; return nullptr; }
   const uint64_t L2 = 2 * (uint64_t)L, N2 = 2 * (uint64_t)N;
@@ -303,7 +329,9 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
        tc::make_kmajor_map(&h->trmm_Ah, h->urm_h, N2, (uint64_t)B * L, N2, tc::BM) &&
        tc::make_kmajor_map(&h->trmm_Al, h->urm_l, N2, (uint64_t)B * L, N2, tc::BM) &&
        tc::make_kmajor_map(&h->trmm_Bh, c->Th, N2, (uint64_t)B * N2, N2, 128) &&
-       tc::make_kmajor_map(&h->trmm_Bl, c->Tl, N2, (uint64_t)B * N2, N2, 128);
+       tc::make_kmajor_map(&h->trmm_Bl, c->Tl, N2, (uint64_t)B * N2, N2, 128) &&
+       tc::make_kmajor_map(&h->trmm2_Bh, c->Th, N2, (uint64_t)B * N2, N2, 256) &&
+       tc::make_kmajor_map(&h->trmm2_Bl, c->Tl, N2, (uint64_t)B * N2, N2, 256);
   if (!ok) { *why = "cuTensorMapEncodeTiled failed"; delete h; return nullptr; }
   return h;
 }
@@ -441,10 +469,12 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
                                                                                   h->urm_l);
   MCK(cudaGetLastError());
   c->timer->end(FM_PH_CHOLESKY);
+  // first pass: 128-wide tiles, fp32 register accumulation every 2 K-blocks
+  // (two TMEM sets); second pass: 256-wide tiles accumulated in TMEM
   p = base_params(c, h);
   p.mode = tc::MODE_TRMM;
-  p.ntiles = h->n_trmm;
-  p.tiles = h->tiles_trmm;
+  p.ntiles = first ? h->n_trmm : h->n_trmm2;
+  p.tiles = first ? h->tiles_trmm : h->tiles_trmm2;
   p.kblocks = 2 * N / tc::BK;
   p.tri_k = 1;
   p.a_rows_per_b = L;
@@ -455,7 +485,8 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
   p.in_f = c->V;
   p.chunk_kb = first ? 2 : 0;
   c->timer->begin(FM_PH_TRMM);
-  MCK(tc::launch(c->st, 128, h->trmm_Ah, h->trmm_Al, h->trmm_Bh, h->trmm_Bl, p, grid));
+  if (first) MCK(tc::launch(c->st, 128, h->trmm_Ah, h->trmm_Al, h->trmm_Bh, h->trmm_Bl, p, grid));
+  else MCK(tc::launch(c->st, 256, h->trmm_Ah, h->trmm_Al, h->trmm2_Bh, h->trmm2_Bl, p, grid));
   c->timer->end(FM_PH_TRMM);
   std::swap(c->V, c->V2);
   return FM_OK;
@@ -518,8 +549,6 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
   MCK(bump_steps(c->st, c->step, B));
   return FM_OK;
 }
-
-bool mixed_entropy_gram(cudaStream_t, const z64*, int, int, z64*) { return false; }
 
 }  // namespace fm
 

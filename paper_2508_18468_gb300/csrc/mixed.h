@@ -14,6 +14,7 @@ struct MixedCtx {
   cudaStream_t st;
   int Lx, Ly, L, N, B;
   int protocol, reorth_interval;
+  int tile_config;         // fm_params.tile_config (validated)
   double dt;
   uint64_t seed;
   int64_t global_step;
@@ -35,12 +36,10 @@ struct MixedCtx {
 
 struct MixedHost;          // tensor maps and tile lists of one state
 
-bool mixed_supported(int Lx, int Ly, int batch, std::string* why);
+bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* why);
 size_t mixed_scratch_bytes(int Lx, int Ly, int batch);
 MixedHost* mixed_create(MixedCtx* c, std::string* why);   // uploads tile lists, encodes tensor maps
 void mixed_free(MixedHost* h);
 int mixed_step(MixedHost* h, MixedCtx* c);               // returns an fm_status value
-// M = Gram of the gathered rows (n x N complex128) on the tensor cores; false = not handled here.
-bool mixed_entropy_gram(cudaStream_t st, const z64* rows, int n, int N, z64* M);
 
 }  // namespace fm

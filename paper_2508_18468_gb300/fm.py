@@ -24,7 +24,7 @@ class fm_params(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("protocol", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("reorth_interval", ctypes.c_int32), ("event_capacity", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("J", ctypes.c_double), ("dt", ctypes.c_double),
+                ("tile_config", ctypes.c_int32), ("J", ctypes.c_double), ("dt", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64), ("traj_id", ctypes.c_uint64)]
 
 
@@ -32,6 +32,12 @@ class fm_event(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("traj", ctypes.c_int32), ("site", ctypes.c_int32),
                 ("u", ctypes.c_double), ("p", ctypes.c_double), ("outcome", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
+
+
+class fm_tuning(ctypes.Structure):
+    _fields_ = [("tile_config", ctypes.c_int32), ("reorth_interval", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_double), ("ortho_err", ctypes.c_double),
+                ("tried", ctypes.c_int32), ("rejected", ctypes.c_int32)]
 
 
 class FmError(RuntimeError):
@@ -74,6 +80,7 @@ def _load():
         "fm_destroy": (None, [vp]),
         "fm_version": (ctypes.c_char_p, []),
         "fm_entropy_noalloc": (i32, [vp, i32, i32, P(i32), i32, vp, vp]),
+        "fm_autotune": (i32, [P(fm_params), vp, sz, vp, i32, i32, dbl, i32, P(fm_tuning)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -91,9 +98,9 @@ def _i32_array(x):
 
 
 def make_params(Lx, Ly=1, batch=1, protocol=FM_PROJECTIVE, precision=FM_FP64, reorth_interval=1,
-                event_capacity=0, J=1.0, dt=0.05, gamma=0.5, seed=0, traj_id=0):
+                event_capacity=0, J=1.0, dt=0.05, gamma=0.5, seed=0, traj_id=0, tile_config=0):
     return fm_params(Lx=Lx, Ly=Ly, batch=batch, protocol=protocol, precision=precision,
-                     reorth_interval=reorth_interval, event_capacity=event_capacity, reserved=0,
+                     reorth_interval=reorth_interval, event_capacity=event_capacity, tile_config=tile_config,
                      J=J, dt=dt, gamma=gamma, seed=seed, traj_id=traj_id)
 
 
@@ -114,6 +121,27 @@ def fm_entropy_noalloc(d_U, L, N, sites, d_S, stream=None):
     a, p = _i32_array(sites)
     return int(lib.fm_entropy_noalloc(ctypes.c_void_p(d_U), int(L), int(N), p, int(a.size), ctypes.c_void_p(d_S),
                                       ctypes.c_void_p(stream)))
+
+
+def autotune(params, steps=4, max_reorth=4, ortho_tol=1e-6, use_graphs=True, device="cuda", stream=None):
+    """fm_autotune on a scratch workspace; returns a dict of the chosen settings and their measurements."""
+    import torch
+    nbytes = fm_workspace_bytes(params)
+    if nbytes == 0:
+        raise FmError(FM_EINVAL, "invalid parameters")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    if stream is None:
+        stream = torch.cuda.current_stream(ws.device)
+    out = fm_tuning()
+    code = lib.fm_autotune(ctypes.byref(params), ctypes.c_void_p(ws.data_ptr()), nbytes,
+                           ctypes.c_void_p(stream.cuda_stream), int(steps), int(max_reorth), float(ortho_tol),
+                           1 if use_graphs else 0, ctypes.byref(out))
+    del ws
+    if code != FM_OK:
+        raise FmError(code, "fm_autotune failed")
+    return {"tile_config": out.tile_config, "reorth_interval": out.reorth_interval,
+            "ms_per_step": out.ms_per_step, "ortho_err": out.ortho_err, "tried": out.tried,
+            "rejected": out.rejected}
 
 
 class Trajectories:

@@ -14,6 +14,11 @@ slot's computation is independent of the others (tests check this).  With
 ``reorth_interval > 1`` the second re-orthonormalisation pass follows the
 group's step count, so results then agree only within the mixed-precision
 tolerance rather than bitwise.
+
+With ``autotune=True`` each (L, protocol) group takes the tile configuration
+and re-orthonormalisation interval that ``fm_autotune`` measures fastest for
+its slot count under the orthonormality bar; ``pretune`` runs those searches
+before serving so that no request waits for one.
 """
 import collections
 import time
@@ -61,12 +66,13 @@ def workspace_bytes(L, protocol, slots, precision, reorth_interval):
 class Group:
     """One fm_state of `slots` trajectories of the same (L, protocol), on its own stream."""
 
-    def __init__(self, L, protocol, slots, precision, seed, reorth_interval, graphs=True):
+    def __init__(self, L, protocol, slots, precision, seed, reorth_interval, graphs=True, tile_config=0):
         import torch
         self.L, self.protocol, self.slots = L, protocol, slots
         prot = fm.FM_HOMODYNE if protocol == "homodyne" else fm.FM_PROJECTIVE
         self.params = fm.make_params(L, batch=slots, protocol=prot, precision=precision,
-                                     reorth_interval=reorth_interval, gamma=0.0, seed=seed)
+                                     reorth_interval=reorth_interval, gamma=0.0, seed=seed,
+                                     tile_config=tile_config)
         self.bytes = fm.fm_workspace_bytes(self.params)
         self.period = 2 * reorth_interval if graphs else 1
         self.stream = torch.cuda.Stream()
@@ -118,7 +124,7 @@ class Server:
     """Admit, step and retire requests until all are answered."""
 
     def __init__(self, memory_budget=64 << 30, slots=8, precision=fm.FM_MIXED, seed=None, reorth_interval=1,
-                 graphs=True, group_factory=Group, size_of=workspace_bytes):
+                 graphs=True, group_factory=Group, size_of=workspace_bytes, autotune=False, tuner=None):
         self.budget = memory_budget
         self.slots = slots
         self.precision = precision
@@ -129,13 +135,37 @@ class Server:
         self.size_of = size_of
         self.groups = {}
         self.used = 0
+        self.autotune = autotune
+        self.tuner = tuner if tuner is not None else self._fm_tuner
+        self.tuned = {}           # (L, protocol) -> {"tile_config", "reorth_interval", ...}
+
+    def _fm_tuner(self, L, protocol):
+        prot = fm.FM_HOMODYNE if protocol == "homodyne" else fm.FM_PROJECTIVE
+        p = fm.make_params(L, batch=self.slots, protocol=prot, precision=self.precision, gamma=1.0, seed=self.seed)
+        return fm.autotune(p, steps=4, max_reorth=4, ortho_tol=1e-6, use_graphs=self.graphs)
+
+    def pretune(self, kinds):
+        """Run the tile / reorth search for every (L, protocol) in `kinds` now."""
+        for key in sorted(set(kinds)):
+            if key not in self.tuned:
+                self.tuned[key] = self.tuner(*key)
+        return dict(self.tuned)
+
+    def _settings(self, key):
+        if not self.autotune:
+            return 0, self.reorth
+        if key not in self.tuned:
+            self.tuned[key] = self.tuner(*key)
+        t = self.tuned[key]
+        return t["tile_config"], t["reorth_interval"]
 
     def _group_for(self, req):
         key = (req.L, req.protocol)
         g = self.groups.get(key)
         if g is not None:
             return g if g.free else None
-        need = self.size_of(req.L, req.protocol, self.slots, self.precision, self.reorth)
+        tile_config, reorth = self._settings(key)
+        need = self.size_of(req.L, req.protocol, self.slots, self.precision, reorth)
         if self.used + need > self.budget:
             # free the memory of groups with nothing in flight
             for k in [k for k, gg in self.groups.items() if not gg.active]:
@@ -143,7 +173,8 @@ class Server:
                 self.groups.pop(k).close()
             if self.used + need > self.budget:
                 return None
-        g = self.factory(req.L, req.protocol, self.slots, self.precision, self.seed, self.reorth, self.graphs)
+        g = self.factory(req.L, req.protocol, self.slots, self.precision, self.seed, reorth, self.graphs,
+                         tile_config)
         self.groups[key] = g
         self.used += g.bytes
         return g
@@ -199,7 +230,8 @@ class Server:
                  "step_latency_ms_p50": float(np.percentile(lat, 50)),
                  "step_latency_ms_p99": float(np.percentile(lat, 99)),
                  "groups": {"%d/%s" % k: g.slots for k, g in self.groups.items()},
-                 "workspace_gb": self.used / 1e9}
+                 "workspace_gb": self.used / 1e9,
+                 "tuned": {"%d/%s" % k: v for k, v in self.tuned.items()}}
         return results, stats
 
 
@@ -220,8 +252,15 @@ if __name__ == "__main__":
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--rate", type=float, default=None, help="arrivals per second (default: workload's)")
+    ap.add_argument("--no-autotune", action="store_true", help="default tiles, reorth_interval 1")
     args = ap.parse_args()
     torch.cuda.set_device(0)
-    srv = Server(slots=args.slots)
-    res, st = srv.run(served_mix_requests(args.requests, args.steps, rate=args.rate))
+    srv = Server(slots=args.slots, autotune=not args.no_autotune)
+    reqs = served_mix_requests(args.requests, args.steps, rate=args.rate)
+    t0 = time.perf_counter()
+    if srv.autotune:
+        srv.pretune((r.L, r.protocol) for r in reqs)
+    tune_s = time.perf_counter() - t0
+    res, st = srv.run(reqs)
+    st["autotune_s"] = tune_s
     print(json.dumps(st))

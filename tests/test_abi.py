@@ -32,6 +32,7 @@ def test_every_declared_symbol_is_exported(fm):
 def test_struct_layouts(fm):
     assert ctypes.sizeof(fm.fm_params) == 72
     assert ctypes.sizeof(fm.fm_event) == 40
+    assert ctypes.sizeof(fm.fm_tuning) == 32
     assert fm.fm_version().startswith("fm ")
 
 
@@ -43,6 +44,28 @@ def test_workspace_bytes_validates_parameters(fm):
                 fm.make_params(64, gamma=-1.0), fm.make_params(64, reorth_interval=0),
                 fm.make_params(5, Ly=4), fm.make_params(64, protocol=7), fm.make_params(1)):
         assert fm.fm_workspace_bytes(bad) == 0
+
+
+def test_tile_config_is_validated(fm):
+    mixed = dict(precision=fm.FM_MIXED, protocol=fm.FM_HOMODYNE)
+    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=0, **mixed)) > 0
+    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=2 | (3 << 2), **mixed)) > 0
+    assert fm.fm_workspace_bytes(fm.make_params(256, tile_config=1, **mixed)) > 0
+    assert fm.fm_workspace_bytes(fm.make_params(256, tile_config=2, **mixed)) == 0    # N = 128: no 256-wide tiles
+    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=3, **mixed)) == 0
+    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=1 << 5, **mixed)) == 0
+    # the workspace does not depend on the tile configuration
+    assert (fm.fm_workspace_bytes(fm.make_params(1024, tile_config=1, **mixed)) ==
+            fm.fm_workspace_bytes(fm.make_params(1024, tile_config=2, **mixed)))
+
+
+def test_autotune_rejects_bad_arguments_without_a_gpu(fm):
+    out = fm.fm_tuning()
+    p = fm.make_params(64)
+    assert fm.lib.fm_autotune(ctypes.byref(p), None, 0, None, 0, 1, 1e-6, 0, ctypes.byref(out)) == fm.FM_EINVAL
+    assert fm.lib.fm_autotune(ctypes.byref(p), None, 0, None, 4, 0, 1e-6, 0, ctypes.byref(out)) == fm.FM_EINVAL
+    assert fm.lib.fm_autotune(ctypes.byref(p), None, 0, None, 4, 1, 0.0, 0, ctypes.byref(out)) == fm.FM_EINVAL
+    assert fm.lib.fm_autotune(ctypes.byref(p), None, 0, None, 4, 1, 1e-6, 0, None) == fm.FM_EINVAL
 
 
 def test_null_state_calls_fail_cleanly(fm):

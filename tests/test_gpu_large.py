@@ -71,3 +71,24 @@ def test_torus160_homodyne_mutual_information(fm):
     I = g.mutual_info(A, B)
     assert I >= -1e-9
     assert g.orthonormality_error(list(range(0, 12800, 199))[:64]) <= 1e-6
+
+
+def test_ring4096_mixed_against_fp64_gpu_over_60_steps(fm):
+    """The mixed path against the all-FP64 GPU path (itself pinned to the oracle)
+    over a long run: half-chain EE within the method's 1e-3 bar, C = U U^dag on
+    a 256-site block within the per-step bound, and U^dag U = 1 to 1e-6."""
+    n = 60
+    kw = dict(protocol=fm.FM_HOMODYNE, gamma=1.0, seed=0x2508184685)
+    gm = fm.Trajectories(fm.make_params(4096, precision=fm.FM_MIXED, **kw))
+    gd = fm.Trajectories(fm.make_params(4096, precision=fm.FM_FP64, **kw))
+    gm.step(n)
+    gd.step(n)
+    half = list(range(2048))
+    Sm, Sd = gm.entropy(half), gd.entropy(half)
+    Um, Ud = gm.copy_U()[:256], gd.copy_U()[:256]
+    dc = float(np.max(np.abs(Um @ Um.conj().T - Ud @ Ud.conj().T)))
+    rel = abs(Sm - Sd) / max(abs(Sd), 1.0)
+    print("L=4096, %d steps: S mixed %.8f fp64 %.8f rel %.2e, max|dC| (256 block) %.2e" % (n, Sm, Sd, rel, dc))
+    assert rel <= 1e-3
+    assert dc <= 2e-6 * n
+    assert gm.orthonormality_error(list(range(0, 2048, 32))) <= 1e-6

@@ -74,3 +74,55 @@ def test_async_entropy_sees_the_state_when_requested(fm, precision):
     b.step(7)
     assert np.array_equal(a.copy_U(1), b.copy_U(1))
     assert a.entropy(half, 1) == b.entropy(half, 1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_many_async_entropies_interleaved_with_steps(fm, precision):
+    """More tickets than C_A buffers, issued between steps (including graph replays),
+    each equal to the synchronous entropy of a twin state at the same point."""
+    L = 512 if precision else 64
+    kw = dict(batch=3, protocol=0, precision=precision, gamma=1.2, seed=33)
+    a = fm.Trajectories(fm.make_params(L, **kw))
+    b = fm.Trajectories(fm.make_params(L, **kw))
+    a.set_graphs(True)
+    sites = [list(range(L // 2)), list(range(0, L, 2)), list(range(L // 4, L))]
+    tickets, refs = [], []
+    for k in range(9):
+        for t in range(3):
+            if (k + t) % 2 == 0:
+                tickets.append(a.entropy_async(sites[(k + t) % 3], t))
+                refs.append(b.entropy(sites[(k + t) % 3], t))
+        a.step(2)
+        b.step(2)
+    got = [a.entropy_wait(t) for t in tickets]
+    assert len(got) > 4
+    assert got == refs
+    for t in range(3):
+        assert np.array_equal(a.copy_U(t), b.copy_U(t))
+
+
+def test_tile_configurations_give_identical_states(fm):
+    """Every output element is one fixed-order K sum whatever the tile shape, so
+    the tile width and raster groups do not change a single bit."""
+    kw = dict(batch=2, protocol=1, precision=1, gamma=0.8, seed=7)
+    ref = fm.Trajectories(fm.make_params(1024, **kw))
+    ref.step(5)
+    for tc in (1 | (2 << 2), 2 | (4 << 2), 1 | (3 << 2)):
+        g = fm.Trajectories(fm.make_params(1024, tile_config=tc, **kw))
+        g.step(5)
+        for t in range(2):
+            assert np.array_equal(g.copy_U(t), ref.copy_U(t)), tc
+
+
+def test_autotune_picks_a_configuration_that_meets_the_bar(fm):
+    p = fm.make_params(512, batch=2, protocol=1, precision=1, gamma=1.0, seed=3)
+    res = fm.autotune(p, steps=2, max_reorth=2, ortho_tol=1e-6)
+    assert res["tried"] == 2 * 3 * 2                     # widths 128/256 x groups 8/16/32 x reorth 1, 2
+    assert res["reorth_interval"] in (1, 2)
+    assert res["ms_per_step"] > 0
+    assert res["ortho_err"] <= 1e-6
+    q = fm.make_params(512, batch=2, protocol=1, precision=1, gamma=1.0, seed=3,
+                       tile_config=res["tile_config"], reorth_interval=res["reorth_interval"])
+    g = fm.Trajectories(q)
+    g.step(4)
+    assert g.orthonormality_error(list(range(0, 256, 8))) <= 1e-6

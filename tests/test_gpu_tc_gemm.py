@@ -128,3 +128,71 @@ def test_chunked_accumulation_is_more_accurate_on_long_positive_sums(env):
     print("relative error, K=16384 positive sums: unchunked %.2e, chunked %.2e" % (errs[0], errs[2]))
     assert errs[2] < 2e-6
     assert errs[2] < errs[0]
+
+
+def _digits(Z, e):
+    """Five signed 7-bit digits of every row of Z (float64) scaled by 2^-e_r, toward zero."""
+    x = np.ldexp(Z, (7 - e)[:, None])
+    out = []
+    for _ in range(5):
+        q = np.trunc(x)
+        out.append(q.astype(np.int64))
+        x = (x - q) * 128.0
+    return out
+
+
+def exact_gram_reference(X):
+    """The exact-product Gram of the float-valued block X (n x N complex), written from
+    the digit definition: integer digit products by class (s + t <= 6) in int64, then
+    M = 2^(e_i+e_j-28) H + 2^(e_i+e_j-56) Lo, H and Lo the classes 0-2 and 3-6."""
+    n, N = X.shape
+    Y = X if n <= N else X.T
+    Z = np.concatenate([Y.real, Y.imag], axis=1)
+    Zs = np.concatenate([Y.imag, -Y.real], axis=1)          # rows read at K + Kp, negated past the wrap
+    mx = np.max(np.abs(Z), axis=1)
+    e = np.where(mx > 0, np.frexp(mx)[1], 0).astype(np.int64)    # max < 2^e, exactly
+    D = _digits(Z, e)
+    Ds = _digits(Zs, e)
+    out = []
+    for B in (D, Ds):
+        A = [sum(D[s] @ B[c - s].T for s in range(5) if 0 <= c - s < 5) for c in range(7)]
+        H = (A[0] << 14) + (A[1] << 7) + A[2]
+        Lo = (A[3] << 21) + (A[4] << 14) + (A[5] << 7) + A[6]
+        ee = e[:, None] + e[None, :]
+        out.append(np.ldexp(H.astype(np.float64), ee - 28) + np.ldexp(Lo.astype(np.float64), ee - 56))
+    return out[0] - 1j * out[1]
+
+
+@pytest.mark.parametrize("n,N", [(200, 384), (300, 256), (640, 512), (513, 768)])
+def test_exact_gram_is_bit_exact_to_its_digit_definition(env, n, N):
+    torch, lib = env
+    lib.fmx_exact_gram.restype = ctypes.c_int
+    lib.fmx_exact_gram.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+    lib.fmx_exact_gram_scratch_bytes.restype = ctypes.c_ulonglong
+    lib.fmx_exact_gram_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    rng = np.random.default_rng(n * 1000 + N)
+    scale = np.ldexp(1.0, rng.integers(-12, 3, size=(n, 1)))
+    X = ((rng.standard_normal((n, N)) + 1j * rng.standard_normal((n, N))) * scale)
+    X = (X.real.astype(np.float32) + 1j * X.imag.astype(np.float32)).astype(np.complex128)
+    X[3] = 0.0                                                  # a zero row
+    X[:, 5] *= 1e-6                                             # entries far below their row maxima
+    m = min(n, N)
+    dX = torch.from_numpy(np.asfortranarray(X).T.copy().reshape(-1).view(np.float64)).cuda()
+    dM = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(int(lib.fmx_exact_gram_scratch_bytes(n, N)), dtype=torch.uint8, device="cuda")
+    rc = lib.fmx_exact_gram(dX.data_ptr(), n, N, dM.data_ptr(), scratch.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    M = dM.cpu().numpy().view(np.complex128).reshape(m, m).T     # column-major
+    ref = exact_gram_reference(X)
+    low = np.tril(np.ones((m, m), dtype=bool))
+    assert np.array_equal(M[low], ref[low])
+    # and it is the Gram of X to the truncation bound
+    G = X @ X.conj().T if n <= N else X.T @ X.conj()
+    Y = X if n <= N else X.T
+    rowmax = np.max(np.maximum(np.abs(Y.real), np.abs(Y.imag)), axis=1)
+    bound = 2.0 ** -24 * (rowmax[:, None] * np.sum(np.abs(Y), axis=1)[None, :] +
+                          rowmax[None, :] * np.sum(np.abs(Y), axis=1)[:, None]) + 1e-300
+    assert np.all(np.abs(M - G)[low] <= bound[low])

@@ -11,8 +11,9 @@ class FakeGroup:
     """Same interface as serve.Group; 'computes' S = rid + steps / 1000."""
     live = []
 
-    def __init__(self, L, protocol, slots, precision, seed, reorth_interval, graphs=True):
+    def __init__(self, L, protocol, slots, precision, seed, reorth_interval, graphs=True, tile_config=0):
         self.L, self.protocol, self.slots = L, protocol, slots
+        self.reorth_interval, self.tile_config = reorth_interval, tile_config
         self.bytes = L * slots
         self.period = 2 * reorth_interval if graphs else 1
         self.free = list(range(slots))[::-1]
@@ -100,3 +101,24 @@ def test_request_larger_than_budget_is_reported():
     srv = serve.Server(memory_budget=10, slots=2, group_factory=FakeGroup, size_of=size_of)
     with pytest.raises(RuntimeError):
         srv.run(make_requests(1), realtime=False)
+
+
+def test_autotuned_settings_reach_each_group_and_are_searched_once():
+    FakeGroup.live = []
+    calls = []
+
+    def tuner(L, protocol):
+        calls.append((L, protocol))
+        return {"tile_config": 1 | (2 << 2) if L < 512 else 2, "reorth_interval": 2 if protocol == "projective" else 1}
+    srv = serve.Server(memory_budget=1 << 40, slots=2, group_factory=FakeGroup, size_of=size_of, autotune=True,
+                       tuner=tuner)
+    reqs = make_requests(12)
+    srv.pretune((r.L, r.protocol) for r in reqs)
+    res, st = srv.run(reqs, realtime=False)
+    assert len(res) == 12
+    assert sorted(calls) == sorted(set((r.L, r.protocol) for r in reqs))     # one search per kind
+    for g in FakeGroup.live:
+        t = tuner(g.L, g.protocol)
+        assert (g.tile_config, g.reorth_interval) == (t["tile_config"], t["reorth_interval"])
+        assert g.period == 2 * t["reorth_interval"]
+    assert set(st["tuned"]) == {"%d/%s" % (r.L, r.protocol) for r in reqs}
