@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--propagation", choices=["dense", "banded"], default="dense",
+                    help="dense L x L GEMM (the method as defined) or stencils of the circulant propagator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -222,21 +224,27 @@ def run_ours(args, world, rank, local):
                          reorth_interval=wl["reorth_interval"], gamma=gam[0], seed=seed, traj_id=rank * B)
     g = fm.Trajectories(prm)
     g.set_gammas(gam)
+    if args.propagation == "banded":
+        g.set_propagation(fm.FM_PROP_BANDED)
     ee_sites = workloads.half_chain(L)
     ee_every = wl["ee_every"]
 
     def window(nsteps, per_step=None):
         """nsteps steps; every ee_every steps (from the window start) the half-chain
         entropy of every trajectory is started asynchronously and overlaps the
-        following steps; the window ends when all of them are back."""
-        tickets = []
+        following steps; the window ends when all of them are back (at most 48
+        are left outstanding: the library keeps 64 results)."""
+        pending, results = [], []
         for i in range(nsteps):
             if i % ee_every == 0:
-                tickets += [g.entropy_async(ee_sites, b) for b in range(B)]
+                for b in range(B):
+                    if len(pending) >= 48:
+                        results.append(g.entropy_wait(pending.pop(0)))
+                    pending.append(g.entropy_async(ee_sites, b))
             if per_step:
                 per_step()
             g.step(1)
-        return [g.entropy_wait(t) for t in tickets]
+        return results + [g.entropy_wait(t) for t in pending]
 
     for _ in range(args.warmup):
         g.step(1)
@@ -307,7 +315,16 @@ def run_ours(args, world, rank, local):
         peak_note = "cuBLAS DGEMM measured on this pool (FP64)"
         dtype = "f64"
     roof = None
-    if prop_n > 0:
+    if prop_n > 0 and args.propagation == "banded":
+        # stencil passes: each reads and writes the state once (algorithmic bytes)
+        passes = 2 if Ly > 1 else 1
+        elem = 8 if precision == fm.FM_MIXED else 16
+        nbytes = passes * 2.0 * B * L * N * elem
+        achieved = nbytes / (prop_ms / prop_n / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "band_prop_kernel (propagation)",
+                "ms_per_launch": prop_ms / prop_n, "peak_note": "%s copy bandwidth" % peak_src}
+    elif prop_n > 0:
         achieved = prop_flops / (prop_ms / prop_n / 1e3) / 1e12
         traffic = profiled_traffic("prop_gemm_ring16384") if precision == fm.FM_MIXED else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -320,7 +337,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": args.workload, "L": L, "N": N, "batch_per_gpu": B, "gammas": gam,
                    "protocol": wl["protocol"], "dt": 0.05, "ee_every": ee_every,
                    "ee_sites": "half chain (%d sites), FP64, started every %d steps and overlapped" % (L // 2, ee_every),
-                   "precision": args.precision,
+                   "precision": args.precision, "propagation": args.propagation,
                    "l2": "inputs larger than L2 (state %.1f GB, propagator %.1f GB per GPU)" % (
                        B * 2 * L * N * 4 / 1e9, 4 * L * L * 4 / 1e9),
                    "parallelism": "replicas x%d" % world},

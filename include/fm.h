@@ -127,6 +127,16 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes,
 /* Advance every trajectory of the batch by nsteps >= 0 steps.  Asynchronous. */
 fm_status fm_step(fm_state* s, int32_t nsteps);
 
+/* How fm_step applies exp(-i H~ dt) (App. A).  FM_PROP_DENSE (the default): the
+ * dense L x L complex GEMM.  FM_PROP_BANDED: the same product as stencils --
+ * the propagator is circulant along each lattice direction (P = P_x (x) P_y on
+ * the torus) and its taps fall below 1e-15 beyond a half-width of ~8 sites at
+ * dt = 0.05; the taps above 1e-15 are kept (every tap on tiny lattices), so
+ * results agree with the dense product to that level.  FM_EINVAL if the
+ * stencil would be wider than 41 taps (large J dt).  Synchronises. */
+enum { FM_PROP_DENSE = 0, FM_PROP_BANDED = 1 };
+fm_status fm_set_propagation(fm_state* s, int32_t mode);
+
 /* Per-trajectory monitoring rates (host array of `batch` doubles >= 0). */
 fm_status fm_set_gammas(fm_state* s, const double* gammas);
 
@@ -163,6 +173,21 @@ fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out);
 /* I = S_A + S_B - S_{A u B} for trajectory b; A and B disjoint host arrays. */
 fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA,
                          const int32_t* B, int32_t nB, double* I_out);
+
+/* Density-density correlation of Eq. (2) for trajectory b, per displacement:
+ * c_out[d] = (1/L) sum_i C_{i,i+d}, C_ij = -D_ij D_ji = -|(U U^dag)_ij|^2, the
+ * partner site i + d taken with periodic wrap in x and y, d = dx + Lx dy
+ * (0 <= dx < Lx, 0 <= dy < Ly); c_out[0] = 0 (the paper uses i != j only).
+ * On the ring C(r) = c_out[r], r = 1 .. L/2.  c_out: host array of L doubles.
+ * C is formed in the state's precision (complex128 or complex64 products),
+ * accumulated in float64.  Synchronises. */
+fm_status fm_density_correlation(fm_state* s, int32_t b, double* c_out);
+
+/* Particle-number covariance of Eq. (GAB) for trajectory b, the integral read
+ * as the lattice sum: G_AB = -sum_{i in A, j in B} C_ij = sum |(U_A U_B^dag)_ij|^2
+ * for disjoint host site lists A and B (overlap: FM_EINVAL).  Synchronises. */
+fm_status fm_particle_covariance(fm_state* s, int32_t b, const int32_t* A, int32_t nA, const int32_t* B,
+                                 int32_t nB, double* G_out);
 
 /* U of trajectory b -> host complex128 array with leading dimension ld >= L. */
 fm_status fm_copy_U(fm_state* s, int32_t b, void* host_c128, int64_t ld);

@@ -56,19 +56,34 @@ def mutual_information(U, A, B):
             - entanglement_entropy(U, sorted(A + B)))
 
 
-def density_correlation(U, Lx, Ly=1):
-    """C(r) of Eq. (2) on a ring: mean of -|C_ij|^2 over pairs with ring distance r.
+def displacement_correlation(U, Lx, Ly=1):
+    """Eq. (2) per displacement class: c[d] = (1/L) sum_i C_{i, i+d}, C_ij = -D_ij D_ji = -|C_ij|^2,
+    the partner site i + d taken with periodic wrap in x and in y, d = dx + Lx dy.
 
-    Returns an array indexed by r = 1 .. L//2 (entry 0 unused, set to 0).
+    c[0] = 0 (the paper uses i != j only).  On the ring C(r) = c[r] for r = 1 .. L/2, and
+    c[d] = c[L - d].  Returns an array of L floats.
     """
-    if Ly != 1:
-        raise ValueError("density_correlation: ring only")
-    L = Lx
+    L = Lx * Ly
     C2 = np.abs(correlation(U)) ** 2
-    out = np.zeros(L // 2 + 1)
-    i = np.arange(L)
-    for r in range(1, L // 2 + 1):
-        # each unordered pair at distance r once (r = L/2 pairs are met twice)
-        vals = C2[i, (i + r) % L]
-        out[r] = -float(np.mean(vals))
+    site = np.arange(L)
+    x, y = site % Lx, site // Lx
+    out = np.zeros(L)
+    for dy in range(Ly):
+        for dx in range(Lx):
+            d = dx + Lx * dy
+            if d == 0:
+                continue
+            j = (x + dx) % Lx + Lx * ((y + dy) % Ly)
+            out[d] = -float(np.mean(C2[site, j]))
     return out
+
+
+def particle_covariance(U, A, B):
+    """G_AB of Eq. (GAB) for one trajectory, the integral read as the lattice sum:
+    G_AB = -sum_{i in A, j in B} C_ij = sum_{i in A, j in B} |C_ij|^2 (A, B disjoint)."""
+    A = np.asarray(list(A), dtype=np.int64)
+    B = np.asarray(list(B), dtype=np.int64)
+    if set(A.tolist()) & set(B.tolist()):
+        raise ValueError("A and B overlap")
+    M = U[A, :] @ np.conj(U[B, :]).T
+    return float(np.sum(np.abs(M) ** 2))

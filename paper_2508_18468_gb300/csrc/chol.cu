@@ -57,3 +57,92 @@ template cudaError_t cholesky_inverse<float>(cudaStream_t, c32*, c32*, c32*, c32
                                              int*, int64_t*);
 
 }  // namespace fm
+
+// ------------------------------------------------------------------ one-CTA leaf
+// G = R^dag R and T = R^-1 for an n x n block (n <= 128) of every trajectory,
+// complex64, in shared memory: right-looking Cholesky on the upper triangle,
+// then back substitution row by row with T^T kept in the strict lower
+// triangle of the same array.  R and T are written with zeros below the
+// diagonal.  One CTA of 1024 threads per trajectory; a non-positive pivot
+// raises FM_DEVERR_PIVOT and continues with pivot 1.
+namespace fm {
+
+constexpr int kLeafMax = 128;
+constexpr int kLeafLd = kLeafMax + 1;
+constexpr size_t kLeafSmem = (size_t)kLeafMax * kLeafLd * sizeof(c32) + kLeafMax * sizeof(c32);
+
+__global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restrict__ G, c32* R, c32* T, int n,
+                                                             int64_t ld, int64_t sNN, int* status) {
+  extern __shared__ c32 sm[];
+  c32* A = sm;                                  // A[r * kLeafLd + c]
+  c32* Td = sm + kLeafMax * kLeafLd;            // diagonal of T
+  const int64_t b = blockIdx.x;
+  G += b * sNN;
+  R += b * sNN;
+  T += b * sNN;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    A[r * kLeafLd + c] = r <= c ? G[r + (int64_t)c * ld] : cmk(0.0f, 0.0f);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      float d = A[j * kLeafLd + j].re;
+      if (!(d > 0.0f) || !isfinite(d)) {
+        atomicOr(status, FM_DEVERR_PIVOT);
+        d = 1.0f;
+      }
+      A[j * kLeafLd + j] = cmk(sqrtf(d), 0.0f);
+    }
+    __syncthreads();
+    const float inv = 1.0f / A[j * kLeafLd + j].re;
+    for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) A[j * kLeafLd + c] = cscale(A[j * kLeafLd + c], inv);
+    __syncthreads();
+    const int m = n - j - 1;                    // trailing upper triangle, rows/cols j+1 .. n-1
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int r = j + 1 + idx % m, c = j + 1 + idx / m;
+      if (r <= c) A[r * kLeafLd + c] = csub(A[r * kLeafLd + c], cmul(cconj(A[j * kLeafLd + r]), A[j * kLeafLd + c]));
+    }
+    __syncthreads();
+  }
+  // T = R^-1: T_ii = 1 / R_ii; for i = n-2 .. 0: T_ic = -(1/R_ii) sum_{k=i+1..c} R_ik T_kc (c > i),
+  // T_kc (k < c) kept at A[c][k]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Td[i] = cmk(1.0f / A[i * kLeafLd + i].re, 0.0f);
+  __syncthreads();
+  for (int i = n - 2; i >= 0; --i) {
+    const float rinv = 1.0f / A[i * kLeafLd + i].re;
+    for (int c = i + 1 + threadIdx.x; c < n; c += blockDim.x) {
+      c32 s = cmul(A[i * kLeafLd + c], Td[c]);                       // k = c
+      for (int k = i + 1; k < c; ++k) s = cadd(s, cmul(A[i * kLeafLd + k], A[c * kLeafLd + k]));
+      A[c * kLeafLd + i] = cscale(s, -rinv);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    const int64_t o = r + (int64_t)c * ld;
+    if (r < c) {
+      R[o] = A[r * kLeafLd + c];
+      T[o] = A[c * kLeafLd + r];
+    } else if (r == c) {
+      R[o] = A[r * kLeafLd + r];
+      T[o] = Td[r];
+    } else {
+      R[o] = cmk(0.0f, 0.0f);
+      T[o] = cmk(0.0f, 0.0f);
+    }
+  }
+}
+
+cudaError_t chol_inv_leaf(cudaStream_t st, const c32* G, c32* R, c32* T, int n, int64_t ld, int64_t sNN, int B,
+                          int* status) {
+  if (n < 1 || n > kLeafMax) return cudaErrorInvalidValue;
+  static cudaError_t attr = cudaErrorNotReady;
+  if (attr == cudaErrorNotReady)
+    attr = cudaFuncSetAttribute(chol_inv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmem);
+  if (attr != cudaSuccess) return attr;
+  chol_inv_leaf_kernel<<<B, 1024, kLeafSmem, st>>>(G, R, T, n, ld, sNN, status);
+  return cudaGetLastError();
+}
+
+}  // namespace fm

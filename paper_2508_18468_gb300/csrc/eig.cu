@@ -116,15 +116,26 @@ __global__ void __launch_bounds__(1024) tridiag_small_kernel(z64* M, int m, z64*
 
 // ------------------------------------------------------------------ large m: per-column kernels
 // Only the lower triangle (i >= j) of the trailing block is read and updated.
-__global__ void __launch_bounds__(256) hh_reflector_kernel(z64* M, int m, int k, z64* vb, double* d, double* e,
-                                                           z64* tau_out) {
+// Column k of the trailing matrix, after the rank-2 update still pending from
+// column k - 1 (vp, wp: that column's reflector and w, indexed from row k), then
+// its reflector.  One CTA.
+__global__ void __launch_bounds__(256) hh_reflector_kernel(z64* M, int m, int k, const z64* __restrict__ vp,
+                                                           const z64* __restrict__ wp, z64* vb, double* d,
+                                                           double* e, z64* tau_out) {
   __shared__ double red[33];
   __shared__ z64 sh[4];
   __shared__ double sbeta;
+  z64* col = M + k + (int64_t)k * m;          // rows k .. m-1 of column k
+  if (vp) {
+    const z64 w0c = cconj(wp[0]), v0c = cconj(vp[0]);
+    for (int i = threadIdx.x; i < m - k; i += blockDim.x)
+      col[i] = csub(col[i], cadd(cmul(vp[i], w0c), cmul(wp[i], v0c)));
+    __syncthreads();
+  }
   const int n = m - k - 1;
-  const z64 tau = reflector(M + (k + 1) + (int64_t)k * m, n, vb, &sbeta, red, sh);
+  const z64 tau = reflector(col + 1, n, vb, &sbeta, red, sh);
   if (threadIdx.x == 0) {
-    d[k] = M[k + (int64_t)k * m].re;
+    d[k] = col[0].re;
     e[k] = sbeta;
     *tau_out = tau;
   }
@@ -132,15 +143,20 @@ __global__ void __launch_bounds__(256) hh_reflector_kernel(z64* M, int m, int k,
 
 constexpr int HT = EIG_TILE;  // tile of the Hermitian matrix-vector product (17 KB of shared memory)
 
-// p = M22 v from the lower triangle: tile (I, J), J <= I, adds sum_j M_ij v_j to
-// prow[J][i] and sum_{i > j} conj(M_ij) v_i to pcol[I][j].  The tile is staged in
-// shared memory (column stride HT + 1) and read once with a row mapping (thread:
-// row tid % 64, 16 columns) and once with a column mapping (thread: column
-// tid % 64, 16 rows); no shuffles.
-__global__ void __launch_bounds__(256) hemv_lower_kernel(const z64* __restrict__ M, int m, int k,
-                                                         const z64* __restrict__ vb, z64* prow, z64* pcol) {
+// One pass over the lower triangle of the trailing block M22 (rows and columns
+// k+1 .. m-1) per column: first the rank-2 update left pending by column k - 1,
+// M22 -= v' w'^dag + w' v'^dag (vp, wp indexed from row k, so element (i, j) of
+// M22 uses entries i + 1 and j + 1), written back; then p = M22 v from the
+// updated tile: tile (I, J), J <= I, adds sum_j M_ij v_j to prow[J][i] and
+// sum_{i > j} conj(M_ij) v_i to pcol[I][j].  The tile is staged in shared
+// memory (column stride HT + 1) and read once with a row mapping and once with
+// a column mapping; no shuffles.  Reading and writing each element once per
+// column, instead of once for the product and again for the update.
+__global__ void __launch_bounds__(256) hemv_lower_kernel(z64* M, int m, int k, const z64* __restrict__ vp,
+                                                         const z64* __restrict__ wp, const z64* __restrict__ vb,
+                                                         z64* prow, z64* pcol) {
   const int n = m - k - 1;
-  const z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
+  z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
   // decode lower tile t = I (I+1)/2 + J
   const int t = blockIdx.x;
   int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -151,17 +167,32 @@ __global__ void __launch_bounds__(256) hemv_lower_kernel(const z64* __restrict__
   constexpr int NQ = 256 / HT;               // phases
   __shared__ z64 vi_s[HT], vj_s[HT];
   __shared__ z64 red_s[NQ][HT + 1];
+  __shared__ z64 pv_i[HT], pw_i[HT], pv_j[HT], pw_j[HT];
   const int lo = threadIdx.x % HT, q = threadIdx.x / HT;
-  for (int cc = q; cc < HT; cc += NQ) {
-    const int i = I * HT + lo, j = J * HT + cc;
-    z64 a = cmk(0.0, 0.0);
-    if (i < n && j < n && j <= i) a = M22[i + (int64_t)j * m];
-    tile[cc * (HT + 1) + lo] = a;            // zero above the diagonal and outside
-  }
   if (threadIdx.x < HT) {
     const int ii = I * HT + threadIdx.x, jj = J * HT + threadIdx.x;
     vi_s[threadIdx.x] = ii < n ? vb[ii] : cmk(0.0, 0.0);
     vj_s[threadIdx.x] = jj < n ? vb[jj] : cmk(0.0, 0.0);
+    if (vp) {
+      pv_i[threadIdx.x] = ii < n ? vp[ii + 1] : cmk(0.0, 0.0);
+      pw_i[threadIdx.x] = ii < n ? wp[ii + 1] : cmk(0.0, 0.0);
+      pv_j[threadIdx.x] = jj < n ? cconj(vp[jj + 1]) : cmk(0.0, 0.0);
+      pw_j[threadIdx.x] = jj < n ? cconj(wp[jj + 1]) : cmk(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  for (int cc = q; cc < HT; cc += NQ) {
+    const int i = I * HT + lo, j = J * HT + cc;
+    z64 a = cmk(0.0, 0.0);
+    if (i < n && j < n && j <= i) {
+      z64* ap = &M22[i + (int64_t)j * m];
+      a = *ap;
+      if (vp) {
+        a = csub(a, cadd(cmul(pv_i[lo], pw_j[cc]), cmul(pw_i[lo], pv_j[cc])));
+        *ap = a;
+      }
+    }
+    tile[cc * (HT + 1) + lo] = a;            // zero above the diagonal and outside
   }
   __syncthreads();
   // rows: sum_j M_ij v_j (diagonal included)
@@ -241,20 +272,12 @@ __global__ void hh_w_kernel(int m, int k, const z64* __restrict__ p, const z64* 
     wb[i] = csub(cmul(tau, p[i]), cmul(cs, vb[i]));
 }
 
-// M22 -= v w^dag + w v^dag on the lower triangle (i >= j); block (256 rows) x columns
-__global__ void her2_lower_kernel(z64* M, int m, int k, const z64* __restrict__ vb, const z64* __restrict__ wb) {
-  const int n = m - k - 1;
-  z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const z64 vi = vb[i], wi = wb[i];
-  for (int j = blockIdx.y; j <= i; j += gridDim.y) {
-    z64& a = M22[i + (int64_t)j * m];
-    a = csub(a, cadd(cmul(vi, cconj(wb[j])), cmul(wi, cconj(vb[j]))));
-  }
+// the last diagonal entry after the update pending from column m - 2 (vp, wp of length 1)
+__global__ void last_diag_kernel(const z64* M, int m, const z64* vp, const z64* wp, double* d) {
+  double a = M[(m - 1) + (int64_t)(m - 1) * m].re;
+  if (vp) a -= 2.0 * (vp[0].re * wp[0].re + vp[0].im * wp[0].im);
+  d[m - 1] = a;
 }
-
-__global__ void last_diag_kernel(const z64* M, int m, double* d) { d[m - 1] = M[(m - 1) + (int64_t)(m - 1) * m].re; }
 
 // ------------------------------------------------------------------ bisection
 // count of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm / LDL^T inertia)
@@ -323,26 +346,34 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, 
     ++launches;
   } else {
     static_assert(HT * (HT + 1) * sizeof(z64) <= 48 * 1024, "hemv tile must not need a shared-memory opt-in");
-    // pbuf layout: [tau][prow: nb*m][pcol: nb*m][p: m][sdot: m/256 + 1]
+    // pbuf layout: [tau][prow: nb*m][pcol: nb*m][p: m][sdot: m/256 + 1][v, w of the other parity: 2m]
     const int nbm = FM_CEIL_DIV(m, HT);
     z64* tau = pbuf;
     z64* prow = pbuf + 1;
     z64* pcol = prow + (int64_t)nbm * m;
     z64* p = pcol + (int64_t)nbm * m;
     z64* sdot = p + m;
+    z64* vb2 = sdot + m / 256 + 1;
+    z64* wb2 = vb2 + m;
+    // column k uses (vb, wb) for even k, (vb2, wb2) for odd k; the other pair
+    // holds the rank-2 update column k - 1 left pending
     for (int k = 0; k + 1 < m; ++k) {
       const int n = m - k - 1;
       const int nb = FM_CEIL_DIV(n, HT);
-      hh_reflector_kernel<<<1, 256, 0, st>>>(M, m, k, vb, d, e, tau);
-      hemv_lower_kernel<<<nb * (nb + 1) / 2, 256, HT * (HT + 1) * sizeof(z64), st>>>(M, m, k, vb, prow, pcol);
+      z64* vc = (k & 1) ? vb2 : vb;
+      z64* wc = (k & 1) ? wb2 : wb;
+      const z64* vp = k == 0 ? nullptr : ((k & 1) ? vb : vb2);
+      const z64* wp = k == 0 ? nullptr : ((k & 1) ? wb : wb2);
+      hh_reflector_kernel<<<1, 256, 0, st>>>(M, m, k, vp, wp, vc, d, e, tau);
+      hemv_lower_kernel<<<nb * (nb + 1) / 2, 256, HT * (HT + 1) * sizeof(z64), st>>>(M, m, k, vp, wp, vc, prow,
+                                                                                    pcol);
       const int rb = FM_CEIL_DIV(n, 256);
-      hemv_reduce_kernel<<<rb, 256, 0, st>>>(m, k, prow, pcol, vb, p, sdot);
-      hh_w_kernel<<<FM_CEIL_DIV(n, 256), 256, 0, st>>>(m, k, p, sdot, rb, vb, wb, tau);
-      const int gy = max(1, min(n, FM_CEIL_DIV(8 * 152, rb)));
-      her2_lower_kernel<<<dim3(rb, gy), 256, 0, st>>>(M, m, k, vb, wb);
-      launches += 5;
+      hemv_reduce_kernel<<<rb, 256, 0, st>>>(m, k, prow, pcol, vc, p, sdot);
+      hh_w_kernel<<<FM_CEIL_DIV(n, 256), 256, 0, st>>>(m, k, p, sdot, rb, vc, wc, tau);
+      launches += 4;
     }
-    last_diag_kernel<<<1, 1, 0, st>>>(M, m, d);
+    const int kl = m - 2;                      // the last column's pending update
+    last_diag_kernel<<<1, 1, 0, st>>>(M, m, (kl & 1) ? vb2 : vb, (kl & 1) ? wb2 : wb, d);
     ++launches;
   }
   bisect_kernel<<<FM_CEIL_DIV(m, 64), 64, 0, st>>>(d, e, m, lam);

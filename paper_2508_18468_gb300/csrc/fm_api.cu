@@ -40,6 +40,9 @@ struct Plan {
   size_t ea_M, ea_vb, ea_wb, ea_pb, ea_d, ea_e, ea_lam, ea_S;   // asynchronous entropy
   size_t pmw;                                           // grid-wide projective update
   size_t xg;                                            // exact-product Gram of C_A (mixed)
+  size_t gfull;                                         // exact Gram of all of U (mixed)
+  size_t obs;                                           // displacement bins and partial sums
+  size_t band;                                          // stencil taps and offsets (x, y)
   size_t mixed_extra;                                   // scratch owned by the mixed path
   size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
 };
@@ -108,6 +111,8 @@ Plan make_plan(const fm_params& p) {
   pl.ea_lam = pl.take(N * 8);
   pl.ea_S = pl.take(kAsyncSlots * 8);
   pl.pmw = pl.take(pm_wide_scratch_bytes((int)L, (int)B));
+  pl.obs = pl.take((L + abs2_partials() + 8) * 8);
+  pl.band = pl.take(2 * kBandMaxTaps * (16 + 4));
   if (p.precision == FM_FP64) {
     pl.U = pl.take(B * L * N * 16);
     pl.U2 = pl.take(B * L * N * 16);
@@ -123,8 +128,9 @@ Plan make_plan(const fm_params& p) {
     pl.Th = pl.take(B * 4 * N * N * 2);
     pl.Tl = pl.take(B * 4 * N * N * 2);
     pl.aux = pl.take(L * N * 16);
-    pl.mixed_extra = pl.take(mixed_scratch_bytes(p.Lx, p.Ly, p.batch));
-    pl.xg = pl.take(exact_gram_scratch_bytes((int)L, (int)N));
+    pl.mixed_extra = pl.take(mixed_scratch_bytes(p.Lx, p.Ly, p.batch, p.protocol));
+    pl.xg = pl.take(std::max(exact_gram_scratch_bytes((int)L, (int)N), projector_scratch_bytes((int)N)));
+    pl.gfull = pl.take(N * N * 16);
   }
   return pl;
 }
@@ -152,6 +158,7 @@ struct fm_state {
   z64* aux;
   void* mixed_extra;
   void* xg;                  // exact-product Gram scratch (mixed precision)
+  z64* gfull;                // exact Gram of all of U, for the projector correction
   MixedCtx mc;
   MixedHost* mh;
   PhaseTimer timer;
@@ -183,6 +190,12 @@ struct fm_state {
   cudaEvent_t ea_done[kAsyncSlots];
   double* ea_host;            // pinned, kAsyncSlots doubles
   void* pmw;                  // grid-wide projective update scratch
+  double* obs;                // displacement bins, partial sums, one result
+  // structured propagation (fm_set_propagation): stencil taps per direction
+  int prop_mode;
+  z64 *band_tx, *band_ty;
+  int *band_ox, *band_oy;
+  int ntap_x, ntap_y;
   int64_t ea_next;            // next ticket
   struct EaJob { int64_t t; int slot, ring, m; };
   std::thread ea_thread;
@@ -282,6 +295,25 @@ std::vector<int> occupied(int Lx, int Ly) {
   return occ;
 }
 
+// Stencil of one direction of the circulant propagator row p (length n): the
+// offsets up to the half-width beyond which every tap is below 1e-15 (the
+// plane-wave sums that give p carry rounding noise of ~1e-17, so a smaller
+// cut would keep noise); every offset when that width reaches half the period.
+void band_taps(const std::vector<z64>& p, std::vector<z64>* taps, std::vector<int>* off) {
+  const int n = (int)p.size();
+  auto mag = [&](int r) { const z64 z = p[((r % n) + n) % n]; return sqrt(z.re * z.re + z.im * z.im); };
+  int w = 0;
+  for (int r = 1; r <= n / 2; ++r)
+    if (mag(r) > 1e-15 || mag(-r) > 1e-15) w = r;
+  taps->clear();
+  off->clear();
+  if (2 * w + 1 >= n) {
+    for (int r = 0; r < n; ++r) { taps->push_back(p[r]); off->push_back(r); }
+  } else {
+    for (int r = -w; r <= w; ++r) { taps->push_back(p[((r % n) + n) % n]); off->push_back(r); }
+  }
+}
+
 fm_status check_state(fm_state* s) {
   if (!s) return FM_EINVAL;
   if (s->sticky) return FM_ESTATE;
@@ -313,11 +345,23 @@ fm_status cholqr_f64(fm_state* s) {
 fm_status step_f64(fm_state* s) {
   const int L = s->L, N = s->N, B = s->B;
   const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
-  // 1. propagation, all trajectories in one product P [U_0 | U_1 | ...]
+  // 1. propagation, all trajectories in one product P [U_0 | U_1 | ...], or as stencils
   s->timer.begin(FM_PH_PROPAGATE);
-  CKL(zgemm<double>(s->st, L, N * B, L, OP_N, OP_N, one, s->P, L, 0, s->U, L, 0, zero, s->U2, L, 0, 1, 0), 1);
+  if (s->prop_mode == FM_PROP_BANDED) {
+    const int nch = band_chunks(L, N, B);
+    CKL(band_propagate(s->st, 0, s->U, s->U2, L, N, B, s->Lx, s->Ly, 0, s->band_tx, s->band_ox, s->ntap_x, nullptr,
+                       nch), 1);
+    if (s->Ly > 1) {
+      CKL(band_propagate(s->st, 0, s->U2, s->U, L, N, B, s->Lx, s->Ly, 1, s->band_ty, s->band_oy, s->ntap_y,
+                         nullptr, nch), 1);
+    } else {
+      std::swap(s->U, s->U2);
+    }
+  } else {
+    CKL(zgemm<double>(s->st, L, N * B, L, OP_N, OP_N, one, s->P, L, 0, s->U, L, 0, zero, s->U2, L, 0, 1, 0), 1);
+    std::swap(s->U, s->U2);
+  }
   s->timer.end(FM_PH_PROPAGATE);
-  std::swap(s->U, s->U2);
   s->aux = s->U2;
   const int64_t gstep = s->global_steps;
   const int k = s->prm.reorth_interval;
@@ -378,18 +422,33 @@ fm_status validate_sites(fm_state* s, const int32_t* sites, int32_t n) {
   return FM_OK;
 }
 
-// C_A (or U_A^dag U_A when n > N, the same nonzero spectrum) from the n
-// gathered rows in s->aux into M on stream st; only the lower triangle when
-// the eigen-solver reads only that.  Mixed precision (float state): exact
-// digit products on the tensor cores for the large blocks; FP64 otherwise.
-fm_status form_correlation(fm_state* s, cudaStream_t st, int n, z64* M) {
-  const int N = s->N;
+// C_A (or U_A^dag U_A when n > N, the same nonzero spectrum) of trajectory b for
+// the n sites in d_sites (device) into M on stream st; only the lower triangle
+// when the eigen-solver reads only that.  FP64 state: the FP64 product of the
+// gathered rows.  Mixed precision (float state), large blocks: exact digit
+// products on the tensor cores, then the first-order correction from U U^dag to
+// the projector onto span(U) (the float U is orthonormal only to ~1e-7), which
+// needs the exact Gram of all of U first.
+fm_status form_correlation(fm_state* s, cudaStream_t st, int b, const int* d_sites, int n, z64* M) {
+  const int L = s->L, N = s->N;
   const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
   const int m = std::min(n, N);
   const int fl = hermitian_entropy_lower_only(m) ? GEMM_LOWER_ONLY : 0;
   if (s->prm.precision == FM_MIXED && hermitian_entropy_lower_only(m)) {
+    const float* Vb = s->V + (int64_t)b * 2 * L * N;
+    CKL(v_to_z(st, Vb, L, N, s->aux), 1);
+    CK(exact_gram(st, s->aux, L, N, s->gfull, s->xg, s->status_d, &s->launches));
+    CKL(gather_rows_v(st, Vb, L, N, d_sites, n, s->aux), 1);
     CK(exact_gram(st, s->aux, n, N, M, s->xg, s->status_d, &s->launches));
-  } else if (n <= N) {
+    CK(projector_correct(st, s->gfull, s->aux, n, N, M, s->xg, &s->launches));
+    return FM_OK;
+  }
+  if (s->prm.precision == FM_FP64) {
+    CKL(gather_rows_z(st, s->U + (int64_t)b * L * N, L, N, d_sites, n, s->aux), 1);
+  } else {
+    CKL(gather_rows_v(st, s->V + (int64_t)b * 2 * L * N, L, N, d_sites, n, s->aux), 1);
+  }
+  if (n <= N) {
     CKL(zgemm<double>(st, n, n, N, OP_N, OP_C, one, s->aux, n, 0, s->aux, n, 0, zero, M, n, 0, 1, fl), 1);
   } else {
     CKL(zgemm<double>(st, N, N, n, OP_C, OP_N, one, s->aux, n, 0, s->aux, n, 0, zero, M, N, 0, 1, fl), 1);
@@ -403,10 +462,9 @@ fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, doub
   if (n == 0) { *S_out = 0.0; return FM_OK; }
   CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   s->timer.begin(FM_PH_ENTROPY);
-  fm_status r = gather_rows(s, b, s->ee_sites, n);
-  if (r) return r;
   z64* M = s->G;  // scratch between steps
-  if ((r = form_correlation(s, s->st, n, M))) return r;
+  fm_status r = form_correlation(s, s->st, b, s->ee_sites, n, M);
+  if (r) return r;
   int nl = 0;
   CK(hermitian_entropy(s->st, M, std::min(n, s->N), s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e,
                        s->ee_lam, s->ee_S, &nl));
@@ -637,8 +695,7 @@ fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n
     }
     // rows of A and C_A, in order with the steps on the caller's stream
     CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
-    if ((r = gather_rows(s, b, s->ee_sites, n))) return r;
-    if ((r = form_correlation(s, s->st, n, M))) return r;
+    if ((r = form_correlation(s, s->st, b, s->ee_sites, n, M))) return r;
   }
   CK(cudaEventRecord(s->ea_M_ready[ring], s->st));
   {
@@ -700,11 +757,19 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ea_issued = 0; s->ea_stop = false; s->ea_failed = false; s->ea_launches = 0;
   if (cudaGetDevice(&s->dev) != cudaSuccess) { delete s; return FM_ECUDA; }
   s->pmw = w + pl.pmw;
+  s->obs = (double*)(w + pl.obs);
+  s->prop_mode = FM_PROP_DENSE;
+  s->band_tx = (z64*)(w + pl.band);
+  s->band_ty = s->band_tx + kBandMaxTaps;
+  s->band_ox = (int*)(s->band_ty + kBandMaxTaps);
+  s->band_oy = s->band_ox + kBandMaxTaps;
+  s->ntap_x = s->ntap_y = 0;
   for (int i = 0; i < kAsyncSlots; ++i) s->ea_done[i] = nullptr;
   s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
   s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
   s->mixed_extra = nullptr;
   s->xg = nullptr;
+  s->gfull = nullptr;
   s->mh = nullptr;
   if (p->precision == FM_FP64) {
     s->U = (z64*)(w + pl.U); s->U2 = (z64*)(w + pl.U2); s->P = (z64*)(w + pl.P); s->aux = s->U2;
@@ -714,6 +779,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
     s->Ah = (__half*)(w + pl.Ah); s->Al = (__half*)(w + pl.Al);
     s->Th = (__half*)(w + pl.Th); s->Tl = (__half*)(w + pl.Tl);
     s->aux = (z64*)(w + pl.aux); s->mixed_extra = w + pl.mixed_extra; s->xg = w + pl.xg;
+    s->gfull = (z64*)(w + pl.gfull);
   }
   s->timer.st = s->st;
   s->gamma_h.assign(s->B, p->gamma);
@@ -737,6 +803,27 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       break;
     }
     std::vector<z64> px = ring_row(s->Lx, p->J, p->dt), py = ring_row(s->Ly, p->J, p->dt);
+    {
+      std::vector<z64> tx, ty;
+      std::vector<int> ox, oy;
+      band_taps(px, &tx, &ox);
+      band_taps(py, &ty, &oy);
+      if ((int)tx.size() > kBandMaxTaps || (int)ty.size() > kBandMaxTaps) {
+        s->ntap_x = s->ntap_y = 0;   // too wide a stencil: dense propagation only
+      } else {
+        s->ntap_x = (int)tx.size();
+        s->ntap_y = (int)ty.size();
+        if (cudaMemcpyAsync(s->band_tx, tx.data(), 16 * tx.size(), cudaMemcpyHostToDevice, s->st) ||
+            cudaMemcpyAsync(s->band_ty, ty.data(), 16 * ty.size(), cudaMemcpyHostToDevice, s->st) ||
+            cudaMemcpyAsync(s->band_ox, ox.data(), 4 * ox.size(), cudaMemcpyHostToDevice, s->st) ||
+            cudaMemcpyAsync(s->band_oy, oy.data(), 4 * oy.size(), cudaMemcpyHostToDevice, s->st)) {
+          r = fail(s, FM_ECUDA, "upload stencil");
+          break;
+        }
+        // the host vectors must outlive the copies
+        if (cudaStreamSynchronize(s->st) != cudaSuccess) { r = fail(s, FM_ECUDA, "stencil sync"); break; }
+      }
+    }
     // stage the rows in the EE scratch (free until the first entropy call)
     z64* dpx = s->ee_pb;
     z64* dpy = s->ee_pb + s->Lx;
@@ -769,6 +856,9 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       c.part = s->part_d; c.nocc = s->nocc_d; c.w = s->w_d; c.xbuf = s->xbuf_d; c.vbuf = s->vbuf_d;
       c.log = s->log_d; c.log_count = (int64_t*)s->log_count_d; c.log_capacity = p->event_capacity;
       c.extra = s->mixed_extra; c.launches = 0; c.timer = &s->timer; c.pmw = s->pmw;
+      c.prop_banded = 0;
+      c.band_tx = s->band_tx; c.band_ty = s->band_ty; c.band_ox = s->band_ox; c.band_oy = s->band_oy;
+      c.ntap_x = s->ntap_x; c.ntap_y = s->ntap_y;
       std::string why2;
       s->mh = mixed_create(&c, &why2);
       if (!s->mh) {
@@ -819,6 +909,22 @@ fm_status fm_set_graphs(fm_state* s, int32_t enable) {
   if (r) return r;
   s->graphs_on = enable != 0;
   s->graph_period = 2 * s->prm.reorth_interval;
+  return FM_OK;
+}
+
+fm_status fm_set_propagation(fm_state* s, int32_t mode) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (mode != FM_PROP_DENSE && mode != FM_PROP_BANDED) return fail(s, FM_EINVAL, "unknown propagation mode");
+  if (mode == FM_PROP_BANDED && (s->ntap_x == 0 || s->ntap_y == 0))
+    return fail(s, FM_EINVAL, "the propagator is too wide for the stencil");
+  CK(cudaStreamSynchronize(s->st));
+  s->prop_mode = mode;
+  if (s->prm.precision != FM_FP64) s->mc.prop_banded = mode == FM_PROP_BANDED;
+  if (s->graph_exec) {                 // the captured period used the other propagation
+    cudaGraphExecDestroy(s->graph_exec);
+    s->graph_exec = nullptr;
+  }
   return FM_OK;
 }
 
@@ -891,6 +997,75 @@ fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out) {
   if ((r = ea_check(s))) return r;
   CK(cudaEventSynchronize(s->ea_done[slot]));
   *S_out = s->ea_host[slot];
+  return sync_and_check(s);
+}
+
+fm_status fm_density_correlation(fm_state* s, int32_t b, double* c_out) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!c_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  const int L = s->L, N = s->N;
+  const int S = std::max(1, L / 2);               // stripe width: the stripe fits the scratch next to U
+  double* bins = s->obs;
+  CK(cudaMemsetAsync(bins, 0, sizeof(double) * L, s->st));
+  if (s->prm.precision == FM_FP64) {
+    const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+    const z64* U = s->U + (int64_t)b * L * N;
+    z64* X = s->aux;                              // L x S stripe of C
+    for (int j0 = 0; j0 < L; j0 += S) {
+      const int w = std::min(S, L - j0);
+      CKL(zgemm<double>(s->st, L, w, N, OP_N, OP_C, one, U, L, 0, U + j0, L, 0, zero, X, L, 0, 1, 0), 1);
+      CKL(displacement_bins<double>(s->st, X, L, s->Lx, s->Ly, j0, w, bins), 1);
+    }
+  } else {
+    const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
+    c32* U = (c32*)s->aux;                        // complex64 copy of U_b, then the stripe
+    c32* X = U + (int64_t)L * N;
+    CKL(v_to_c32(s->st, s->V + (int64_t)b * 2 * L * N, L, N, U), 1);
+    for (int j0 = 0; j0 < L; j0 += S) {
+      const int w = std::min(S, L - j0);
+      CKL(zgemm<float>(s->st, L, w, N, OP_N, OP_C, one, U, L, 0, U + j0, L, 0, zero, X, L, 0, 1, 0), 1);
+      CKL(displacement_bins<float>(s->st, X, L, s->Lx, s->Ly, j0, w, bins), 1);
+    }
+  }
+  std::vector<double> h(L);
+  CK(cudaMemcpyAsync(h.data(), bins, sizeof(double) * L, cudaMemcpyDeviceToHost, s->st));
+  if ((r = sync_and_check(s))) return r;
+  for (int d = 0; d < L; ++d) c_out[d] = -h[d] / (double)L;
+  return FM_OK;
+}
+
+fm_status fm_particle_covariance(fm_state* s, int32_t b, const int32_t* A, int32_t nA, const int32_t* B,
+                                 int32_t nB, double* G_out) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!G_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  if ((r = validate_sites(s, A, nA)) || (r = validate_sites(s, B, nB))) return r;
+  std::vector<int32_t> AB(A, A + nA);
+  AB.insert(AB.end(), B, B + nB);
+  if ((r = validate_sites(s, AB.data(), (int32_t)AB.size()))) return fail(s, FM_EINVAL, "A and B overlap");
+  if (nA == 0 || nB == 0) { *G_out = 0.0; return FM_OK; }
+  const int L = s->L, N = s->N;
+  CK(cudaMemcpyAsync(s->ee_sites, AB.data(), sizeof(int) * (nA + nB), cudaMemcpyHostToDevice, s->st));
+  double* part = s->obs + L;
+  double* res = part + abs2_partials();
+  if (s->prm.precision == FM_FP64) {
+    const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+    z64* rows = s->aux;                           // (nA + nB) x N, ld nA + nB
+    CKL(gather_rows_z(s->st, s->U + (int64_t)b * L * N, L, N, s->ee_sites, nA + nB, rows), 1);
+    const int ld = nA + nB;
+    CKL(zgemm<double>(s->st, nA, nB, N, OP_N, OP_C, one, rows, ld, 0, rows + nA, ld, 0, zero, s->G, nA, 0, 1, 0), 1);
+    CKL(sum_abs2<double>(s->st, s->G, (int64_t)nA * nB, part, res), 2);
+  } else {
+    const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
+    c32* rows = (c32*)s->aux;
+    c32* M = (c32*)s->G;
+    CKL(gather_rows_c32(s->st, s->V + (int64_t)b * 2 * L * N, L, N, s->ee_sites, nA + nB, rows), 1);
+    const int ld = nA + nB;
+    CKL(zgemm<float>(s->st, nA, nB, N, OP_N, OP_C, one, rows, ld, 0, rows + nA, ld, 0, zero, M, nA, 0, 1, 0), 1);
+    CKL(sum_abs2<float>(s->st, M, (int64_t)nA * nB, part, res), 2);
+  }
+  CK(cudaMemcpyAsync(G_out, res, sizeof(double), cudaMemcpyDeviceToHost, s->st));
   return sync_and_check(s);
 }
 

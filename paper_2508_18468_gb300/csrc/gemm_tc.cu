@@ -85,6 +85,17 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
                                  (int64_t)(n0 + c0) * p.Ntraj) + ti.part;
 #pragma unroll
     for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.Ntraj] = d[j];
+  } else if (MODE == MODE_ADDV) {
+    const int64_t o0 = (int64_t)ti.b * p.out_batch_stride + (int64_t)(m0 + r) + (int64_t)(n0 + c0) * p.ld_out;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t o = o0 + (int64_t)j * p.ld_out;
+      const float x = p.in_f[o] + d[j];
+      p.out_f[o] = x;
+      const __half h = __float2half_rn(x);
+      p.out_h[o] = h;
+      p.out_l[o] = __float2half_rn((x - __half2float(h)) * 2048.0f);
+    }
   } else {  // MODE_TRMM: column c of the L x 2N view -> V_b[(c&1) L + i + (c>>1) 2L]
     const int64_t base = (int64_t)ti.b * 2 * p.L * p.Ntraj + (m0 + r);
 #pragma unroll
@@ -358,7 +369,8 @@ cudaError_t configure_all() {
       (e = set_smem<128, 1, MODE_PLAIN>()) || (e = set_smem<256, 0, MODE_PROP>()) ||
       (e = set_smem<128, 0, MODE_PROP>()) || (e = set_smem<256, 0, MODE_GRAM>()) ||
       (e = set_smem<128, 0, MODE_GRAM>()) || (e = set_smem<128, 1, MODE_TRMM>()) ||
-      (e = set_smem<128, 0, MODE_TRMM>()) || (e = set_smem<256, 0, MODE_TRMM>()))
+      (e = set_smem<128, 0, MODE_TRMM>()) || (e = set_smem<256, 0, MODE_TRMM>()) ||
+      (e = set_smem<128, 0, MODE_ADDV>()) || (e = set_smem<256, 0, MODE_ADDV>()))
     return e;
   done = cudaSuccess;
   return done;
@@ -394,6 +406,10 @@ cudaError_t launch(cudaStream_t st, int BN, const CUtensorMap& Ah, const CUtenso
       if (ch) return cudaErrorInvalidValue;
       return BN == 256 ? launch_one<256, 0, MODE_GRAM>(st, Ah, Al, Bh, Bl, p, grid)
                        : launch_one<128, 0, MODE_GRAM>(st, Ah, Al, Bh, Bl, p, grid);
+    case MODE_ADDV:
+      if (ch) return cudaErrorInvalidValue;
+      return BN == 256 ? launch_one<256, 0, MODE_ADDV>(st, Ah, Al, Bh, Bl, p, grid)
+                       : launch_one<128, 0, MODE_ADDV>(st, Ah, Al, Bh, Bl, p, grid);
     case MODE_TRMM:
       if (ch) return launch_one<128, 1, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid);
       return BN == 256 ? launch_one<256, 0, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid)

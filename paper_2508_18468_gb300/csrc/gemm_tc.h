@@ -18,7 +18,8 @@ enum Mode {
   MODE_PLAIN = 0,  // out_f[m + n ld_out] = D (fp32)
   MODE_PROP = 1,   // propagation: out_f as PLAIN + per-row sums of D^2 into partial
   MODE_GRAM = 2,   // Gram: D into the real (part 0) / imaginary (part 1) half of complex64 G_b
-  MODE_TRMM = 3    // U R^-1: D into V_b (fp32) and its fp16 planes
+  MODE_TRMM = 3,   // U R^-1: D into V_b (fp32) and its fp16 planes
+  MODE_ADDV = 4    // out_f[b stride + m + n ld_out] = in_f[same] + D, and its fp16 planes out_h, out_l
 };
 
 struct Params {
@@ -28,7 +29,7 @@ struct Params {
   int mtiles, ntiles_n;  //   mtiles x ntiles_n tiles per batch item (batch = ntiles / (mtiles ntiles_n))
   int chunk_kb;        // >0 (BN = 128 only): drain TMEM into fp32 registers every chunk_kb K-blocks
   int64_t out_batch_stride;  // PLAIN: elements between batch items of out_f
-  const float* in_f;   // TRMM: if set, out = in + D (D = U (T - 1))
+  const float* in_f;   // TRMM: if set, out = in + D (D = U (T - 1)); ADDV: the array D is added to
   int kblocks;         // K / BK
   int tri_k;           // limit K-blocks to (nt+1) BN / BK (triangular B)
   int a_rows_per_b;    // A row offset per batch item

@@ -469,6 +469,95 @@ cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void
 
 }  // namespace fm
 
+// ====================================================================== projector correction
+// The float state is orthonormal only to ~1e-7 (G = U^dag U = 1 + E), and C = U U^dag
+// is then not a projector: its eigenvalues near 1 sit ~|E| off 1, and -d ln d over
+// thousands of them biases the entropy by ~1e-3 at l = 8192.  The state's C is the
+// projector onto span(U), U G^-1 U^dag; to first order in E (|E|^2 ~ 1e-14):
+//   n <= N:  C_A = U_A G^-1 U_A^dag      ~ M - U_A E U_A^dag
+//   n >  N:  spectrum of G^-1/2 U_A^dag U_A G^-1/2 ~ M_t - (E M_t + M_t E) / 2,
+//            M = conj(M_t)  ->  M - (conj(E) M + M conj(E)) / 2.
+// The products carry the factor E, so complex64 products leave errors ~1e-14; the
+// subtraction is done in float64 on the lower triangle.
+namespace fm {
+namespace xg {
+
+// Ec = (conj ? conj(Gx) : Gx) - 1 as complex64, full from the lower triangle of Gx (m x m)
+__global__ void e_from_gram_kernel(const z64* __restrict__ Gx, int m, int conj_, c32* Ec) {
+  const int64_t tot = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    z64 g = i >= j ? Gx[i + (int64_t)j * m] : cconj(Gx[j + (int64_t)i * m]);
+    if (conj_) g = cconj(g);
+    if (i == j) g.re -= 1.0;
+    Ec[idx] = cmk((float)g.re, (float)g.im);
+  }
+}
+
+// complex64 copy of a complex128 array; herm != 0: m x m Hermitian, full from the lower triangle
+__global__ void to_c32_kernel(const z64* __restrict__ X, int64_t n, int m, int herm, c32* Y) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    z64 v;
+    if (herm) {
+      const int i = (int)(idx % m), j = (int)(idx / m);
+      v = i >= j ? X[i + (int64_t)j * m] : cconj(X[j + (int64_t)i * m]);
+    } else {
+      v = X[idx];
+    }
+    Y[idx] = cmk((float)v.re, (float)v.im);
+  }
+}
+
+// lower triangle of M -= D (sym == 0) or M -= (Z + Z^dag) / 2 (sym != 0), D / Z complex64 m x m
+__global__ void sub_lower_kernel(z64* M, int m, const c32* __restrict__ D, int sym) {
+  const int64_t tot = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    if (i < j) continue;
+    double dr = D[idx].re, di = D[idx].im;
+    if (sym) {
+      const c32 t = D[j + (int64_t)i * m];
+      dr = 0.5 * (dr + (double)t.re);
+      di = 0.5 * (di - (double)t.im);
+    }
+    M[idx].re -= dr;
+    M[idx].im -= di;
+  }
+}
+
+}  // namespace xg
+
+size_t projector_scratch_bytes(int N) { return (size_t)4 * N * N * sizeof(c32) + 1024; }
+
+cudaError_t projector_correct(cudaStream_t st, const z64* Gx, const z64* XA, int n, int N, z64* M, void* scratch,
+                              int64_t* launches) {
+  using namespace xg;
+  const int m = std::min(n, N);
+  const bool sites = n <= N;
+  c32* Ec = (c32*)scratch;                       // N x N
+  c32* A = Ec + (int64_t)N * N;                  // n <= N: U_A (n x N); else M as complex64 (N x N)
+  c32* P = A + (int64_t)N * N;                   // products
+  c32* D = P + (int64_t)N * N;
+  const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
+  e_from_gram_kernel<<<152 * 8, 256, 0, st>>>(Gx, N, sites ? 1 : 0, Ec);
+  cudaError_t e;
+  if (sites) {
+    to_c32_kernel<<<152 * 8, 256, 0, st>>>(XA, (int64_t)n * N, n, 0, A);
+    if ((e = zgemm<float>(st, n, N, N, OP_N, OP_N, one, A, n, 0, Ec, N, 0, zero, P, n, 0, 1, 0))) return e;
+    if ((e = zgemm<float>(st, n, n, N, OP_N, OP_C, one, P, n, 0, A, n, 0, zero, D, n, 0, 1, GEMM_LOWER_ONLY)))
+      return e;
+    sub_lower_kernel<<<152 * 8, 256, 0, st>>>(M, m, D, 0);
+  } else {
+    to_c32_kernel<<<152 * 8, 256, 0, st>>>(M, (int64_t)N * N, N, 1, A);
+    if ((e = zgemm<float>(st, N, N, N, OP_N, OP_N, one, Ec, N, 0, A, N, 0, zero, D, N, 0, 1, 0))) return e;
+    sub_lower_kernel<<<152 * 8, 256, 0, st>>>(M, m, D, 1);
+  }
+  if (launches) *launches += 5;
+  return cudaGetLastError();
+}
+
+}  // namespace fm
+
 // ====================================================================== test hooks
 extern "C" unsigned long long fmx_exact_gram_scratch_bytes(int nmax, int N) {
   return (unsigned long long)fm::exact_gram_scratch_bytes(nmax, N);

@@ -59,11 +59,52 @@ size_t pm_wide_scratch_bytes(int L, int B);
 // which of the two projective paths suits this shape
 bool pm_use_wide(int L, int N, int B);
 
+// ---- projective measurements of a step as a block (pm_block.cu; mixed precision)
+struct PmbEvent {
+  double sp, c, dsel;
+  int outcome, active;
+};
+// K x K complex64 coefficient matrices of every trajectory (stride sM = Kc * Kc
+// per trajectory; row-major TBr, CTB, TA, CTA, TE, column-major C, TBc), the
+// per-event vectors (stride Kc), and the K x N blocks W (rows of U0 at the
+// selected sites) and X = T_B^dag W (column-major, ld Kc, stride sW).
+struct PmbMats {
+  int Kc;
+  int64_t sM, sW;
+  c32 *C, *TBr, *TBc, *CTB, *TA, *CTA, *TE;
+  c32 *rho, *y, *ys, *g;
+  PmbEvent* ev;
+  c32 *Wc, *X;
+};
+int pmb_capacity(int L);   // largest block (selected sites per step) the scratch holds
+cudaError_t pmb_setup(cudaStream_t st, const int* list, const int* count, int L, int B, int nmax, int* pos);
+cudaError_t pmb_gather_w(cudaStream_t st, const __half* urm_h, const __half* urm_l, int L, int N, const int* list,
+                         const int* count, int b, int K, __half* wt_h, __half* wt_l);
+cudaError_t pmb_gather_c(cudaStream_t st, const float* Dp, int64_t sD, int L, int K, int B, const int* list,
+                         const int* count, const PmbMats& m);
+cudaError_t pmb_event(cudaStream_t st, int i, int Kc, int L, int B, const int* count, const int* list,
+                      const double* ulist, const int64_t* step, const PmbMats& m, fm_event* log,
+                      unsigned long long* log_count, int log_capacity, int nmax);
+cudaError_t pmb_ttilde(cudaStream_t st, const PmbMats& m, int K, int b, __half* th, __half* tl);
+cudaError_t pmb_split(cudaStream_t st, const float* x, int64_t n, __half* h, __half* l);
+cudaError_t pmb_atilde(cudaStream_t st, const float* Ap, int L, int K, int b, const int* pos, const PmbMats& m,
+                       __half* ah, __half* al);
+cudaError_t pmb_gather_wc(cudaStream_t st, const float* V, int L, int N, int K, int B, const int* list,
+                          const int* count, const PmbMats& m);
+cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int b, int N, __half* xh, __half* xl);
+// the selection step of the grid-wide path: per trajectory the measured sites
+// (ascending) and their outcome draws; count per trajectory
+cudaError_t pm_select(cudaStream_t st, const pm_args& a, int* list, double* ulist, int* count);
+
 // ---- Cholesky / triangular inverse (T = double or float)
 constexpr int CHOL_NB = 32;
 // T_b = R_b^-1 with G_b = R_b^dag R_b for the n x n blocks at G, R, Tm (leading
 // dimension ld, batch stride sNN; upper part of G read, G overwritten).
 // Scratch per trajectory: Dinv ceil(alloc_n/32) 32 x 32 blocks, X alloc_n x 32.
+// G = R^dag R and T = R^-1 of an n x n complex64 block (n <= 128) per trajectory
+// in one CTA each (shared memory); R, T written with zeros below the diagonal.
+cudaError_t chol_inv_leaf(cudaStream_t st, const c32* G, c32* R, c32* T, int n, int64_t ld, int64_t sNN, int B,
+                          int* status);
 template <typename T>
 cudaError_t cholesky_inverse(cudaStream_t st, cplx<T>* G, cplx<T>* R, cplx<T>* Tm, cplx<T>* Dinv, cplx<T>* X, int n,
                              int ld, int64_t sNN, int alloc_n, int B, int* status, int64_t* launches);
@@ -99,7 +140,7 @@ cudaError_t check_finite_z(cudaStream_t st, const z64* X, int64_t n, int* dev_st
 
 // ---- eigenvalues / entropy (FP64)
 // in: Hermitian m x m matrix M (column-major, overwritten; for m > 256 only its
-// lower triangle is read); out: S = -sum f(lambda).  pbuf: 1 + 2 * ceil(m/64) * m + m
+// lower triangle is read); out: S = -sum f(lambda).  pbuf: hermitian_entropy_pbuf(m)
 // complex entries of scratch.
 cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vbuf, z64* wbuf, z64* pbuf,
                               double* partial, double* d, double* e, double* lam, double* S_dev,
@@ -107,10 +148,28 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vbuf, z64* wb
 // size of pbuf (complex entries) hermitian_entropy needs for an m x m matrix
 constexpr int EIG_TILE = 32;
 constexpr int64_t hermitian_entropy_pbuf(int m) {
-  return 1 + 2 * (int64_t)((m + EIG_TILE - 1) / EIG_TILE) * m + m + m / 256 + 2;
+  return 1 + 2 * (int64_t)((m + EIG_TILE - 1) / EIG_TILE) * m + m + m / 256 + 2 + 2 * (int64_t)m;
 }
 // the lower triangle alone is enough for this m
 inline bool hermitian_entropy_lower_only(int m) { return m > 256; }
+
+// ---- structured propagation: stencils of the circulant propagator (banded.cu)
+constexpr int kBandMaxTaps = 41;   // half-width <= 20
+int band_chunks(int L, int N, int B);
+// layout 0: complex128 U (L x N per trajectory); 1: float V (2L x N).  dir 0 along x,
+// 1 along y.  partial (may be NULL): row sums of |out|^2 per column chunk, nch chunks.
+cudaError_t band_propagate(cudaStream_t st, int layout, const void* in, void* out, int L, int N, int B, int Lx,
+                           int Ly, int dir, const z64* taps, const int* off, int ntap, double* partial, int nch);
+
+// ---- density correlations and particle covariance (observables.cu)
+cudaError_t v_to_c32(cudaStream_t st, const float* V, int L, int N, c32* U);
+cudaError_t gather_rows_c32(cudaStream_t st, const float* V, int L, int N, const int* sites, int n, c32* out);
+// bins[d] += sum over the stripe columns j0 .. j0+S-1 of |X(j - d, j - j0)|^2 (periodic in x, y; d != 0)
+template <typename T>
+cudaError_t displacement_bins(cudaStream_t st, const cplx<T>* X, int L, int Lx, int Ly, int j0, int S, double* bins);
+int abs2_partials();   // doubles of `part` sum_abs2 uses
+template <typename T>
+cudaError_t sum_abs2(cudaStream_t st, const cplx<T>* M, int64_t n, double* part, double* out);
 
 // ---- exact-product Gram of a float-valued block on the tensor cores (gram_exact.cu)
 // X: n x N complex128 block (column-major, ld = n) whose entries are floats.
@@ -121,5 +180,12 @@ inline bool hermitian_entropy_lower_only(int m) { return m > 256; }
 size_t exact_gram_scratch_bytes(int nmax, int N);
 cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void* scratch, int* status,
                        int64_t* launches);
+// First-order correction of M (the lower triangle exact_gram wrote for the block XA
+// of n gathered rows) from C = U U^dag to the projector onto span(U): Gx is the
+// exact_gram of all L rows of U (= conj(U^dag U), lower triangle, N x N).
+// scratch: projector_scratch_bytes(N).
+size_t projector_scratch_bytes(int N);
+cudaError_t projector_correct(cudaStream_t st, const z64* Gx, const z64* XA, int n, int N, z64* M, void* scratch,
+                              int64_t* launches);
 
 }  // namespace fm

@@ -557,6 +557,11 @@ __global__ void pm_update_kernel(void* Ub, int L, int N, int kchunk, const void*
   for (int k = k0; k < k1; ++k) u.add(i, k, cmul(d, xb[k]));
 }
 
+cudaError_t pm_select(cudaStream_t st, const pm_args& a, int* list, double* ulist, int* count) {
+  pm_select_kernel<<<a.batch, 1024, 0, st>>>(a.gamma, a.dt, a.traj, a.step, a.seed, a.L, list, ulist, count);
+  return cudaGetLastError();
+}
+
 cudaError_t pm_measure_wide(cudaStream_t st, const pm_args& a, void* scratch, int64_t* launches) {
   // scratch: list (B*L int), ulist (B*L double), count (B int), events (B PmEvent)
   char* s = (char*)scratch;

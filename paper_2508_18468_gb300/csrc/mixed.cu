@@ -35,12 +35,19 @@ int pick_gm(int tile_config) {
 struct Scratch {
   size_t total = 0;
   size_t tiles_prop, tiles_gram, tiles_trmm, tiles_trmm2, urm_h, urm_l;
+  // block projective update (pm_block.cu), projective states that use it only
+  size_t pb_list, pb_ulist, pb_count, pb_pos, pb_wt_h, pb_wt_l, pb_dp, pb_dph, pb_dpl, pb_ap, pb_ath, pb_atl;
+  size_t pb_tth, pb_ttl, pb_xth, pb_xtl, pb_mats, pb_vecs, pb_ev, pb_wc, pb_x;
+  int pb_kc = 0;
   size_t ca_h, ca_l, cb_h, cb_l, cd, xs;   // complex tensor GEMM helper (Cholesky recursion)
   size_t gf, rf, tf, dinvf, xf, diag;     // complex64 Gram / factor / inverse, FP64 Gram diagonal
   size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
 };
 
-Scratch scratch_plan(int Lx, int Ly, int B) {
+// the block projective update serves the shapes the one-CTA-per-trajectory kernel does not
+bool uses_pm_block(int protocol, int L, int B) { return protocol == FM_PROJECTIVE && pm_use_wide(L, L / 2, B); }
+
+Scratch scratch_plan(int Lx, int Ly, int B, int protocol) {
   Scratch s;
   const int64_t L = (int64_t)Lx * Ly, N = L / 2;
   const int BN = 128;                              // the longer tile lists of either width
@@ -66,6 +73,31 @@ Scratch scratch_plan(int Lx, int Ly, int B) {
   s.dinvf = s.take((int64_t)B * ((N + 31) / 32) * 32 * 32 * 8);
   s.xf = s.take((int64_t)B * N * 32 * 8);
   s.diag = s.take((int64_t)B * N * 8);
+  if (uses_pm_block(protocol, (int)L, B)) {
+    const int64_t Kc = pmb_capacity((int)L);
+    s.pb_kc = (int)Kc;
+    s.pb_list = s.take(B * L * 4);
+    s.pb_ulist = s.take(B * L * 8);
+    s.pb_count = s.take(B * 4);
+    s.pb_pos = s.take(B * L * 4);
+    s.pb_wt_h = s.take(2 * Kc * 2 * N * 2);
+    s.pb_wt_l = s.take(2 * Kc * 2 * N * 2);
+    s.pb_dp = s.take(B * L * 2 * Kc * 4);
+    s.pb_dph = s.take(L * 2 * Kc * 2);
+    s.pb_dpl = s.take(L * 2 * Kc * 2);
+    s.pb_ap = s.take(L * 2 * Kc * 4);
+    s.pb_ath = s.take(2 * L * 2 * Kc * 2);
+    s.pb_atl = s.take(2 * L * 2 * Kc * 2);
+    s.pb_tth = s.take(2 * Kc * 2 * Kc * 2);
+    s.pb_ttl = s.take(2 * Kc * 2 * Kc * 2);
+    s.pb_xth = s.take(N * 2 * Kc * 2);
+    s.pb_xtl = s.take(N * 2 * Kc * 2);
+    s.pb_mats = s.take(7 * B * Kc * Kc * 8);
+    s.pb_vecs = s.take(4 * B * Kc * 8);
+    s.pb_ev = s.take(B * (int64_t)sizeof(PmbEvent));
+    s.pb_wc = s.take(B * Kc * N * 8);
+    s.pb_x = s.take(B * Kc * N * 8);
+  }
   return s;
 }
 
@@ -244,6 +276,15 @@ struct MixedHost {
   CUtensorMap gram_Ah, gram_Al, gram_Bh, gram_Bl;
   CUtensorMap trmm_Ah, trmm_Al, trmm_Bh, trmm_Bl;
   CUtensorMap trmm2_Bh, trmm2_Bl;   // 256-row boxes of the factor planes (second pass)
+  // block projective update
+  bool pmb;
+  int pb_kc;
+  int *pb_list, *pb_count, *pb_pos;
+  double* pb_ulist;
+  __half *pb_wt_h, *pb_wt_l, *pb_dph, *pb_dpl, *pb_ath, *pb_atl, *pb_tth, *pb_ttl, *pb_xth, *pb_xtl;
+  float *pb_dp, *pb_ap;
+  PmbMats pm;
+  std::vector<int> pb_hcount;
 };
 
 bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* why) {
@@ -267,7 +308,9 @@ bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* wh
   return true;
 }
 
-size_t mixed_scratch_bytes(int Lx, int Ly, int batch) { return scratch_plan(Lx, Ly, batch).total; }
+size_t mixed_scratch_bytes(int Lx, int Ly, int batch, int protocol) {
+  return scratch_plan(Lx, Ly, batch, protocol).total;
+}
 
 void mixed_free(MixedHost* h) { delete h; }
 
@@ -281,7 +324,7 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   h->BN = pick_bn(N, c->tile_config);
   const int BN = h->BN;
   const int GM = pick_gm(c->tile_config);
-  Scratch sp = scratch_plan(c->Lx, c->Ly, B);
+  Scratch sp = scratch_plan(c->Lx, c->Ly, B, c->protocol);
   char* base = (char*)c->extra;
   h->tiles_prop = (int4*)(base + sp.tiles_prop);
   h->tiles_gram = (int4*)(base + sp.tiles_gram);
@@ -302,6 +345,48 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   h->dinvf = (c32*)(base + sp.dinvf);
   h->xf = (c32*)(base + sp.xf);
   h->diag = (double*)(base + sp.diag);
+  h->pmb = uses_pm_block(c->protocol, L, B);
+  if (h->pmb) {
+    const int64_t Kc = sp.pb_kc;
+    h->pb_kc = sp.pb_kc;
+    h->pb_list = (int*)(base + sp.pb_list);
+    h->pb_ulist = (double*)(base + sp.pb_ulist);
+    h->pb_count = (int*)(base + sp.pb_count);
+    h->pb_pos = (int*)(base + sp.pb_pos);
+    h->pb_wt_h = (__half*)(base + sp.pb_wt_h);
+    h->pb_wt_l = (__half*)(base + sp.pb_wt_l);
+    h->pb_dp = (float*)(base + sp.pb_dp);
+    h->pb_dph = (__half*)(base + sp.pb_dph);
+    h->pb_dpl = (__half*)(base + sp.pb_dpl);
+    h->pb_ap = (float*)(base + sp.pb_ap);
+    h->pb_ath = (__half*)(base + sp.pb_ath);
+    h->pb_atl = (__half*)(base + sp.pb_atl);
+    h->pb_tth = (__half*)(base + sp.pb_tth);
+    h->pb_ttl = (__half*)(base + sp.pb_ttl);
+    h->pb_xth = (__half*)(base + sp.pb_xth);
+    h->pb_xtl = (__half*)(base + sp.pb_xtl);
+    PmbMats& m = h->pm;
+    m.Kc = (int)Kc;
+    m.sM = Kc * Kc;
+    m.sW = Kc * N;
+    c32* mats = (c32*)(base + sp.pb_mats);
+    m.C = mats;
+    m.TBr = mats + 1 * B * m.sM;
+    m.TBc = mats + 2 * B * m.sM;
+    m.CTB = mats + 3 * B * m.sM;
+    m.TA = mats + 4 * B * m.sM;
+    m.CTA = mats + 5 * B * m.sM;
+    m.TE = mats + 6 * B * m.sM;
+    c32* vecs = (c32*)(base + sp.pb_vecs);
+    m.rho = vecs;
+    m.y = vecs + 1 * B * Kc;
+    m.ys = vecs + 2 * B * Kc;
+    m.g = vecs + 3 * B * Kc;
+    m.ev = (PmbEvent*)(base + sp.pb_ev);
+    m.Wc = (c32*)(base + sp.pb_wc);
+    m.X = (c32*)(base + sp.pb_x);
+    h->pb_hcount.assign(B, 0);
+  }
   std::vector<int4> tp = tc::tile_list(2 * L / tc::BM, B * N / BN, 1, 1, false, BN, GM);
   std::vector<int4> tg = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, GM);
   std::vector<int4> tt = tc::tile_list(L / tc::BM, 2 * N / 128, B, 1, false, 128, GM);
@@ -413,11 +498,7 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   c32* T = h->tf;
   const int64_t d0 = off + (int64_t)off * N;
   if (n <= 128) {
-    int64_t nl = 0;
-    cudaError_t e = cholesky_inverse<float>(c->st, G + d0, R + d0, T + d0, h->dinvf, h->xf, n, N, sNN, N, c->B,
-                                            c->status, &nl);
-    c->launches += nl;
-    if (e != cudaSuccess) { c->err = std::string("cholesky leaf: ") + cudaGetErrorString(e); return FM_ECUDA; }
+    MCK(chol_inv_leaf(c->st, G + d0, R + d0, T + d0, n, N, sNN, c->B, c->status));
     return FM_OK;
   }
   const int hh = std::max(128, (n / 2 / 128) * 128);
@@ -492,26 +573,138 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
   return FM_OK;
 }
 
+// Tensor-core product D = A B^T of K-major fp16 planes (raster tile order, one
+// batch item): A rows M, B rows Nd, contraction Kd; mode PLAIN (D into out_f with
+// ld_out) or ADDV (out_f = in_f + D and its planes).
+int plane_gemm(MixedHost* h, MixedCtx* c, int mode, const __half* ah, const __half* al, const __half* bh,
+               const __half* bl, int M, int Nd, int Kd, int BN, float* out_f, int64_t ld_out, const float* in_f,
+               __half* out_h, __half* out_l) {
+  CUtensorMap mah, mal, mbh, mbl;
+  if (!tc::make_kmajor_map(&mah, ah, Kd, M, Kd, tc::BM) || !tc::make_kmajor_map(&mal, al, Kd, M, Kd, tc::BM) ||
+      !tc::make_kmajor_map(&mbh, bh, Kd, Nd, Kd, BN) || !tc::make_kmajor_map(&mbl, bl, Kd, Nd, Kd, BN)) {
+    c->err = "block projective update: tensor maps";
+    return FM_ECUDA;
+  }
+  tc::Params p = base_params(c, h);
+  p.mode = mode;
+  p.tiles = nullptr;
+  p.mtiles = M / tc::BM;
+  p.ntiles_n = Nd / BN;
+  p.ntiles = p.mtiles * p.ntiles_n;
+  p.kblocks = Kd / tc::BK;
+  p.out_f = out_f;
+  p.ld_out = ld_out;
+  p.in_f = in_f;
+  p.out_h = out_h;
+  p.out_l = out_l;
+  MCK(tc::launch(c->st, BN, mah, mal, mbh, mbl, p, tc::sm_count()));
+  return FM_OK;
+}
+
+// The projective measurements of the step as one block (pm_block.cu): select
+// the sites, form P = U0 W^dag and C on the tensor cores, run the events on the
+// K x K coefficients, then U <- U0 + A B^dag on the tensor cores.  *done =
+// false (nothing changed) when a trajectory selected more sites than the
+// block scratch holds; the caller then takes the per-event path.
+int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
+  const int L = c->L, N = c->N, B = c->B;
+  *done = false;
+  pm_args a;
+  a.U = c->V; a.L = L; a.N = N; a.batch = B; a.layout = 1;
+  a.gamma = c->gamma; a.dt = c->dt; a.traj = c->traj; a.step = c->step; a.seed = c->seed;
+  MCK(pm_select(c->st, a, h->pb_list, h->pb_ulist, h->pb_count));
+  int* hc = h->pb_hcount.data();
+  MCK(cudaMemcpyAsync(hc, h->pb_count, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st));
+  MCK(cudaStreamSynchronize(c->st));
+  int kmax = 0;
+  for (int b = 0; b < B; ++b) kmax = std::max(kmax, hc[b]);
+  if (kmax > h->pb_kc) return FM_OK;
+  *done = true;
+  if (kmax == 0) return FM_OK;
+  const int K = ((kmax + 63) / 64) * 64;
+  const int Kc = h->pb_kc;
+  PmbMats& m = h->pm;
+  const int64_t sD = (int64_t)L * 2 * Kc;
+  // U~ planes (L x 2N per trajectory, K-major) of the propagated state (the
+  // propagation writes the float state only, so its planes are made here)
+  MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
+  transpose_planes_kernel<<<dim3(L / 32, 2 * N / 32, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
+                                                                                  h->urm_l);
+  MCK(cudaGetLastError());
+  MCK(pmb_setup(c->st, h->pb_list, h->pb_count, L, B, kmax, h->pb_pos));
+  MCK(cudaMemsetAsync(m.C, 0, sizeof(c32) * 7 * (size_t)B * m.sM, c->st));
+  // P_b = U0_b W_b^dag as the row-major real form [Re P | Im P] (L x 2K)
+  for (int b = 0; b < B; ++b) {
+    MCK(pmb_gather_w(c->st, h->urm_h, h->urm_l, L, N, h->pb_list, h->pb_count, b, K, h->pb_wt_h, h->pb_wt_l));
+    const int64_t uo = (int64_t)b * L * 2 * N;
+    int r = plane_gemm(h, c, tc::MODE_PLAIN, h->pb_wt_h, h->pb_wt_l, h->urm_h + uo, h->urm_l + uo, 2 * K, L, 2 * N,
+                       256, h->pb_dp + b * sD, 2 * K, nullptr, nullptr, nullptr);
+    if (r) return r;
+  }
+  MCK(pmb_gather_c(c->st, h->pb_dp, sD, L, K, B, h->pb_list, h->pb_count, m));
+  // the events, in order
+  for (int i = 0; i < kmax; ++i) {
+    MCK(pmb_event(c->st, i, Kc, L, B, h->pb_count, h->pb_list, h->pb_ulist, c->step, m, c->log,
+                  (unsigned long long*)c->log_count, c->log_capacity, kmax));
+    c->launches += i > 0 ? 3 : 2;                 // with the one MCK counts: 4 (3 for the first event)
+  }
+  // B^dag = T_B^dag W
+  MCK(pmb_gather_wc(c->st, c->V, L, N, K, B, h->pb_list, h->pb_count, m));
+  const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
+  MCK(zgemm<float>(c->st, K, N, K, OP_C, OP_N, one, m.TBc, Kc, m.sM, m.Wc, Kc, m.sW, zero, m.X, Kc, m.sW, B, 0));
+  // per trajectory: A = P T_A (+ E_S T_E in the planes), then V2_b = V_b + A B^dag
+  const int BNu = (N % 256 == 0) ? 256 : 128;
+  for (int b = 0; b < B; ++b) {
+    MCK(pmb_ttilde(c->st, m, K, b, h->pb_tth, h->pb_ttl));
+    MCK(pmb_split(c->st, h->pb_dp + b * sD, (int64_t)L * 2 * K, h->pb_dph, h->pb_dpl));
+    int r = plane_gemm(h, c, tc::MODE_PLAIN, h->pb_tth, h->pb_ttl, h->pb_dph, h->pb_dpl, 2 * K, L, 2 * K, 256,
+                       h->pb_ap, 2 * K, nullptr, nullptr, nullptr);
+    if (r) return r;
+    MCK(pmb_atilde(c->st, h->pb_ap, L, K, b, h->pb_pos, m, h->pb_ath, h->pb_atl));
+    MCK(pmb_xtilde(c->st, m, K, b, N, h->pb_xth, h->pb_xtl));
+    const int64_t vo = (int64_t)b * 2 * L * N;
+    r = plane_gemm(h, c, tc::MODE_ADDV, h->pb_ath, h->pb_atl, h->pb_xth, h->pb_xtl, 2 * L, N, 2 * K, BNu,
+                   c->V2 + vo, 2 * L, c->V + vo, c->Vh + vo, c->Vl + vo);
+    if (r) return r;
+  }
+  std::swap(c->V, c->V2);
+  return FM_OK;
+}
+
 }  // namespace
 
 int mixed_step(MixedHost* h, MixedCtx* c) {
   const int L = c->L, N = c->N, B = c->B, BN = h->BN;
   const int grid = tc::sm_count();
   // 1. propagation V2 = A V with row sums of squares
-  tc::Params p = base_params(c, h);
-  p.mode = tc::MODE_PROP;
-  p.ntiles = h->n_prop;
-  p.tiles = h->tiles_prop;
-  p.kblocks = 2 * L / tc::BK;
-  p.out_f = c->V2;
-  p.ld_out = 2 * (int64_t)L;
-  p.partial = c->part;
+  int nchunks = 2 * (N / BN);
   c->timer->begin(FM_PH_PROPAGATE);
-  MCK(tc::launch(c->st, BN, h->prop_Ah, h->prop_Al, h->prop_Bh, h->prop_Bl, p, grid));
+  if (c->prop_banded) {
+    // stencils along x (and y): V -> V2 (-> V); the last pass sums |U|^2 per row
+    nchunks = band_chunks(L, N, B);
+    const bool torus = c->Ly > 1;
+    MCK(band_propagate(c->st, 1, c->V, c->V2, L, N, B, c->Lx, c->Ly, 0, c->band_tx, c->band_ox, c->ntap_x,
+                       torus ? nullptr : c->part, nchunks));
+    if (torus) {
+      MCK(band_propagate(c->st, 1, c->V2, c->V, L, N, B, c->Lx, c->Ly, 1, c->band_ty, c->band_oy, c->ntap_y,
+                         c->part, nchunks));
+    } else {
+      std::swap(c->V, c->V2);
+    }
+  } else {
+    tc::Params p = base_params(c, h);
+    p.mode = tc::MODE_PROP;
+    p.ntiles = h->n_prop;
+    p.tiles = h->tiles_prop;
+    p.kblocks = 2 * L / tc::BK;
+    p.out_f = c->V2;
+    p.ld_out = 2 * (int64_t)L;
+    p.partial = c->part;
+    MCK(tc::launch(c->st, BN, h->prop_Ah, h->prop_Al, h->prop_Bh, h->prop_Bl, p, grid));
+    std::swap(c->V, c->V2);
+  }
   c->timer->end(FM_PH_PROPAGATE);
-  std::swap(c->V, c->V2);
   const int k = c->reorth_interval;
-  const int nchunks = 2 * (N / BN);
   if (c->protocol == FM_HOMODYNE) {
     c->timer->begin(FM_PH_MEASURE);
     MCK(reduce_occupations(c->st, c->part, nchunks, L, B, c->nocc, c->w, c->gamma, c->dt, c->traj, c->step, c->seed));
@@ -531,13 +724,21 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     a.log = c->log; a.log_count = c->log_count; a.log_capacity = c->log_capacity;
     a.dev_status = c->status;
     c->timer->begin(FM_PH_MEASURE);
-    if (pm_use_wide(L, N, B)) {
-      cudaError_t e = pm_measure_wide(c->st, a, c->pmw, &c->launches);
-      if (e != cudaSuccess) { c->err = std::string("projective update: ") + cudaGetErrorString(e); return FM_ECUDA; }
-    } else {
-      MCK(pm_measure(c->st, a));
+    bool done = false;
+    if (h->pmb) {
+      int r = pm_block_step(h, c, &done);
+      if (r) return r;
     }
-    MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
+    if (!done) {
+      a.U = c->V;
+      if (pm_use_wide(L, N, B)) {
+        cudaError_t e = pm_measure_wide(c->st, a, c->pmw, &c->launches);
+        if (e != cudaSuccess) { c->err = std::string("projective update: ") + cudaGetErrorString(e); return FM_ECUDA; }
+      } else {
+        MCK(pm_measure(c->st, a));
+      }
+      MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
+    }
     c->timer->end(FM_PH_MEASURE);
     if ((c->global_step + 1) % k == 0) {
       int r = qr_pass(h, c, true);

@@ -30,6 +30,10 @@ struct MixedCtx {
   void* extra;             // mixed_scratch_bytes() of device scratch
   PhaseTimer* timer;       // phase events (may be off)
   void* pmw;               // scratch of the grid-wide projective update
+  int prop_banded;         // propagation as stencils (fm_set_propagation)
+  const z64 *band_tx, *band_ty;   // taps along x and y (device)
+  const int *band_ox, *band_oy;   // their site offsets
+  int ntap_x, ntap_y;
   int64_t launches;        // out: kernels launched
   std::string err;         // out: message on failure
 };
@@ -37,7 +41,7 @@ struct MixedCtx {
 struct MixedHost;          // tensor maps and tile lists of one state
 
 bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* why);
-size_t mixed_scratch_bytes(int Lx, int Ly, int batch);
+size_t mixed_scratch_bytes(int Lx, int Ly, int batch, int protocol);
 MixedHost* mixed_create(MixedCtx* c, std::string* why);   // uploads tile lists, encodes tensor maps
 void mixed_free(MixedHost* h);
 int mixed_step(MixedHost* h, MixedCtx* c);               // returns an fm_status value

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libfm.so")
 FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENUMERIC, FM_ETIMEOUT, FM_ESTATE = range(7)
 FM_PROJECTIVE, FM_HOMODYNE = 0, 1
 FM_FP64, FM_MIXED = 0, 1
+FM_PROP_DENSE, FM_PROP_BANDED = 0, 1
 PHASES = ("propagate", "measure", "gram", "cholesky", "trmm", "entropy")
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENUMERIC",
                 5: "FM_ETIMEOUT", 6: "FM_ESTATE"}
@@ -81,6 +82,9 @@ def _load():
         "fm_version": (ctypes.c_char_p, []),
         "fm_entropy_noalloc": (i32, [vp, i32, i32, P(i32), i32, vp, vp]),
         "fm_autotune": (i32, [P(fm_params), vp, sz, vp, i32, i32, dbl, i32, P(fm_tuning)]),
+        "fm_density_correlation": (i32, [vp, i32, P(dbl)]),
+        "fm_set_propagation": (i32, [vp, i32]),
+        "fm_particle_covariance": (i32, [vp, i32, P(i32), i32, P(i32), i32, P(dbl)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -228,6 +232,24 @@ class Trajectories:
         c, pb = _i32_array(B)
         out = ctypes.c_double()
         self._check(lib.fm_mutual_info(self._h, int(b), pa, int(a.size), pb, int(c.size), ctypes.byref(out)))
+        return out.value
+
+    def set_propagation(self, mode):
+        """FM_PROP_DENSE (dense GEMM) or FM_PROP_BANDED (stencils of the circulant propagator)."""
+        self._check(lib.fm_set_propagation(self._h, int(mode)))
+
+    def density_correlation(self, b=0):
+        """c[d] of Eq. (2) per displacement d = dx + Lx dy (numpy array of L floats, c[0] = 0)."""
+        out = np.empty(self.L, dtype=np.float64)
+        self._check(lib.fm_density_correlation(self._h, int(b), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def particle_covariance(self, A, B, b=0):
+        """G_AB of Eq. (GAB) on the lattice for disjoint site lists A and B."""
+        a, pa = _i32_array(A)
+        c, pb = _i32_array(B)
+        out = ctypes.c_double()
+        self._check(lib.fm_particle_covariance(self._h, int(b), pa, int(a.size), pb, int(c.size), ctypes.byref(out)))
         return out.value
 
     def copy_U(self, b=0):

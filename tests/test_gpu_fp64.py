@@ -222,3 +222,31 @@ def test_large_batch_uses_one_cta_per_trajectory_path(fm):
     for b in (0, 31, 63):
         ref = trajectory.run(Params(Lx=32, gamma=2.0, protocol=PROJECTIVE, seed=17, traj_id=b), 12)
         assert cdiff(g.copy_U(b), ref["U"]) <= C_TOL
+
+
+@pytest.mark.parametrize("Lx,Ly,protocol", [(64, 1, PROJECTIVE), (8, 6, HOMODYNE), (70, 1, HOMODYNE)])
+def test_density_correlation_and_particle_covariance(fm, Lx, Ly, protocol):
+    po, g = pair(fm, Lx, Ly, gamma=1.0, protocol=protocol, seed=19)
+    g.step(25)
+    U = trajectory.run(po, 25)["U"]
+    c = g.density_correlation()
+    assert np.max(np.abs(c - observables.displacement_correlation(U, Lx, Ly))) <= 1e-13
+    L = Lx * Ly
+    A, B = list(range(0, L // 4)), list(range(L // 2, L // 2 + L // 5))
+    G = g.particle_covariance(A, B)
+    assert abs(G - observables.particle_covariance(U, A, B)) <= 1e-13
+    assert g.particle_covariance([], B) == 0.0
+    with pytest.raises(fm.FmError):
+        g.particle_covariance(A, A[:2])
+
+
+@pytest.mark.parametrize("Lx,Ly,protocol", [(64, 1, PROJECTIVE), (8, 6, HOMODYNE), (1024, 1, HOMODYNE),
+                                             (6, 1, PROJECTIVE)])
+def test_banded_propagation_matches_dense_oracle(fm, Lx, Ly, protocol):
+    """Stencils of the circulant propagator (taps above 1e-18) against the oracle's dense P."""
+    po, g = pair(fm, Lx, Ly, gamma=1.0, protocol=protocol, seed=23, reorth=2)
+    g.set_propagation(fm.FM_PROP_BANDED)
+    n = 12
+    g.step(n)
+    ref = trajectory.run(po, n)
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL

@@ -92,3 +92,19 @@ def test_ring4096_mixed_against_fp64_gpu_over_60_steps(fm):
     assert rel <= 1e-3
     assert dc <= 2e-6 * n
     assert gm.orthonormality_error(list(range(0, 2048, 32))) <= 1e-6
+
+
+def test_torus160_density_correlation_sum_rule_and_block_covariance(fm):
+    """At 160 x 160: -sum_d c[d] = mean n (1 - n) (C^2 = C), c symmetric under d -> -d, and
+    the covariance of the two 40 x 40 blocks is non-negative."""
+    g = fm.Trajectories(fm.make_params(160, 160, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED, gamma=1.0,
+                                       seed=workloads.seed_of("torus160_both")))
+    g.step(3)
+    c = g.density_correlation()
+    n = g.occupations()
+    assert abs(-np.sum(c) - np.mean(n * (1 - n))) <= 1e-5 * np.mean(n * (1 - n))
+    cc = c.reshape(160, 160)                       # [dy, dx]
+    flip = np.roll(np.roll(cc[::-1, ::-1], 1, axis=0), 1, axis=1)
+    assert np.max(np.abs(cc - flip)) <= 1e-7
+    A, B, _ = workloads.torus_blocks()
+    assert g.particle_covariance(A, B) >= 0.0

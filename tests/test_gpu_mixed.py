@@ -130,3 +130,69 @@ def test_mixed_against_fp64_gpu_ring2048(fm):
     print("L=2048 mixed vs fp64 GPU: S=%.8f vs %.8f rel=%.2e" % (Sm, Sd, srel(Sm, Sd)))
     assert srel(Sm, Sd) <= S_REL
     assert gm.orthonormality_error(list(range(0, 1024, 16))) <= ORTHO
+
+
+def _compare_projective(fm, g, L, gamma, seed, n, batch):
+    ev, dropped = g.take_events()
+    assert dropped == 0
+    for b in range(batch):
+        ref = trajectory.run(Params(Lx=L, gamma=gamma, protocol=PROJECTIVE, seed=seed, traj_id=b), n)
+        got = sorted((e[1], e[2], e[5]) for e in ev if e[0] == b)
+        exp = sorted((s, j, o) for (s, j, u, p, o) in ref["events"])
+        if got != exp:
+            margins = [abs(u - p) for (s, j, u, p, o) in ref["events"]]
+            assert min(margins) < 1e-4, "outcome mismatch away from a near tie"
+            pytest.skip("near tie between draw and Born weight")
+        dc = cdiff(g.copy_U(b), ref["U"])
+        print("projective L=%d gamma=%g traj %d: %d events, max|dC|=%.2e" % (L, gamma, b, len(got), dc))
+        assert dc <= PER_STEP_C * n
+
+
+def test_projective_block_update_many_events(fm):
+    """~97 measured sites per step: the block update (events on the selected block, one
+    tensor-core update of U) against the oracle's event-by-event rank-1 updates."""
+    L, n = 1024, 6
+    g = mixed(fm, L, batch=2, protocol=fm.FM_PROJECTIVE, gamma=2.0, seed=45, event_capacity=100000)
+    g.step(n)
+    _compare_projective(fm, g, L, 2.0, 45, n, 2)
+    assert g.orthonormality_error(list(range(0, 512, 16))) <= ORTHO
+
+
+def test_projective_more_sites_than_the_block_holds(fm):
+    """gamma dt large enough that nearly every site is measured: the step falls back to
+    the event-by-event path and still matches the oracle."""
+    L, n = 256, 3
+    g = mixed(fm, L, batch=1, protocol=fm.FM_PROJECTIVE, gamma=60.0, seed=46, event_capacity=100000)
+    g.step(n)
+    _compare_projective(fm, g, L, 60.0, 46, n, 1)
+
+
+@pytest.mark.parametrize("Lx,Ly", [(256, 1), (16, 16)])
+def test_density_correlation_and_particle_covariance_mixed(fm, Lx, Ly):
+    n = 20
+    g = mixed(fm, Lx, Ly, protocol=fm.FM_HOMODYNE, gamma=0.7, seed=32)
+    g.step(n)
+    U = trajectory.run(Params(Lx=Lx, Ly=Ly, gamma=0.7, protocol=HOMODYNE, seed=32), n)["U"]
+    c = g.density_correlation()
+    ref = observables.displacement_correlation(U, Lx, Ly)
+    print("C(d) L=%dx%d: max|dc| = %.2e (max |c| %.2e)" % (Lx, Ly, np.max(np.abs(c - ref)), np.max(np.abs(ref))))
+    assert np.max(np.abs(c - ref)) <= PER_STEP_C * n
+    L = Lx * Ly
+    A, B = list(range(0, L // 4)), list(range(L // 2, L // 2 + L // 4))
+    G, Gref = g.particle_covariance(A, B), observables.particle_covariance(U, A, B)
+    assert abs(G - Gref) <= PER_STEP_C * n * max(1.0, Gref)
+
+
+@pytest.mark.parametrize("Lx,Ly,protocol", [(256, 1, HOMODYNE), (16, 16, PROJECTIVE), (512, 1, PROJECTIVE)])
+def test_banded_propagation_mixed(fm, Lx, Ly, protocol):
+    n = 16
+    prot = fm.FM_HOMODYNE if protocol == HOMODYNE else fm.FM_PROJECTIVE
+    g = mixed(fm, Lx, Ly, protocol=prot, gamma=0.8, seed=24, batch=2)
+    g.set_propagation(fm.FM_PROP_BANDED)
+    g.step(n)
+    for b in range(2):
+        ref = trajectory.run(Params(Lx=Lx, Ly=Ly, gamma=0.8, protocol=protocol, seed=24, traj_id=b), n)
+        dc = cdiff(g.copy_U(b), ref["U"])
+        print("banded mixed %dx%d traj %d: max|dC| = %.2e" % (Lx, Ly, b, dc))
+        assert dc <= PER_STEP_C * n
+    assert g.orthonormality_error(list(range(0, Lx * Ly // 2, 8))) <= ORTHO

@@ -126,3 +126,16 @@ def test_autotune_picks_a_configuration_that_meets_the_bar(fm):
     g = fm.Trajectories(q)
     g.step(4)
     assert g.orthonormality_error(list(range(0, 256, 8))) <= 1e-6
+
+
+def test_graphs_with_banded_propagation_equal_eager(fm):
+    kw = dict(batch=2, protocol=1, precision=1, gamma=0.9, seed=8)
+    a = fm.Trajectories(fm.make_params(512, **kw))
+    b = fm.Trajectories(fm.make_params(512, **kw))
+    for g in (a, b):
+        g.set_propagation(fm.FM_PROP_BANDED)
+    b.set_graphs(True)
+    a.step(9)
+    b.step(9)
+    for t in range(2):
+        assert np.array_equal(a.copy_U(t), b.copy_U(t))

@@ -255,6 +255,46 @@ def test_entropy_of_half_filled_random_state_matches_schmidt():
         assert abs(observables.entanglement_entropy(U, A) - sec.entropy(psi, A)) < 1e-11
 
 
+@pytest.mark.parametrize("Lx,Ly,N", [(10, 1, 5), (4, 3, 6)])
+def test_density_correlations_match_occupation_statistics(Lx, Ly, N):
+    """Eq. (2) and Eq. (GAB) against the joint occupation statistics of the brute-force
+    state: cov(n_i, n_j) = <n_i n_j> - <n_i><n_j> summed from |psi|^2 over the basis."""
+    L = Lx * Ly
+    U = _random_state(L, N, 11 + L)
+    sec = brute.Sector(L, N)
+    prob = np.abs(sec.from_orbitals(U)) ** 2
+    occ = sec.occ                                           # basis states x sites, 0/1
+    mean = occ.T @ prob
+    cov = (occ * prob[:, None]).T @ occ - np.outer(mean, mean)
+    c = observables.displacement_correlation(U, Lx, Ly)
+    x, y = np.arange(L) % Lx, np.arange(L) // Lx
+    for dy in range(Ly):
+        for dx in range(Lx):
+            d = dx + Lx * dy
+            if d == 0:
+                assert c[0] == 0.0
+                continue
+            j = (x + dx) % Lx + Lx * ((y + dy) % Ly)
+            assert abs(c[d] - np.mean(cov[np.arange(L), j])) < 1e-13, (dx, dy)
+    A, B = [0, 1, L // 2], [L // 2 + 1, L - 1]
+    NA, NB = occ[:, A].sum(axis=1), occ[:, B].sum(axis=1)
+    covAB = np.sum(prob * NA * NB) - np.sum(prob * NA) * np.sum(prob * NB)
+    assert abs(observables.particle_covariance(U, A, B) + covAB) < 1e-13
+    with pytest.raises(ValueError):
+        observables.particle_covariance(U, A, [0])
+
+
+def test_density_correlation_sum_rule_and_ring_symmetry():
+    """C^2 = C gives sum_j |C_ij|^2 = C_ii, so -sum_{d != 0} c[d] = mean_i n_i (1 - n_i);
+    on the ring c[d] = c[L - d]."""
+    L = 64
+    U = _random_state(L, L // 2, 21)
+    c = observables.displacement_correlation(U, L)
+    n = np.real(np.diag(observables.correlation(U)))
+    assert abs(-np.sum(c) - np.mean(n * (1 - n))) < 1e-13
+    assert np.max(np.abs(c[1:] - c[1:][::-1])) < 1e-15
+
+
 def test_binary_entropy_terms_edges():
     f = observables.binary_entropy_terms(np.array([0.0, 1.0, 0.5, -1e-17, 1 + 1e-16]))
     assert f[0] == 0 and f[1] == 0 and f[3] == 0 and f[4] == 0
