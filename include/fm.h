@@ -66,7 +66,22 @@ typedef enum {
   FM_ESTATE = 6      /* the state holds an earlier (sticky) error */
 } fm_status;
 
-typedef enum { FM_PROJECTIVE = 0, FM_HOMODYNE = 1 } fm_protocol;
+/* FM_PROJECTIVE: projective occupation measurements (Eqs. (A1), (A2)) after the
+ * propagation of each fixed step.  FM_HOMODYNE: the QSD protocol of Eq.
+ * (QSD_evo) as a split step (propagate, then weight).  FM_HOMODYNE_RK4: the
+ * same equation integrated as App. A does, one classical fourth-order
+ * Runge-Kutta step with the noise and <n>_t of the step's start held fixed
+ * (the hopping enters through H~ itself, nearest neighbours, so no propagator
+ * is used); the fixed-dt split step is its dt -> 0 limit.  FM_PROJECTIVE_POISSON:
+ * the projective protocol as App. A runs it, in continuous time: events of a
+ * Poisson process of total rate gamma N (N = L/2), each measuring one site drawn
+ * uniformly, exp(-i H~ tau) between events (stencils of Bessel-function taps);
+ * a step advances every trajectory by dt; QR every reorth_interval steps.
+ * Draws of event e: Philox counter (e, e >> 32, traj_lo, tag | traj_hi << 8);
+ * tag 3: waiting time -ln(1 - u) / (gamma N) with u from words 0-1, site
+ * floor(u' L) with u' from words 2-3; tag 4: Born draw from words 0-1 (53-bit
+ * uniforms as for the other protocols). */
+typedef enum { FM_PROJECTIVE = 0, FM_HOMODYNE = 1, FM_HOMODYNE_RK4 = 2, FM_PROJECTIVE_POISSON = 3 } fm_protocol;
 
 /* FM_FP64: every step in float64 / complex128.
  * FM_MIXED: U held as complex float32; the propagation, Gram and triangular
@@ -137,7 +152,9 @@ fm_status fm_step(fm_state* s, int32_t nsteps);
 enum { FM_PROP_DENSE = 0, FM_PROP_BANDED = 1 };
 fm_status fm_set_propagation(fm_state* s, int32_t mode);
 
-/* Per-trajectory monitoring rates (host array of `batch` doubles >= 0). */
+/* Per-trajectory monitoring rates (host array of `batch` doubles >= 0).  Under
+ * FM_PROJECTIVE_POISSON the event times of each trajectory become those of the
+ * new rate from t = 0 (events already past stay applied). */
 fm_status fm_set_gammas(fm_state* s, const double* gammas);
 
 /* Restart trajectory b from the Neel state at step 0 with a new id and rate

@@ -44,6 +44,17 @@ unsigned long long fmx_exact_gram_scratch_bytes(int nmax, int N);
  * same routine the mixed-precision entropy uses for m > 256. */
 int fmx_exact_gram(const void* X, int n, int N, void* M, void* d_scratch, void* stream);
 
+/* Host-only hooks of the continuous-time projective protocol (no device
+ * needed).  fmx_poisson_draw: the draws of event e of trajectory traj under
+ * seed, out[0] = u_wait, out[1] = site, out[2] = Born draw.  fmx_poisson_taps:
+ * the stencil of exp(-i H~ tau) along a direction of length n (half-width w:
+ * 2w + 1 taps at the offsets -w .. w; w < 0: n taps at 0 .. n-1), out as
+ * (re, im) pairs.  fmx_poisson_width: the half-width used for every tau <= dt
+ * (-1: every offset).  Return 0, or -1 on invalid arguments. */
+int fmx_poisson_draw(unsigned long long seed, unsigned long long traj, long long e, int L, double* out);
+int fmx_poisson_taps(int n, int w, double J, double tau, double* out);
+int fmx_poisson_width(int n, double J, double dt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,8 @@ MASK32 = np.uint64(0xFFFFFFFF)
 
 TAG_MEASURE = 1
 TAG_NOISE = 2
+TAG_EVENT = 3           # continuous-time projective protocol: waiting time and site of event e
+TAG_EVENT_OUTCOME = 4   # ... and its Born draw
 
 
 def philox4x32_10(ctr, key):
@@ -85,3 +87,17 @@ def noise_normals(seed, traj_id, step, L):
     u1 = uniform53(w[0], w[1])
     u2 = uniform53(w[2], w[3])
     return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def poisson_event(seed, traj_id, e, L):
+    """Continuous-time projective protocol (App. A): the draws of event e of a trajectory.
+
+    Counter (e & 0xffffffff, e >> 32, trajectory, tag): u_wait from words 0-1 of tag
+    EVENT (the waiting time is -ln(1 - u_wait) / rate), the site floor(u_site L) from
+    words 2-3, the Born draw u from words 0-1 of tag EVENT_OUTCOME."""
+    e = int(e)
+    w = philox4x32_10(counter(e & 0xFFFFFFFF, e >> 32, traj_id, TAG_EVENT), key_of(seed))
+    v = philox4x32_10(counter(e & 0xFFFFFFFF, e >> 32, traj_id, TAG_EVENT_OUTCOME), key_of(seed))
+    u_wait = float(uniform53(w[0], w[1]))
+    site = min(int(float(uniform53(w[2], w[3])) * L), L - 1)
+    return u_wait, site, float(uniform53(v[0], v[1]))

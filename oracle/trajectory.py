@@ -22,6 +22,8 @@ A step t -> t + dt (fixed dt) is
    * homodyne / QSD protocol (Eq. (A4)): U <- exp(dW + (2<n> - 1) gamma dt) U
      with dW_i = sqrt(gamma dt) xi_i, xi_i ~ N(0,1), and <n_i> = sum_k |U_ik|^2
      of the propagated state;
+   * the same protocol integrated as App. A does it (``HOMODYNE_RK4``): steps 1
+     and 2 together as one Runge-Kutta step of Eq. (QSD_evo) (``step_rk4``);
 3. re-orthonormalisation U <- Q of U = QR (App. A), every step for the
    homodyne protocol and every ``reorth_interval`` steps for the projective one
    (whose rank-1 updates keep U^dag U = 1 up to rounding).
@@ -34,6 +36,8 @@ from . import lattice, philox
 
 PROJECTIVE = 0
 HOMODYNE = 1
+HOMODYNE_RK4 = 2       # App. A's own integrator for Eq. (QSD_evo), see ``step_rk4``
+PROJECTIVE_POISSON = 3 # App. A's own continuous-time projective protocol, see ``run_poisson``
 
 
 @dataclass
@@ -121,11 +125,38 @@ def projective_measurements(U, p_meas, u_sel, u_out, forced=None):
     return U, events
 
 
-def step(U, P, prm, step_index, forced=None):
-    """Advance U from t = step_index*dt to t + dt.  Returns (U, events)."""
+def step_rk4(U, H, xi, gamma, dt):
+    """One step of Eq. (QSD_evo) by the classical fourth-order Runge-Kutta method (App. A).
+
+    Over the step the noise dW_i = sqrt(gamma dt) xi_i and <n_i>_t (of the state at the
+    start of the step) are held fixed, so dU/dt = A U with the constant matrix
+    A dt = -i dt H~ + diag(m), m_i = dW_i + (2 <n_i>_t - 1) gamma dt.  The four RK4 stages
+    k1 = A U, k2 = A (U + dt k1 / 2), k3 = A (U + dt k2 / 2), k4 = A (U + dt k3) give
+    U + dt (k1 + 2 k2 + 2 k3 + k4) / 6.  The caller re-orthonormalises.
+    """
+    n = occupations(U)
+    m = np.sqrt(gamma * dt) * xi + (2.0 * n - 1.0) * gamma * dt
+    A = -1j * H + np.diag(m / dt)
+    k1 = A @ U
+    k2 = A @ (U + 0.5 * dt * k1)
+    k3 = A @ (U + 0.5 * dt * k2)
+    k4 = A @ (U + dt * k3)
+    return U + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+
+def step(U, P, prm, step_index, forced=None, H=None):
+    """Advance U from t = step_index*dt to t + dt.  Returns (U, events).
+
+    P is the propagator of the split step; H (the hopping matrix) is used by the
+    Runge-Kutta protocol instead."""
     L = U.shape[0]
-    U = P @ U
     events = []
+    if prm.protocol == HOMODYNE_RK4:
+        if H is None:
+            H = lattice.hopping_matrix(prm.Lx, prm.Ly, prm.J)
+        xi = philox.noise_normals(prm.seed, prm.traj_id, step_index, L)
+        return orthonormalize(step_rk4(U, H, xi, prm.gamma, prm.dt)), events
+    U = P @ U
     if prm.protocol == HOMODYNE:
         xi = philox.noise_normals(prm.seed, prm.traj_id, step_index, L)
         U = orthonormalize(homodyne_weight(U, xi, prm.gamma, prm.dt))
@@ -138,19 +169,76 @@ def step(U, P, prm, step_index, forced=None):
     return U, events
 
 
+def run_poisson(prm, nsteps, U=None):
+    """The projective protocol as App. A runs it, in continuous time.
+
+    Measurement events come at the times of a Poisson process of total rate gamma N
+    (N = L/2 particles; the waiting time of event e is -ln(1 - u_wait) / (gamma N), the
+    form of tau = ln(eta) / (gamma N) with the sign that makes it positive); at each
+    event one site j, uniform over the L sites, is measured with the Born weight
+    p = C_jj and the outcome u < p, by the same rank-1 updates as the fixed-dt
+    protocol; between events the state evolves by exp(-i H~ tau) (here ``expm``).  The
+    events are a fixed sequence per trajectory (``philox.poisson_event``), their times
+    the running sum of the waiting times; step s covers (s dt, (s+1) dt] and ends with
+    the propagation to (s+1) dt.  QR every ``reorth_interval`` steps.
+    Returns dict(U, events=[(step, site, u, p, outcome)]).
+    """
+    import scipy.linalg
+    L = prm.L
+    N = prm.N
+    H = lattice.hopping_matrix(prm.Lx, prm.Ly, prm.J)
+    if U is None:
+        U = lattice.initial_orbitals(prm.Lx, prm.Ly)
+    rate = prm.gamma * N
+    e = 0
+    t_next = np.inf
+    if rate > 0:
+        t_next = -np.log1p(-philox.poisson_event(prm.seed, prm.traj_id, 0, L)[0]) / rate
+    t = 0.0
+    events = []
+    for s in range(nsteps):
+        t1 = (s + 1) * prm.dt
+        while t_next <= t1:
+            U = scipy.linalg.expm(-1j * (t_next - t) * H) @ U
+            t = t_next
+            _, j, u = philox.poisson_event(prm.seed, prm.traj_id, e, L)
+            x = U[j, :]
+            p = min(max(float(np.real(np.vdot(x, x))), 0.0), 1.0)
+            outcome = 1 if u < p else 0
+            events.append((s, j, u, p, outcome))
+            if p >= 1e-300:
+                U = project_site(U, j, outcome)
+            e += 1
+            t_next = t_next + (-np.log1p(-philox.poisson_event(prm.seed, prm.traj_id, e, L)[0]) / rate)
+        U = scipy.linalg.expm(-1j * (t1 - t) * H) @ U
+        t = t1
+        if (s + 1) % prm.reorth_interval == 0:
+            U = orthonormalize(U)
+    return {"U": U, "events": events}
+
+
 def run(prm, nsteps, U=None, P=None, start_step=0, ee_every=0, ee_sites=None, forced=None):
     """Run ``nsteps`` steps.  Returns dict(U, events, ee=[(steps_done, S)]).
 
     ``forced`` optionally maps step index -> {site: outcome}.
     """
     from . import observables
-    if P is None:
+    if prm.protocol == PROJECTIVE_POISSON:
+        if start_step or ee_every or forced:
+            raise ValueError("run_poisson: whole trajectories from t = 0 only")
+        out = run_poisson(prm, nsteps, U)
+        out["ee"] = []
+        return out
+    H = None
+    if prm.protocol == HOMODYNE_RK4:
+        H = lattice.hopping_matrix(prm.Lx, prm.Ly, prm.J)
+    elif P is None:
         P = lattice.propagator(prm.Lx, prm.Ly, prm.J, prm.dt)
     if U is None:
         U = lattice.initial_orbitals(prm.Lx, prm.Ly)
     events, ee = [], []
     for s in range(start_step, start_step + nsteps):
-        U, ev = step(U, P, prm, s, None if forced is None else forced.get(s))
+        U, ev = step(U, P, prm, s, None if forced is None else forced.get(s), H=H)
         events.extend((s,) + e for e in ev)
         done = s + 1
         if ee_every and ee_sites is not None and done % ee_every == 0:

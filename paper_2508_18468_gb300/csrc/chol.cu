@@ -61,7 +61,9 @@ template cudaError_t cholesky_inverse<float>(cudaStream_t, c32*, c32*, c32*, c32
 // ------------------------------------------------------------------ one-CTA leaf
 // G = R^dag R and T = R^-1 for an n x n block (n <= 128) of every trajectory,
 // complex64, in shared memory: right-looking Cholesky on the upper triangle,
-// then back substitution row by row with T^T kept in the strict lower
+// then T by 32 x 32 blocks -- each diagonal block inverted by one warp (a
+// column per lane), then T_IJ = -T_II sum_{I < K <= J} R_IK T_KJ by all
+// threads, J ascending, I descending -- with T^T kept in the strict lower
 // triangle of the same array.  R and T are written with zeros below the
 // diagonal.  One CTA of 1024 threads per trajectory; a non-positive pivot
 // raises FM_DEVERR_PIVOT and continues with pivot 1.
@@ -69,24 +71,26 @@ namespace fm {
 
 constexpr int kLeafMax = 128;
 constexpr int kLeafLd = kLeafMax + 1;
-constexpr size_t kLeafSmem = (size_t)kLeafMax * kLeafLd * sizeof(c32) + kLeafMax * sizeof(c32);
+constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + kLeafMax + 32 * 33) * sizeof(c32);
 
 __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restrict__ G, c32* R, c32* T, int n,
                                                              int64_t ld, int64_t sNN, int* status) {
   extern __shared__ c32 sm[];
   c32* A = sm;                                  // A[r * kLeafLd + c]
   c32* Td = sm + kLeafMax * kLeafLd;            // diagonal of T
+  c32* Z = Td + kLeafMax;                       // 32 x 33 block scratch
   const int64_t b = blockIdx.x;
   G += b * sNN;
   R += b * sNN;
   T += b * sNN;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int r = idx % n, c = idx / n;
     A[r * kLeafLd + c] = r <= c ? G[r + (int64_t)c * ld] : cmk(0.0f, 0.0f);
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       float d = A[j * kLeafLd + j].re;
       if (!(d > 0.0f) || !isfinite(d)) {
         atomicOr(status, FM_DEVERR_PIVOT);
@@ -96,29 +100,58 @@ __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restri
     }
     __syncthreads();
     const float inv = 1.0f / A[j * kLeafLd + j].re;
-    for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) A[j * kLeafLd + c] = cscale(A[j * kLeafLd + c], inv);
+    for (int c = j + 1 + tid; c < n; c += blockDim.x) A[j * kLeafLd + c] = cscale(A[j * kLeafLd + c], inv);
     __syncthreads();
     const int m = n - j - 1;                    // trailing upper triangle, rows/cols j+1 .. n-1
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
       const int r = j + 1 + idx % m, c = j + 1 + idx / m;
       if (r <= c) A[r * kLeafLd + c] = csub(A[r * kLeafLd + c], cmul(cconj(A[j * kLeafLd + r]), A[j * kLeafLd + c]));
     }
     __syncthreads();
   }
-  // T = R^-1: T_ii = 1 / R_ii; for i = n-2 .. 0: T_ic = -(1/R_ii) sum_{k=i+1..c} R_ik T_kc (c > i),
-  // T_kc (k < c) kept at A[c][k]
-  for (int i = threadIdx.x; i < n; i += blockDim.x) Td[i] = cmk(1.0f / A[i * kLeafLd + i].re, 0.0f);
-  __syncthreads();
-  for (int i = n - 2; i >= 0; --i) {
-    const float rinv = 1.0f / A[i * kLeafLd + i].re;
-    for (int c = i + 1 + threadIdx.x; c < n; c += blockDim.x) {
-      c32 s = cmul(A[i * kLeafLd + c], Td[c]);                       // k = c
-      for (int k = i + 1; k < c; ++k) s = cadd(s, cmul(A[i * kLeafLd + k], A[c * kLeafLd + k]));
-      A[c * kLeafLd + i] = cscale(s, -rinv);
+  // T(k, c), k <= c: Td[c] on the diagonal, A[c][k] above it
+  auto tget = [&](int k, int c) -> c32 {
+    if (k > c) return cmk(0.0f, 0.0f);
+    return k == c ? Td[c] : A[c * kLeafLd + k];
+  };
+  const int nbk = (n + 31) / 32;
+  // diagonal blocks: warp w, lane = column within the block
+  if (warp < nbk) {
+    const int o = warp * 32, sw = min(32, n - o);
+    if (lane < sw) {
+      const int c = o + lane;
+      Td[c] = cmk(1.0f / A[c * kLeafLd + c].re, 0.0f);
+      for (int i = c - 1; i >= o; --i) {
+        c32 acc = cmul(A[i * kLeafLd + c], Td[c]);
+        for (int k = i + 1; k < c; ++k) acc = cadd(acc, cmul(A[i * kLeafLd + k], A[c * kLeafLd + k]));
+        A[c * kLeafLd + i] = cscale(acc, -1.0f / A[i * kLeafLd + i].re);
+      }
     }
-    __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+  __syncthreads();
+  // off-diagonal blocks
+  const int a = tid >> 5, q = tid & 31;         // element (a, q) of a 32 x 32 block
+  for (int J = 1; J < nbk; ++J) {
+    const int oj = J * 32, swj = min(32, n - oj);
+    for (int I = J - 1; I >= 0; --I) {
+      const int oi = I * 32;
+      // Z = sum_{K = I+1 .. J} R_IK T_KJ
+      c32 z = cmk(0.0f, 0.0f);
+      if (q < swj) {
+        for (int k = oi + 32; k <= oj + q; ++k) z = cadd(z, cmul(A[(oi + a) * kLeafLd + k], tget(k, oj + q)));
+      }
+      Z[a * 33 + q] = z;
+      __syncthreads();
+      // T_IJ = -T_II Z (T_II upper: rows a .. 31)
+      c32 t = cmk(0.0f, 0.0f);
+      if (q < swj)
+        for (int p = a; p < 32; ++p) t = cadd(t, cmul(tget(oi + a, oi + p), Z[p * 33 + q]));
+      __syncthreads();
+      if (q < swj) A[(oj + q) * kLeafLd + (oi + a)] = cmk(-t.re, -t.im);
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int r = idx % n, c = idx / n;
     const int64_t o = r + (int64_t)c * ld;
     if (r < c) {

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <complex>
 #include <condition_variable>
@@ -26,6 +27,15 @@ const int kCholNB = CHOL_NB;   // Cholesky / triangular-inverse block
 const int kMaxChunks = 128;    // occupation partial sums
 const int kAsyncSlots = 64;    // outstanding asynchronous entropies
 const int kEaRing = 4;         // C_A buffers of the asynchronous entropies
+const int kPoisSlots = 128;    // continuous-time projective: propagation slots per upload
+
+// continuous-time projective scratch: taps (slot, trajectory, x then y), event
+// sites and draws (trajectory, slot), event counts, then the tap offsets
+int64_t pois_al(int64_t x) { return (x + 255) & ~(int64_t)255; }
+int64_t pois_bytes(int64_t B) {
+  return pois_al(kPoisSlots * B * 2 * kBandMaxTaps * 16) + pois_al(kPoisSlots * B * 4) + pois_al(kPoisSlots * B * 8) +
+         pois_al(B * 4) + pois_al(2 * kBandMaxTaps * 4);
+}
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -43,6 +53,8 @@ struct Plan {
   size_t gfull;                                         // exact Gram of all of U (mixed)
   size_t obs;                                           // displacement bins and partial sums
   size_t band;                                          // stencil taps and offsets (x, y)
+  size_t rk4;                                           // Runge-Kutta stage buffer
+  size_t pois;                                          // continuous-time projective: taps, offsets
   size_t mixed_extra;                                   // scratch owned by the mixed path
   size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
 };
@@ -55,7 +67,11 @@ bool valid_params(const fm_params* p, std::string* why) {
   if (p->Ly > 1 && (p->Lx % 2)) { *why = "torus needs even Lx for the checkerboard start"; return false; }
   if (L > 65536) { *why = "L > 65536 not supported"; return false; }
   if (p->batch < 1 || p->batch > 65535) { *why = "batch must be in [1, 65535]"; return false; }
-  if (p->protocol != FM_PROJECTIVE && p->protocol != FM_HOMODYNE) { *why = "bad protocol"; return false; }
+  if (p->protocol != FM_PROJECTIVE && p->protocol != FM_HOMODYNE && p->protocol != FM_HOMODYNE_RK4 &&
+      p->protocol != FM_PROJECTIVE_POISSON) {
+    *why = "bad protocol";
+    return false;
+  }
   if (p->precision != FM_FP64 && p->precision != FM_MIXED) { *why = "bad precision"; return false; }
   if (p->reorth_interval < 1) { *why = "reorth_interval must be >= 1"; return false; }
   if (p->event_capacity < 0) { *why = "event_capacity must be >= 0"; return false; }
@@ -113,6 +129,8 @@ Plan make_plan(const fm_params& p) {
   pl.pmw = pl.take(pm_wide_scratch_bytes((int)L, (int)B));
   pl.obs = pl.take((L + abs2_partials() + 8) * 8);
   pl.band = pl.take(2 * kBandMaxTaps * (16 + 4));
+  pl.rk4 = pl.take(p.protocol == FM_HOMODYNE_RK4 ? B * L * N * (p.precision == FM_FP64 ? 16 : 8) : 0);
+  pl.pois = pl.take(p.protocol == FM_PROJECTIVE_POISSON ? pois_bytes(B) : 0);
   if (p.precision == FM_FP64) {
     pl.U = pl.take(B * L * N * 16);
     pl.U2 = pl.take(B * L * N * 16);
@@ -196,6 +214,17 @@ struct fm_state {
   z64 *band_tx, *band_ty;
   int *band_ox, *band_oy;
   int ntap_x, ntap_y;
+  void* rk4buf;               // Runge-Kutta stage buffer (FM_HOMODYNE_RK4)
+  // continuous-time projective protocol: next event index and time per trajectory,
+  // device taps (slot, trajectory, x then y) and the common offsets of each direction
+  std::vector<int64_t> pois_e;
+  std::vector<double> pois_t;
+  z64* pois_taps;
+  int* pois_list;              // B x kPoisSlots sites of a chunk of slots
+  double* pois_u;              // their Born draws
+  int* pois_cnt;               // events of each trajectory in the chunk
+  int* pois_off;               // x offsets, then y offsets (kBandMaxTaps each)
+  int pois_wx, pois_wy;        // half-widths; -1: every offset of that direction
   int64_t ea_next;            // next ticket
   struct EaJob { int64_t t; int slot, ring, m; };
   std::thread ea_thread;
@@ -314,6 +343,111 @@ void band_taps(const std::vector<z64>& p, std::vector<z64>* taps, std::vector<in
   }
 }
 
+// ------------------------------------------------------------------ continuous-time projective protocol
+// Philox4x32-10 on the host (Salmon et al., SC'11), for the event draws the host
+// needs to schedule the propagation between events.
+std::array<uint32_t, 4> philox_host(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+double u53_host(uint32_t wa, uint32_t wb) {
+  return ((double)(wa >> 5) * 67108864.0 + (double)(wb >> 6)) * (1.0 / 9007199254740992.0);
+}
+struct PoisDraw { double u_wait; int site; double u; };
+PoisDraw poisson_draw(uint64_t seed, uint64_t traj, int64_t e, int L) {
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  const uint32_t c0 = (uint32_t)((uint64_t)e & 0xFFFFFFFFu), c1 = (uint32_t)((uint64_t)e >> 32);
+  const uint32_t c2 = (uint32_t)(traj & 0xFFFFFFFFu), hi = (uint32_t)(traj >> 32) << 8;
+  const auto w = philox_host(c0, c1, c2, 3u | hi, k0, k1);
+  const auto v = philox_host(c0, c1, c2, 4u | hi, k0, k1);
+  PoisDraw d;
+  d.u_wait = u53_host(w[0], w[1]);
+  d.site = std::min((int)(u53_host(w[2], w[3]) * L), L - 1);
+  d.u = u53_host(v[0], v[1]);
+  return d;
+}
+// taps of exp(-i H~ tau) along one direction of length n: at the offsets -w .. w
+// from the Jacobi-Anger series, p_r = (-i)^|r| J_|r|(2 J tau) (the aliased terms
+// J_{n - |r|} are below 1e-17 wherever this form is used), or (w < 0) at every
+// offset 0 .. n-1 from the plane-wave sum
+void poisson_taps(int n, int w, double J, double tau, z64* out) {
+  if (w < 0) {
+    std::vector<z64> row = ring_row(n, J, tau);
+    for (int r = 0; r < n; ++r) out[r] = row[r];
+    return;
+  }
+  static const double re4[4] = {1.0, 0.0, -1.0, 0.0}, im4[4] = {0.0, -1.0, 0.0, 1.0};  // (-i)^r
+  const double z = 2.0 * std::fabs(J) * tau;
+  for (int t = 0; t <= 2 * w; ++t) {
+    const int r = std::abs(t - w);
+    double jr = std::cyl_bessel_j((double)r, z);
+    if (J < 0.0 && (r & 1)) jr = -jr;            // J_r(-z) = (-1)^r J_r(z)
+    out[t].re = re4[r % 4] * jr;
+    out[t].im = im4[r % 4] * jr;
+  }
+}
+
+// half-width of that stencil for every tau <= dt along a direction of length n
+// (J_r(2 |J| tau) grows with tau for r > 2 |J| tau): -1 when 2w + 1 reaches n
+int poisson_width(int n, double J, double dt) {
+  const double z = 2.0 * std::fabs(J) * dt;
+  int w = 0;
+  for (; w < 4 * kBandMaxTaps; ++w) {
+    bool small = w + 1 > z;
+    for (int r = w + 1; small && r <= w + 8; ++r) small = std::fabs(std::cyl_bessel_j((double)r, z)) < 1e-17;
+    if (small) break;
+  }
+  return 2 * w + 1 >= n ? -1 : w;
+}
+
+double poisson_wait(const fm_state* s, int b, int64_t e) {
+  const double rate = s->gamma_h[b] * (double)s->N;
+  if (!(rate > 0.0)) return INFINITY;
+  return -std::log1p(-poisson_draw(s->prm.seed, s->traj_h[b], e, s->L).u_wait) / rate;
+}
+
+// index and time of trajectory b's next event at its step count: the events up to
+// step_h[b] dt replayed (the running sum of the waiting times)
+void poisson_sync(fm_state* s, int b) {
+  int64_t e = 0;
+  double t = poisson_wait(s, b, 0);
+  if (s->step_h[b] > 0) {
+    const double t0 = (double)s->step_h[b] * s->prm.dt;
+    while (t <= t0) {
+      ++e;
+      t = t + poisson_wait(s, b, e);
+    }
+  }
+  s->pois_e[b] = e;
+  s->pois_t[b] = t;
+}
+
+fm_status poisson_setup(fm_state* s) {
+  const double J = s->prm.J, dt = s->prm.dt;
+  s->pois_wx = poisson_width(s->Lx, J, dt);
+  s->pois_wy = s->Ly > 1 ? poisson_width(s->Ly, J, dt) : -1;
+  const int ntx = s->pois_wx < 0 ? s->Lx : 2 * s->pois_wx + 1;
+  const int nty = s->pois_wy < 0 ? s->Ly : 2 * s->pois_wy + 1;
+  if (ntx > kBandMaxTaps || nty > kBandMaxTaps)
+    return fail(s, FM_EINVAL, "continuous-time protocol: J dt too large for the stencil propagation");
+  std::vector<int> off(2 * kBandMaxTaps, 0);
+  for (int t = 0; t < ntx; ++t) off[t] = s->pois_wx < 0 ? t : t - s->pois_wx;
+  for (int t = 0; t < nty; ++t) off[kBandMaxTaps + t] = s->pois_wy < 0 ? t : t - s->pois_wy;
+  CK(cudaMemcpyAsync(s->pois_off, off.data(), 4 * off.size(), cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  s->pois_e.assign(s->B, 0);
+  s->pois_t.assign(s->B, 0.0);
+  for (int b = 0; b < s->B; ++b) poisson_sync(s, b);
+  return FM_OK;
+}
+
 fm_status check_state(fm_state* s) {
   if (!s) return FM_EINVAL;
   if (s->sticky) return FM_ESTATE;
@@ -345,6 +479,30 @@ fm_status cholqr_f64(fm_state* s) {
 fm_status step_f64(fm_state* s) {
   const int L = s->L, N = s->N, B = s->B;
   const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  if (s->prm.protocol == FM_HOMODYNE_RK4) {
+    // App. A's integrator: <n> of U(t), the weights' logarithms, four Horner stages
+    const int nch = occupation_chunks(L, N, B);
+    s->timer.begin(FM_PH_MEASURE);
+    CKL(rownorm_partials_z(s->st, s->U, L, N, B, s->part_d, nch), 1);
+    CKL(reduce_occupations(s->st, s->part_d, nch, L, B, s->nocc_d, s->w_d, s->gamma_d, s->prm.dt, s->traj_d,
+                           s->step_d, s->prm.seed), 1);
+    s->timer.end(FM_PH_MEASURE);
+    s->timer.begin(FM_PH_PROPAGATE);
+    const double h = s->prm.dt * s->prm.J;
+    void* R4 = s->rk4buf;
+    CKL(rk4_stage(s->st, 0, s->U, s->U, R4, L, N, B, s->Lx, s->Ly, s->w_d, h, 0.25), 1);
+    CKL(rk4_stage(s->st, 0, s->U, R4, s->U2, L, N, B, s->Lx, s->Ly, s->w_d, h, 1.0 / 3.0), 1);
+    CKL(rk4_stage(s->st, 0, s->U, s->U2, R4, L, N, B, s->Lx, s->Ly, s->w_d, h, 0.5), 1);
+    CKL(rk4_stage(s->st, 0, s->U, R4, s->U2, L, N, B, s->Lx, s->Ly, s->w_d, h, 1.0), 1);
+    s->timer.end(FM_PH_PROPAGATE);
+    std::swap(s->U, s->U2);
+    s->aux = s->U2;
+    fm_status r = cholqr_f64(s);
+    if (r) return r;
+    if ((s->global_steps + 1) % s->prm.reorth_interval == 0 && (r = cholqr_f64(s))) return r;
+    CKL(bump_steps(s->st, s->step_d, B), 1);
+    return FM_OK;
+  }
   // 1. propagation, all trajectories in one product P [U_0 | U_1 | ...], or as stencils
   s->timer.begin(FM_PH_PROPAGATE);
   if (s->prop_mode == FM_PROP_BANDED) {
@@ -401,13 +559,121 @@ fm_status step_f64(fm_state* s) {
   return FM_OK;
 }
 
-// gather rows `sites` of trajectory b into aux (n x N complex128)
-fm_status gather_rows(fm_state* s, int b, const int* d_sites, int n) {
-  if (s->prm.precision == FM_FP64) {
-    CKL(gather_rows_z(s->st, s->U + (int64_t)b * s->L * s->N, s->L, s->N, d_sites, n, s->aux), 1);
-  } else {
-    CKL(gather_rows_v(s->st, s->V + (int64_t)b * 2 * s->L * s->N, s->L, s->N, d_sites, n, s->aux), 1);
+// One step of the continuous-time projective protocol (App. A), all trajectories.
+// The host draws each trajectory's events in (t, t + dt] (the waiting times need
+// no state) and lays the step out in slots: slot q propagates every trajectory
+// by its q-th interval (the time to its q-th event, then the rest of the step,
+// then zero) as two stencils with per-trajectory taps, and applies the q-th
+// event of every trajectory that has one (row and Born weight, v = U x^dag,
+// rank-1 update).  Taps and events go up in chunks of kPoisSlots slots.
+fm_status step_poisson(fm_state* s) {
+  const int L = s->L, N = s->N, B = s->B;
+  const double dt = s->prm.dt, J = s->prm.J;
+  const bool fp64 = s->prm.precision == FM_FP64;
+  const int ntx = s->pois_wx < 0 ? s->Lx : 2 * s->pois_wx + 1;
+  const int nty = s->pois_wy < 0 ? s->Ly : 2 * s->pois_wy + 1;
+  const int tstride = ntx + (s->Ly > 1 ? nty : 0);
+  // the schedule: intervals (events + 1) and events per trajectory
+  std::vector<std::vector<double>> tau(B);
+  std::vector<std::vector<int>> site(B);
+  std::vector<std::vector<double>> uo(B);
+  int kmax = 0;
+  for (int b = 0; b < B; ++b) {
+    const double t1 = (double)(s->step_h[b] + 1) * dt;
+    double t = (double)s->step_h[b] * dt;
+    while (s->pois_t[b] <= t1) {
+      const PoisDraw d = poisson_draw(s->prm.seed, s->traj_h[b], s->pois_e[b], L);
+      tau[b].push_back(s->pois_t[b] - t);
+      site[b].push_back(d.site);
+      uo[b].push_back(d.u);
+      t = s->pois_t[b];
+      s->pois_e[b] += 1;
+      s->pois_t[b] = s->pois_t[b] + poisson_wait(s, b, s->pois_e[b]);
+    }
+    tau[b].push_back(t1 - t);
+    kmax = std::max(kmax, (int)site[b].size());
   }
+  pm_args a;
+  a.L = L; a.N = N; a.batch = B; a.layout = fp64 ? 0 : 1;
+  a.gamma = s->gamma_d; a.dt = dt; a.traj = s->traj_d; a.step = s->step_d; a.seed = s->prm.seed;
+  a.xbuf = s->xbuf_d; a.vbuf = s->vbuf_d;
+  a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
+  a.dev_status = s->status_d;
+  const int nch = band_chunks(L, N, B);
+  std::vector<z64> taps;
+  std::vector<int> list, cnt(B);
+  std::vector<double> ul;
+  const int nslot = kmax + 1;
+  for (int q0 = 0; q0 < nslot; q0 += kPoisSlots) {
+    const int S = std::min(kPoisSlots, nslot - q0);
+    taps.assign((size_t)S * B * tstride, z64{0.0, 0.0});
+    list.assign((size_t)B * S, 0);
+    ul.assign((size_t)B * S, 0.0);
+    for (int b = 0; b < B; ++b) {
+      const int nev = (int)site[b].size();
+      cnt[b] = std::max(0, std::min(S, nev - q0));
+      for (int j = 0; j < S; ++j) {
+        const int q = q0 + j;
+        const double tq = q < (int)tau[b].size() ? tau[b][q] : 0.0;
+        z64* tp = taps.data() + ((size_t)j * B + b) * tstride;
+        poisson_taps(s->Lx, s->pois_wx, J, tq, tp);
+        if (s->Ly > 1) poisson_taps(s->Ly, s->pois_wy, J, tq, tp + ntx);
+        if (q < nev) {
+          list[(size_t)b * S + j] = site[b][q];
+          ul[(size_t)b * S + j] = uo[b][q];
+        }
+      }
+    }
+    // pageable sources: each copy returns once its bytes are staged, so the vectors
+    // may be refilled (next chunk) or freed (end of the step) at once
+    s->timer.begin(FM_PH_MEASURE);
+    CK(cudaMemcpyAsync(s->pois_taps, taps.data(), 16 * taps.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->pois_list, list.data(), 4 * list.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->pois_u, ul.data(), 8 * ul.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->pois_cnt, cnt.data(), 4 * B, cudaMemcpyHostToDevice, s->st));
+    s->timer.end(FM_PH_MEASURE);
+    for (int j = 0; j < S; ++j) {
+      void* cur = fp64 ? (void*)s->U : (void*)s->V;
+      void* oth = fp64 ? (void*)s->U2 : (void*)s->V2;
+      const z64* tp = s->pois_taps + (size_t)j * B * tstride;
+      s->timer.begin(FM_PH_PROPAGATE);
+      CKL(band_propagate(s->st, a.layout, cur, oth, L, N, B, s->Lx, s->Ly, 0, tp, s->pois_off, ntx, nullptr, nch,
+                         tstride), 1);
+      if (s->Ly > 1) {
+        CKL(band_propagate(s->st, a.layout, oth, cur, L, N, B, s->Lx, s->Ly, 1, tp + ntx, s->pois_off + kBandMaxTaps,
+                           nty, nullptr, nch, tstride), 1);
+      } else if (fp64) {
+        std::swap(s->U, s->U2);
+      } else {
+        std::swap(s->V, s->V2);
+      }
+      s->timer.end(FM_PH_PROPAGATE);
+      if (q0 + j < kmax) {
+        a.U = fp64 ? (void*)s->U : (void*)s->V;
+        s->timer.begin(FM_PH_MEASURE);
+        CKL(pm_wide_event(s->st, a, j, s->pois_list, s->pois_u, S, s->pois_cnt, s->pmw), 3);
+        s->timer.end(FM_PH_MEASURE);
+      }
+    }
+  }
+  if (fp64) s->aux = s->U2;
+  if ((s->global_steps + 1) % s->prm.reorth_interval == 0) {
+    if (fp64) {
+      fm_status r = cholqr_f64(s);
+      if (r) return r;
+      if ((r = cholqr_f64(s))) return r;
+    } else {
+      MixedCtx& c = s->mc;
+      c.st = s->st;
+      c.V = s->V; c.V2 = s->V2;
+      c.launches = 0;
+      const int r = mixed_reorth(s->mh, &c);
+      s->V = c.V; s->V2 = c.V2;
+      s->launches += c.launches;
+      if (r) return fail(s, (fm_status)r, c.err);
+    }
+  }
+  CKL(bump_steps(s->st, s->step_d, B), 1);
   return FM_OK;
 }
 
@@ -477,7 +743,8 @@ fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, doub
 // one eager step of the whole batch on s->st
 fm_status step_once(fm_state* s) {
   fm_status r;
-  if (s->prm.precision == FM_FP64) r = step_f64(s);
+  if (s->prm.protocol == FM_PROJECTIVE_POISSON) r = step_poisson(s);
+  else if (s->prm.precision == FM_FP64) r = step_f64(s);
   else {
     MixedCtx& c = s->mc;
     c.st = s->st;
@@ -543,7 +810,9 @@ fm_status capture_period(fm_state* s) {
 fm_status step_many(fm_state* s, int32_t nsteps) {
   fm_status r;
   int i = 0;
-  const bool graph_ok = !(s->prm.protocol == FM_PROJECTIVE && pm_use_wide(s->L, s->N, s->B));
+  // host-scheduled steps (event counts read back, or drawn on the host) do not replay
+  const bool graph_ok = !(s->prm.protocol == FM_PROJECTIVE && pm_use_wide(s->L, s->N, s->B)) &&
+                        s->prm.protocol != FM_PROJECTIVE_POISSON;
   if (s->graphs_on && graph_ok) {
     const int P = s->graph_period;
     while (i < nsteps && (s->global_steps % P) != 0) {
@@ -591,6 +860,8 @@ fm_status retune(fm_state* s, int tile_config, int reorth) {
   }
   s->global_steps = 0;
   for (int b = 0; b < B; ++b) s->step_h[b] = 0;
+  if (s->prm.protocol == FM_PROJECTIVE_POISSON)
+    for (int b = 0; b < B; ++b) poisson_sync(s, b);
   CK(cudaMemsetAsync(s->step_d, 0, 8 * (size_t)B, s->st));
   CK(cudaStreamSynchronize(s->st));
   return FM_OK;
@@ -764,6 +1035,20 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->band_ox = (int*)(s->band_ty + kBandMaxTaps);
   s->band_oy = s->band_ox + kBandMaxTaps;
   s->ntap_x = s->ntap_y = 0;
+  s->rk4buf = w + pl.rk4;
+  {
+    char* q = w + pl.pois;
+    const int64_t B = p->batch;
+    s->pois_taps = (z64*)q;
+    q += pois_al(kPoisSlots * B * 2 * kBandMaxTaps * 16);
+    s->pois_list = (int*)q;
+    q += pois_al(kPoisSlots * B * 4);
+    s->pois_u = (double*)q;
+    q += pois_al(kPoisSlots * B * 8);
+    s->pois_cnt = (int*)q;
+    q += pois_al(B * 4);
+    s->pois_off = (int*)q;
+  }
   for (int i = 0; i < kAsyncSlots; ++i) s->ea_done[i] = nullptr;
   s->U = s->U2 = s->P = nullptr; s->V = s->V2 = nullptr;
   s->Vh = s->Vl = s->Ah = s->Al = s->Th = s->Tl = nullptr;
@@ -824,6 +1109,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
         if (cudaStreamSynchronize(s->st) != cudaSuccess) { r = fail(s, FM_ECUDA, "stencil sync"); break; }
       }
     }
+    if (p->protocol == FM_PROJECTIVE_POISSON && (r = poisson_setup(s)) != FM_OK) break;
     // stage the rows in the EE scratch (free until the first entropy call)
     z64* dpx = s->ee_pb;
     z64* dpy = s->ee_pb + s->Lx;
@@ -848,7 +1134,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       s->launches += 2;
       MixedCtx& c = s->mc;
       c.st = s->st; c.Lx = s->Lx; c.Ly = s->Ly; c.L = s->L; c.N = s->N; c.B = s->B;
-      c.protocol = p->protocol; c.reorth_interval = p->reorth_interval; c.dt = p->dt; c.seed = p->seed;
+      c.protocol = p->protocol; c.reorth_interval = p->reorth_interval; c.dt = p->dt; c.J = p->J; c.seed = p->seed;
       c.tile_config = p->tile_config;
       c.global_step = 0; c.V = s->V; c.V2 = s->V2; c.Vh = s->Vh; c.Vl = s->Vl; c.Ah = s->Ah; c.Al = s->Al;
       c.Th = s->Th; c.Tl = s->Tl; c.G = s->G; c.R = s->R; c.T = s->T; c.Dinv = s->Dinv; c.X = s->X;
@@ -859,6 +1145,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       c.prop_banded = 0;
       c.band_tx = s->band_tx; c.band_ty = s->band_ty; c.band_ox = s->band_ox; c.band_oy = s->band_oy;
       c.ntap_x = s->ntap_x; c.ntap_y = s->ntap_y;
+      c.rk4buf = (float*)s->rk4buf;
       std::string why2;
       s->mh = mixed_create(&c, &why2);
       if (!s->mh) {
@@ -935,6 +1222,9 @@ fm_status fm_set_gammas(fm_state* s, const double* gammas) {
   for (int b = 0; b < s->B; ++b)
     if (!(gammas[b] >= 0.0) || !isfinite(gammas[b])) return fail(s, FM_EINVAL, "gamma must be finite, >= 0");
   for (int b = 0; b < s->B; ++b) s->gamma_h[b] = gammas[b];
+  // continuous-time protocol: the event times as if the new rates held from t = 0
+  if (s->prm.protocol == FM_PROJECTIVE_POISSON)
+    for (int b = 0; b < s->B; ++b) poisson_sync(s, b);
   CK(cudaMemcpyAsync(s->gamma_d, s->gamma_h.data(), 8 * s->B, cudaMemcpyHostToDevice, s->st));
   CK(cudaStreamSynchronize(s->st));
   return FM_OK;
@@ -949,6 +1239,7 @@ fm_status fm_reset_trajectory(fm_state* s, int32_t b, uint64_t traj_id, double g
   s->gamma_h[b] = gamma;
   s->traj_h[b] = traj_id;
   s->step_h[b] = 0;
+  if (s->prm.protocol == FM_PROJECTIVE_POISSON) poisson_sync(s, b);
   CK(cudaMemcpyAsync(s->gamma_d + b, &s->gamma_h[b], 8, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->traj_d + b, &s->traj_h[b], 8, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->step_d + b, &s->step_h[b], 8, cudaMemcpyHostToDevice, s->st));
@@ -1227,6 +1518,8 @@ fm_status fm_load(fm_state* s, const char* path) {
     return fail(s, FM_EINVAL, "checkpoint does not match this state's parameters");
   CK(cudaStreamSynchronize(s->st));
   s->gamma_h = g; s->traj_h = t; s->step_h = st; s->global_steps = gsteps;
+  if (s->prm.protocol == FM_PROJECTIVE_POISSON)
+    for (int b = 0; b < s->B; ++b) poisson_sync(s, b);
   CK(cudaMemcpy(s->gamma_d, g.data(), 8 * s->B, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->traj_d, t.data(), 8 * s->B, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->step_d, st.data(), 8 * s->B, cudaMemcpyHostToDevice));
@@ -1252,6 +1545,27 @@ fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts) {
   if (r) return r;
   if (!s->timer.collect(ms, counts)) return fail(s, FM_ECUDA, "event timing failed");
   return FM_OK;
+}
+
+extern "C" int fmx_poisson_draw(unsigned long long seed, unsigned long long traj, long long e, int L, double* out) {
+  if (!out || L < 1 || e < 0) return -1;
+  const PoisDraw d = poisson_draw(seed, traj, e, L);
+  out[0] = d.u_wait;
+  out[1] = d.site;
+  out[2] = d.u;
+  return 0;
+}
+
+extern "C" int fmx_poisson_taps(int n, int w, double J, double tau, double* out) {
+  if (!out || n < 1 || w > 4 * kBandMaxTaps || !std::isfinite(J) || !(tau >= 0.0)) return -1;
+  if (w >= 0 && 2 * w + 1 > n) return -1;
+  poisson_taps(n, w, J, tau, (z64*)out);
+  return 0;
+}
+
+extern "C" int fmx_poisson_width(int n, double J, double dt) {
+  if (n < 1 || !std::isfinite(J) || !(dt >= 0.0)) return -2;
+  return poisson_width(n, J, dt);
 }
 
 fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, void* cuda_stream, int32_t steps,

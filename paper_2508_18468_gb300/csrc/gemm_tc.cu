@@ -86,27 +86,38 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
 #pragma unroll
     for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.Ntraj] = d[j];
   } else if (MODE == MODE_ADDV) {
+    // all 32 loads before the first store: the stores could alias the loads as far as
+    // the compiler knows, so interleaving them would serialise on memory latency
     const int64_t o0 = (int64_t)ti.b * p.out_batch_stride + (int64_t)(m0 + r) + (int64_t)(n0 + c0) * p.ld_out;
+    float x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = __ldg(&p.in_f[o0 + (int64_t)j * p.ld_out]);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int64_t o = o0 + (int64_t)j * p.ld_out;
-      const float x = p.in_f[o] + d[j];
-      p.out_f[o] = x;
-      const __half h = __float2half_rn(x);
+      const float v = x[j] + d[j];
+      p.out_f[o] = v;
+      const __half h = __float2half_rn(v);
       p.out_h[o] = h;
-      p.out_l[o] = __float2half_rn((x - __half2float(h)) * 2048.0f);
+      p.out_l[o] = __float2half_rn((v - __half2float(h)) * 2048.0f);
     }
   } else {  // MODE_TRMM: column c of the L x 2N view -> V_b[(c&1) L + i + (c>>1) 2L]
     const int64_t base = (int64_t)ti.b * 2 * p.L * p.Ntraj + (m0 + r);
+    float x[32];                              // loads first (see MODE_ADDV)
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int c = n0 + c0 + j;
+      x[j] = p.in_f ? __ldg(&p.in_f[base + (int64_t)(c & 1) * p.L + (int64_t)(c >> 1) * 2 * p.L]) : 0.0f;
+    }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int c = n0 + c0 + j;
       const int64_t o = base + (int64_t)(c & 1) * p.L + (int64_t)(c >> 1) * 2 * p.L;
-      const float x = p.in_f ? p.in_f[o] + d[j] : d[j];
-      p.out_f[o] = x;
-      const __half h = __float2half_rn(x);
+      const float v = x[j] + d[j];
+      p.out_f[o] = v;
+      const __half h = __float2half_rn(v);
       p.out_h[o] = h;
-      p.out_l[o] = __float2half_rn((x - __half2float(h)) * 2048.0f);
+      p.out_l[o] = __float2half_rn((v - __half2float(h)) * 2048.0f);
     }
   }
 }

@@ -79,19 +79,19 @@ struct PmbMats {
 int pmb_capacity(int L);   // largest block (selected sites per step) the scratch holds
 cudaError_t pmb_setup(cudaStream_t st, const int* list, const int* count, int L, int B, int nmax, int* pos);
 cudaError_t pmb_gather_w(cudaStream_t st, const __half* urm_h, const __half* urm_l, int L, int N, const int* list,
-                         const int* count, int b, int K, __half* wt_h, __half* wt_l);
+                         const int* count, int B, int K, __half* wt_h, __half* wt_l);
 cudaError_t pmb_gather_c(cudaStream_t st, const float* Dp, int64_t sD, int L, int K, int B, const int* list,
                          const int* count, const PmbMats& m);
 cudaError_t pmb_event(cudaStream_t st, int i, int Kc, int L, int B, const int* count, const int* list,
                       const double* ulist, const int64_t* step, const PmbMats& m, fm_event* log,
                       unsigned long long* log_count, int log_capacity, int nmax);
-cudaError_t pmb_ttilde(cudaStream_t st, const PmbMats& m, int K, int b, __half* th, __half* tl);
+cudaError_t pmb_ttilde(cudaStream_t st, const PmbMats& m, int K, int B, __half* th, __half* tl);
 cudaError_t pmb_split(cudaStream_t st, const float* x, int64_t n, __half* h, __half* l);
-cudaError_t pmb_atilde(cudaStream_t st, const float* Ap, int L, int K, int b, const int* pos, const PmbMats& m,
+cudaError_t pmb_atilde(cudaStream_t st, const float* Ap, int L, int K, int B, const int* pos, const PmbMats& m,
                        __half* ah, __half* al);
 cudaError_t pmb_gather_wc(cudaStream_t st, const float* V, int L, int N, int K, int B, const int* list,
                           const int* count, const PmbMats& m);
-cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int b, int N, __half* xh, __half* xl);
+cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int B, int N, __half* xh, __half* xl);
 // the selection step of the grid-wide path: per trajectory the measured sites
 // (ascending) and their outcome draws; count per trajectory
 cudaError_t pm_select(cudaStream_t st, const pm_args& a, int* list, double* ulist, int* count);
@@ -158,8 +158,20 @@ constexpr int kBandMaxTaps = 41;   // half-width <= 20
 int band_chunks(int L, int N, int B);
 // layout 0: complex128 U (L x N per trajectory); 1: float V (2L x N).  dir 0 along x,
 // 1 along y.  partial (may be NULL): row sums of |out|^2 per column chunk, nch chunks.
+// off: consecutive offsets; tap_stride > 0: trajectory b uses taps + b tap_stride.
 cudaError_t band_propagate(cudaStream_t st, int layout, const void* in, void* out, int L, int N, int B, int Lx,
-                           int Ly, int dir, const z64* taps, const int* off, int ntap, double* partial, int nch);
+                           int Ly, int dir, const z64* taps, const int* off, int ntap, double* partial, int nch,
+                           int tap_stride = 0);
+// the projective event e of the grid-wide path (row and outcome, v = U x^dag / sqrt(p),
+// rank-1 update) for every trajectory with e < count[b]; list / ulist hold the sites and
+// Born draws of trajectory b at b ld_list + e.  scratch: pm_wide_scratch_bytes(L, B).
+cudaError_t pm_wide_event(cudaStream_t st, const pm_args& a, int e, const int* list, const double* ulist,
+                          int ld_list, const int* count, void* scratch);
+
+// one Horner stage out = U0 + c (A dt) Y of the Runge-Kutta step of Eq. (QSD_evo):
+// A dt = -i dt J (nearest-neighbour sum) + diag(ln w); layout as band_propagate
+cudaError_t rk4_stage(cudaStream_t st, int layout, const void* U0, const void* Y, void* out, int L, int N, int B,
+                      int Lx, int Ly, const double* w, double dtJ, double c);
 
 // ---- density correlations and particle covariance (observables.cu)
 cudaError_t v_to_c32(cudaStream_t st, const float* V, int L, int N, c32* U);

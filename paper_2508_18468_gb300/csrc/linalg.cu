@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(1024) pm_select_kernel(const double* gamma, do
 
 template <typename T, int LAYOUT>
 __global__ void __launch_bounds__(1024) pm_row_kernel(void* Ub, int L, int N, int e, const int* list,
-                                                      const double* ulist, const int* count, const int64_t* step,
+                                                      const double* ulist, int ld_list, const int* count,
+                                                      const int64_t* step,
                                                       void* xbuf, PmEvent* ev, fm_event* log,
                                                       unsigned long long* log_count, int log_capacity) {
   const int b = blockIdx.x;
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(1024) pm_row_kernel(void* Ub, int L, int N, in
   u.init(Ub, b, L, N);
   cplx<T>* xb = (cplx<T>*)xbuf + (int64_t)b * N;
   const bool has = e < count[b];
-  const int js = has ? list[(int64_t)b * L + e] : 0;
+  const int js = has ? list[(int64_t)b * ld_list + e] : 0;
   double ps = 0.0;
   if (has)
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(1024) pm_row_kernel(void* Ub, int L, int N, in
     r.pad = 0;
     if (has) {
       p = fmin(fmax(p, 0.0), 1.0);
-      const double uu = ulist[(int64_t)b * L + e];
+      const double uu = ulist[(int64_t)b * ld_list + e];
       r.outcome = (uu < p) ? 1 : 0;
       r.p = p;
       r.sp = sqrt(p);
@@ -585,12 +586,12 @@ cudaError_t pm_measure_wide(cudaStream_t st, const pm_args& a, void* scratch, in
   const dim3 g_gemv(FM_CEIL_DIV(a.L, 32), 1, a.batch), g_upd(FM_CEIL_DIV(a.L, 256), FM_CEIL_DIV(a.N, kchunk), a.batch);
   for (int ev_i = 0; ev_i < emax; ++ev_i) {
     if (a.layout == 0) {
-      pm_row_kernel<double, 0><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, ev_i, list, ulist, count, a.step, a.xbuf, ev,
+      pm_row_kernel<double, 0><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, ev_i, list, ulist, a.L, count, a.step, a.xbuf, ev,
                                                          a.log, (unsigned long long*)a.log_count, a.log_capacity);
       pm_gemv_kernel<double, 0><<<g_gemv, dim3(32, 8), 0, st>>>(a.U, a.L, a.N, a.xbuf, ev, a.vbuf);
       pm_update_kernel<double, 0><<<g_upd, 256, 0, st>>>(a.U, a.L, a.N, kchunk, a.xbuf, ev, a.vbuf);
     } else {
-      pm_row_kernel<float, 1><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, ev_i, list, ulist, count, a.step, a.xbuf, ev,
+      pm_row_kernel<float, 1><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, ev_i, list, ulist, a.L, count, a.step, a.xbuf, ev,
                                                         a.log, (unsigned long long*)a.log_count, a.log_capacity);
       pm_gemv_kernel<float, 1><<<g_gemv, dim3(32, 8), 0, st>>>(a.U, a.L, a.N, a.xbuf, ev, a.vbuf);
       pm_update_kernel<float, 1><<<g_upd, 256, 0, st>>>(a.U, a.L, a.N, kchunk, a.xbuf, ev, a.vbuf);
@@ -599,6 +600,30 @@ cudaError_t pm_measure_wide(cudaStream_t st, const pm_args& a, void* scratch, in
     *launches += 3;
   }
   return cudaSuccess;
+}
+
+cudaError_t pm_wide_event(cudaStream_t st, const pm_args& a, int e, const int* list, const double* ulist,
+                          int ld_list, const int* count, void* scratch) {
+  // the PmEvent array sits where pm_measure_wide keeps it in the same scratch
+  char* s = (char*)scratch;
+  s += (((int64_t)a.batch * a.L * 4) + 255) & ~(int64_t)255;
+  s += (((int64_t)a.batch * a.L * 8) + 255) & ~(int64_t)255;
+  s += (((int64_t)a.batch * 4) + 255) & ~(int64_t)255;
+  PmEvent* ev = (PmEvent*)s;
+  const int kchunk = std::max(32, FM_CEIL_DIV(a.N, std::max(1, (4 * 152) / std::max(1, FM_CEIL_DIV(a.L, 256) * a.batch))));
+  const dim3 g_gemv(FM_CEIL_DIV(a.L, 32), 1, a.batch), g_upd(FM_CEIL_DIV(a.L, 256), FM_CEIL_DIV(a.N, kchunk), a.batch);
+  if (a.layout == 0) {
+    pm_row_kernel<double, 0><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, e, list, ulist, ld_list, count, a.step, a.xbuf, ev, a.log,
+                                                       (unsigned long long*)a.log_count, a.log_capacity);
+    pm_gemv_kernel<double, 0><<<g_gemv, dim3(32, 8), 0, st>>>(a.U, a.L, a.N, a.xbuf, ev, a.vbuf);
+    pm_update_kernel<double, 0><<<g_upd, 256, 0, st>>>(a.U, a.L, a.N, kchunk, a.xbuf, ev, a.vbuf);
+  } else {
+    pm_row_kernel<float, 1><<<a.batch, 1024, 0, st>>>(a.U, a.L, a.N, e, list, ulist, ld_list, count, a.step, a.xbuf, ev, a.log,
+                                                      (unsigned long long*)a.log_count, a.log_capacity);
+    pm_gemv_kernel<float, 1><<<g_gemv, dim3(32, 8), 0, st>>>(a.U, a.L, a.N, a.xbuf, ev, a.vbuf);
+    pm_update_kernel<float, 1><<<g_upd, 256, 0, st>>>(a.U, a.L, a.N, kchunk, a.xbuf, ev, a.vbuf);
+  }
+  return cudaGetLastError();
 }
 
 size_t pm_wide_scratch_bytes(int L, int B) {

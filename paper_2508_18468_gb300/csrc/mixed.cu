@@ -44,8 +44,13 @@ struct Scratch {
   size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
 };
 
-// the block projective update serves the shapes the one-CTA-per-trajectory kernel does not
-bool uses_pm_block(int protocol, int L, int B) { return protocol == FM_PROJECTIVE && pm_use_wide(L, L / 2, B); }
+// mixed-precision projective steps run as blocks (pm_block.cu); the per-event
+// paths remain for steps that select more sites than the block holds
+bool uses_pm_block(int protocol, int L, int B) {
+  (void)L;
+  (void)B;
+  return protocol == FM_PROJECTIVE;
+}
 
 Scratch scratch_plan(int Lx, int Ly, int B, int protocol) {
   Scratch s;
@@ -80,18 +85,19 @@ Scratch scratch_plan(int Lx, int Ly, int B, int protocol) {
     s.pb_ulist = s.take(B * L * 8);
     s.pb_count = s.take(B * 4);
     s.pb_pos = s.take(B * L * 4);
-    s.pb_wt_h = s.take(2 * Kc * 2 * N * 2);
-    s.pb_wt_l = s.take(2 * Kc * 2 * N * 2);
+    // every operand for all trajectories, so that each product is one launch
+    s.pb_wt_h = s.take(B * 2 * Kc * 2 * N * 2);
+    s.pb_wt_l = s.take(B * 2 * Kc * 2 * N * 2);
     s.pb_dp = s.take(B * L * 2 * Kc * 4);
-    s.pb_dph = s.take(L * 2 * Kc * 2);
-    s.pb_dpl = s.take(L * 2 * Kc * 2);
-    s.pb_ap = s.take(L * 2 * Kc * 4);
-    s.pb_ath = s.take(2 * L * 2 * Kc * 2);
-    s.pb_atl = s.take(2 * L * 2 * Kc * 2);
-    s.pb_tth = s.take(2 * Kc * 2 * Kc * 2);
-    s.pb_ttl = s.take(2 * Kc * 2 * Kc * 2);
-    s.pb_xth = s.take(N * 2 * Kc * 2);
-    s.pb_xtl = s.take(N * 2 * Kc * 2);
+    s.pb_dph = s.take(B * L * 2 * Kc * 2);
+    s.pb_dpl = s.take(B * L * 2 * Kc * 2);
+    s.pb_ap = s.take(B * L * 2 * Kc * 4);
+    s.pb_ath = s.take(B * 2 * L * 2 * Kc * 2);
+    s.pb_atl = s.take(B * 2 * L * 2 * Kc * 2);
+    s.pb_tth = s.take(B * 2 * Kc * 2 * Kc * 2);
+    s.pb_ttl = s.take(B * 2 * Kc * 2 * Kc * 2);
+    s.pb_xth = s.take(B * N * 2 * Kc * 2);
+    s.pb_xtl = s.take(B * N * 2 * Kc * 2);
     s.pb_mats = s.take(7 * B * Kc * Kc * 8);
     s.pb_vecs = s.take(4 * B * Kc * 8);
     s.pb_ev = s.take(B * (int64_t)sizeof(PmbEvent));
@@ -577,11 +583,12 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
 // batch item): A rows M, B rows Nd, contraction Kd; mode PLAIN (D into out_f with
 // ld_out) or ADDV (out_f = in_f + D and its planes).
 int plane_gemm(MixedHost* h, MixedCtx* c, int mode, const __half* ah, const __half* al, const __half* bh,
-               const __half* bl, int M, int Nd, int Kd, int BN, float* out_f, int64_t ld_out, const float* in_f,
-               __half* out_h, __half* out_l) {
+               const __half* bl, int M, int Nd, int Kd, int BN, int batch, float* out_f, int64_t ld_out,
+               int64_t out_stride, const float* in_f, __half* out_h, __half* out_l) {
   CUtensorMap mah, mal, mbh, mbl;
-  if (!tc::make_kmajor_map(&mah, ah, Kd, M, Kd, tc::BM) || !tc::make_kmajor_map(&mal, al, Kd, M, Kd, tc::BM) ||
-      !tc::make_kmajor_map(&mbh, bh, Kd, Nd, Kd, BN) || !tc::make_kmajor_map(&mbl, bl, Kd, Nd, Kd, BN)) {
+  const uint64_t Mb = (uint64_t)M * batch, Nb = (uint64_t)Nd * batch;
+  if (!tc::make_kmajor_map(&mah, ah, Kd, Mb, Kd, tc::BM) || !tc::make_kmajor_map(&mal, al, Kd, Mb, Kd, tc::BM) ||
+      !tc::make_kmajor_map(&mbh, bh, Kd, Nb, Kd, BN) || !tc::make_kmajor_map(&mbl, bl, Kd, Nb, Kd, BN)) {
     c->err = "block projective update: tensor maps";
     return FM_ECUDA;
   }
@@ -590,7 +597,10 @@ int plane_gemm(MixedHost* h, MixedCtx* c, int mode, const __half* ah, const __ha
   p.tiles = nullptr;
   p.mtiles = M / tc::BM;
   p.ntiles_n = Nd / BN;
-  p.ntiles = p.mtiles * p.ntiles_n;
+  p.ntiles = p.mtiles * p.ntiles_n * batch;
+  p.a_rows_per_b = M;
+  p.b_rows_per_b = Nd;
+  p.out_batch_stride = out_stride;
   p.kblocks = Kd / tc::BK;
   p.out_f = out_f;
   p.ld_out = ld_out;
@@ -624,7 +634,7 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   const int K = ((kmax + 63) / 64) * 64;
   const int Kc = h->pb_kc;
   PmbMats& m = h->pm;
-  const int64_t sD = (int64_t)L * 2 * Kc;
+  const int64_t sD = (int64_t)L * 2 * K;          // per-trajectory stride of the L x 2K arrays
   // U~ planes (L x 2N per trajectory, K-major) of the propagated state (the
   // propagation writes the float state only, so its planes are made here)
   MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
@@ -633,14 +643,11 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   MCK(cudaGetLastError());
   MCK(pmb_setup(c->st, h->pb_list, h->pb_count, L, B, kmax, h->pb_pos));
   MCK(cudaMemsetAsync(m.C, 0, sizeof(c32) * 7 * (size_t)B * m.sM, c->st));
-  // P_b = U0_b W_b^dag as the row-major real form [Re P | Im P] (L x 2K)
-  for (int b = 0; b < B; ++b) {
-    MCK(pmb_gather_w(c->st, h->urm_h, h->urm_l, L, N, h->pb_list, h->pb_count, b, K, h->pb_wt_h, h->pb_wt_l));
-    const int64_t uo = (int64_t)b * L * 2 * N;
-    int r = plane_gemm(h, c, tc::MODE_PLAIN, h->pb_wt_h, h->pb_wt_l, h->urm_h + uo, h->urm_l + uo, 2 * K, L, 2 * N,
-                       256, h->pb_dp + b * sD, 2 * K, nullptr, nullptr, nullptr);
-    if (r) return r;
-  }
+  // P_b = U0_b W_b^dag as the row-major real form [Re P | Im P] (L x 2K), all trajectories
+  MCK(pmb_gather_w(c->st, h->urm_h, h->urm_l, L, N, h->pb_list, h->pb_count, B, K, h->pb_wt_h, h->pb_wt_l));
+  int r = plane_gemm(h, c, tc::MODE_PLAIN, h->pb_wt_h, h->pb_wt_l, h->urm_h, h->urm_l, 2 * K, L, 2 * N, 256, B,
+                     h->pb_dp, 2 * K, sD, nullptr, nullptr, nullptr);
+  if (r) return r;
   MCK(pmb_gather_c(c->st, h->pb_dp, sD, L, K, B, h->pb_list, h->pb_count, m));
   // the events, in order
   for (int i = 0; i < kmax; ++i) {
@@ -652,30 +659,57 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   MCK(pmb_gather_wc(c->st, c->V, L, N, K, B, h->pb_list, h->pb_count, m));
   const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
   MCK(zgemm<float>(c->st, K, N, K, OP_C, OP_N, one, m.TBc, Kc, m.sM, m.Wc, Kc, m.sW, zero, m.X, Kc, m.sW, B, 0));
-  // per trajectory: A = P T_A (+ E_S T_E in the planes), then V2_b = V_b + A B^dag
+  // A = P T_A (+ E_S T_E in the planes), then V2_b = V_b + A B^dag, all trajectories
+  MCK(pmb_ttilde(c->st, m, K, B, h->pb_tth, h->pb_ttl));
+  MCK(pmb_split(c->st, h->pb_dp, (int64_t)B * L * 2 * K, h->pb_dph, h->pb_dpl));
+  r = plane_gemm(h, c, tc::MODE_PLAIN, h->pb_tth, h->pb_ttl, h->pb_dph, h->pb_dpl, 2 * K, L, 2 * K, 256, B,
+                 h->pb_ap, 2 * K, sD, nullptr, nullptr, nullptr);
+  if (r) return r;
+  MCK(pmb_atilde(c->st, h->pb_ap, L, K, B, h->pb_pos, m, h->pb_ath, h->pb_atl));
+  MCK(pmb_xtilde(c->st, m, K, B, N, h->pb_xth, h->pb_xtl));
   const int BNu = (N % 256 == 0) ? 256 : 128;
-  for (int b = 0; b < B; ++b) {
-    MCK(pmb_ttilde(c->st, m, K, b, h->pb_tth, h->pb_ttl));
-    MCK(pmb_split(c->st, h->pb_dp + b * sD, (int64_t)L * 2 * K, h->pb_dph, h->pb_dpl));
-    int r = plane_gemm(h, c, tc::MODE_PLAIN, h->pb_tth, h->pb_ttl, h->pb_dph, h->pb_dpl, 2 * K, L, 2 * K, 256,
-                       h->pb_ap, 2 * K, nullptr, nullptr, nullptr);
-    if (r) return r;
-    MCK(pmb_atilde(c->st, h->pb_ap, L, K, b, h->pb_pos, m, h->pb_ath, h->pb_atl));
-    MCK(pmb_xtilde(c->st, m, K, b, N, h->pb_xth, h->pb_xtl));
-    const int64_t vo = (int64_t)b * 2 * L * N;
-    r = plane_gemm(h, c, tc::MODE_ADDV, h->pb_ath, h->pb_atl, h->pb_xth, h->pb_xtl, 2 * L, N, 2 * K, BNu,
-                   c->V2 + vo, 2 * L, c->V + vo, c->Vh + vo, c->Vl + vo);
-    if (r) return r;
-  }
+  r = plane_gemm(h, c, tc::MODE_ADDV, h->pb_ath, h->pb_atl, h->pb_xth, h->pb_xtl, 2 * L, N, 2 * K, BNu, B, c->V2,
+                 2 * L, (int64_t)2 * L * N, c->V, c->Vh, c->Vl);
+  if (r) return r;
   std::swap(c->V, c->V2);
   return FM_OK;
 }
 
 }  // namespace
 
+int mixed_reorth(MixedHost* h, MixedCtx* c) {
+  const int L = c->L, N = c->N, B = c->B;
+  MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
+  int r = qr_pass(h, c, true);
+  if (r) return r;
+  return qr_pass(h, c, false);
+}
+
 int mixed_step(MixedHost* h, MixedCtx* c) {
   const int L = c->L, N = c->N, B = c->B, BN = h->BN;
   const int grid = tc::sm_count();
+  if (c->protocol == FM_HOMODYNE_RK4) {
+    // App. A's integrator: <n> of U(t), the weights' logarithms, four Horner stages
+    const int nch = occupation_chunks(L, N, B);
+    c->timer->begin(FM_PH_MEASURE);
+    MCK(rownorm_partials_v(c->st, c->V, L, N, B, c->part, nch));
+    MCK(reduce_occupations(c->st, c->part, nch, L, B, c->nocc, c->w, c->gamma, c->dt, c->traj, c->step, c->seed));
+    c->timer->end(FM_PH_MEASURE);
+    c->timer->begin(FM_PH_PROPAGATE);
+    const double hJ = c->dt * c->J;
+    MCK(rk4_stage(c->st, 1, c->V, c->V, c->rk4buf, L, N, B, c->Lx, c->Ly, c->w, hJ, 0.25));
+    MCK(rk4_stage(c->st, 1, c->V, c->rk4buf, c->V2, L, N, B, c->Lx, c->Ly, c->w, hJ, 1.0 / 3.0));
+    MCK(rk4_stage(c->st, 1, c->V, c->V2, c->rk4buf, L, N, B, c->Lx, c->Ly, c->w, hJ, 0.5));
+    MCK(rk4_stage(c->st, 1, c->V, c->rk4buf, c->V2, L, N, B, c->Lx, c->Ly, c->w, hJ, 1.0));
+    std::swap(c->V, c->V2);
+    MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
+    c->timer->end(FM_PH_PROPAGATE);
+    int r = qr_pass(h, c, true);
+    if (r) return r;
+    if ((c->global_step + 1) % c->reorth_interval == 0 && (r = qr_pass(h, c, false))) return r;
+    MCK(bump_steps(c->st, c->step, B));
+    return FM_OK;
+  }
   // 1. propagation V2 = A V with row sums of squares
   int nchunks = 2 * (N / BN);
   c->timer->begin(FM_PH_PROPAGATE);

@@ -15,7 +15,7 @@ struct MixedCtx {
   int Lx, Ly, L, N, B;
   int protocol, reorth_interval;
   int tile_config;         // fm_params.tile_config (validated)
-  double dt;
+  double dt, J;
   uint64_t seed;
   int64_t global_step;
   float *V, *V2;           // state (2L x N float per trajectory) and its double buffer
@@ -34,6 +34,7 @@ struct MixedCtx {
   const z64 *band_tx, *band_ty;   // taps along x and y (device)
   const int *band_ox, *band_oy;   // their site offsets
   int ntap_x, ntap_y;
+  float* rk4buf;           // Runge-Kutta stage buffer (FM_HOMODYNE_RK4)
   int64_t launches;        // out: kernels launched
   std::string err;         // out: message on failure
 };
@@ -45,5 +46,6 @@ size_t mixed_scratch_bytes(int Lx, int Ly, int batch, int protocol);
 MixedHost* mixed_create(MixedCtx* c, std::string* why);   // uploads tile lists, encodes tensor maps
 void mixed_free(MixedHost* h);
 int mixed_step(MixedHost* h, MixedCtx* c);               // returns an fm_status value
+int mixed_reorth(MixedHost* h, MixedCtx* c);             // fp16 planes of V, then both CholeskyQR passes
 
 }  // namespace fm

@@ -65,9 +65,10 @@ __global__ void pmb_pos_kernel(const int* list, const int* count, int L, int* po
 // (re, im) turned into (-im, re) (so that the product gives Im P); zero rows
 // past the trajectory's count.
 __global__ void pmb_gather_w_kernel(const __half* __restrict__ urm_h, const __half* __restrict__ urm_l, int L,
-                                    int N, const int* list, const int* count, int b, int K, __half* wt_h,
+                                    int N, const int* list, const int* count, int K, __half* wt_h,
                                     __half* wt_l) {
-  const int row = blockIdx.y;                 // 0 .. 2K-1
+  const int b = blockIdx.z;
+  const int row = blockIdx.y;                 // 0 .. 2K-1 of trajectory b (planes rows b 2K + row)
   const int l = row < K ? row : row - K;
   const bool ok = l < count[b];
   const int64_t src = ok ? ((int64_t)b * L + list[(int64_t)b * L + l]) * 2 * N : 0;
@@ -83,7 +84,7 @@ __global__ void pmb_gather_w_kernel(const __half* __restrict__ urm_h, const __ha
         h1 = th; l1 = tl;
       }
     }
-    const int64_t o = (int64_t)row * 2 * N + 2 * n;
+    const int64_t o = ((int64_t)b * 2 * K + row) * 2 * N + 2 * n;
     wt_h[o] = h0; wt_h[o + 1] = h1;
     wt_l[o] = l0; wt_l[o + 1] = l1;
   }
@@ -252,8 +253,11 @@ __global__ void pmb_update_kernel(int i, int Kc, const int* count, const PmbEven
 
 // ------------------------------------------------------------------ operands of the final products
 // K-major planes of M^T, M = [[Re T_A, Im T_A], [-Im T_A, Re T_A]] (2K x 2K), trajectory b
-__global__ void pmb_ttilde_kernel(const c32* TA, int64_t sM, int Kc, int K, int b, __half* th, __half* tl) {
+__global__ void pmb_ttilde_kernel(const c32* TA, int64_t sM, int Kc, int K, __half* th, __half* tl) {
+  const int b = blockIdx.z;
   const int cp = blockIdx.y;                            // row of the plane = column c' of M
+  th += (int64_t)b * 4 * K * K;
+  tl += (int64_t)b * 4 * K * K;
   for (int kp = blockIdx.x * blockDim.x + threadIdx.x; kp < 2 * K; kp += gridDim.x * blockDim.x) {
     const int c = cp < K ? cp : cp - K, k = kp < K ? kp : kp - K;
     const c32 t = TA[b * sM + (int64_t)k * Kc + c];
@@ -278,9 +282,13 @@ __global__ void pmb_split_kernel(const float* x, int64_t n, __half* h, __half* l
 
 // K-major planes of the real embedding of A = P T_A + E_S T_E (2L x 2K): row i
 // [Re A_i, -Im A_i], row L + i [Im A_i, Re A_i]; Ap = row-major [Re(P T_A) | Im(P T_A)].
-__global__ void pmb_atilde_kernel(const float* Ap, int L, int K, int Kc, int b, const int* pos, const c32* TE,
+__global__ void pmb_atilde_kernel(const float* Ap, int L, int K, int Kc, const int* pos, const c32* TE,
                                   int64_t sM, __half* ah, __half* al) {
+  const int b = blockIdx.z;
   const int i = blockIdx.y;
+  Ap += (int64_t)b * L * 2 * K;
+  ah += (int64_t)b * 2 * L * 2 * K;
+  al += (int64_t)b * 2 * L * 2 * K;
   const int r = pos[(int64_t)b * L + i];
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
     float re = Ap[(int64_t)i * 2 * K + c], im = Ap[(int64_t)i * 2 * K + K + c];
@@ -315,8 +323,11 @@ __global__ void pmb_gather_wc_kernel(const float* V, int L, int N, int K, int Kc
 }
 
 // K-major planes of X~ (N x 2K): row n = [Re X[:, n], Im X[:, n]], X = T_B^dag W (K x N, ld Kc)
-__global__ void pmb_xtilde_kernel(const c32* X, int64_t sX, int K, int Kc, int b, int N, __half* xh, __half* xl) {
+__global__ void pmb_xtilde_kernel(const c32* X, int64_t sX, int K, int Kc, int N, __half* xh, __half* xl) {
+  const int b = blockIdx.z;
   const int n = blockIdx.y;
+  xh += (int64_t)b * N * 2 * K;
+  xl += (int64_t)b * N * 2 * K;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     const c32 x = X[b * sX + k + (int64_t)n * Kc];
     const float vals[2] = {x.re, x.im};
@@ -344,9 +355,9 @@ cudaError_t pmb_setup(cudaStream_t st, const int* list, const int* count, int L,
 }
 
 cudaError_t pmb_gather_w(cudaStream_t st, const __half* urm_h, const __half* urm_l, int L, int N, const int* list,
-                         const int* count, int b, int K, __half* wt_h, __half* wt_l) {
-  pmb_gather_w_kernel<<<dim3(FM_CEIL_DIV(N, 256), 2 * K), 256, 0, st>>>(urm_h, urm_l, L, N, list, count, b, K, wt_h,
-                                                                          wt_l);
+                         const int* count, int B, int K, __half* wt_h, __half* wt_l) {
+  pmb_gather_w_kernel<<<dim3(FM_CEIL_DIV(N, 256), 2 * K, B), 256, 0, st>>>(urm_h, urm_l, L, N, list, count, K, wt_h,
+                                                                             wt_l);
   return cudaGetLastError();
 }
 
@@ -356,8 +367,8 @@ cudaError_t pmb_gather_c(cudaStream_t st, const float* Dp, int64_t sD, int L, in
   return cudaGetLastError();
 }
 
-cudaError_t pmb_ttilde(cudaStream_t st, const PmbMats& m, int K, int b, __half* th, __half* tl) {
-  pmb_ttilde_kernel<<<dim3(FM_CEIL_DIV(2 * K, 256), 2 * K), 256, 0, st>>>(m.TA, m.sM, m.Kc, K, b, th, tl);
+cudaError_t pmb_ttilde(cudaStream_t st, const PmbMats& m, int K, int B, __half* th, __half* tl) {
+  pmb_ttilde_kernel<<<dim3(FM_CEIL_DIV(2 * K, 256), 2 * K, B), 256, 0, st>>>(m.TA, m.sM, m.Kc, K, th, tl);
   return cudaGetLastError();
 }
 
@@ -367,9 +378,9 @@ cudaError_t pmb_split(cudaStream_t st, const float* x, int64_t n, __half* h, __h
   return cudaGetLastError();
 }
 
-cudaError_t pmb_atilde(cudaStream_t st, const float* Ap, int L, int K, int b, const int* pos, const PmbMats& m,
+cudaError_t pmb_atilde(cudaStream_t st, const float* Ap, int L, int K, int B, const int* pos, const PmbMats& m,
                        __half* ah, __half* al) {
-  pmb_atilde_kernel<<<dim3(FM_CEIL_DIV(K, 256), L), 256, 0, st>>>(Ap, L, K, m.Kc, b, pos, m.TE, m.sM, ah, al);
+  pmb_atilde_kernel<<<dim3(FM_CEIL_DIV(K, 256), L, B), 256, 0, st>>>(Ap, L, K, m.Kc, pos, m.TE, m.sM, ah, al);
   return cudaGetLastError();
 }
 
@@ -379,8 +390,8 @@ cudaError_t pmb_gather_wc(cudaStream_t st, const float* V, int L, int N, int K, 
   return cudaGetLastError();
 }
 
-cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int b, int N, __half* xh, __half* xl) {
-  pmb_xtilde_kernel<<<dim3(FM_CEIL_DIV(K, 256), N), 256, 0, st>>>(m.X, m.sW, K, m.Kc, b, N, xh, xl);
+cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int B, int N, __half* xh, __half* xl) {
+  pmb_xtilde_kernel<<<dim3(FM_CEIL_DIV(K, 256), N, B), 256, 0, st>>>(m.X, m.sW, K, m.Kc, N, xh, xl);
   return cudaGetLastError();
 }
 

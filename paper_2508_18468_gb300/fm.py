@@ -13,7 +13,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfm.so")
 
 FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENUMERIC, FM_ETIMEOUT, FM_ESTATE = range(7)
-FM_PROJECTIVE, FM_HOMODYNE = 0, 1
+FM_PROJECTIVE, FM_HOMODYNE, FM_HOMODYNE_RK4, FM_PROJECTIVE_POISSON = 0, 1, 2, 3
 FM_FP64, FM_MIXED = 0, 1
 FM_PROP_DENSE, FM_PROP_BANDED = 0, 1
 PHASES = ("propagate", "measure", "gram", "cholesky", "trmm", "entropy")

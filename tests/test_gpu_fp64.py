@@ -243,10 +243,79 @@ def test_density_correlation_and_particle_covariance(fm, Lx, Ly, protocol):
 @pytest.mark.parametrize("Lx,Ly,protocol", [(64, 1, PROJECTIVE), (8, 6, HOMODYNE), (1024, 1, HOMODYNE),
                                              (6, 1, PROJECTIVE)])
 def test_banded_propagation_matches_dense_oracle(fm, Lx, Ly, protocol):
-    """Stencils of the circulant propagator (taps above 1e-18) against the oracle's dense P."""
+    """Stencils of the circulant propagator (taps above 1e-15) against the oracle's dense P."""
     po, g = pair(fm, Lx, Ly, gamma=1.0, protocol=protocol, seed=23, reorth=2)
     g.set_propagation(fm.FM_PROP_BANDED)
     n = 12
     g.step(n)
     ref = trajectory.run(po, n)
     assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+
+
+@pytest.mark.parametrize("Lx,Ly,reorth", [(64, 1, 1), (8, 6, 2), (2, 4, 1), (130, 1, 3)])
+def test_runge_kutta_protocol_matches_oracle(fm, Lx, Ly, reorth):
+    """App. A's integrator (RK4 of Eq. (QSD_evo), nearest-neighbour H~) against the oracle."""
+    po, g = pair(fm, Lx, Ly, gamma=1.2, protocol=trajectory.HOMODYNE_RK4, seed=27, reorth=reorth)
+    n = 20
+    g.step(n)
+    ref = trajectory.run(po, n)
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    A = list(range(Lx * Ly // 2))
+    assert srel(g.entropy(A), observables.entanglement_entropy(ref["U"], A)) <= S_TOL
+
+
+@pytest.mark.parametrize("Lx,Ly,gamma,reorth", [(64, 1, 3.0, 1), (16, 1, 6.0, 2), (20, 4, 1.5, 3), (6, 6, 2.0, 1)])
+def test_continuous_time_projective_matches_oracle(fm, Lx, Ly, gamma, reorth):
+    """App. A's continuous-time projective protocol: Poisson events, exp(-i H~ tau) between
+    them (Bessel-tap stencils on long directions, the plane-wave row on short ones)."""
+    po, g = pair(fm, Lx, Ly, gamma=gamma, protocol=trajectory.PROJECTIVE_POISSON, seed=41, traj_id=5,
+                 reorth=reorth, events=100000)
+    n = 30
+    g.step(n)
+    ref = trajectory.run(po, n)
+    ev, dropped = g.take_events()
+    assert dropped == 0 and len(ev) == len(ref["events"]) > 0
+    got = [(e[1], e[2], e[3], e[5]) for e in ev]                 # event order is the time order
+    exp = [(s, j, u, o) for (s, j, u, p, o) in ref["events"]]
+    assert got == exp                                            # sites, draws, outcomes bit-identical
+    assert max(abs(e[4] - r[3]) for e, r in zip(ev, ref["events"])) < 1e-12
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    A = list(range(Lx * Ly // 2))
+    assert srel(g.entropy(A), observables.entanglement_entropy(ref["U"], A)) <= S_TOL
+
+
+def test_continuous_time_projective_batch_rates_and_restart(fm):
+    """Three trajectories at their own rates, one restarted halfway: each equals its own
+    oracle trajectory (the event schedule is per trajectory)."""
+    Lx, rates = 32, [0.0, 2.0, 5.0]
+    pg = fm.make_params(Lx, batch=3, protocol=fm.FM_PROJECTIVE_POISSON, precision=fm.FM_FP64, gamma=1.0,
+                        seed=9, traj_id=100)
+    g = fm.Trajectories(pg)
+    g.set_gammas(rates)
+    g.step(10)
+    g.reset_trajectory(1, 777, 3.0)
+    g.step(15)
+    for b, (tid, gam, n) in enumerate([(100, 0.0, 25), (777, 3.0, 15), (102, 5.0, 25)]):
+        ref = trajectory.run(Params(Lx=Lx, gamma=gam, protocol=trajectory.PROJECTIVE_POISSON, seed=9,
+                                    traj_id=tid), n)
+        assert cdiff(g.copy_U(b), ref["U"]) <= C_TOL, b
+
+
+def test_continuous_time_projective_checkpoint_and_graph_request(fm, tmp_path):
+    """A checkpoint restores the event schedule (replayed from the step counts), and
+    asking for CUDA graphs leaves the host-scheduled protocol eager: both equal an
+    uninterrupted run bit for bit."""
+    pg = fm.make_params(24, batch=2, protocol=fm.FM_PROJECTIVE_POISSON, precision=fm.FM_FP64, gamma=2.5,
+                        seed=13, reorth_interval=2)
+    a = fm.Trajectories(pg)
+    a.step(17)
+    b = fm.Trajectories(pg)
+    b.set_graphs(True)
+    b.step(7)
+    path = str(tmp_path / "pois.ckpt")
+    b.save(path)
+    c = fm.Trajectories(pg)
+    c.load(path)
+    c.step(10)
+    for t in range(2):
+        assert np.array_equal(a.copy_U(t), c.copy_U(t))

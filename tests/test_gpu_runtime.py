@@ -22,7 +22,7 @@ def fm():
 
 
 @pytest.mark.parametrize("precision,protocol,L,reorth", [(0, 1, 64, 1), (0, 0, 64, 2), (1, 1, 256, 1),
-                                                          (1, 0, 512, 3)])
+                                                          (1, 0, 512, 3), (0, 2, 64, 2), (1, 2, 256, 1)])
 def test_graph_replay_equals_eager(fm, precision, protocol, L, reorth):
     kw = dict(batch=2, protocol=protocol, precision=precision, reorth_interval=reorth, gamma=1.0, seed=4)
     a = fm.Trajectories(fm.make_params(L, **kw))

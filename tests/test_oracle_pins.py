@@ -295,6 +295,97 @@ def test_density_correlation_sum_rule_and_ring_symmetry():
     assert np.max(np.abs(c[1:] - c[1:][::-1])) < 1e-15
 
 
+def test_rk4_step_is_the_quartic_taylor_polynomial_and_close_to_expm():
+    """For the constant A of a step, RK4 equals sum_{k<=4} (A dt)^k / k! applied to U
+    (written here from the series, not from the stages), and differs from
+    expm(A dt) U by at most the series remainder."""
+    L, N, dt, gamma = 12, 6, 0.05, 1.3
+    U = _random_state(L, N, 31)
+    H = lattice.hopping_matrix(6, 2)
+    xi = np.random.default_rng(4).standard_normal(L)
+    got = trajectory.step_rk4(U, H, xi, gamma, dt)
+    n = np.real(np.sum(U * np.conj(U), axis=1))
+    X = -1j * dt * H + np.diag(np.sqrt(gamma * dt) * xi + (2 * n - 1) * gamma * dt)
+    series, term = U.copy(), U.copy()
+    for k in range(1, 5):
+        term = X @ term / k
+        series = series + term
+    assert np.max(np.abs(got - series)) < 1e-14
+    nx = np.linalg.norm(X, 2)
+    bound = nx ** 5 / 120 / (1 - nx / 6) * np.linalg.norm(U, 2)
+    assert np.linalg.norm(scipy.linalg.expm(X) @ U - got, 2) <= bound
+
+
+def test_rk4_and_split_step_agree_as_dt_goes_to_zero():
+    """One step from the same state and the same normals: the Runge-Kutta step of
+    Eq. (QSD_evo) and the split step (propagate, then weight) differ by the
+    commutator of H~ and the weight, O(dt^(3/2)) -- the fixed-dt path is the dt -> 0
+    limit of the paper's integrator.  Checked: the difference falls by ~8 when dt
+    falls by 4."""
+    L, N, gamma = 16, 8, 1.0
+    U = _random_state(L, N, 41)
+    H = lattice.hopping_matrix(L)
+    xi = np.random.default_rng(6).standard_normal(L)
+    diffs = []
+    for dt in (0.02, 0.005, 0.00125):
+        a = trajectory.orthonormalize(trajectory.step_rk4(U, H, xi, gamma, dt))
+        P = scipy.linalg.expm(-1j * dt * H)
+        b = trajectory.orthonormalize(trajectory.homodyne_weight(P @ U, xi, gamma, dt))
+        diffs.append(np.max(np.abs(observables.correlation(a) - observables.correlation(b))))
+    r1, r2 = diffs[0] / diffs[1], diffs[1] / diffs[2]
+    assert 6.0 < r1 < 10.0 and 6.0 < r2 < 10.0, diffs
+
+
+@pytest.mark.parametrize("Lx,Ly,gamma,seed", [(8, 1, 2.0, 3), (4, 2, 3.0, 7)])
+def test_continuous_time_projective_matches_brute_force(Lx, Ly, gamma, seed):
+    """App. A's continuous-time protocol: the many-body state driven by the same event
+    sequence (waiting times, sites, Born draws) -- exp(-i H tau) between events, n_j or
+    1 - n_j at each event -- has C = conj(D) of the oracle's orbitals at every step end."""
+    prm = Params(Lx=Lx, Ly=Ly, gamma=gamma, protocol=trajectory.PROJECTIVE_POISSON, reorth_interval=2, seed=seed,
+                 traj_id=4)
+    L, N = prm.L, prm.N
+    nsteps = 30
+    out = trajectory.run(prm, nsteps)
+    sec = brute.Sector(L, N)
+    bonds = brute.ring_bonds(L) if Ly == 1 else brute.torus_bonds(Lx, Ly)
+    Hmb = sec.hamiltonian(bonds, prm.J)
+    psi = sec.from_orbitals(lattice.initial_orbitals(Lx, Ly))
+    rate = gamma * N
+    e, t = 0, 0.0
+    t_next = -np.log1p(-philox.poisson_event(seed, 4, 0, L)[0]) / rate
+    seen = []
+    for s in range(nsteps):
+        t1 = (s + 1) * prm.dt
+        while t_next <= t1:
+            psi = scipy.linalg.expm(-1j * (t_next - t) * Hmb) @ psi
+            t = t_next
+            _, j, u = philox.poisson_event(seed, 4, e, L)
+            _, w1 = sec.project(psi, j, 1)
+            outcome = 1 if u < w1 else 0
+            psi, _ = sec.project(psi, j, outcome)
+            seen.append((s, j, outcome, w1))
+            e += 1
+            t_next += -np.log1p(-philox.poisson_event(seed, 4, e, L)[0]) / rate
+        psi = scipy.linalg.expm(-1j * (t1 - t) * Hmb) @ psi
+        t = t1
+    assert [(a, b, c) for a, b, c, _ in seen] == [(a, b, o) for a, b, u, p, o in out["events"]]
+    assert max(abs(w - p) for (_, _, _, w), (_, _, _, p, _) in zip(seen, out["events"])) < 1e-11
+    assert len(seen) >= 10 and {o for (_, _, o, _) in seen} == {0, 1}
+    D = sec.d_matrix(psi)
+    assert np.max(np.abs(observables.correlation(out["U"]) - np.conj(D))) < 1e-12
+
+
+def test_continuous_time_event_statistics():
+    """Waiting times exponential with mean 1 / (gamma N), sites uniform over the lattice."""
+    L, N, gamma = 40, 20, 1.5
+    draws = [philox.poisson_event(9, 2, e, L) for e in range(20000)]
+    taus = np.array([-np.log1p(-d[0]) / (gamma * N) for d in draws])
+    assert abs(taus.mean() * gamma * N - 1.0) < 0.03
+    assert abs(np.std(taus) * gamma * N - 1.0) < 0.03
+    counts = np.bincount([d[1] for d in draws], minlength=L)
+    assert counts.min() > 380 and counts.max() < 620
+
+
 def test_binary_entropy_terms_edges():
     f = observables.binary_entropy_terms(np.array([0.0, 1.0, 0.5, -1e-17, 1 + 1e-16]))
     assert f[0] == 0 and f[1] == 0 and f[3] == 0 and f[4] == 0
