@@ -169,7 +169,7 @@ def step(U, P, prm, step_index, forced=None, H=None):
     return U, events
 
 
-def run_poisson(prm, nsteps, U=None):
+def run_poisson(prm, nsteps, U=None, forced=None):
     """The projective protocol as App. A runs it, in continuous time.
 
     Measurement events come at the times of a Poisson process of total rate gamma N
@@ -180,7 +180,8 @@ def run_poisson(prm, nsteps, U=None):
     protocol; between events the state evolves by exp(-i H~ tau) (here ``expm``).  The
     events are a fixed sequence per trajectory (``philox.poisson_event``), their times
     the running sum of the waiting times; step s covers (s dt, (s+1) dt] and ends with
-    the propagation to (s+1) dt.  QR every ``reorth_interval`` steps.
+    the propagation to (s+1) dt.  QR every ``reorth_interval`` steps.  ``forced``
+    optionally maps event index -> outcome to replay a given sequence.
     Returns dict(U, events=[(step, site, u, p, outcome)]).
     """
     import scipy.linalg
@@ -205,6 +206,8 @@ def run_poisson(prm, nsteps, U=None):
             x = U[j, :]
             p = min(max(float(np.real(np.vdot(x, x))), 0.0), 1.0)
             outcome = 1 if u < p else 0
+            if forced is not None and e in forced:
+                outcome = forced[e]
             events.append((s, j, u, p, outcome))
             if p >= 1e-300:
                 U = project_site(U, j, outcome)
@@ -220,13 +223,14 @@ def run_poisson(prm, nsteps, U=None):
 def run(prm, nsteps, U=None, P=None, start_step=0, ee_every=0, ee_sites=None, forced=None):
     """Run ``nsteps`` steps.  Returns dict(U, events, ee=[(steps_done, S)]).
 
-    ``forced`` optionally maps step index -> {site: outcome}.
+    ``forced`` optionally maps step index -> {site: outcome} (the continuous-time
+    protocol: event index -> outcome).
     """
     from . import observables
     if prm.protocol == PROJECTIVE_POISSON:
-        if start_step or ee_every or forced:
+        if start_step or ee_every:
             raise ValueError("run_poisson: whole trajectories from t = 0 only")
-        out = run_poisson(prm, nsteps, U)
+        out = run_poisson(prm, nsteps, U, forced)
         out["ee"] = []
         return out
     H = None

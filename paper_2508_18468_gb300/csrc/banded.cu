@@ -37,64 +37,160 @@ struct band_io<T, 1> {  // float V, 2L x N per trajectory (column k = [Re; Im])
   }
 };
 
-// out[i, k] = sum_t taps[t] in[site i shifted back by off[t] along dir, k]; thread per
-// site, a chunk of `per` columns per blockIdx.y; with `partial`, the row sums of
-// |out|^2 over the chunk go to partial[(b nch + chunk) L + i].  The offsets are
-// consecutive (off[t] = off[0] + t), so the source site steps back by one along
-// dir (with wrap) from tap to tap: no per-tap index array.
+// out[i, k] = sum_t taps[t] in[site i shifted back by off[t] along dir, k].  The
+// offsets are consecutive (off[t] = off[0] + t), so the sources of a run of
+// outputs along dir are one contiguous (periodic) run of inputs: each block
+// stages that run plus the stencil's halo in shared memory (coalesced loads),
+// then every thread sums its taps from shared memory.
+//   dir 0 (x, unit stride): a block covers 256 consecutive x of one row y and
+//     kBandCols columns per stage.
+//   dir 1 (y, stride Lx): a block covers 32 consecutive x (one per lane) and 64
+//     (float) or 32 (double) consecutive y, one column per stage.
+// blockIdx.y picks a chunk of columns, blockIdx.z the trajectory; with
+// `partial`, the row sums of |out|^2 over the chunk go to partial[(b nch + chunk) L + i].
+constexpr int kBandSegX = 256;
+constexpr int kBandCols = 8;
+constexpr int seg_y(int layout) { return layout == 0 ? 32 : 64; }
+
 template <typename T, int LAYOUT>
-__global__ void __launch_bounds__(256) band_prop_kernel(const void* in, void* out, int L, int N, int Lx, int Ly,
-                                                        int dir, const z64* taps, const int* off, int ntap, int per,
-                                                        double* partial, int nch, int tap_stride) {
+__global__ void __launch_bounds__(256) band_x_kernel(const void* __restrict__ in, void* out, int L, int N, int Lx,
+                                                     const z64* __restrict__ taps, const int* __restrict__ off,
+                                                     int ntap, int per, double* partial, int nch, int tap_stride) {
+  constexpr int W = kBandSegX + kBandMaxTaps - 1;
+  __shared__ cplx<T> buf[kBandCols][W];
   __shared__ cplx<T> tp[kBandMaxTaps];
   const int64_t b = blockIdx.z;
-  taps += b * tap_stride;                     // per-trajectory taps when tap_stride > 0
-  for (int t = threadIdx.x; t < ntap; t += blockDim.x) tp[t] = cmk<T>((T)taps[t].re, (T)taps[t].im);
-  __syncthreads();
+  taps += b * tap_stride;
+  const int tid = threadIdx.x;
+  if (tid < ntap) tp[tid] = cmk<T>((T)taps[tid].re, (T)taps[tid].im);
+  const int nseg = (Lx + kBandSegX - 1) / kBandSegX;
+  const int seg = blockIdx.x % nseg, y = blockIdx.x / nseg;
+  const int p0 = seg * kBandSegX;
+  const int offmax = off[0] + ntap - 1;
+  const int w = kBandSegX + ntap - 1;               // staged inputs per column
+  const int pos = p0 + tid;
+  const int i = pos + Lx * y;
   const int c = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L) return;
-  const int x = i % Lx, y = i / Lx;
-  const int n = dir == 0 ? Lx : Ly;           // period along dir
-  const int stride = dir == 0 ? 1 : Lx;       // site step along dir
-  const int pos = dir == 0 ? x : y;
-  int p0 = (pos - off[0]) % n;                // source position of tap 0
-  if (p0 < 0) p0 += n;
-  const int base = i - pos * stride;          // site with coordinate 0 along dir
   const int k0 = c * per, k1 = min(N, k0 + per);
   double s = 0.0;
-  for (int k = k0; k < k1; ++k) {
-    cplx<T> acc = cmk<T>((T)0, (T)0);
-    int p = p0;
-    for (int t = 0; t < ntap; ++t) {
-      const cplx<T> u = band_io<T, LAYOUT>::ld(in, b, L, N, base + p * stride, k);
-      acc.re += tp[t].re * u.re - tp[t].im * u.im;
-      acc.im += tp[t].re * u.im + tp[t].im * u.re;
-      p = p == 0 ? n - 1 : p - 1;
-    }
-    band_io<T, LAYOUT>::st(out, b, L, N, i, k, acc);
-    if (partial) s += (double)(acc.re * acc.re + acc.im * acc.im);
+  for (int kb = k0; kb < k1; kb += kBandCols) {
+    const int nk = min(kBandCols, k1 - kb);
+    __syncthreads();                                 // previous stage consumed (and tp written)
+    for (int kk = 0; kk < nk; ++kk)
+      for (int q = tid; q < w; q += blockDim.x) {
+        int src = (p0 - offmax + q) % Lx;
+        if (src < 0) src += Lx;
+        buf[kk][q] = band_io<T, LAYOUT>::ld(in, b, L, N, src + Lx * y, kb + kk);
+      }
+    __syncthreads();
+    if (pos < Lx)
+      for (int kk = 0; kk < nk; ++kk) {
+        cplx<T> acc = cmk<T>((T)0, (T)0);
+        const cplx<T>* src = &buf[kk][tid + ntap - 1];
+        for (int t = 0; t < ntap; ++t) {
+          const cplx<T> u = src[-t];
+          acc.re += tp[t].re * u.re - tp[t].im * u.im;
+          acc.im += tp[t].re * u.im + tp[t].im * u.re;
+        }
+        band_io<T, LAYOUT>::st(out, b, L, N, i, kb + kk, acc);
+        if (partial) s += (double)(acc.re * acc.re + acc.im * acc.im);
+      }
   }
-  if (partial) partial[(b * nch + c) * L + i] = s;
+  if (partial && pos < Lx) partial[(b * nch + c) * L + i] = s;
 }
 
-int band_chunks(int L, int N, int B) {
-  const int blocks = FM_CEIL_DIV(L, 256) * B;
-  return std::max(1, std::min(std::min(N, 128), FM_CEIL_DIV(4 * 152, blocks)));
+template <typename T, int LAYOUT, int SEGY>
+__global__ void __launch_bounds__(256) band_y_kernel(const void* __restrict__ in, void* out, int L, int N, int Lx,
+                                                     int Ly, const z64* __restrict__ taps,
+                                                     const int* __restrict__ off, int ntap, int per,
+                                                     double* partial, int nch, int tap_stride) {
+  constexpr int H = SEGY + kBandMaxTaps - 1;
+  __shared__ cplx<T> buf[H][32];
+  __shared__ cplx<T> tp[kBandMaxTaps];
+  const int64_t b = blockIdx.z;
+  taps += b * tap_stride;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  if (tid < ntap) tp[tid] = cmk<T>((T)taps[tid].re, (T)taps[tid].im);
+  const int nxt = (Lx + 31) / 32;
+  const int xt = blockIdx.x % nxt, ys = blockIdx.x / nxt;
+  const int x = xt * 32 + tx, y0 = ys * SEGY;
+  const int offmax = off[0] + ntap - 1;
+  const int h = SEGY + ntap - 1;
+  const int c = blockIdx.y;
+  const int k0 = c * per, k1 = min(N, k0 + per);
+  double s[SEGY / 8];
+#pragma unroll
+  for (int r = 0; r < SEGY / 8; ++r) s[r] = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    __syncthreads();
+    if (x < Lx)
+      for (int q = ty; q < h; q += 8) {
+        int src = (y0 - offmax + q) % Ly;
+        if (src < 0) src += Ly;
+        buf[q][tx] = band_io<T, LAYOUT>::ld(in, b, L, N, x + Lx * src, k);
+      }
+    __syncthreads();
+    if (x < Lx)
+#pragma unroll
+      for (int r = 0; r < SEGY / 8; ++r) {
+        const int yy = ty + 8 * r, y = y0 + yy;
+        if (y < Ly) {
+          cplx<T> acc = cmk<T>((T)0, (T)0);
+          for (int t = 0; t < ntap; ++t) {
+            const cplx<T> u = buf[yy + ntap - 1 - t][tx];
+            acc.re += tp[t].re * u.re - tp[t].im * u.im;
+            acc.im += tp[t].re * u.im + tp[t].im * u.re;
+          }
+          band_io<T, LAYOUT>::st(out, b, L, N, x + Lx * y, k, acc);
+          if (partial) s[r] += (double)(acc.re * acc.re + acc.im * acc.im);
+        }
+      }
+  }
+  if (partial && x < Lx)
+#pragma unroll
+    for (int r = 0; r < SEGY / 8; ++r) {
+      const int y = y0 + ty + 8 * r;
+      if (y < Ly) partial[(b * nch + c) * L + x + Lx * y] = s[r];
+    }
 }
+
+namespace {
+int clamp_chunks(int64_t blocks, int N) {
+  const int64_t want = (8 * 152 + blocks - 1) / blocks;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min(N, 128)));
+}
+}  // namespace
+
+int band_chunks(int Lx, int Ly, int N, int B, int dir, int layout) {
+  const int64_t blocks = dir == 0 ? (int64_t)FM_CEIL_DIV(Lx, kBandSegX) * Ly * B
+                                  : (int64_t)FM_CEIL_DIV(Lx, 32) * FM_CEIL_DIV(Ly, seg_y(layout)) * B;
+  return clamp_chunks(blocks, N);
+}
+
+int site_chunks(int L, int N, int B) { return clamp_chunks((int64_t)FM_CEIL_DIV(L, 256) * B, N); }
 
 cudaError_t band_propagate(cudaStream_t st, int layout, const void* in, void* out, int L, int N, int B, int Lx,
                            int Ly, int dir, const z64* taps, const int* off, int ntap, double* partial, int nch,
                            int tap_stride) {
-  if (ntap < 1 || ntap > kBandMaxTaps) return cudaErrorInvalidValue;
+  if (ntap < 1 || ntap > kBandMaxTaps || nch < 1 || Lx * Ly != L) return cudaErrorInvalidValue;
   const int per = FM_CEIL_DIV(N, nch);
-  const dim3 grid(FM_CEIL_DIV(L, 256), nch, B);
-  if (layout == 0)
-    band_prop_kernel<double, 0><<<grid, 256, 0, st>>>(in, out, L, N, Lx, Ly, dir, taps, off, ntap, per, partial, nch,
-                                                      tap_stride);
-  else
-    band_prop_kernel<float, 1><<<grid, 256, 0, st>>>(in, out, L, N, Lx, Ly, dir, taps, off, ntap, per, partial, nch,
+  if (dir == 0) {
+    const dim3 grid(FM_CEIL_DIV(Lx, kBandSegX) * Ly, nch, B);
+    if (layout == 0)
+      band_x_kernel<double, 0><<<grid, 256, 0, st>>>(in, out, L, N, Lx, taps, off, ntap, per, partial, nch,
                                                      tap_stride);
+    else
+      band_x_kernel<float, 1><<<grid, 256, 0, st>>>(in, out, L, N, Lx, taps, off, ntap, per, partial, nch,
+                                                    tap_stride);
+  } else {
+    const dim3 grid(FM_CEIL_DIV(Lx, 32) * FM_CEIL_DIV(Ly, seg_y(layout)), nch, B);
+    if (layout == 0)
+      band_y_kernel<double, 0, seg_y(0)><<<grid, dim3(32, 8), 0, st>>>(in, out, L, N, Lx, Ly, taps, off, ntap, per,
+                                                                       partial, nch, tap_stride);
+    else
+      band_y_kernel<float, 1, seg_y(1)><<<grid, dim3(32, 8), 0, st>>>(in, out, L, N, Lx, Ly, taps, off, ntap, per,
+                                                                      partial, nch, tap_stride);
+  }
   return cudaGetLastError();
 }
 
@@ -132,7 +228,7 @@ __global__ void rk4_stage_kernel(const void* U0, const void* Y, void* out, int L
 
 cudaError_t rk4_stage(cudaStream_t st, int layout, const void* U0, const void* Y, void* out, int L, int N, int B,
                       int Lx, int Ly, const double* w, double dtJ, double c) {
-  const int nch = band_chunks(L, N, B);
+  const int nch = site_chunks(L, N, B);
   const int per = FM_CEIL_DIV(N, nch);
   const dim3 grid(FM_CEIL_DIV(L, 256), nch, B);
   if (layout == 0)

@@ -60,96 +60,150 @@ template cudaError_t cholesky_inverse<float>(cudaStream_t, c32*, c32*, c32*, c32
 
 // ------------------------------------------------------------------ one-CTA leaf
 // G = R^dag R and T = R^-1 for an n x n block (n <= 128) of every trajectory,
-// complex64, in shared memory: right-looking Cholesky on the upper triangle,
-// then T by 32 x 32 blocks -- each diagonal block inverted by one warp (a
-// column per lane), then T_IJ = -T_II sum_{I < K <= J} R_IK T_KJ by all
-// threads, J ascending, I descending -- with T^T kept in the strict lower
-// triangle of the same array.  R and T are written with zeros below the
-// diagonal.  One CTA of 1024 threads per trajectory; a non-positive pivot
+// complex64, one CTA of 1024 threads per trajectory.  Thread (warp w, lane l)
+// keeps the elements (w + 32q, l + 32p), q, p = 0..3, of the upper triangle in
+// registers.
+//   Cholesky, right-looking with the rows left unscaled: step j reads the final
+//   row j and its pivot d_j from shared memory and updates every element r, c
+//   with j < r <= c by a_rc -= conj(a_jr) a_jc / d_j; the owners of row j + 1
+//   then store it (now final), one barrier per step.  Afterwards
+//   R_jc = a_jc / sqrt(d_j).
+//   Inverse, by rows from the bottom: W = 1; row j of T is W_j / R_jj once every
+//   row below it has been subtracted, W_i -= R_ij T_j (i < j).  T is kept
+//   transposed in the strict lower triangle of the same array, its diagonal
+//   apart; again one barrier per step.
+// R and T are written with zeros below the diagonal.  A non-positive pivot
 // raises FM_DEVERR_PIVOT and continues with pivot 1.
 namespace fm {
 
 constexpr int kLeafMax = 128;
 constexpr int kLeafLd = kLeafMax + 1;
-constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + kLeafMax + 32 * 33) * sizeof(c32);
+constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + 2 * kLeafMax) * sizeof(c32);
 
 __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restrict__ G, c32* R, c32* T, int n,
                                                              int64_t ld, int64_t sNN, int* status) {
   extern __shared__ c32 sm[];
   c32* A = sm;                                  // A[r * kLeafLd + c]
   c32* Td = sm + kLeafMax * kLeafLd;            // diagonal of T
-  c32* Z = Td + kLeafMax;                       // 32 x 33 block scratch
+  float* Rd = (float*)(Td + kLeafMax);          // sqrt of the pivots
   const int64_t b = blockIdx.x;
   G += b * sNN;
   R += b * sNN;
   T += b * sNN;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, l = tid & 31, w = tid >> 5;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int r = idx % n, c = idx / n;
-    A[r * kLeafLd + c] = r <= c ? G[r + (int64_t)c * ld] : cmk(0.0f, 0.0f);
+    if (r <= c) A[r * kLeafLd + c] = G[r + (int64_t)c * ld];
   }
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      float d = A[j * kLeafLd + j].re;
-      if (!(d > 0.0f) || !isfinite(d)) {
-        atomicOr(status, FM_DEVERR_PIVOT);
-        d = 1.0f;
-      }
-      A[j * kLeafLd + j] = cmk(sqrtf(d), 0.0f);
+  c32 a[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int r = w + 32 * q, c = l + 32 * p;
+      a[q][p] = (r <= c && c < n) ? A[r * kLeafLd + c] : cmk(0.0f, 0.0f);
     }
-    __syncthreads();
-    const float inv = 1.0f / A[j * kLeafLd + j].re;
-    for (int c = j + 1 + tid; c < n; c += blockDim.x) A[j * kLeafLd + c] = cscale(A[j * kLeafLd + c], inv);
-    __syncthreads();
-    const int m = n - j - 1;                    // trailing upper triangle, rows/cols j+1 .. n-1
-    for (int idx = tid; idx < m * m; idx += blockDim.x) {
-      const int r = j + 1 + idx % m, c = j + 1 + idx / m;
-      if (r <= c) A[r * kLeafLd + c] = csub(A[r * kLeafLd + c], cmul(cconj(A[j * kLeafLd + r]), A[j * kLeafLd + c]));
+  // ---- Cholesky (unscaled rows)
+  for (int j = 0; j + 1 < n; ++j) {
+    float d = A[j * kLeafLd + j].re;
+    if (!(d > 0.0f) || !isfinite(d)) {
+      if (tid == 0) atomicOr(status, FM_DEVERR_PIVOT);
+      d = 1.0f;
+    }
+    const float inv = 1.0f / d;
+    c32 pr[4], pc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = w + 32 * q;
+      pr[q] = (r > j && r < n) ? A[j * kLeafLd + r] : cmk(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int c = l + 32 * p;
+      pc[p] = (c > j && c < n) ? cscale(A[j * kLeafLd + c], inv) : cmk(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int r = w + 32 * q, c = l + 32 * p;
+        if (r > j && r <= c && c < n) a[q][p] = csub(a[q][p], cmul(cconj(pr[q]), pc[p]));
+      }
+    // row j + 1 is final: its owners store it
+    const int nr = j + 1;
+    if (w == (nr & 31)) {
+      const int q = nr >> 5;
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq)
+        if (qq == q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int c = l + 32 * p;
+            if (c >= nr && c < n) A[nr * kLeafLd + c] = a[qq][p];
+          }
     }
     __syncthreads();
   }
-  // T(k, c), k <= c: Td[c] on the diagonal, A[c][k] above it
-  auto tget = [&](int k, int c) -> c32 {
-    if (k > c) return cmk(0.0f, 0.0f);
-    return k == c ? Td[c] : A[c * kLeafLd + k];
-  };
-  const int nbk = (n + 31) / 32;
-  // diagonal blocks: warp w, lane = column within the block
-  if (warp < nbk) {
-    const int o = warp * 32, sw = min(32, n - o);
-    if (lane < sw) {
-      const int c = o + lane;
-      Td[c] = cmk(1.0f / A[c * kLeafLd + c].re, 0.0f);
-      for (int i = c - 1; i >= o; --i) {
-        c32 acc = cmul(A[i * kLeafLd + c], Td[c]);
-        for (int k = i + 1; k < c; ++k) acc = cadd(acc, cmul(A[i * kLeafLd + k], A[c * kLeafLd + k]));
-        A[c * kLeafLd + i] = cscale(acc, -1.0f / A[i * kLeafLd + i].re);
-      }
+  // ---- R = rows scaled by 1 / sqrt(pivot)
+  for (int j = tid; j < n; j += blockDim.x) {
+    float d = A[j * kLeafLd + j].re;
+    if (!(d > 0.0f) || !isfinite(d)) {
+      atomicOr(status, FM_DEVERR_PIVOT);
+      d = 1.0f;
     }
+    Rd[j] = sqrtf(d);
   }
   __syncthreads();
-  // off-diagonal blocks
-  const int a = tid >> 5, q = tid & 31;         // element (a, q) of a 32 x 32 block
-  for (int J = 1; J < nbk; ++J) {
-    const int oj = J * 32, swj = min(32, n - oj);
-    for (int I = J - 1; I >= 0; --I) {
-      const int oi = I * 32;
-      // Z = sum_{K = I+1 .. J} R_IK T_KJ
-      c32 z = cmk(0.0f, 0.0f);
-      if (q < swj) {
-        for (int k = oi + 32; k <= oj + q; ++k) z = cadd(z, cmul(A[(oi + a) * kLeafLd + k], tget(k, oj + q)));
-      }
-      Z[a * 33 + q] = z;
-      __syncthreads();
-      // T_IJ = -T_II Z (T_II upper: rows a .. 31)
-      c32 t = cmk(0.0f, 0.0f);
-      if (q < swj)
-        for (int p = a; p < 32; ++p) t = cadd(t, cmul(tget(oi + a, oi + p), Z[p * 33 + q]));
-      __syncthreads();
-      if (q < swj) A[(oj + q) * kLeafLd + (oi + a)] = cmk(-t.re, -t.im);
-      __syncthreads();
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int c = idx % n, r = idx / n;
+    if (r < c) A[r * kLeafLd + c] = cscale(A[r * kLeafLd + c], 1.0f / Rd[r]);
+    else if (r == c) A[r * kLeafLd + r] = cmk(Rd[r], 0.0f);
+  }
+  __syncthreads();
+  // ---- T = R^-1 by rows from the bottom; W in registers
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) a[q][p] = cmk((w + 32 * q == l + 32 * p) ? 1.0f : 0.0f, 0.0f);
+  if (tid == 0) Td[n - 1] = cmk(1.0f / Rd[n - 1], 0.0f);
+  __syncthreads();
+  for (int j = n - 1; j >= 1; --j) {
+    // T_jc for the owned columns c >= j, R_rj for the owned rows r < j
+    c32 t[4], rr[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int c = l + 32 * p;
+      t[p] = (c > j && c < n) ? A[c * kLeafLd + j] : (c == j ? Td[j] : cmk(0.0f, 0.0f));
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = w + 32 * q;
+      rr[q] = r < j ? A[r * kLeafLd + j] : cmk(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int r = w + 32 * q, c = l + 32 * p;
+        if (r < j && c >= j && c < n) a[q][p] = csub(a[q][p], cmul(rr[q], t[p]));
+      }
+    // row j - 1 of W is final: T_{j-1, c} = W_{j-1, c} / R_{j-1, j-1}
+    const int nr = j - 1;
+    if (w == (nr & 31)) {
+      const int q = nr >> 5;
+      const float s = 1.0f / Rd[nr];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq)
+        if (qq == q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int c = l + 32 * p;
+            if (c == nr) Td[nr] = cscale(a[qq][p], s);
+            else if (c > nr && c < n) A[c * kLeafLd + nr] = cscale(a[qq][p], s);
+          }
+    }
+    __syncthreads();
   }
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int r = idx % n, c = idx / n;

@@ -506,12 +506,11 @@ fm_status step_f64(fm_state* s) {
   // 1. propagation, all trajectories in one product P [U_0 | U_1 | ...], or as stencils
   s->timer.begin(FM_PH_PROPAGATE);
   if (s->prop_mode == FM_PROP_BANDED) {
-    const int nch = band_chunks(L, N, B);
     CKL(band_propagate(s->st, 0, s->U, s->U2, L, N, B, s->Lx, s->Ly, 0, s->band_tx, s->band_ox, s->ntap_x, nullptr,
-                       nch), 1);
+                       band_chunks(s->Lx, s->Ly, N, B, 0, 0)), 1);
     if (s->Ly > 1) {
       CKL(band_propagate(s->st, 0, s->U2, s->U, L, N, B, s->Lx, s->Ly, 1, s->band_ty, s->band_oy, s->ntap_y,
-                         nullptr, nch), 1);
+                         nullptr, band_chunks(s->Lx, s->Ly, N, B, 1, 0)), 1);
     } else {
       std::swap(s->U, s->U2);
     }
@@ -599,7 +598,7 @@ fm_status step_poisson(fm_state* s) {
   a.xbuf = s->xbuf_d; a.vbuf = s->vbuf_d;
   a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
   a.dev_status = s->status_d;
-  const int nch = band_chunks(L, N, B);
+  const int nchx = band_chunks(s->Lx, s->Ly, N, B, 0, a.layout), nchy = band_chunks(s->Lx, s->Ly, N, B, 1, a.layout);
   std::vector<z64> taps;
   std::vector<int> list, cnt(B);
   std::vector<double> ul;
@@ -637,11 +636,11 @@ fm_status step_poisson(fm_state* s) {
       void* oth = fp64 ? (void*)s->U2 : (void*)s->V2;
       const z64* tp = s->pois_taps + (size_t)j * B * tstride;
       s->timer.begin(FM_PH_PROPAGATE);
-      CKL(band_propagate(s->st, a.layout, cur, oth, L, N, B, s->Lx, s->Ly, 0, tp, s->pois_off, ntx, nullptr, nch,
+      CKL(band_propagate(s->st, a.layout, cur, oth, L, N, B, s->Lx, s->Ly, 0, tp, s->pois_off, ntx, nullptr, nchx,
                          tstride), 1);
       if (s->Ly > 1) {
         CKL(band_propagate(s->st, a.layout, oth, cur, L, N, B, s->Lx, s->Ly, 1, tp + ntx, s->pois_off + kBandMaxTaps,
-                           nty, nullptr, nch, tstride), 1);
+                           nty, nullptr, nchy, tstride), 1);
       } else if (fp64) {
         std::swap(s->U, s->U2);
       } else {

@@ -155,7 +155,9 @@ inline bool hermitian_entropy_lower_only(int m) { return m > 256; }
 
 // ---- structured propagation: stencils of the circulant propagator (banded.cu)
 constexpr int kBandMaxTaps = 41;   // half-width <= 20
-int band_chunks(int L, int N, int B);
+// column chunks (blockIdx.y) of a stencil pass along dir, and of a thread-per-site pass
+int band_chunks(int Lx, int Ly, int N, int B, int dir, int layout);
+int site_chunks(int L, int N, int B);
 // layout 0: complex128 U (L x N per trajectory); 1: float V (2L x N).  dir 0 along x,
 // 1 along y.  partial (may be NULL): row sums of |out|^2 per column chunk, nch chunks.
 // off: consecutive offsets; tap_stride > 0: trajectory b uses taps + b tap_stride.

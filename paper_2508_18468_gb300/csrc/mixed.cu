@@ -121,116 +121,161 @@ FM_DEVFN void split16_f(float v, __half& h, __half& l) {
 // mode 1: Z = -F, F = strict upper part of G plus half of (diag G - 1) (the
 //         diagonal taken from the float64 Gram diagonal): the first-order
 //         inverse factor of G = 1 + E, (1 + F)^dag (1 + F) = G + O(E^2).
-__global__ void build_ttilde_kernel(const c32* __restrict__ Z, const double* __restrict__ diag, int mode, int N,
-                                    int B, __half* Th, __half* Tl) {
-  const int64_t N2 = 2 * (int64_t)N;
-  const int64_t tot = (int64_t)B * N2 * N2;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = idx % N2, row = idx / N2;
-    const int64_t b = row / N2, c = row % N2;
-    const int64_t n = c >> 1, l = j >> 1;
-    const int sp = (int)(c & 1), s = (int)(j & 1);
-    float v = 0.0f;
-    if (l <= n) {
-      c32 z = Z[b * (int64_t)N * N + l + n * (int64_t)N];
-      if (mode == 0) {
-        if (l == n) z.re -= 1.0f;
-      } else if (l == n) {
-        z.re = (float)(-(diag[b * N + n] - 1.0) * 0.5);
-        z.im = 0.0f;
-      } else {
-        z.re = -z.re;
-        z.im = -z.im;
+// One block per row (b, c) of Z~ (2N halves), eight K positions per thread and
+// pass, written as 16-byte stores of each plane.
+__global__ void __launch_bounds__(256) build_ttilde_kernel(const c32* __restrict__ Z, const double* __restrict__ diag,
+                                                           int mode, int N, __half* Th, __half* Tl) {
+  const int N2 = 2 * N;
+  const int64_t row = blockIdx.x;
+  const int64_t b = row / N2;
+  const int c = (int)(row - b * N2);
+  const int n = c >> 1, sp = c & 1;
+  const c32* Zc = Z + b * (int64_t)N * N + (int64_t)n * N;   // column n
+  __half* th = Th + row * N2;
+  __half* tl = Tl + row * N2;
+  for (int j0 = threadIdx.x * 8; j0 < N2; j0 += blockDim.x * 8) {
+    __align__(16) __half hh[8];
+    __align__(16) __half ll[8];
+    const int l0 = j0 >> 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int l = l0 + q;
+      float re = 0.0f, im = 0.0f;
+      if (l <= n) {
+        c32 z = Zc[l];
+        if (mode == 0) {
+          if (l == n) z.re -= 1.0f;
+        } else if (l == n) {
+          z.re = (float)(-(diag[b * N + n] - 1.0) * 0.5);
+          z.im = 0.0f;
+        } else {
+          z.re = -z.re;
+          z.im = -z.im;
+        }
+        re = z.re;
+        im = z.im;
       }
-      v = (s == sp) ? z.re : (s == 0 ? z.im : -z.im);
+      split16_f(sp == 0 ? re : im, hh[2 * q], ll[2 * q]);          // K position 2l   (s = 0)
+      split16_f(sp == 1 ? re : -im, hh[2 * q + 1], ll[2 * q + 1]);  // K position 2l+1 (s = 1)
     }
-    __half h, lo;
-    split16_f(v, h, lo);
-    Th[idx] = h;
-    Tl[idx] = lo;
+    *(uint4*)(th + j0) = *(const uint4*)hh;
+    *(uint4*)(tl + j0) = *(const uint4*)ll;
   }
 }
 
 // Planes of the real embedding of op(X) (m x k complex; op: 0 = none, 2 = conjugate
-// transpose): A (2m x 2k, row-major) = [[Re, -Im], [Im, Re]].
-__global__ void embed_a_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op, int m, int k,
-                               __half* Ah, __half* Al) {
-  const int64_t b = blockIdx.y;
-  const int64_t tot = 4 * (int64_t)m * k;
+// transpose): A (2m x 2k, row-major) = [[Re, -Im], [Im, Re]].  32 x 32 tiles of
+// op(X) staged in shared memory so both the read and the writes are coalesced;
+// m and k multiples of 32.  Grid (m / 32, k / 32, B), block (32, 8).
+__global__ void __launch_bounds__(256) embed_a_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op,
+                                                      int m, int k, __half* Ah, __half* Al) {
+  __shared__ c32 t[32][33];                       // t[row][col] of op(X)
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int64_t b = blockIdx.z;
+  const c32* Xb = X + b * sX;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    if (op == 2) {
+      c32 x = Xb[(c0 + tx) + (int64_t)(r0 + q) * ldx];
+      x.im = -x.im;
+      t[q][tx] = x;
+    } else {
+      t[tx][q] = Xb[(r0 + tx) + (int64_t)(c0 + q) * ldx];
+    }
+  }
+  __syncthreads();
   const int64_t k2 = 2 * (int64_t)k;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / k2, c = idx % k2;
-    const int64_t rr = r % m, cc = c % k;
-    const bool rb = r >= m, cb = c >= k;
-    c32 x = (op == 2) ? X[b * sX + cc + rr * ldx] : X[b * sX + rr + cc * ldx];
-    if (op == 2) x.im = -x.im;
-    const float v = (!rb && !cb) ? x.re : (!rb && cb) ? -x.im : (rb && !cb) ? x.im : x.re;
+  const int64_t base = b * 4 * (int64_t)m * k;
+  for (int q = ty; q < 32; q += 8) {
+    const c32 x = t[q][tx];
+    const int64_t top = base + (int64_t)(r0 + q) * k2 + c0 + tx;
+    const int64_t bot = top + (int64_t)m * k2;
     __half h, lo;
-    split16_f(v, h, lo);
-    Ah[b * tot + idx] = h;
-    Al[b * tot + idx] = lo;
+    split16_f(x.re, h, lo);
+    Ah[top] = h; Al[top] = lo; Ah[bot + k] = h; Al[bot + k] = lo;
+    split16_f(-x.im, h, lo);
+    Ah[top + k] = h; Al[top + k] = lo;
+    split16_f(x.im, h, lo);
+    Ah[bot] = h; Al[bot] = lo;
   }
 }
 
 // Planes of B (n x 2k, row-major): row j = [Re op(Y)[:, j], Im op(Y)[:, j]].
-__global__ void embed_b_kernel(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int op, int k, int n,
-                               __half* Bh, __half* Bl) {
-  const int64_t b = blockIdx.y;
-  const int64_t tot = 2 * (int64_t)k * n;
-  const int64_t k2 = 2 * (int64_t)k;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = idx / k2, c = idx % k2;
-    const int64_t kk = c % k;
-    c32 y = (op == 2) ? Y[b * sY + j + kk * ldy] : Y[b * sY + kk + j * ldy];
-    if (op == 2) y.im = -y.im;
-    const float v = (c >= k) ? y.im : y.re;
-    __half h, lo;
-    split16_f(v, h, lo);
-    Bh[b * tot + idx] = h;
-    Bl[b * tot + idx] = lo;
-  }
-}
-
-// C = alpha (D_re + i D_im) + beta C, D = [D_re; D_im] (2m x n, column-major, per trajectory)
-__global__ void combine_kernel(const float* __restrict__ D, int m, int n, float alpha, float beta, c32* C,
-                               int64_t ldc, int64_t sC) {
-  const int64_t b = blockIdx.y;
-  const int64_t tot = (int64_t)m * n;
-  const float* Db = D + b * 2 * tot;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx % m, j = idx / m;
-    const float re = Db[r + j * 2 * (int64_t)m], im = Db[m + r + j * 2 * (int64_t)m];
-    c32* c = C + b * sC + r + j * ldc;
-    c32 out = cmk(alpha * re, alpha * im);
-    if (beta != 0.0f) { out.re += beta * c->re; out.im += beta * c->im; }
-    *c = out;
-  }
-}
-
-// Urm[(b L + i) 2N + c] = Vplane_b[(c&1) L + i + (c>>1) 2L]  (both planes)
-__global__ void transpose_planes_kernel(const __half* __restrict__ Vh, const __half* __restrict__ Vl, int L, int N,
-                                        __half* Uh, __half* Ul) {
-  __shared__ __half th[32][34];
-  __shared__ __half tl[32][34];
-  const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+// Grid (k / 32, n / 32, B), block (32, 8); k and n multiples of 32.
+__global__ void __launch_bounds__(256) embed_b_kernel(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int op,
+                                                      int k, int n, __half* Bh, __half* Bl) {
+  __shared__ c32 t[32][33];                       // t[j][kk] = op(Y)[kk][j]
+  const int k0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   const int64_t b = blockIdx.z;
-  const int64_t vb = b * 2 * (int64_t)L * N;
-  for (int cc = threadIdx.y; cc < 32; cc += 8) {
-    const int c = c0 + cc, i = i0 + threadIdx.x;
-    const int64_t o = vb + (int64_t)(c & 1) * L + i + (int64_t)(c >> 1) * 2 * L;
-    th[cc][threadIdx.x] = Vh[o];
-    tl[cc][threadIdx.x] = Vl[o];
+  const c32* Yb = Y + b * sY;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    if (op == 2) {
+      c32 y = Yb[(j0 + tx) + (int64_t)(k0 + q) * ldy];
+      y.im = -y.im;
+      t[tx][q] = y;
+    } else {
+      t[q][tx] = Yb[(k0 + tx) + (int64_t)(j0 + q) * ldy];
+    }
   }
   __syncthreads();
-  for (int ii = threadIdx.y; ii < 32; ii += 8) {
-    const int i = i0 + ii, c = c0 + threadIdx.x;
-    const int64_t o = (b * L + i) * 2 * (int64_t)N + c;
-    Uh[o] = th[threadIdx.x][ii];
-    Ul[o] = tl[threadIdx.x][ii];
+  const int64_t k2 = 2 * (int64_t)k;
+  const int64_t base = b * 2 * (int64_t)k * n;
+  for (int q = ty; q < 32; q += 8) {
+    const c32 y = t[q][tx];
+    const int64_t o = base + (int64_t)(j0 + q) * k2 + k0 + tx;
+    __half h, lo;
+    split16_f(y.re, h, lo);
+    Bh[o] = h; Bl[o] = lo;
+    split16_f(y.im, h, lo);
+    Bh[o + k] = h; Bl[o + k] = lo;
+  }
+}
+
+// C = alpha (D_re + i D_im) + beta C, D = [D_re; D_im] (2m x n, column-major, per
+// trajectory).  Grid (ceil(m / 256), n, B).
+__global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ D, int m, int n, float alpha,
+                                                      float beta, c32* C, int64_t ldc, int64_t sC) {
+  const int64_t b = blockIdx.z;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (r >= m) return;
+  const float* Dj = D + b * 2 * (int64_t)m * n + (int64_t)j * 2 * m;
+  c32* c = C + b * sC + r + (int64_t)j * ldc;
+  c32 out = cmk(alpha * Dj[r], alpha * Dj[m + r]);
+  if (beta != 0.0f) {
+    const c32 old = *c;
+    out.re += beta * old.re;
+    out.im += beta * old.im;
+  }
+  *c = out;
+}
+
+// Urm[(b L + i) 2N + c] = plane_b[i + L c] (V_b read as the L x 2N column-major
+// matrix U~), both planes.  64 x 64 tiles, half2 reads along i and writes along c.
+// Grid (L / 64, 2N / 64, B), block (32, 8).
+__global__ void __launch_bounds__(256) transpose_planes_kernel(const __half* __restrict__ Vh,
+                                                               const __half* __restrict__ Vl, int L, int N,
+                                                               __half* Uh, __half* Ul) {
+  __shared__ __half2 sh[64][33];                  // [c][i pair]
+  __shared__ __half2 sl[64][33];
+  const int i0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  const int64_t b = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t vb = b * 2 * (int64_t)L * N;
+  for (int cc = ty; cc < 64; cc += 8) {
+    const int64_t o = vb + (int64_t)(c0 + cc) * L + i0 + 2 * tx;
+    sh[cc][tx] = *(const __half2*)(Vh + o);
+    sl[cc][tx] = *(const __half2*)(Vl + o);
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 64; ii += 8) {
+    const int64_t o = (b * L + i0 + ii) * 2 * (int64_t)N + c0 + 2 * tx;
+    const __half2 h0 = sh[2 * tx][ii >> 1], h1 = sh[2 * tx + 1][ii >> 1];
+    const __half2 l0 = sl[2 * tx][ii >> 1], l1 = sl[2 * tx + 1][ii >> 1];
+    *(__half2*)(Uh + o) = (ii & 1) ? __halves2half2(__high2half(h0), __high2half(h1))
+                                   : __halves2half2(__low2half(h0), __low2half(h1));
+    *(__half2*)(Ul + o) = (ii & 1) ? __halves2half2(__high2half(l0), __high2half(l1))
+                                   : __halves2half2(__low2half(l0), __low2half(l1));
   }
 }
 
@@ -456,11 +501,13 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
              int64_t ldy, int64_t sY, int m, int n, int k, float alpha, float beta, c32* C, int64_t ldc,
              int64_t sC) {
   const int B = c->B;
-  const unsigned gx = (unsigned)std::min<int64_t>(FM_CEIL_DIV(4 * (int64_t)m * k, 256), 2048);
-  embed_a_kernel<<<dim3(gx, B), 256, 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+  if (m % 32 || k % 32 || n % 128) {
+    c->err = "cgemm sizes";
+    return FM_EINVAL;
+  }
+  embed_a_kernel<<<dim3(m / 32, k / 32, B), dim3(32, 8), 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
   MCK(cudaGetLastError());
-  const unsigned gy = (unsigned)std::min<int64_t>(FM_CEIL_DIV(2 * (int64_t)k * n, 256), 2048);
-  embed_b_kernel<<<dim3(gy, B), 256, 0, c->st>>>(Y, ldy, sY, opY, k, n, h->cb_h, h->cb_l);
+  embed_b_kernel<<<dim3(k / 32, n / 32, B), dim3(32, 8), 0, c->st>>>(Y, ldy, sY, opY, k, n, h->cb_h, h->cb_l);
   MCK(cudaGetLastError());
   CUtensorMap ah, al, bh, bl;
   const uint64_t K2 = 2 * (uint64_t)k;
@@ -484,8 +531,7 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
   p.ld_out = 2 * (int64_t)m;
   p.out_batch_stride = 2 * (int64_t)m * n;
   MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, tc::sm_count()));
-  const unsigned gc = (unsigned)std::min<int64_t>(FM_CEIL_DIV((int64_t)m * n, 256), 2048);
-  combine_kernel<<<dim3(gc, B), 256, 0, c->st>>>(h->cd, m, n, alpha, beta, C, ldc, sC);
+  combine_kernel<<<dim3(FM_CEIL_DIV(m, 256), n, B), 256, 0, c->st>>>(h->cd, m, n, alpha, beta, C, ldc, sC);
   MCK(cudaGetLastError());
   return FM_OK;
 }
@@ -549,10 +595,10 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
     int r = chol_inv_rec(h, c, 0, N);
     if (r) return r;
   }
-  build_ttilde_kernel<<<152 * 8, 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag, first ? 0 : 1, N, B, c->Th,
-                                                  c->Tl);
+  build_ttilde_kernel<<<(unsigned)(2 * (int64_t)B * N), 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag,
+                                                                          first ? 0 : 1, N, c->Th, c->Tl);
   MCK(cudaGetLastError());
-  transpose_planes_kernel<<<dim3(L / 32, 2 * N / 32, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
+  transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
                                                                                   h->urm_l);
   MCK(cudaGetLastError());
   c->timer->end(FM_PH_CHOLESKY);
@@ -638,7 +684,7 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   // U~ planes (L x 2N per trajectory, K-major) of the propagated state (the
   // propagation writes the float state only, so its planes are made here)
   MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
-  transpose_planes_kernel<<<dim3(L / 32, 2 * N / 32, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
+  transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
                                                                                   h->urm_l);
   MCK(cudaGetLastError());
   MCK(pmb_setup(c->st, h->pb_list, h->pb_count, L, B, kmax, h->pb_pos));
@@ -715,13 +761,14 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
   c->timer->begin(FM_PH_PROPAGATE);
   if (c->prop_banded) {
     // stencils along x (and y): V -> V2 (-> V); the last pass sums |U|^2 per row
-    nchunks = band_chunks(L, N, B);
     const bool torus = c->Ly > 1;
+    const int nx = band_chunks(c->Lx, c->Ly, N, B, 0, 1), ny = band_chunks(c->Lx, c->Ly, N, B, 1, 1);
+    nchunks = torus ? ny : nx;                     // chunks of the pass that sums |U|^2 per row
     MCK(band_propagate(c->st, 1, c->V, c->V2, L, N, B, c->Lx, c->Ly, 0, c->band_tx, c->band_ox, c->ntap_x,
-                       torus ? nullptr : c->part, nchunks));
+                       torus ? nullptr : c->part, nx));
     if (torus) {
       MCK(band_propagate(c->st, 1, c->V2, c->V, L, N, B, c->Lx, c->Ly, 1, c->band_ty, c->band_oy, c->ntap_y,
-                         c->part, nchunks));
+                         c->part, ny));
     } else {
       std::swap(c->V, c->V2);
     }

@@ -1,18 +1,29 @@
-"""Summarise an ncu launch list (``--metrics gpu__time_duration.sum --csv``) per kernel.
+"""Profiling helpers: workloads to run under ncu, and a launch-list summary.
 
-Usage: python -m paper_2508_18468_gb300.profiling <launches.csv>
-Prints launches, total time and share of every kernel, largest first.
+    python -m paper_2508_18468_gb300.profiling steps L B K [protocol] [propagation]
+        L-site ring (or Lx x Ly torus written "LxxLy"), B trajectories, mixed precision:
+        three warm-up steps, then K steps inside the NVTX range "steps" (capture them with
+        ncu --nvtx --nvtx-include "steps/").  protocol: homodyne (default), projective,
+        poisson, rk4; propagation: dense (default) or banded.  Prints one JSON line.
+    python -m paper_2508_18468_gb300.profiling entropy L
+        one step of a single homodyne trajectory, then the half-chain entropy inside the
+        NVTX range "entropy".
+    python -m paper_2508_18468_gb300.profiling summary <launches.csv>
+        launches, total time and share of every kernel of an ncu launch list
+        (--metrics gpu__time_duration.sum --csv), largest first.
 """
 import collections
 import csv
+import json
 import re
 import sys
+import time
 
 SCALE = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3,
          "second": 1e3}
 
 
-def main(path):
+def summary(path):
     rows = list(csv.reader(open(path)))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[hi]
@@ -31,5 +42,63 @@ def main(path):
         print("%8d %12.2f %6.1f%%  %s" % (cnt[k], v, 100 * v / T, k))
 
 
+def _lattice(spec):
+    if "x" in spec:
+        a, b = spec.split("x")
+        return int(a), int(b)
+    return int(spec), 1
+
+
+def steps(spec, B, K, protocol="homodyne", propagation="dense"):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from . import fm, workloads
+    Lx, Ly = _lattice(spec)
+    prot = {"homodyne": fm.FM_HOMODYNE, "projective": fm.FM_PROJECTIVE, "poisson": fm.FM_PROJECTIVE_POISSON,
+            "rk4": fm.FM_HOMODYNE_RK4}[protocol]
+    g = fm.Trajectories(fm.make_params(Lx, Ly, batch=B, protocol=prot, precision=fm.FM_MIXED, gamma=1.0,
+                                       seed=workloads.seed_of("ring16384_homodyne")))
+    g.set_gammas(([0.3, 0.3, 1.0, 1.0] * B)[:B])
+    if propagation == "banded":
+        g.set_propagation(fm.FM_PROP_BANDED)
+    g.step(3)
+    torch.cuda.synchronize()
+    l0 = g.kernel_launches
+    torch.cuda.nvtx.range_push("steps")
+    t0 = time.perf_counter()
+    g.step(K)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"Lx": Lx, "Ly": Ly, "B": B, "steps": K, "protocol": protocol, "propagation": propagation,
+                      "s_per_step": t / K, "launches_per_step": (g.kernel_launches - l0) / K}))
+
+
+def entropy(L):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from . import fm
+    g = fm.Trajectories(fm.make_params(L, batch=1, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED, gamma=1.0,
+                                       seed=1))
+    g.step(1)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("entropy")
+    t0 = time.perf_counter()
+    S = g.entropy(list(range(L // 2)))
+    t = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"L": L, "S": S, "entropy_s": t}))
+
+
 if __name__ == "__main__":
-    main(sys.argv[1])
+    cmd = sys.argv[1]
+    if cmd == "steps":
+        steps(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), *sys.argv[5:7])
+    elif cmd == "entropy":
+        entropy(int(sys.argv[2]))
+    elif cmd == "summary":
+        summary(sys.argv[2])
+    else:
+        summary(cmd)

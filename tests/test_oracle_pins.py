@@ -375,6 +375,23 @@ def test_continuous_time_projective_matches_brute_force(Lx, Ly, gamma, seed):
     assert np.max(np.abs(observables.correlation(out["U"]) - np.conj(D))) < 1e-12
 
 
+def test_continuous_time_forced_replay():
+    """Forcing every outcome to the oracle's own gives the same run; forcing one flip
+    keeps every event's site and draws (they do not depend on the state) and logs the
+    forced outcome, also when the run stops right after that event's step."""
+    prm = Params(Lx=12, gamma=2.0, protocol=trajectory.PROJECTIVE_POISSON, seed=21, traj_id=1)
+    a = trajectory.run(prm, 8)
+    same = trajectory.run(prm, 8, forced={e: ev[4] for e, ev in enumerate(a["events"])})
+    assert np.array_equal(a["U"], same["U"]) and a["events"] == same["events"]
+    k = next(e for e, ev in enumerate(a["events"]) if 1e-3 < ev[3] < 1 - 1e-3)
+    b = trajectory.run(prm, 8, forced={k: 1 - a["events"][k][4]})
+    assert [ev[:3] for ev in b["events"]] == [ev[:3] for ev in a["events"]]
+    assert b["events"][k][4] == 1 - a["events"][k][4]
+    cut = a["events"][k][0]
+    pre = trajectory.run(prm, cut + 1, forced={k: 1 - a["events"][k][4]})
+    assert pre["events"][k][4] == b["events"][k][4]
+
+
 def test_continuous_time_event_statistics():
     """Waiting times exponential with mean 1 / (gamma N), sites uniform over the lattice."""
     L, N, gamma = 40, 20, 1.5
