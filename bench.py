@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--propagation", choices=["dense", "banded"], default="dense",
                     help="dense L x L GEMM (the method as defined) or stencils of the circulant propagator")
+    ap.add_argument("--ee-method", choices=["sketch", "full"], default="sketch",
+                    help="entropy method of the in-window entropies (mixed precision): the cross-block "
+                         "sketch (falls back to the full method when it does not converge) or the full "
+                         "eigen-decomposition of C_A")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -231,6 +235,9 @@ def run_ours(args, world, rank, local):
     g.set_gammas(gam)
     if args.propagation == "banded":
         g.set_propagation(fm.FM_PROP_BANDED)
+    ee_method = args.ee_method if precision == fm.FM_MIXED else "full"
+    if ee_method == "sketch":
+        g.set_entropy_method(fm.FM_EE_SKETCH)
     ee_sites = workloads.half_chain(L)
     ee_every = wl["ee_every"]
 
@@ -344,6 +351,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": args.workload, "L": L, "N": N, "batch_per_gpu": B, "gammas": gam,
                    "protocol": wl["protocol"], "dt": 0.05, "ee_every": ee_every,
                    "ee_sites": "half chain (%d sites), FP64, started every %d steps and overlapped" % (L // 2, ee_every),
+                   "ee_method": ee_method,
                    "precision": args.precision, "propagation": args.propagation,
                    "l2": "inputs larger than L2 (state %.1f GB, propagator %.1f GB per GPU)" % (
                        B * 2 * L * N * 4 / 1e9, 4 * L * L * 4 / 1e9),

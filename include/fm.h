@@ -187,6 +187,28 @@ fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t
 /* Block until the entropy of `ticket` is ready and return it. */
 fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out);
 
+/* How fm_entropy, fm_entropy_async and fm_mutual_info compute S_A.
+ * FM_EE_FULL (default): the eigenvalues lambda of C_A as above.
+ * FM_EE_SKETCH (mixed precision only): for orthonormal orbitals C is a
+ * projector, so lambda (1 - lambda) = sigma^2 with sigma the singular values of
+ * the cross block C_AB = U_A U_B^dag (B the complement of A), and the terms of
+ * S_A (Sec. II) depend on sigma^2 only.  A randomized subspace iteration on C_AB
+ * (complex64 products with U, float64 orthonormal bases, rank r = 128, 256,
+ * ... up to min(1024, N/2)) finds the sigma above the noise, whose squares are
+ * the FP64 eigenvalues of an r x r Rayleigh-Ritz matrix formed with exact
+ * products.  The rank grows until the (r/8)-th smallest sigma^2 is below 1e-9;
+ * if it never is, the full method runs instead.  Subsystems or complements
+ * below 512 sites always take the full method.  The state keeps a snapshot of
+ * U for this (asynchronous tickets keep theirs in their C_A buffer).  FM_EINVAL
+ * for an FP64 state or an unknown method.  Synchronises. */
+enum { FM_EE_FULL = 0, FM_EE_SKETCH = 1 };
+fm_status fm_set_entropy_method(fm_state* s, int32_t method);
+
+/* The last synchronous FM_EE_SKETCH entropy: the rank it settled on (0 if the
+ * full method ran), its convergence value (the (r/8)-th smallest sigma^2) and
+ * whether it fell back to the full method.  Any pointer may be NULL. */
+fm_status fm_entropy_sketch_info(fm_state* s, int32_t* rank, double* check, int32_t* fell_back);
+
 /* I = S_A + S_B - S_{A u B} for trajectory b; A and B disjoint host arrays. */
 fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA,
                          const int32_t* B, int32_t nB, double* I_out);

@@ -112,24 +112,27 @@ __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restri
       d = 1.0f;
     }
     const float inv = 1.0f / d;
-    c32 pr[4], pc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = w + 32 * q;
-      pr[q] = (r > j && r < n) ? A[j * kLeafLd + r] : cmk(0.0f, 0.0f);
-    }
+    c32 pc[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       const int c = l + 32 * p;
       pc[p] = (c > j && c < n) ? cscale(A[j * kLeafLd + c], inv) : cmk(0.0f, 0.0f);
     }
+    // rows r = w + 32 q and column groups p are warp-uniform: skip the finished ones
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q) {
+      const int r = w + 32 * q;
+      if (r > j && r < n) {
+        const c32 prc = cconj(A[j * kLeafLd + r]);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int r = w + 32 * q, c = l + 32 * p;
-        if (r > j && r <= c && c < n) a[q][p] = csub(a[q][p], cmul(cconj(pr[q]), pc[p]));
+        for (int p = 0; p < 4; ++p) {
+          if (32 * p + 31 >= r) {
+            const int c = l + 32 * p;
+            if (c >= r && c < n) a[q][p] = csub(a[q][p], cmul(prc, pc[p]));
+          }
+        }
       }
+    }
     // row j + 1 is final: its owners store it
     const int nr = j + 1;
     if (w == (nr & 31)) {
@@ -169,8 +172,8 @@ __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restri
   if (tid == 0) Td[n - 1] = cmk(1.0f / Rd[n - 1], 0.0f);
   __syncthreads();
   for (int j = n - 1; j >= 1; --j) {
-    // T_jc for the owned columns c >= j, R_rj for the owned rows r < j
-    c32 t[4], rr[4];
+    // T_jc for the owned columns c >= j, R_rj for the owned rows r < j (warp-uniform rows)
+    c32 t[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       const int c = l + 32 * p;
@@ -179,15 +182,17 @@ __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restri
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = w + 32 * q;
-      rr[q] = r < j ? A[r * kLeafLd + j] : cmk(0.0f, 0.0f);
-    }
+      if (r < j) {
+        const c32 rr = A[r * kLeafLd + j];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int r = w + 32 * q, c = l + 32 * p;
-        if (r < j && c >= j && c < n) a[q][p] = csub(a[q][p], cmul(rr[q], t[p]));
+        for (int p = 0; p < 4; ++p) {
+          if (32 * p + 31 >= j) {
+            const int c = l + 32 * p;
+            if (c >= j && c < n) a[q][p] = csub(a[q][p], cmul(rr, t[p]));
+          }
+        }
       }
+    }
     // row j - 1 of W is final: T_{j-1, c} = W_{j-1, c} / R_{j-1, j-1}
     const int nr = j - 1;
     if (w == (nr & 31)) {

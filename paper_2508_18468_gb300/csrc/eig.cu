@@ -317,12 +317,20 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
   lam[q] = 0.5 * (lo + hi);
 }
 
-// S = -sum f(clamp(lambda, 0, 1)), one CTA, fixed order
-__global__ void __launch_bounds__(1024) entropy_sum_kernel(const double* lam, int m, double* S) {
+// S = -sum f(clamp(lambda, 0, 1)), one CTA, fixed order.  cross != 0: the inputs are
+// sigma^2 = lambda (1 - lambda) in [0, 1/4], lambda = 2 sigma^2 / (1 + sqrt(1 - 4 sigma^2))
+// (the root below 1/2; f is symmetric, so the other root gives the same term)
+__global__ void __launch_bounds__(1024) entropy_sum_kernel(const double* lam, int m, double* S, int cross) {
   __shared__ double red[33];
   double s = 0.0;
   for (int q = threadIdx.x; q < m; q += blockDim.x) {
-    const double x = fmin(fmax(lam[q], 0.0), 1.0);
+    double x;
+    if (cross) {
+      const double y = fmin(fmax(lam[q], 0.0), 0.25);
+      x = 2.0 * y / (1.0 + sqrt(1.0 - 4.0 * y));
+    } else {
+      x = fmin(fmax(lam[q], 0.0), 1.0);
+    }
     if (x > 0.0 && x < 1.0) s += x * log(x) + (1.0 - x) * log1p(-x);
   }
   const double tot = bsum(s, red);
@@ -334,7 +342,7 @@ __global__ void one_by_one_kernel(const z64* M, double* d) { d[0] = M[0].re; }
 
 
 cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, z64* pbuf, double* partial_unused,
-                              double* d, double* e, double* lam, double* S, int* nlaunch) {
+                              double* d, double* e, double* lam, double* S, int* nlaunch, int cross) {
   (void)partial_unused;
   int launches = 0;
   if (m <= 0) return cudaSuccess;
@@ -377,7 +385,7 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, 
     ++launches;
   }
   bisect_kernel<<<FM_CEIL_DIV(m, 64), 64, 0, st>>>(d, e, m, lam);
-  entropy_sum_kernel<<<1, 1024, 0, st>>>(lam, m, S);
+  entropy_sum_kernel<<<1, 1024, 0, st>>>(lam, m, S, cross);
   launches += 2;
   if (nlaunch) *nlaunch += launches;
   return cudaGetLastError();

@@ -28,6 +28,13 @@ const int kMaxChunks = 128;    // occupation partial sums
 const int kAsyncSlots = 64;    // outstanding asynchronous entropies
 const int kEaRing = 4;         // C_A buffers of the asynchronous entropies
 const int kPoisSlots = 128;    // continuous-time projective: propagation slots per upload
+// entropy sketch (FM_EE_SKETCH): first rank, power iterations, convergence bound on the
+// (r/8)-th smallest Ritz value sigma^2, smallest subsystem (and complement) it is used for
+const int kSketchR0 = 128;
+const int kSketchQ = 1;
+const double kSketchTol = 1e-9;
+const int kSketchMinSites = 4 * kSketchR0;
+int sketch_rmax(int64_t N) { return N >= kSketchMinSites ? (int)std::min<int64_t>(1024, (N / 2) / 32 * 32) : 0; }
 
 // continuous-time projective scratch: taps (slot, trajectory, x then y), event
 // sites and draws (trajectory, slot), event counts, then the tap offsets
@@ -55,6 +62,7 @@ struct Plan {
   size_t band;                                          // stencil taps and offsets (x, y)
   size_t rk4;                                           // Runge-Kutta stage buffer
   size_t pois;                                          // continuous-time projective: taps, offsets
+  size_t sk_snap, sk_sync, sk_async, sk_res;            // entropy sketch (mixed)
   size_t mixed_extra;                                   // scratch owned by the mixed path
   size_t take(size_t bytes) { size_t o = total; total += align256(bytes); return o; }
 };
@@ -149,6 +157,13 @@ Plan make_plan(const fm_params& p) {
     pl.mixed_extra = pl.take(mixed_scratch_bytes(p.Lx, p.Ly, p.batch, p.protocol));
     pl.xg = pl.take(std::max(exact_gram_scratch_bytes((int)L, (int)N), projector_scratch_bytes((int)N)));
     pl.gfull = pl.take(N * N * 16);
+    const int rmax = sketch_rmax(N);
+    if (rmax) {
+      pl.sk_snap = pl.take(L * N * 8);
+      pl.sk_sync = pl.take(sketch_scratch_bytes((int)L, (int)N, rmax));
+      pl.sk_async = pl.take(sketch_scratch_bytes((int)L, (int)N, rmax));
+    }
+    pl.sk_res = pl.take(64);
   }
   return pl;
 }
@@ -225,8 +240,24 @@ struct fm_state {
   int* pois_cnt;               // events of each trajectory in the chunk
   int* pois_off;               // x offsets, then y offsets (kBandMaxTaps each)
   int pois_wx, pois_wy;        // half-widths; -1: every offset of that direction
+  // entropy method (fm_set_entropy_method) and the sketch's buffers: a snapshot of U
+  // with A's rows first for the synchronous path (asynchronous tickets keep theirs in
+  // their C_A ring buffer), one scratch set per path, and device results
+  int ee_method;
+  int sk_rmax;
+  c32* sk_snap;
+  SketchScratch sk_sync, sk_async;
+  double* sk_res;             // [0] S, [1] check (synchronous); [2] check (library thread)
+  int sk_last_rank;
+  double sk_last_chk;
+  int sk_last_fallback;
+  // aux, gfull and xg are shared by the caller's thread (the full method) and the
+  // library thread (the full method after a sketch that did not converge): a user
+  // holds ee_buf_mu while it enqueues and orders its stream after ee_buf_ev
+  std::mutex ee_buf_mu;
+  cudaEvent_t ee_buf_ev;
   int64_t ea_next;            // next ticket
-  struct EaJob { int64_t t; int slot, ring, m; };
+  struct EaJob { int64_t t; int slot, ring, m, sketch_nA; };   // sketch_nA > 0: the ring holds a snapshot
   std::thread ea_thread;
   std::mutex ea_mu;
   std::condition_variable ea_cv;
@@ -721,14 +752,98 @@ fm_status form_correlation(fm_state* s, cudaStream_t st, int b, const int* d_sit
   return FM_OK;
 }
 
+// ---- shared buffers of the full method (aux, gfull, xg): see fm_state::ee_buf_mu
+void buf_acquire(fm_state* s, cudaStream_t st) {
+  s->ee_buf_mu.lock();
+  if (s->ee_buf_ev) cudaStreamWaitEvent(st, s->ee_buf_ev, 0);
+}
+void buf_release(fm_state* s, cudaStream_t st) {
+  if (s->ee_buf_ev) cudaEventRecord(s->ee_buf_ev, st);
+  s->ee_buf_mu.unlock();
+}
+
+struct BufGuard {
+  fm_state* s;
+  cudaStream_t st;
+  BufGuard(fm_state* s_, cudaStream_t st_) : s(s_), st(st_) { buf_acquire(s, st); }
+  ~BufGuard() { buf_release(s, st); }
+};
+
+bool sketch_applicable(const fm_state* s, int n) {
+  return s->ee_method == FM_EE_SKETCH && s->sk_rmax > 0 && std::min(n, s->L - n) >= kSketchMinSites;
+}
+
+// sites of A (as given), then the rest in ascending order, into the device list
+fm_status upload_permutation(fm_state* s, const int32_t* sites, int32_t n) {
+  std::vector<int> perm(sites, sites + n);
+  std::vector<char> in(s->L, 0);
+  for (int i = 0; i < n; ++i) in[sites[i]] = 1;
+  for (int i = 0; i < s->L; ++i)
+    if (!in[i]) perm.push_back(i);
+  CK(cudaMemcpyAsync(s->ee_sites, perm.data(), sizeof(int) * s->L, cudaMemcpyHostToDevice, s->st));
+  // the pageable source is staged before the call returns
+  return FM_OK;
+}
+
+// The adaptive sketch on `st` over a snapshot (A's rows first, ld L): ranks kSketchR0,
+// 2 kSketchR0, ... while below both side sizes and sk_rmax.  Returns 1 when converged (S
+// at S_dev), 0 when not, -1 on a CUDA error (message in *err).
+int run_sketch(fm_state* s, cudaStream_t st, const c32* snap, int nA, const SketchScratch& w, double* S_dev,
+               double* chk_dev, int64_t* launches, int* rank, double* chk, std::string* err) {
+  const int nB = s->L - nA;
+  const uint64_t seed = s->prm.seed ^ 0x5eedc0de5eedc0deull;
+  *rank = 0;
+  *chk = 0.0;
+  for (int r = kSketchR0; r <= s->sk_rmax && r < std::min(nA, nB); r *= 2) {
+    cudaError_t e = sketch_entropy(st, snap, s->L, nA, nB, s->N, r, kSketchQ, seed, w, S_dev, chk_dev, launches);
+    double c = 0.0;
+    int stat = 0;
+    if (!e) e = cudaMemcpyAsync(&c, chk_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(&stat, w.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) {
+      *err = std::string("entropy sketch: ") + cudaGetErrorString(e);
+      return -1;
+    }
+    *rank = r;
+    *chk = c;
+    if (stat == 0 && std::isfinite(c) && c <= kSketchTol) return 1;
+  }
+  return 0;
+}
+
 // S_A of trajectory b; enqueues and synchronises.  Uses its own scratch, so
 // asynchronous entropies still in flight are not disturbed.
 fm_status entropy_impl(fm_state* s, int b, const int32_t* sites, int32_t n, double* S_out) {
   if (n == 0) { *S_out = 0.0; return FM_OK; }
-  CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  fm_status r;
   s->timer.begin(FM_PH_ENTROPY);
+  if (sketch_applicable(s, n)) {
+    if ((r = upload_permutation(s, sites, n))) return r;
+    CKL(gather_rows_c32(s->st, s->V + (int64_t)b * 2 * s->L * s->N, s->L, s->N, s->ee_sites, s->L, s->sk_snap), 1);
+    std::string err;
+    const int c = run_sketch(s, s->st, s->sk_snap, n, s->sk_sync, s->sk_res, s->sk_res + 1, &s->launches,
+                             &s->sk_last_rank, &s->sk_last_chk, &err);
+    if (c < 0) return fail(s, FM_ECUDA, err);
+    s->sk_last_fallback = c == 0;
+    if (c == 1) {
+      s->timer.end(FM_PH_ENTROPY);
+      CK(cudaMemcpyAsync(S_out, s->sk_res, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+      return sync_and_check(s);
+    }
+    // not converged: the full method below (the list still starts with A's sites)
+  } else {
+    CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+    if (s->ee_method == FM_EE_SKETCH) {
+      s->sk_last_rank = 0;
+      s->sk_last_chk = 0.0;
+      s->sk_last_fallback = 1;
+    }
+  }
   z64* M = s->G;  // scratch between steps
-  fm_status r = form_correlation(s, s->st, b, s->ee_sites, n, M);
+  buf_acquire(s, s->st);
+  r = form_correlation(s, s->st, b, s->ee_sites, n, M);
+  buf_release(s, s->st);
   if (r) return r;
   int nl = 0;
   CK(hermitian_entropy(s->st, M, std::min(n, s->N), s->ee_vb, s->ee_wb, s->ee_pb, nullptr, s->ee_d, s->ee_e,
@@ -870,6 +985,25 @@ fm_status retune(fm_state* s, int tile_config, int reorth) {
 // The library thread: for each job, wait for its C_A, run the eigen-solver on
 // ea_st, copy S to the pinned slot and record the slot's event.  Launch errors
 // are kept for fm_entropy_wait (the state's error fields belong to the caller).
+// The full method from an asynchronous ticket's snapshot (U, A's nA rows first, ld L,
+// complex64) on the library thread: the exact Gram of all rows (the projector
+// correction's U^dag U), then C_A of the smaller of A and its complement (the same
+// entropy for a pure state), written over the snapshot.  *m: order of that C_A.
+cudaError_t sketch_fallback(fm_state* s, cudaStream_t st, z64* slot, int nA, int* m, int64_t* launches) {
+  const int L = s->L, N = s->N;
+  const int nS = std::min(nA, L - nA), off = nA <= L - nA ? 0 : nA;
+  const c32* snap = (const c32*)slot;
+  buf_acquire(s, st);
+  cudaError_t e = exact_gram_c32(st, snap, L, L, N, s->gfull, s->xg, s->status_d, launches);
+  if (!e) e = rows_c32_to_z64(st, snap + off, L, nS, N, s->aux);
+  if (!e) ++*launches;
+  if (!e) e = exact_gram(st, s->aux, nS, N, slot, s->xg, s->status_d, launches);
+  if (!e) e = projector_correct(st, s->gfull, s->aux, nS, N, slot, s->xg, launches);
+  buf_release(s, st);
+  *m = nS;
+  return e;
+}
+
 void ea_worker(fm_state* s) {
   cudaSetDevice(s->dev);
   for (;;) {
@@ -883,14 +1017,38 @@ void ea_worker(fm_state* s) {
     }
     cudaError_t e = cudaStreamWaitEvent(s->ea_st, s->ea_M_ready[j.ring], 0);
     const char* what = "cudaStreamWaitEvent";
-    if (e == cudaSuccess) {
-      if (j.m == 0) {
+    z64* M = s->ea_M + (int64_t)j.ring * s->N * s->N;
+    int m = j.m;
+    bool done = false;
+    if (e == cudaSuccess && j.m > 0 && j.sketch_nA > 0) {
+      int rank = 0;
+      double chk = 0.0;
+      int64_t nl = 0;
+      std::string err;
+      const int c = run_sketch(s, s->ea_st, (const c32*)M, j.sketch_nA, s->sk_async, s->ea_S + j.slot,
+                               s->sk_res + 2, &nl, &rank, &chk, &err);
+      s->ea_launches += nl;
+      if (c < 0) {
+        e = cudaErrorLaunchFailure;
+        what = "entropy sketch";
+      } else if (c == 1) {
+        done = true;
+      } else {
+        // not converged: C_A of the smaller side from the snapshot, then the full method
+        nl = 0;
+        e = sketch_fallback(s, s->ea_st, M, j.sketch_nA, &m, &nl);
+        s->ea_launches += nl;
+        what = "entropy fallback";
+      }
+    }
+    if (e == cudaSuccess && !done) {
+      if (m == 0) {
         e = cudaMemsetAsync(s->ea_S + j.slot, 0, sizeof(double), s->ea_st);
         what = "cudaMemsetAsync";
       } else {
         int nl = 0;
-        e = hermitian_entropy(s->ea_st, s->ea_M + (int64_t)j.ring * s->N * s->N, j.m, s->ea_vb, s->ea_wb, s->ea_pb,
-                              nullptr, s->ea_d, s->ea_e, s->ea_lam, s->ea_S + j.slot, &nl);
+        e = hermitian_entropy(s->ea_st, M, m, s->ea_vb, s->ea_wb, s->ea_pb, nullptr, s->ea_d, s->ea_e, s->ea_lam,
+                              s->ea_S + j.slot, &nl);
         s->ea_launches += nl;
         what = "eigen-solver launch";
       }
@@ -917,6 +1075,7 @@ fm_status ea_setup(fm_state* s) {
   CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   CK(cudaStreamCreateWithPriority(&s->ea_st, cudaStreamNonBlocking, least));
   CK(cudaStreamCreateWithPriority(&s->hp_st, cudaStreamNonBlocking, greatest));
+  CK(cudaEventCreateWithFlags(&s->ee_buf_ev, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->hp_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->hp_out, cudaEventDisableTiming));
   for (int i = 0; i < kEaRing; ++i) {
@@ -956,6 +1115,7 @@ fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n
     CK(cudaEventSynchronize(s->ea_done[slot]));
   }
   z64* M = s->ea_M + (int64_t)ring * N * N;
+  int sketch_nA = 0;
   if (m > 0) {
     // C_A buffer reuse: the eigen-solve of ticket t - kEaRing must be queued before
     // the caller's stream may wait for it to release the buffer
@@ -963,14 +1123,25 @@ fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n
       ea_wait_issued(s, t - kEaRing + 1);
       CK(cudaStreamWaitEvent(s->st, s->ea_M_free[ring], 0));
     }
-    // rows of A and C_A, in order with the steps on the caller's stream
-    CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
-    if ((r = form_correlation(s, s->st, b, s->ee_sites, n, M))) return r;
+    if (sketch_applicable(s, n)) {
+      // U with A's rows first into the C_A buffer (16 N^2 bytes either way), in order
+      // with the steps; the library thread runs the sketch on it
+      if ((r = upload_permutation(s, sites, n))) return r;
+      CKL(gather_rows_c32(s->st, s->V + (int64_t)b * 2 * s->L * N, s->L, N, s->ee_sites, s->L, (c32*)M), 1);
+      sketch_nA = n;
+    } else {
+      // rows of A and C_A, in order with the steps on the caller's stream
+      CK(cudaMemcpyAsync(s->ee_sites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+      buf_acquire(s, s->st);
+      r = form_correlation(s, s->st, b, s->ee_sites, n, M);
+      buf_release(s, s->st);
+      if (r) return r;
+    }
   }
   CK(cudaEventRecord(s->ea_M_ready[ring], s->st));
   {
     std::lock_guard<std::mutex> lk(s->ea_mu);
-    s->ea_q.push_back(fm_state::EaJob{t, slot, ring, m});
+    s->ea_q.push_back(fm_state::EaJob{t, slot, ring, m, sketch_nA});
   }
   s->ea_cv.notify_all();
   s->ea_next = t + 1;
@@ -1035,6 +1206,18 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->band_oy = s->band_ox + kBandMaxTaps;
   s->ntap_x = s->ntap_y = 0;
   s->rk4buf = w + pl.rk4;
+  s->ee_method = FM_EE_FULL;
+  s->sk_rmax = p->precision == FM_MIXED ? sketch_rmax(p->Lx * (int64_t)p->Ly / 2) : 0;
+  s->sk_snap = nullptr;
+  if (s->sk_rmax) {
+    const int Lh = p->Lx * p->Ly, Nh = Lh / 2;
+    s->sk_snap = (c32*)(w + pl.sk_snap);
+    s->sk_sync = sketch_layout(w + pl.sk_sync, Lh, Nh, s->sk_rmax);
+    s->sk_async = sketch_layout(w + pl.sk_async, Lh, Nh, s->sk_rmax);
+  }
+  s->sk_res = (double*)(w + pl.sk_res);
+  s->sk_last_rank = 0; s->sk_last_chk = 0.0; s->sk_last_fallback = 0;
+  s->ee_buf_ev = nullptr;
   {
     char* q = w + pl.pois;
     const int64_t B = p->batch;
@@ -1290,6 +1473,27 @@ fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out) {
   return sync_and_check(s);
 }
 
+fm_status fm_set_entropy_method(fm_state* s, int32_t method) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (method != FM_EE_FULL && method != FM_EE_SKETCH) return fail(s, FM_EINVAL, "unknown entropy method");
+  if (method == FM_EE_SKETCH && s->prm.precision != FM_MIXED)
+    return fail(s, FM_EINVAL, "the entropy sketch needs a mixed-precision state");
+  CK(cudaStreamSynchronize(s->st));
+  if (s->ea_st) CK(cudaStreamSynchronize(s->ea_st));
+  s->ee_method = method;
+  return FM_OK;
+}
+
+fm_status fm_entropy_sketch_info(fm_state* s, int32_t* rank, double* check, int32_t* fell_back) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (rank) *rank = s->sk_last_fallback ? 0 : s->sk_last_rank;
+  if (check) *check = s->sk_last_chk;
+  if (fell_back) *fell_back = s->sk_last_fallback;
+  return FM_OK;
+}
+
 fm_status fm_density_correlation(fm_state* s, int32_t b, double* c_out) {
   fm_status r = check_state(s);
   if (r) return r;
@@ -1297,6 +1501,7 @@ fm_status fm_density_correlation(fm_state* s, int32_t b, double* c_out) {
   const int L = s->L, N = s->N;
   const int S = std::max(1, L / 2);               // stripe width: the stripe fits the scratch next to U
   double* bins = s->obs;
+  BufGuard guard(s, s->st);                       // s->aux
   CK(cudaMemsetAsync(bins, 0, sizeof(double) * L, s->st));
   if (s->prm.precision == FM_FP64) {
     const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
@@ -1336,6 +1541,7 @@ fm_status fm_particle_covariance(fm_state* s, int32_t b, const int32_t* A, int32
   if ((r = validate_sites(s, AB.data(), (int32_t)AB.size()))) return fail(s, FM_EINVAL, "A and B overlap");
   if (nA == 0 || nB == 0) { *G_out = 0.0; return FM_OK; }
   const int L = s->L, N = s->N;
+  BufGuard guard(s, s->st);                       // s->aux
   CK(cudaMemcpyAsync(s->ee_sites, AB.data(), sizeof(int) * (nA + nB), cudaMemcpyHostToDevice, s->st));
   double* part = s->obs + L;
   double* res = part + abs2_partials();
@@ -1383,6 +1589,7 @@ fm_status fm_copy_U(fm_state* s, int32_t b, void* host_c128, int64_t ld) {
   if (r) return r;
   if (b < 0 || b >= s->B || !host_c128 || ld < s->L) return fail(s, FM_EINVAL, "bad copy_U arguments");
   const z64* src;
+  BufGuard guard(s, s->st);                       // s->aux
   if (s->prm.precision == FM_FP64) src = s->U + (int64_t)b * s->L * s->N;
   else {
     CKL(v_to_z(s->st, s->V + (int64_t)b * 2 * s->L * s->N, s->L, s->N, s->aux), 1);
@@ -1402,6 +1609,7 @@ fm_status fm_set_U(fm_state* s, int32_t b, const void* host_c128, int64_t ld) {
     CK(cudaMemcpy2DAsync(s->U + (int64_t)b * s->L * s->N, (size_t)s->L * 16, host_c128, ld * 16,
                          (size_t)s->L * 16, s->N, cudaMemcpyHostToDevice, s->st));
   } else {
+    BufGuard guard(s, s->st);                     // s->aux
     CK(cudaMemcpy2DAsync(s->aux, (size_t)s->L * 16, host_c128, ld * 16, (size_t)s->L * 16, s->N,
                          cudaMemcpyHostToDevice, s->st));
     const int64_t o = (int64_t)b * 2 * s->L * s->N;
@@ -1436,6 +1644,7 @@ fm_status fm_orthonormality_error(fm_state* s, int32_t b, const int32_t* cols, i
   const int L = s->L, N = s->N;
   // aux <- U_b as complex128 (L x N), then Gs = U[:, cols]^dag U (ncols x N) in R
   const z64* U;
+  BufGuard guard(s, s->st);                       // s->aux
   if (s->prm.precision == FM_FP64) U = s->U + (int64_t)b * L * N;
   else {
     CKL(v_to_z(s->st, s->V + (int64_t)b * 2 * L * N, L, N, s->aux), 1);
@@ -1666,6 +1875,7 @@ void fm_destroy(fm_state* s) {
     for (int i = 0; i < kAsyncSlots; ++i) cudaEventDestroy(s->ea_done[i]);
     cudaFreeHost(s->ea_host);
   }
+  if (s->ee_buf_ev) cudaEventDestroy(s->ee_buf_ev);
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   mixed_free(s->mh);

@@ -286,29 +286,34 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 // ------------------------------------------------------------------ digit planes
-// Y[r][k] of the two layouts: ROWS_ARE_SITES (n <= N): Y = X, X[r + k n];
-// otherwise Y = X^T: X[k + r n].  X is the n x N column-major block.
+// Y[r][k] of the two layouts: ROWS_ARE_SITES (n <= N): Y = X, X[r + k ld];
+// otherwise Y = X^T: X[k + r ld].  X is the n x N column-major block (leading
+// dimension ld >= n) of complex128 or complex64 entries.
 
 // rowmax[r] = max_k max(|Re Y_rk|, |Im Y_rk|) as the bits of a nonnegative double
-__global__ void rowmax_sites_kernel(const z64* __restrict__ X, int n, int N, unsigned long long* rowmax) {
+template <typename T>
+__global__ void rowmax_sites_kernel(const cplx<T>* __restrict__ X, int64_t ld, int n, int N,
+                                    unsigned long long* rowmax) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int per = FM_CEIL_DIV(N, (int)gridDim.y);
   const int k0 = blockIdx.y * per, k1 = min(N, k0 + per);
   double mx = 0.0;
   for (int k = k0; k < k1; ++k) {
-    const z64 v = X[r + (int64_t)k * n];
-    mx = fmax(mx, fmax(fabs(v.re), fabs(v.im)));
+    const cplx<T> v = X[r + (int64_t)k * ld];
+    mx = fmax(mx, fmax(fabs((double)v.re), fabs((double)v.im)));
   }
   atomicMax(&rowmax[r], (unsigned long long)__double_as_longlong(mx));
 }
 
-__global__ void rowmax_orbitals_kernel(const z64* __restrict__ X, int n, unsigned long long* rowmax) {
+template <typename T>
+__global__ void rowmax_orbitals_kernel(const cplx<T>* __restrict__ X, int64_t ld, int n,
+                                       unsigned long long* rowmax) {
   const int r = blockIdx.x;
   double mx = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const z64 v = X[k + (int64_t)r * n];
-    mx = fmax(mx, fmax(fabs(v.re), fabs(v.im)));
+    const cplx<T> v = X[k + (int64_t)r * ld];
+    mx = fmax(mx, fmax(fabs((double)v.re), fabs((double)v.im)));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -343,9 +348,9 @@ FM_DEVFN void digits(double v, int e, __half (&d)[NSLICE]) {
 // planes[s][r][kk], kk < Kp: Re Y[r][kk], kk >= Kp: Im Y[r][kk - Kp]; zero padding
 // outside m x Kc.  32 x 32 tiles through shared memory so that both the read of
 // X and the write of the planes are coalesced.
-template <bool ROWS_ARE_SITES>
-__global__ void slice_kernel(const z64* __restrict__ X, int n, int m, int Kc, int Kp, const int* __restrict__ expo,
-                             __half* planes, int64_t plane_stride) {
+template <bool ROWS_ARE_SITES, typename T>
+__global__ void slice_kernel(const cplx<T>* __restrict__ X, int64_t ld, int m, int Kc, int Kp,
+                             const int* __restrict__ expo, __half* planes, int64_t plane_stride) {
   __shared__ z64 tile[32][33];   // [k][r]
   const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -355,11 +360,17 @@ __global__ void slice_kernel(const z64* __restrict__ X, int n, int m, int Kc, in
     z64 v = cmk(0.0, 0.0);
     if (ROWS_ARE_SITES) {       // read along r
       const int r = r0 + tx, k = k0 + a;
-      if (r < m && k < Kc) v = X[r + (int64_t)k * n];
+      if (r < m && k < Kc) {
+        const cplx<T> x = X[r + (int64_t)k * ld];
+        v = cmk((double)x.re, (double)x.im);
+      }
       tile[a][tx] = v;
     } else {                    // read along k
       const int k = k0 + tx, r = r0 + a;
-      if (r < m && k < Kc) v = X[k + (int64_t)r * n];
+      if (r < m && k < Kc) {
+        const cplx<T> x = X[k + (int64_t)r * ld];
+        v = cmk((double)x.re, (double)x.im);
+      }
       tile[tx][a] = v;
     }
   }
@@ -411,8 +422,9 @@ size_t exact_gram_scratch_bytes(int nmax, int N) {
   return b;
 }
 
-cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void* scratch, int* status,
-                       int64_t* launches) {
+template <typename T>
+cudaError_t exact_gram_t(cudaStream_t st, const cplx<T>* X, int64_t ld, int n, int N, z64* M, void* scratch,
+                         int* status, int64_t* launches) {
   using namespace xg;
   const bool sites = n <= N;
   const XgLayout l = xg_layout(n, N);
@@ -427,14 +439,14 @@ cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void
   if ((e = cudaMemsetAsync(rowmax, 0, (size_t)mp * 8, st))) return e;
   if (sites) {
     const int gy = std::max(1, std::min(64, (4 * 152) / std::max(1, FM_CEIL_DIV(m, 256))));
-    rowmax_sites_kernel<<<dim3(FM_CEIL_DIV(m, 256), gy), 256, 0, st>>>(X, n, N, rowmax);
+    rowmax_sites_kernel<T><<<dim3(FM_CEIL_DIV(m, 256), gy), 256, 0, st>>>(X, ld, n, N, rowmax);
   } else {
-    rowmax_orbitals_kernel<<<m, 256, 0, st>>>(X, n, rowmax);
+    rowmax_orbitals_kernel<T><<<m, 256, 0, st>>>(X, ld, n, rowmax);
   }
   exponents_kernel<<<FM_CEIL_DIV(mp, 256), 256, 0, st>>>(rowmax, m, mp, expo);
   const dim3 sg(Kp / 32, mp / 32), sb(32, 8);
-  if (sites) slice_kernel<true><<<sg, sb, 0, st>>>(X, n, m, Kc, Kp, expo, planes, plane_stride);
-  else slice_kernel<false><<<sg, sb, 0, st>>>(X, n, m, Kc, Kp, expo, planes, plane_stride);
+  if (sites) slice_kernel<true, T><<<sg, sb, 0, st>>>(X, ld, m, Kc, Kp, expo, planes, plane_stride);
+  else slice_kernel<false, T><<<sg, sb, 0, st>>>(X, ld, m, Kc, Kp, expo, planes, plane_stride);
   if ((e = cudaGetLastError())) return e;
   CUtensorMap am[NSLICE], bm[NSLICE];
   for (int s = 0; s < NSLICE; ++s) {
@@ -465,6 +477,16 @@ cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void
   if ((e = cudaGetLastError())) return e;
   if (launches) *launches += 5;
   return cudaSuccess;
+}
+
+cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void* scratch, int* status,
+                       int64_t* launches) {
+  return exact_gram_t<double>(st, X, n, n, N, M, scratch, status, launches);
+}
+
+cudaError_t exact_gram_c32(cudaStream_t st, const c32* X, int64_t ld, int n, int N, z64* M, void* scratch,
+                           int* status, int64_t* launches) {
+  return exact_gram_t<float>(st, X, ld, n, N, M, scratch, status, launches);
 }
 
 }  // namespace fm

@@ -142,9 +142,12 @@ cudaError_t check_finite_z(cudaStream_t st, const z64* X, int64_t n, int* dev_st
 // in: Hermitian m x m matrix M (column-major, overwritten; for m > 256 only its
 // lower triangle is read); out: S = -sum f(lambda).  pbuf: hermitian_entropy_pbuf(m)
 // complex entries of scratch.
+// cross != 0: M's eigenvalues are sigma^2 = lambda (1 - lambda) (the cross-block form
+// of the entropy sketch); each gives the term of its root lambda <= 1/2.
+// lam: the eigenvalues, ascending.
 cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vbuf, z64* wbuf, z64* pbuf,
                               double* partial, double* d, double* e, double* lam, double* S_dev,
-                              int* nlaunch);
+                              int* nlaunch, int cross = 0);
 // size of pbuf (complex entries) hermitian_entropy needs for an m x m matrix
 constexpr int EIG_TILE = 32;
 constexpr int64_t hermitian_entropy_pbuf(int m) {
@@ -194,6 +197,9 @@ cudaError_t sum_abs2(cudaStream_t st, const cplx<T>* M, int64_t n, double* part,
 size_t exact_gram_scratch_bytes(int nmax, int N);
 cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void* scratch, int* status,
                        int64_t* launches);
+// the same for a complex64 block with leading dimension ld >= n
+cudaError_t exact_gram_c32(cudaStream_t st, const c32* X, int64_t ld, int n, int N, z64* M, void* scratch,
+                           int* status, int64_t* launches);
 // First-order correction of M (the lower triangle exact_gram wrote for the block XA
 // of n gathered rows) from C = U U^dag to the projector onto span(U): Gx is the
 // exact_gram of all L rows of U (= conj(U^dag U), lower triangle, N x N).
@@ -201,5 +207,33 @@ cudaError_t exact_gram(cudaStream_t st, const z64* X, int n, int N, z64* M, void
 size_t projector_scratch_bytes(int N);
 cudaError_t projector_correct(cudaStream_t st, const z64* Gx, const z64* XA, int n, int N, z64* M, void* scratch,
                               int64_t* launches);
+
+// ---- entanglement entropy from a sketch of the cross block C_AB = U_A U_B^dag (ee_sketch.cu)
+constexpr int kSketchPartials = 17;   // partial-Gram capacity, in rmax x rmax matrices
+struct SketchScratch {
+  int nmax, N, rmax;
+  c32 *Om, *Yc, *Z;           // nmax x rmax, nmax x rmax, N x rmax
+  z64 *Yz, *Yz2;              // nmax x rmax (float64 orthonormalisation)
+  z64 *G, *R, *T, *Dinv, *Xc; // rmax x rmax Cholesky factors and their scratch
+  z64* H;                     // rmax x rmax Rayleigh-Ritz matrix
+  z64* Gp;                    // kSketchPartials x rmax x rmax partial Grams
+  z64 *vb, *wb, *pb;
+  double *d, *e, *lam, *S;
+  int* status;
+  void* xg;                   // exact-Gram scratch
+  size_t bytes;
+};
+// carve the scratch of a sketch (subsystem and complement of at most nmax sites, rank
+// at most rmax) out of `base` (NULL: sizes only)
+SketchScratch sketch_layout(void* base, int nmax, int N, int rmax);
+// out (n x N, ld n) = the rows of the complex64 block X (column-major, ld) as complex128
+cudaError_t rows_c32_to_z64(cudaStream_t st, const c32* X, int64_t ld, int n, int N, z64* out);
+size_t sketch_scratch_bytes(int nmax, int N, int rmax);
+// U: L x N complex64 rows, A's nA rows first, then B's nB rows (column-major, ld);
+// r: sketch rank (multiple of 32, r < nA, nB), q: power iterations.  Writes S (entropy
+// of A, nats) to S_out and the (max(8, r/8))-th smallest Ritz value to chk_out (the
+// sketch has converged when it is below ~1e-9); w.status gets Cholesky pivot flags.
+cudaError_t sketch_entropy(cudaStream_t st, const c32* U, int64_t ld, int nA, int nB, int N, int r, int q,
+                           uint64_t seed, const SketchScratch& w, double* S_out, double* chk_out, int64_t* launches);
 
 }  // namespace fm

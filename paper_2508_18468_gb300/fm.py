@@ -16,6 +16,7 @@ FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENUMERIC, FM_ETIMEOUT, FM_ESTATE = ran
 FM_PROJECTIVE, FM_HOMODYNE, FM_HOMODYNE_RK4, FM_PROJECTIVE_POISSON = 0, 1, 2, 3
 FM_FP64, FM_MIXED = 0, 1
 FM_PROP_DENSE, FM_PROP_BANDED = 0, 1
+FM_EE_FULL, FM_EE_SKETCH = 0, 1
 PHASES = ("propagate", "measure", "gram", "cholesky", "trmm", "entropy")
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENUMERIC",
                 5: "FM_ETIMEOUT", 6: "FM_ESTATE"}
@@ -85,6 +86,8 @@ def _load():
         "fm_density_correlation": (i32, [vp, i32, P(dbl)]),
         "fm_set_propagation": (i32, [vp, i32]),
         "fm_particle_covariance": (i32, [vp, i32, P(i32), i32, P(i32), i32, P(dbl)]),
+        "fm_set_entropy_method": (i32, [vp, i32]),
+        "fm_entropy_sketch_info": (i32, [vp, P(i32), P(dbl), P(i32)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -233,6 +236,17 @@ class Trajectories:
         out = ctypes.c_double()
         self._check(lib.fm_mutual_info(self._h, int(b), pa, int(a.size), pb, int(c.size), ctypes.byref(out)))
         return out.value
+
+    def set_entropy_method(self, method):
+        """FM_EE_FULL (eigenvalues of C_A) or FM_EE_SKETCH (cross-block sketch, mixed precision)."""
+        self._check(lib.fm_set_entropy_method(self._h, int(method)))
+
+    def entropy_sketch_info(self):
+        """(rank, check, fell_back) of the last synchronous sketch entropy."""
+        r, f = ctypes.c_int32(), ctypes.c_int32()
+        c = ctypes.c_double()
+        self._check(lib.fm_entropy_sketch_info(self._h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(f)))
+        return r.value, c.value, bool(f.value)
 
     def set_propagation(self, mode):
         """FM_PROP_DENSE (dense GEMM) or FM_PROP_BANDED (stencils of the circulant propagator)."""

@@ -5,9 +5,9 @@
         three warm-up steps, then K steps inside the NVTX range "steps" (capture them with
         ncu --nvtx --nvtx-include "steps/").  protocol: homodyne (default), projective,
         poisson, rk4; propagation: dense (default) or banded.  Prints one JSON line.
-    python -m paper_2508_18468_gb300.profiling entropy L
-        one step of a single homodyne trajectory, then the half-chain entropy inside the
-        NVTX range "entropy".
+    python -m paper_2508_18468_gb300.profiling entropy L [full|sketch] [steps]
+        `steps` steps (default 1) of a single homodyne trajectory, then the half-chain
+        entropy by the given method (default full) inside the NVTX range "entropy".
     python -m paper_2508_18468_gb300.profiling summary <launches.csv>
         launches, total time and share of every kernel of an ncu launch list
         (--metrics gpu__time_duration.sum --csv), largest first.
@@ -75,21 +75,24 @@ def steps(spec, B, K, protocol="homodyne", propagation="dense"):
                       "s_per_step": t / K, "launches_per_step": (g.kernel_launches - l0) / K}))
 
 
-def entropy(L):
+def entropy(L, method="full", nsteps=1):
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from . import fm
     g = fm.Trajectories(fm.make_params(L, batch=1, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED, gamma=1.0,
                                        seed=1))
-    g.step(1)
+    g.step(nsteps)
+    if method == "sketch":
+        g.set_entropy_method(fm.FM_EE_SKETCH)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("entropy")
     t0 = time.perf_counter()
     S = g.entropy(list(range(L // 2)))
     t = time.perf_counter() - t0
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"L": L, "S": S, "entropy_s": t}))
+    info = g.entropy_sketch_info() if method == "sketch" else None
+    print(json.dumps({"L": L, "steps": nsteps, "method": method, "S": S, "entropy_s": t, "sketch_info": info}))
 
 
 if __name__ == "__main__":
@@ -97,7 +100,7 @@ if __name__ == "__main__":
     if cmd == "steps":
         steps(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), *sys.argv[5:7])
     elif cmd == "entropy":
-        entropy(int(sys.argv[2]))
+        entropy(int(sys.argv[2]), *(sys.argv[3:4]), *[int(x) for x in sys.argv[4:5]])
     elif cmd == "summary":
         summary(sys.argv[2])
     else:
