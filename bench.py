@@ -340,7 +340,7 @@ def run_ours(args, world, rank, local):
         achieved = prop_flops / (prop_ms / prop_n / 1e3) / 1e12
         traffic = profiled_traffic("prop_gemm_ring16384") if precision == fm.FM_MIXED else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "tc_gemm_kernel<256> (propagation)",
+                "traffic": traffic, "kernel": "tc_gemm_kernel (propagation, split-fp16 tcgen05)",
                 "ms_per_launch": prop_ms / prop_n, "peak_note": peak_note}
     line = {
         "metric": METRIC if args.workload == WORKLOAD else "trajectory steps/s (%s)" % args.workload,

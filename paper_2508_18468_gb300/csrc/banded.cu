@@ -73,15 +73,28 @@ __global__ void __launch_bounds__(256) band_x_kernel(const void* __restrict__ in
   const int c = blockIdx.y;
   const int k0 = c * per, k1 = min(N, k0 + per);
   double s = 0.0;
+  // the staged run of one column holds w <= kBandSegX + kBandMaxTaps - 1 < 2 x 256 inputs:
+  // two per thread, all of a stage loaded into registers before any is stored
+  int srcq[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int src = (p0 - offmax + tid + 256 * h) % Lx;
+    srcq[h] = (src < 0 ? src + Lx : src) + Lx * y;
+  }
   for (int kb = k0; kb < k1; kb += kBandCols) {
     const int nk = min(kBandCols, k1 - kb);
+    cplx<T> v[kBandCols][2];
+#pragma unroll
+    for (int kk = 0; kk < kBandCols; ++kk)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (kk < nk && tid + 256 * h < w) v[kk][h] = band_io<T, LAYOUT>::ld(in, b, L, N, srcq[h], kb + kk);
     __syncthreads();                                 // previous stage consumed (and tp written)
-    for (int kk = 0; kk < nk; ++kk)
-      for (int q = tid; q < w; q += blockDim.x) {
-        int src = (p0 - offmax + q) % Lx;
-        if (src < 0) src += Lx;
-        buf[kk][q] = band_io<T, LAYOUT>::ld(in, b, L, N, src + Lx * y, kb + kk);
-      }
+#pragma unroll
+    for (int kk = 0; kk < kBandCols; ++kk)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (kk < nk && tid + 256 * h < w) buf[kk][tid + 256 * h] = v[kk][h];
     __syncthreads();
     if (pos < Lx)
       for (int kk = 0; kk < nk; ++kk) {
@@ -121,14 +134,24 @@ __global__ void __launch_bounds__(256) band_y_kernel(const void* __restrict__ in
   double s[SEGY / 8];
 #pragma unroll
   for (int r = 0; r < SEGY / 8; ++r) s[r] = 0.0;
+  // staged rows of one column: h <= SEGY + kBandMaxTaps - 1, at most RY per thread, loaded
+  // into registers before any is stored
+  constexpr int RY = (H + 7) / 8;
+  int srcr[RY];
+#pragma unroll
+  for (int i = 0; i < RY; ++i) {
+    int src = (y0 - offmax + ty + 8 * i) % Ly;
+    srcr[i] = x + Lx * (src < 0 ? src + Ly : src);
+  }
   for (int k = k0; k < k1; ++k) {
+    cplx<T> v[RY];
+#pragma unroll
+    for (int i = 0; i < RY; ++i)
+      if (x < Lx && ty + 8 * i < h) v[i] = band_io<T, LAYOUT>::ld(in, b, L, N, srcr[i], k);
     __syncthreads();
-    if (x < Lx)
-      for (int q = ty; q < h; q += 8) {
-        int src = (y0 - offmax + q) % Ly;
-        if (src < 0) src += Ly;
-        buf[q][tx] = band_io<T, LAYOUT>::ld(in, b, L, N, x + Lx * src, k);
-      }
+#pragma unroll
+    for (int i = 0; i < RY; ++i)
+      if (x < Lx && ty + 8 * i < h) buf[ty + 8 * i][tx] = v[i];
     __syncthreads();
     if (x < Lx)
 #pragma unroll

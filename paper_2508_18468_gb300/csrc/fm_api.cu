@@ -110,11 +110,14 @@ Plan make_plan(const fm_params& p) {
   pl.w = pl.take(B * L * 8);
   pl.xbuf = pl.take(B * N * 16);
   pl.vbuf = pl.take(B * L * 16);
-  pl.G = pl.take(B * N * N * 16);
-  pl.R = pl.take(B * N * N * 16);
-  pl.T = pl.take(B * N * N * 16);
-  pl.Dinv = pl.take(B * nblk * kCholNB * kCholNB * 16);
-  pl.X = pl.take(B * N * kCholNB * 16);
+  // float64 CholeskyQR factors of every trajectory (FP64 path); the mixed path keeps its
+  // factors in its own scratch and uses G only as one N x N matrix (entropy, covariance)
+  const int64_t nf = p.precision == FM_FP64 ? B : 0;
+  pl.G = pl.take(std::max<int64_t>(nf, 1) * N * N * 16);
+  pl.R = pl.take(nf * N * N * 16);
+  pl.T = pl.take(nf * N * N * 16);
+  pl.Dinv = pl.take(nf * nblk * kCholNB * kCholNB * 16);
+  pl.X = pl.take(nf * N * kCholNB * 16);
   pl.ee_vb = pl.take(N * 16);
   pl.ee_wb = pl.take(N * 16);
   pl.ee_pb = pl.take(std::max<int64_t>(hermitian_entropy_pbuf((int)N), 1 + 32 * N) * 16);
@@ -1185,6 +1188,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->xbuf_d = w + pl.xbuf; s->vbuf_d = w + pl.vbuf;
   s->G = (z64*)(w + pl.G); s->R = (z64*)(w + pl.R); s->T = (z64*)(w + pl.T);
   s->Dinv = (z64*)(w + pl.Dinv); s->X = (z64*)(w + pl.X);
+  if (p->precision != FM_FP64) s->R = s->T = s->Dinv = s->X = nullptr;   // not allocated
   s->ee_vb = (z64*)(w + pl.ee_vb); s->ee_wb = (z64*)(w + pl.ee_wb); s->ee_pb = (z64*)(w + pl.ee_pb);
   s->ee_d = (double*)(w + pl.ee_d); s->ee_e = (double*)(w + pl.ee_e); s->ee_lam = (double*)(w + pl.ee_lam);
   s->ee_S = (double*)(w + pl.ee_S); s->ee_max = (double*)(w + pl.ee_max); s->ee_sites = (int*)(w + pl.ee_sites);

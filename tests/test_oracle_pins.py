@@ -375,6 +375,30 @@ def test_continuous_time_projective_matches_brute_force(Lx, Ly, gamma, seed):
     assert np.max(np.abs(observables.correlation(out["U"]) - np.conj(D))) < 1e-12
 
 
+@pytest.mark.parametrize("Lx,Ly,protocol", [(64, 1, trajectory.HOMODYNE), (8, 6, trajectory.PROJECTIVE)])
+def test_cross_block_identity_behind_the_entropy_sketch(Lx, Ly, protocol):
+    """For orthonormal U, C = U U^dag is a projector, so C_A - C_A^2 = C_AB C_BA: the
+    eigenvalues of C_A satisfy lambda (1 - lambda) = sigma^2 (sigma: singular values of
+    C_AB, B the complement), and S_A, whose terms are symmetric under lambda <-> 1 - lambda,
+    follows from the sigma^2 alone through lambda = 2 s / (1 + sqrt(1 - 4 s))."""
+    prm = Params(Lx=Lx, Ly=Ly, gamma=0.8, protocol=protocol, seed=17)
+    U = trajectory.run(prm, 25)["U"]
+    L = Lx * Ly
+    rng = np.random.default_rng(4)
+    A = sorted(rng.choice(L, size=L // 3, replace=False).tolist())
+    B = [i for i in range(L) if i not in set(A)]
+    C = observables.correlation(U)
+    lam = np.clip(np.linalg.eigvalsh(C[np.ix_(A, A)]), 0.0, 1.0)
+    sig = np.linalg.svd(C[np.ix_(A, B)], compute_uv=False)
+    x = np.sort(np.concatenate([sig**2, np.zeros(len(A) - len(sig))]))
+    assert np.max(np.abs(np.sort(lam * (1 - lam)) - x)) < 1e-12
+    y = np.clip(x, 0.0, 0.25)
+    lam_low = 2 * y / (1 + np.sqrt(1 - 4 * y))
+    keep = (lam_low > 0) & (lam_low < 1)
+    S = -np.sum(lam_low[keep] * np.log(lam_low[keep]) + (1 - lam_low[keep]) * np.log1p(-lam_low[keep]))
+    assert abs(S - observables.entanglement_entropy(U, A)) < 1e-10
+
+
 def test_continuous_time_forced_replay():
     """Forcing every outcome to the oracle's own gives the same run; forcing one flip
     keeps every event's site and draws (they do not depend on the state) and logs the
