@@ -172,13 +172,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest x over the ranks (the timing reduction; NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_traj_id(rank, batch):
+    """Replicas: rank r advances trajectories r * batch .. (r + 1) * batch - 1 of the workload."""
+    return rank * batch
 
 
 # ---------------------------------------------------------------- reference arm
@@ -230,7 +237,8 @@ def run_ours(args, world, rank, local):
     precision = fm.FM_MIXED if args.precision == "mixed" else fm.FM_FP64
     protocol = fm.FM_HOMODYNE if wl["protocol"] == "homodyne" else fm.FM_PROJECTIVE
     prm = fm.make_params(Lx, Ly, batch=B, protocol=protocol, precision=precision,
-                         reorth_interval=wl["reorth_interval"], gamma=gam[0], seed=seed, traj_id=rank * B)
+                         reorth_interval=wl["reorth_interval"], gamma=gam[0], seed=seed,
+                         traj_id=replica_traj_id(rank, B))
     g = fm.Trajectories(prm)
     g.set_gammas(gam)
     if args.propagation == "banded":

@@ -105,9 +105,9 @@ typedef struct {
 } fm_params;
 
 /* fm_params.tile_config of the mixed-precision path: bits 0-1 the output tile
- * width of the propagation and Gram products (0 automatic: 128; 1: 128; 2: 256,
- * needs N % 256 == 0); bits 2-4 g the height of the tile raster groups, 2^(g+1)
- * row tiles (0: 8).  Any other
+ * width of the propagation and Gram products (0 automatic: 128 up to N = 8192,
+ * 256 beyond when N % 256 == 0; 1: 128; 2: 256, needs N % 256 == 0); bits 2-4 g
+ * the height of the tile raster groups, 2^(g+1) row tiles (0: 8).  Any other
  * bit set is FM_EINVAL.  Results do not depend on it beyond float rounding
  * order inside a tile (none: each output is one fixed-order sum per tile). */
 #define FM_TILE_BN_AUTO 0

@@ -21,14 +21,16 @@ namespace fm {
 namespace {
 
 // tile width of the propagation and Gram products, raster group height (fm.h, FM_TILE_*).
-// Defaults: 128-wide tiles (two TMEM accumulator sets, so a tile's epilogue overlaps the
-// next tile's products: the Gram at L = 16384 takes 63 ms instead of 79 ms per pair of
-// passes, the propagation is unchanged) in raster groups of 8 row tiles.
+// Defaults (measured): up to N = 8192, 128-wide tiles (two TMEM accumulator sets, so a
+// tile's epilogue overlaps the next tile's products: the Gram at L = 16384 takes 63 ms
+// instead of 79 ms per pair of passes, the propagation is unchanged); beyond, 256-wide
+// tiles, whose operand panels are read half as often (the 160 x 160 torus Gram: 614 ms
+// instead of 904 ms); raster groups of 8 row tiles.
 int pick_bn(int N, int tile_config) {
   const int c = tile_config & 3;
+  if (c == 1) return 128;
   if (c == 2) return 256;
-  (void)N;
-  return 128;
+  return (N > 8192 && N % 256 == 0) ? 256 : 128;
 }
 int pick_gm(int tile_config) {
   const int g = (tile_config >> 2) & 7;
@@ -575,7 +577,7 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
 //   the product accumulates in fp32 registers every 2 K-blocks;
 // first == false: G = 1 + E with |E| small after a full pass, T = 1 - F to first
 //   order (O(|E|^2) error), F built from G with its float64 diagonal.
-int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
+int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired) {
   const int L = c->L, N = c->N, B = c->B, BN = h->BN;
   const int grid = tc::sm_count();
   tc::Params p = base_params(c, h);
@@ -605,8 +607,8 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
                                                                                   h->urm_l);
   MCK(cudaGetLastError());
   c->timer->end(FM_PH_CHOLESKY);
-  // first pass: 128-wide tiles, fp32 register accumulation every 2 K-blocks
-  // (two TMEM sets); second pass: tiles of the state's width accumulated in TMEM
+  // first pass: 128-wide tiles (fp32 register accumulation every 2 K-blocks when no
+  // second pass follows); second pass: tiles of the state's width accumulated in TMEM
   // (128: two accumulator sets, the epilogue overlapping the next tile)
   const bool wide2 = !first && h->BN == 256;
   p = base_params(c, h);
@@ -621,7 +623,11 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first) {
   p.out_h = c->Vh;
   p.out_l = c->Vl;
   p.in_f = c->V;
-  p.chunk_kb = first ? 2 : 0;
+  // the first pass drains TMEM into fp32 registers every 2 K-blocks when its result
+  // stays the state until the next step (the fp32 TMEM accumulators round toward zero:
+  // up to ~1e-4 relative over 16384 terms); when the second pass follows at once it
+  // removes that error with the rest (to O(|E|^2) ~ 1e-8), so the plain kernel serves
+  p.chunk_kb = (first && !paired) ? 2 : 0;
   c->timer->begin(FM_PH_TRMM);
   if (wide2) MCK(tc::launch(c->st, 256, h->trmm_Ah, h->trmm_Al, h->trmm2_Bh, h->trmm2_Bl, p, grid));
   else MCK(tc::launch(c->st, 128, h->trmm_Ah, h->trmm_Al, h->trmm_Bh, h->trmm_Bl, p, grid));
@@ -731,9 +737,9 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
 int mixed_reorth(MixedHost* h, MixedCtx* c) {
   const int L = c->L, N = c->N, B = c->B;
   MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
-  int r = qr_pass(h, c, true);
+  int r = qr_pass(h, c, true, true);
   if (r) return r;
-  return qr_pass(h, c, false);
+  return qr_pass(h, c, false, true);
 }
 
 int mixed_step(MixedHost* h, MixedCtx* c) {
@@ -755,9 +761,10 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     std::swap(c->V, c->V2);
     MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
     c->timer->end(FM_PH_PROPAGATE);
-    int r = qr_pass(h, c, true);
+    const bool second = (c->global_step + 1) % c->reorth_interval == 0;
+    int r = qr_pass(h, c, true, second);
     if (r) return r;
-    if ((c->global_step + 1) % c->reorth_interval == 0 && (r = qr_pass(h, c, false))) return r;
+    if (second && (r = qr_pass(h, c, false, true))) return r;
     MCK(bump_steps(c->st, c->step, B));
     return FM_OK;
   }
@@ -796,10 +803,11 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     MCK(reduce_occupations(c->st, c->part, nchunks, L, B, c->nocc, c->w, c->gamma, c->dt, c->traj, c->step, c->seed));
     MCK(scale_rows_v(c->st, c->V, c->Vh, c->Vl, L, N, B, c->w));
     c->timer->end(FM_PH_MEASURE);
-    int r = qr_pass(h, c, true);
+    const bool second = (c->global_step + 1) % k == 0;
+    int r = qr_pass(h, c, true, second);
     if (r) return r;
-    if ((c->global_step + 1) % k == 0) {
-      r = qr_pass(h, c, false);
+    if (second) {
+      r = qr_pass(h, c, false, true);
       if (r) return r;
     }
   } else {
@@ -827,9 +835,9 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     }
     c->timer->end(FM_PH_MEASURE);
     if ((c->global_step + 1) % k == 0) {
-      int r = qr_pass(h, c, true);
+      int r = qr_pass(h, c, true, true);
       if (r) return r;
-      r = qr_pass(h, c, false);
+      r = qr_pass(h, c, false, true);
       if (r) return r;
     }
   }

@@ -108,3 +108,25 @@ def test_torus160_density_correlation_sum_rule_and_block_covariance(fm):
     assert np.max(np.abs(cc - flip)) <= 1e-7
     A, B, _ = workloads.torus_blocks()
     assert g.particle_covariance(A, B) >= 0.0
+
+
+def test_ring16384_entropy_sketch_equals_full_method(fm):
+    """The bench's entropy configuration at full size: the half-chain sketch of every
+    trajectory of the L = 16384 homodyne batch after 60 steps against the full method on the
+    same state (<= 1e-5 of max(S, 1)); the asynchronous sketch equals the synchronous one."""
+    L = 16384
+    wl = workloads.WORKLOADS["ring16384_homodyne"]
+    g = fm.Trajectories(fm.make_params(L, batch=4, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED,
+                                       seed=workloads.seed_of("ring16384_homodyne")))
+    g.set_gammas(wl["gammas"])
+    g.step(60)
+    half = workloads.half_chain(L)
+    g.set_entropy_method(fm.FM_EE_SKETCH)
+    sk = [g.entropy(half, b) for b in range(4)]
+    tickets = [g.entropy_async(half, b) for b in range(4)]
+    assert [g.entropy_wait(t) for t in tickets] == sk
+    g.set_entropy_method(fm.FM_EE_FULL)
+    full = g.entropy(half, 0)
+    print("L=16384 after 60 steps: sketch %s, full (trajectory 0) %.9f" % (sk, full))
+    assert abs(sk[0] - full) <= 1e-5 * max(full, 1.0)
+    assert all(s > 0.0 for s in sk)
