@@ -170,16 +170,17 @@ fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, do
 
 /* Asynchronous S_A of trajectory b at the current point of the step sequence.
  * The rows of A are gathered and C_A is formed on the caller's stream, in
- * order with the steps (one of 4 C_A buffers of the workspace); the FP64
+ * order with the steps (one of the workspace's C_A buffers: as many as fit in
+ * 4 GiB, between 4 and 64, 16 N^2 bytes each); the FP64
  * eigen-solve (Householder tridiagonalisation, about 5 launches per row of
  * C_A) is issued by a library-owned host thread onto a low-priority stream.
  * From the first call on, fm_step runs its kernels on a high-priority stream
  * ordered after and before the caller's stream by events, so later steps
  * proceed while the eigen-solve fills what their kernels leave of each SM.
  * *ticket identifies the result for fm_entropy_wait.  Up to 64 results may be
- * outstanding (a 65th call first waits for the oldest); a 5th call while 4
- * eigen-solves are still queued makes the caller's stream wait for the
- * oldest to release its C_A buffer.  Results live in a small pinned host
+ * outstanding (a 65th call first waits for the oldest); a call while every
+ * C_A buffer still waits for its eigen-solve makes the caller's stream wait
+ * for the oldest to release its buffer.  Results live in a small pinned host
  * buffer the state allocates on first use.  A launch error of the library
  * thread is reported by fm_entropy_wait (FM_ECUDA, sticky). */
 fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t n, int64_t* ticket);

@@ -26,7 +26,13 @@ namespace {
 const int kCholNB = CHOL_NB;   // Cholesky / triangular-inverse block
 const int kMaxChunks = 128;    // occupation partial sums
 const int kAsyncSlots = 64;    // outstanding asynchronous entropies
-const int kEaRing = 4;         // C_A buffers of the asynchronous entropies
+// C_A buffers of the asynchronous entropies: as many as fit in 4 GiB, 4 to 64 (many
+// small trajectories then keep their tickets in flight together)
+const int kEaRingMax = 64;
+int ea_ring_size(int64_t N) {
+  const int64_t per = 16 * N * N;
+  return (int)std::max<int64_t>(4, std::min<int64_t>(kEaRingMax, (int64_t(4) << 30) / std::max<int64_t>(per, 1)));
+}
 const int kPoisSlots = 128;    // continuous-time projective: propagation slots per upload
 // entropy sketch (FM_EE_SKETCH): first rank, power iterations, convergence bound on the
 // (r/8)-th smallest Ritz value sigma^2, smallest subsystem (and complement) it is used for
@@ -129,7 +135,7 @@ Plan make_plan(const fm_params& p) {
   pl.ee_sites = pl.take(L * 4);
   pl.chk_cols = pl.take(L * std::min<int64_t>(N, 64) * 16);
   pl.chk_G = pl.take(std::min<int64_t>(N, 64) * N * 16);
-  pl.ea_M = pl.take(kEaRing * N * N * 16);
+  pl.ea_M = pl.take(ea_ring_size(N) * N * N * 16);
   pl.ea_vb = pl.take(N * 16);
   pl.ea_wb = pl.take(N * 16);
   pl.ea_pb = pl.take(hermitian_entropy_pbuf((int)N) * 16);
@@ -210,19 +216,20 @@ struct fm_state {
   int* ee_sites;
   z64 *chk_cols, *chk_G;
   // Asynchronous entropy.  The caller's thread gathers the rows of A and
-  // forms C_A on the caller's stream (into one of kEaRing buffers); a library
+  // forms C_A on the caller's stream (into one of ea_ring buffers); a library
   // thread issues the eigen-solver launches (about 5 per row of C_A) on a
   // low-priority stream.  Steps then run on a high-priority stream bridged to
   // the caller's by events, so the FP64 eigen-solve fills what the steps'
   // kernels leave of each SM and the caller's thread never waits on the
   // launch queue.
   int dev;
-  z64* ea_M;                  // kEaRing x N x N
+  z64* ea_M;                  // ea_ring x N x N
+  int ea_ring;
   z64 *ea_vb, *ea_wb, *ea_pb;
   double *ea_d, *ea_e, *ea_lam, *ea_S;
   cudaStream_t ea_st, hp_st;
   cudaEvent_t hp_in, hp_out;
-  cudaEvent_t ea_M_ready[kEaRing], ea_M_free[kEaRing];
+  cudaEvent_t ea_M_ready[kEaRingMax], ea_M_free[kEaRingMax];
   cudaEvent_t ea_done[kAsyncSlots];
   double* ea_host;            // pinned, kAsyncSlots doubles
   void* pmw;                  // grid-wide projective update scratch
@@ -1081,7 +1088,7 @@ fm_status ea_setup(fm_state* s) {
   CK(cudaEventCreateWithFlags(&s->ee_buf_ev, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->hp_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->hp_out, cudaEventDisableTiming));
-  for (int i = 0; i < kEaRing; ++i) {
+  for (int i = 0; i < s->ea_ring; ++i) {
     CK(cudaEventCreateWithFlags(&s->ea_M_ready[i], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&s->ea_M_free[i], cudaEventDisableTiming));
   }
@@ -1110,7 +1117,7 @@ fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n
   if ((r = ea_check(s))) return r;
   const int64_t t = s->ea_next;
   const int slot = (int)(t % kAsyncSlots);
-  const int ring = (int)(t % kEaRing);
+  const int ring = (int)(t % s->ea_ring);
   const int N = s->N;
   const int m = std::min(n, N);
   if (t >= kAsyncSlots) {                                   // slot reuse: the oldest result must be back
@@ -1120,10 +1127,10 @@ fm_status entropy_async_impl(fm_state* s, int b, const int32_t* sites, int32_t n
   z64* M = s->ea_M + (int64_t)ring * N * N;
   int sketch_nA = 0;
   if (m > 0) {
-    // C_A buffer reuse: the eigen-solve of ticket t - kEaRing must be queued before
+    // C_A buffer reuse: the eigen-solve of ticket t - ea_ring must be queued before
     // the caller's stream may wait for it to release the buffer
-    if (t >= kEaRing) {
-      ea_wait_issued(s, t - kEaRing + 1);
+    if (t >= s->ea_ring) {
+      ea_wait_issued(s, t - s->ea_ring + 1);
       CK(cudaStreamWaitEvent(s->st, s->ea_M_free[ring], 0));
     }
     if (sketch_applicable(s, n)) {
@@ -1198,7 +1205,8 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ea_d = (double*)(w + pl.ea_d); s->ea_e = (double*)(w + pl.ea_e); s->ea_lam = (double*)(w + pl.ea_lam);
   s->ea_S = (double*)(w + pl.ea_S);
   s->ea_st = s->hp_st = nullptr; s->hp_in = s->hp_out = nullptr; s->ea_host = nullptr; s->ea_next = 0;
-  for (int i = 0; i < kEaRing; ++i) s->ea_M_ready[i] = s->ea_M_free[i] = nullptr;
+  s->ea_ring = ea_ring_size(s->N);
+  for (int i = 0; i < kEaRingMax; ++i) s->ea_M_ready[i] = s->ea_M_free[i] = nullptr;
   s->ea_issued = 0; s->ea_stop = false; s->ea_failed = false; s->ea_launches = 0;
   if (cudaGetDevice(&s->dev) != cudaSuccess) { delete s; return FM_ECUDA; }
   s->pmw = w + pl.pmw;
@@ -1872,7 +1880,7 @@ void fm_destroy(fm_state* s) {
     cudaStreamDestroy(s->hp_st);
     cudaEventDestroy(s->hp_in);
     cudaEventDestroy(s->hp_out);
-    for (int i = 0; i < kEaRing; ++i) {
+    for (int i = 0; i < s->ea_ring; ++i) {
       cudaEventDestroy(s->ea_M_ready[i]);
       cudaEventDestroy(s->ea_M_free[i]);
     }
