@@ -48,10 +48,10 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--propagation", choices=["dense", "banded"], default="dense",
                     help="dense L x L GEMM (the method as defined) or stencils of the circulant propagator")
-    ap.add_argument("--ee-method", choices=["sketch", "full"], default="sketch",
-                    help="entropy method of the in-window entropies (mixed precision): the cross-block "
-                         "sketch (falls back to the full method when it does not converge) or the full "
-                         "eigen-decomposition of C_A")
+    ap.add_argument("--ee-method", choices=["auto", "sketch", "full"], default="auto",
+                    help="entropy method of the in-window entropies (mixed precision): auto (the "
+                         "cross-block sketch for subsystems of 1024 sites or more, else the full "
+                         "method), the sketch, or the full eigen-decomposition of C_A")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -244,8 +244,8 @@ def run_ours(args, world, rank, local):
     if args.propagation == "banded":
         g.set_propagation(fm.FM_PROP_BANDED)
     ee_method = args.ee_method if precision == fm.FM_MIXED else "full"
-    if ee_method == "sketch":
-        g.set_entropy_method(fm.FM_EE_SKETCH)
+    if ee_method != "full":
+        g.set_entropy_method(fm.FM_EE_SKETCH if ee_method == "sketch" else fm.FM_EE_AUTO)
     ee_sites = workloads.half_chain(L)
     ee_every = wl["ee_every"]
 

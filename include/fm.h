@@ -200,9 +200,12 @@ fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out);
  * products.  The rank grows until the (r/8)-th smallest sigma^2 is below 1e-9;
  * if it never is, the full method runs instead.  Subsystems or complements
  * below 512 sites always take the full method.  The state keeps a snapshot of
- * U for this (asynchronous tickets keep theirs in their C_A buffer).  FM_EINVAL
- * for an FP64 state or an unknown method.  Synchronises. */
-enum { FM_EE_FULL = 0, FM_EE_SKETCH = 1 };
+ * U for this (asynchronous tickets keep theirs in their C_A buffer).
+ * FM_EE_AUTO (mixed precision): the sketch when A and its complement both
+ * have at least 1024 sites, the full method otherwise (the measured crossover:
+ * at 512 sites the full method is faster).  FM_EINVAL for FM_EE_SKETCH or
+ * FM_EE_AUTO on an FP64 state, or an unknown method.  Synchronises. */
+enum { FM_EE_FULL = 0, FM_EE_SKETCH = 1, FM_EE_AUTO = 2 };
 fm_status fm_set_entropy_method(fm_state* s, int32_t method);
 
 /* The last synchronous FM_EE_SKETCH entropy: the rank it settled on (0 if the

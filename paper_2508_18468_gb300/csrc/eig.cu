@@ -85,13 +85,25 @@ __global__ void __launch_bounds__(1024) tridiag_small_kernel(z64* M, int m, z64*
     z64* M22 = M + (k + 1) + (int64_t)(k + 1) * m;
     const z64 tau = reflector(col, n, vb, &sbeta, red, sh);
     if (threadIdx.x == 0) { d[k] = M[k + (int64_t)k * m].re; e[k] = sbeta; }
-    // p = M22 v ; s = v^dag p
+    // p = M22 v, one warp per row i: p_i = sum_j conj(M22[j, i]) v_j (M22 Hermitian, so
+    // the lanes read column i, contiguous); then s = v^dag p
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += (int)(blockDim.x >> 5)) {
+      const z64* ci = M22 + (int64_t)i * m;
+      double ar = 0.0, ai = 0.0;
+      for (int j = lane; j < n; j += 32) {
+        const z64 a = ci[j], x = vb[j];
+        ar += a.re * x.re + a.im * x.im;             // conj(a) x
+        ai += a.re * x.im - a.im * x.re;
+      }
+      ar = warp_sum(ar);
+      ai = warp_sum(ai);
+      if (lane == 0) wb[i] = cmk(ar, ai);
+    }
+    __syncthreads();
     double sr = 0.0, si = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      z64 acc = cmk(0.0, 0.0);
-      for (int j = 0; j < n; ++j) cfma(acc, M22[i + (int64_t)j * m], vb[j]);
-      wb[i] = acc;
-      const z64 t = cmul(cconj(vb[i]), acc);
+      const z64 t = cmul(cconj(vb[i]), wb[i]);
       sr += t.re; si += t.im;
     }
     const double s_re = bsum(sr, red);
@@ -101,13 +113,11 @@ __global__ void __launch_bounds__(1024) tridiag_small_kernel(z64* M, int m, z64*
     const z64 cs = cmk(t2 * s_re, t2 * s_im);
     for (int i = threadIdx.x; i < n; i += blockDim.x) wb[i] = csub(cmul(tau, wb[i]), cmul(cs, vb[i]));
     __syncthreads();
-    // M22 -= v w^dag + w v^dag
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const z64 vi = vb[i], wi = wb[i];
-      for (int j = 0; j < n; ++j) {
-        z64& a = M22[i + (int64_t)j * m];
-        a = csub(a, cadd(cmul(vi, cconj(wb[j])), cmul(wi, cconj(vb[j]))));
-      }
+    // M22 -= v w^dag + w v^dag, every element by its own thread (coalesced along i)
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx % n, j = idx / n;
+      z64& a = M22[i + (int64_t)j * m];
+      a = csub(a, cadd(cmul(vb[i], cconj(wb[j])), cmul(wb[i], cconj(vb[j]))));
     }
     __syncthreads();
   }
@@ -294,7 +304,10 @@ __device__ int sturm_count(const double* d, const double* e, int m, double x, do
   return c;
 }
 
-__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int m, double* lam) {
+// Eigenvalue q of the tridiagonal (d, e) by bisection, one thread per eigenvalue (large m:
+// enough threads to fill the GPU, and the fewest Sturm sequences).
+__global__ void bisect_thread_kernel(const double* __restrict__ d, const double* __restrict__ e, int m,
+                                     double* lam) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m) return;
   double lo = d[0], hi = d[0], emax2 = 0.0;
@@ -315,6 +328,50 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
     else lo = mid;
   }
   lam[q] = 0.5 * (lo + hi);
+}
+
+// Eigenvalue q of the tridiagonal (d, e) by multisection, one warp per eigenvalue (small
+// m, where one thread per eigenvalue leaves most of the GPU idle): each
+// round the 32 lanes count the eigenvalues below 32 interior points of [lo, hi] that
+// split it into 33 equal parts (one Sturm sequence per lane), and the part holding
+// eigenvalue q becomes the new interval -- ~5 bits per round instead of bisection's 1.
+// Gershgorin bounds and the stopping rule are bisection's: width <= 1e-18 + 2 eps |mid|.
+__global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ d, const double* __restrict__ e,
+                                                     int m, double* lam) {
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= m) return;                              // warp-uniform
+  double lo = INFINITY, hi = -INFINITY, emax2 = 0.0;
+  for (int i = lane; i < m; i += 32) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i + 1 < m) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+  }
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  const double span = fmax(fabs(lo), fabs(hi));
+  lo -= 2.0 * DBL_EPSILON * span + pivmin;
+  hi += 2.0 * DBL_EPSILON * span + pivmin;
+  for (int it = 0; it < 64; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 1e-18 + 2.0 * DBL_EPSILON * fabs(mid)) break;
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const bool above = (x > lo && x < hi) ? sturm_count(d, e, m, x, pivmin) > q : (x >= hi);
+    const unsigned b = __ballot_sync(0xffffffffu, above);
+    // points 0..k-1 have at most q eigenvalues below them, point k more (k = 32: none)
+    const int k = b ? __ffs(b) - 1 : 32;
+    const double nlo = k > 0 ? __shfl_sync(0xffffffffu, x, k - 1) : lo;
+    const double nhi = k < 32 ? __shfl_sync(0xffffffffu, x, k) : hi;
+    if (nlo == lo && nhi == hi) break;             // no representable progress
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) lam[q] = 0.5 * (lo + hi);
 }
 
 // S = -sum f(clamp(lambda, 0, 1)), one CTA, fixed order.  cross != 0: the inputs are
@@ -384,7 +441,10 @@ cudaError_t hermitian_entropy(cudaStream_t st, z64* M, int m, z64* vb, z64* wb, 
     last_diag_kernel<<<1, 1, 0, st>>>(M, m, (kl & 1) ? vb2 : vb, (kl & 1) ? wb2 : wb, d);
     ++launches;
   }
-  bisect_kernel<<<FM_CEIL_DIV(m, 64), 64, 0, st>>>(d, e, m, lam);
+  // measured: at m = 512 multisection brought the whole entropy from 34 ms to 21 ms; at
+  // m = 8192 (GPU already full) its 32 Sturm sequences per round cost more than they save
+  if (m <= 2048) bisect_kernel<<<FM_CEIL_DIV(m, 4), 128, 0, st>>>(d, e, m, lam);
+  else bisect_thread_kernel<<<FM_CEIL_DIV(m, 64), 64, 0, st>>>(d, e, m, lam);
   entropy_sum_kernel<<<1, 1024, 0, st>>>(lam, m, S, cross);
   launches += 2;
   if (nlaunch) *nlaunch += launches;

@@ -16,7 +16,7 @@ FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ENUMERIC, FM_ETIMEOUT, FM_ESTATE = ran
 FM_PROJECTIVE, FM_HOMODYNE, FM_HOMODYNE_RK4, FM_PROJECTIVE_POISSON = 0, 1, 2, 3
 FM_FP64, FM_MIXED = 0, 1
 FM_PROP_DENSE, FM_PROP_BANDED = 0, 1
-FM_EE_FULL, FM_EE_SKETCH = 0, 1
+FM_EE_FULL, FM_EE_SKETCH, FM_EE_AUTO = 0, 1, 2
 PHASES = ("propagate", "measure", "gram", "cholesky", "trmm", "entropy")
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENUMERIC",
                 5: "FM_ETIMEOUT", 6: "FM_ESTATE"}
@@ -238,7 +238,8 @@ class Trajectories:
         return out.value
 
     def set_entropy_method(self, method):
-        """FM_EE_FULL (eigenvalues of C_A) or FM_EE_SKETCH (cross-block sketch, mixed precision)."""
+        """FM_EE_FULL (eigenvalues of C_A), FM_EE_SKETCH (cross-block sketch) or FM_EE_AUTO
+        (the sketch from 1024 sites on), the last two for mixed precision."""
         self._check(lib.fm_set_entropy_method(self._h, int(method)))
 
     def entropy_sketch_info(self):

@@ -136,3 +136,18 @@ def test_sketch_method_needs_mixed_precision(fm):
     assert g2.entropy_sketch_info()[2]
     g2.set_entropy_method(fm.FM_EE_FULL)
     assert g2.entropy(list(range(64))) == s
+
+
+def test_auto_method_picks_by_size(fm):
+    """FM_EE_AUTO: the sketch for subsystems (and complements) of 1024 sites or more, the
+    full method below; each result equals that method's."""
+    g = fm.Trajectories(fm.make_params(4096, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED, gamma=0.5, seed=19))
+    g.step(20)
+    big, small = list(range(2048)), list(range(700))
+    g.set_entropy_method(fm.FM_EE_SKETCH)
+    s_big = g.entropy(big)
+    g.set_entropy_method(fm.FM_EE_FULL)
+    f_small = g.entropy(small)
+    g.set_entropy_method(fm.FM_EE_AUTO)
+    assert g.entropy(big) == s_big and not g.entropy_sketch_info()[2]
+    assert g.entropy(small) == f_small and g.entropy_sketch_info()[2]
