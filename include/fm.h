@@ -173,7 +173,9 @@ fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, do
  * order with the steps (one of the workspace's C_A buffers: as many as fit in
  * 4 GiB, between 4 and 64, 16 N^2 bytes each); the FP64
  * eigen-solve (Householder tridiagonalisation, about 5 launches per row of
- * C_A) is issued by a library-owned host thread onto a low-priority stream.
+ * C_A) is issued by library-owned host threads, each onto its own low-priority
+ * stream (1 to 4 threads: as many as fit their scratch in 1 GiB, so that small
+ * eigen-solves run side by side; tickets may then complete out of order).
  * From the first call on, fm_step runs its kernels on a high-priority stream
  * ordered after and before the caller's stream by events, so later steps
  * proceed while the eigen-solve fills what their kernels leave of each SM.

@@ -1,6 +1,7 @@
 // Blocked Cholesky G = R^dag R (upper R) and triangular inverse T = R^-1,
 // batched over trajectories.  Diagonal 32 x 32 blocks are factored and
 // inverted by one CTA each; panels and trailing updates are complex GEMMs.
+#include <mutex>
 #include <algorithm>
 
 #include "kernels.h"
@@ -229,9 +230,11 @@ __global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restri
 cudaError_t chol_inv_leaf(cudaStream_t st, const c32* G, c32* R, c32* T, int n, int64_t ld, int64_t sNN, int B,
                           int* status) {
   if (n < 1 || n > kLeafMax) return cudaErrorInvalidValue;
-  static cudaError_t attr = cudaErrorNotReady;
-  if (attr == cudaErrorNotReady)
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
     attr = cudaFuncSetAttribute(chol_inv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmem);
+  });
   if (attr != cudaSuccess) return attr;
   chol_inv_leaf_kernel<<<B, 1024, kLeafSmem, st>>>(G, R, T, n, ld, sNN, status);
   return cudaGetLastError();

@@ -29,6 +29,10 @@ const int kAsyncSlots = 64;    // outstanding asynchronous entropies
 // C_A buffers of the asynchronous entropies: as many as fit in 4 GiB, 4 to 64 (many
 // small trajectories then keep their tickets in flight together)
 const int kEaRingMax = 64;
+// library threads of the asynchronous entropies: as many as fit their scratch in 1 GiB, 1
+// to 4 (small eigen-solves are latency-bound: several run side by side)
+const int kEaWorkersMax = 4;
+const int kEaIssuedCap = 256;   // > outstanding tickets (64 results, 64 C_A buffers)
 int ea_ring_size(int64_t N) {
   const int64_t per = 16 * N * N;
   return (int)std::max<int64_t>(4, std::min<int64_t>(kEaRingMax, (int64_t(4) << 30) / std::max<int64_t>(per, 1)));
@@ -64,7 +68,8 @@ struct Plan {
   size_t V, V2, Vh, Vl, Ah, Al, Th, Tl, aux;           // mixed path
   size_t ee_vb, ee_wb, ee_pb, ee_d, ee_e, ee_lam, ee_S, ee_sites, ee_max;
   size_t chk_cols, chk_G;                               // orthonormality check (<= 64 columns)
-  size_t ea_M, ea_vb, ea_wb, ea_pb, ea_d, ea_e, ea_lam, ea_S;   // asynchronous entropy
+  size_t ea_M, ea_vb, ea_wb, ea_pb, ea_d, ea_e, ea_lam, ea_S;   // asynchronous entropy (ea_vb .. ea_lam per worker)
+  int ea_workers = 1;
   size_t pmw;                                           // grid-wide projective update
   size_t xg;                                            // exact-product Gram of C_A (mixed)
   size_t gfull;                                         // exact Gram of all of U (mixed)
@@ -104,6 +109,15 @@ bool valid_params(const fm_params* p, std::string* why) {
   return true;
 }
 
+// library threads of the asynchronous entropies for these parameters (kEaWorkersMax at most)
+int ea_workers(const fm_params& p) {
+  const int64_t L = (int64_t)p.Lx * p.Ly, N = L / 2;
+  int64_t per = 2 * N * 16 + hermitian_entropy_pbuf((int)N) * 16 + 3 * N * 8;
+  const int rmax = p.precision == FM_MIXED ? sketch_rmax(N) : 0;
+  if (rmax) per += (int64_t)sketch_scratch_bytes((int)L, (int)N, rmax);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kEaWorkersMax, (int64_t(1) << 30) / std::max<int64_t>(per, 1)));
+}
+
 Plan make_plan(const fm_params& p) {
   Plan pl;
   const int64_t L = (int64_t)p.Lx * p.Ly, N = L / 2, B = p.batch;
@@ -140,12 +154,13 @@ Plan make_plan(const fm_params& p) {
   pl.chk_cols = pl.take(L * std::min<int64_t>(N, 64) * 16);
   pl.chk_G = pl.take(std::min<int64_t>(N, 64) * N * 16);
   pl.ea_M = pl.take(ea_ring_size(N) * N * N * 16);
-  pl.ea_vb = pl.take(N * 16);
-  pl.ea_wb = pl.take(N * 16);
-  pl.ea_pb = pl.take(hermitian_entropy_pbuf((int)N) * 16);
-  pl.ea_d = pl.take(N * 8);
-  pl.ea_e = pl.take(N * 8);
-  pl.ea_lam = pl.take(N * 8);
+  pl.ea_workers = ea_workers(p);
+  pl.ea_vb = pl.take(pl.ea_workers * N * 16);
+  pl.ea_wb = pl.take(pl.ea_workers * N * 16);
+  pl.ea_pb = pl.take(pl.ea_workers * hermitian_entropy_pbuf((int)N) * 16);
+  pl.ea_d = pl.take(pl.ea_workers * N * 8);
+  pl.ea_e = pl.take(pl.ea_workers * N * 8);
+  pl.ea_lam = pl.take(pl.ea_workers * N * 8);
   pl.ea_S = pl.take(kAsyncSlots * 8);
   pl.pmw = pl.take(pm_wide_scratch_bytes((int)L, (int)B));
   pl.obs = pl.take((L + abs2_partials() + 8) * 8);
@@ -174,7 +189,7 @@ Plan make_plan(const fm_params& p) {
     if (rmax) {
       pl.sk_snap = pl.take(L * N * 8);
       pl.sk_sync = pl.take(sketch_scratch_bytes((int)L, (int)N, rmax));
-      pl.sk_async = pl.take(sketch_scratch_bytes((int)L, (int)N, rmax));
+      pl.sk_async = pl.take(pl.ea_workers * align256(sketch_scratch_bytes((int)L, (int)N, rmax)));
     }
     pl.sk_res = pl.take(64);
   }
@@ -229,9 +244,18 @@ struct fm_state {
   int dev;
   z64* ea_M;                  // ea_ring x N x N
   int ea_ring;
-  z64 *ea_vb, *ea_wb, *ea_pb;
-  double *ea_d, *ea_e, *ea_lam, *ea_S;
-  cudaStream_t ea_st, hp_st;
+  // one library thread per worker, each with its own low-priority stream and scratch
+  struct EaWorker {
+    std::thread th;
+    cudaStream_t st = nullptr;
+    z64 *vb, *wb, *pb;
+    double *d, *e, *lam, *chk;
+    SketchScratch sk;
+  };
+  int ea_nw;
+  EaWorker ea_w[kEaWorkersMax];
+  double* ea_S;
+  cudaStream_t ea_st, hp_st;  // ea_st: worker 0's stream
   cudaEvent_t hp_in, hp_out;
   cudaEvent_t ea_M_ready[kEaRingMax], ea_M_free[kEaRingMax];
   cudaEvent_t ea_done[kAsyncSlots];
@@ -260,8 +284,8 @@ struct fm_state {
   int ee_method;
   int sk_rmax;
   c32* sk_snap;
-  SketchScratch sk_sync, sk_async;
-  double* sk_res;             // [0] S, [1] check (synchronous); [2] check (library thread)
+  SketchScratch sk_sync;
+  double* sk_res;             // [0] S, [1] check (synchronous); [2 + w] check (library thread w)
   int sk_last_rank;
   double sk_last_chk;
   int sk_last_fallback;
@@ -272,11 +296,11 @@ struct fm_state {
   cudaEvent_t ee_buf_ev;
   int64_t ea_next;            // next ticket
   struct EaJob { int64_t t; int slot, ring, m, sketch_nA; };   // sketch_nA > 0: the ring holds a snapshot
-  std::thread ea_thread;
+  std::vector<char> ea_issued_flag;   // tickets done, by ticket % kEaIssuedCap
   std::mutex ea_mu;
   std::condition_variable ea_cv;
   std::deque<EaJob> ea_q;
-  int64_t ea_issued;          // tickets whose launches are all enqueued (in ticket order)
+  int64_t ea_issued;          // every ticket below it has all its launches enqueued
   bool ea_stop;
   bool ea_failed;
   std::string ea_errmsg;
@@ -1000,9 +1024,11 @@ fm_status retune(fm_state* s, int tile_config, int reorth) {
 }
 
 // ------------------------------------------------------------------ asynchronous entropy
-// The library thread: for each job, wait for its C_A, run the eigen-solver on
-// ea_st, copy S to the pinned slot and record the slot's event.  Launch errors
-// are kept for fm_entropy_wait (the state's error fields belong to the caller).
+// The library threads (ea_nw of them, each with its own low-priority stream and
+// scratch): for each job, wait for its C_A (or snapshot), run the eigen-solver or the
+// sketch on the thread's stream, copy S to the pinned slot and record the slot's event.
+// Launch errors are kept for fm_entropy_wait (the state's error fields belong to the
+// caller).
 // The full method from an asynchronous ticket's snapshot (U, A's nA rows first, ld L,
 // complex64) on the library thread: the exact Gram of all rows (the projector
 // correction's U^dag U), then C_A of the smaller of A and its complement (the same
@@ -1022,8 +1048,10 @@ cudaError_t sketch_fallback(fm_state* s, cudaStream_t st, z64* slot, int nA, int
   return e;
 }
 
-void ea_worker(fm_state* s) {
+void ea_worker(fm_state* s, int wk) {
   cudaSetDevice(s->dev);
+  fm_state::EaWorker& ew = s->ea_w[wk];
+  const cudaStream_t st = ew.st;
   for (;;) {
     fm_state::EaJob j;
     {
@@ -1033,7 +1061,7 @@ void ea_worker(fm_state* s) {
       j = s->ea_q.front();
       s->ea_q.pop_front();
     }
-    cudaError_t e = cudaStreamWaitEvent(s->ea_st, s->ea_M_ready[j.ring], 0);
+    cudaError_t e = cudaStreamWaitEvent(st, s->ea_M_ready[j.ring], 0);
     const char* what = "cudaStreamWaitEvent";
     z64* M = s->ea_M + (int64_t)j.ring * s->N * s->N;
     int m = j.m;
@@ -1043,8 +1071,8 @@ void ea_worker(fm_state* s) {
       double chk = 0.0;
       int64_t nl = 0;
       std::string err;
-      const int c = run_sketch(s, s->ea_st, (const c32*)M, j.sketch_nA, s->sk_async, s->ea_S + j.slot,
-                               s->sk_res + 2, &nl, &rank, &chk, &err);
+      const int c = run_sketch(s, st, (const c32*)M, j.sketch_nA, ew.sk, s->ea_S + j.slot, ew.chk, &nl, &rank, &chk,
+                               &err);
       s->ea_launches += nl;
       if (c < 0) {
         e = cudaErrorLaunchFailure;
@@ -1054,35 +1082,39 @@ void ea_worker(fm_state* s) {
       } else {
         // not converged: C_A of the smaller side from the snapshot, then the full method
         nl = 0;
-        e = sketch_fallback(s, s->ea_st, M, j.sketch_nA, &m, &nl);
+        e = sketch_fallback(s, st, M, j.sketch_nA, &m, &nl);
         s->ea_launches += nl;
         what = "entropy fallback";
       }
     }
     if (e == cudaSuccess && !done) {
       if (m == 0) {
-        e = cudaMemsetAsync(s->ea_S + j.slot, 0, sizeof(double), s->ea_st);
+        e = cudaMemsetAsync(s->ea_S + j.slot, 0, sizeof(double), st);
         what = "cudaMemsetAsync";
       } else {
         int nl = 0;
-        e = hermitian_entropy(s->ea_st, M, m, s->ea_vb, s->ea_wb, s->ea_pb, nullptr, s->ea_d, s->ea_e, s->ea_lam,
-                              s->ea_S + j.slot, &nl);
+        e = hermitian_entropy(st, M, m, ew.vb, ew.wb, ew.pb, nullptr, ew.d, ew.e, ew.lam, s->ea_S + j.slot, &nl);
         s->ea_launches += nl;
         what = "eigen-solver launch";
       }
     }
     if (e == cudaSuccess) {
-      e = cudaMemcpyAsync(s->ea_host + j.slot, s->ea_S + j.slot, sizeof(double), cudaMemcpyDeviceToHost, s->ea_st);
+      e = cudaMemcpyAsync(s->ea_host + j.slot, s->ea_S + j.slot, sizeof(double), cudaMemcpyDeviceToHost, st);
       what = "cudaMemcpyAsync";
     }
-    if (e == cudaSuccess) e = cudaEventRecord(s->ea_M_free[j.ring], s->ea_st);
-    if (e == cudaSuccess) e = cudaEventRecord(s->ea_done[j.slot], s->ea_st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ea_M_free[j.ring], st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ea_done[j.slot], st);
     std::lock_guard<std::mutex> lk(s->ea_mu);
     if (e != cudaSuccess && !s->ea_failed) {
       s->ea_failed = true;
       s->ea_errmsg = std::string("asynchronous entropy: ") + what + ": " + cudaGetErrorString(e);
     }
-    s->ea_issued = j.t + 1;
+    // tickets finish out of order across the threads: advance the issued prefix
+    s->ea_issued_flag[j.t % kEaIssuedCap] = 1;
+    while (s->ea_issued_flag[s->ea_issued % kEaIssuedCap]) {
+      s->ea_issued_flag[s->ea_issued % kEaIssuedCap] = 0;
+      ++s->ea_issued;
+    }
     s->ea_cv.notify_all();
   }
 }
@@ -1091,7 +1123,9 @@ fm_status ea_setup(fm_state* s) {
   if (s->ea_st) return FM_OK;
   int least = 0, greatest = 0;
   CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-  CK(cudaStreamCreateWithPriority(&s->ea_st, cudaStreamNonBlocking, least));
+  for (int k = 0; k < s->ea_nw; ++k)
+    CK(cudaStreamCreateWithPriority(&s->ea_w[k].st, cudaStreamNonBlocking, least));
+  s->ea_st = s->ea_w[0].st;
   CK(cudaStreamCreateWithPriority(&s->hp_st, cudaStreamNonBlocking, greatest));
   CK(cudaEventCreateWithFlags(&s->ee_buf_ev, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->hp_in, cudaEventDisableTiming));
@@ -1103,7 +1137,7 @@ fm_status ea_setup(fm_state* s) {
   for (int i = 0; i < kAsyncSlots; ++i) CK(cudaEventCreateWithFlags(&s->ea_done[i], cudaEventDisableTiming));
   CK(cudaHostAlloc((void**)&s->ea_host, kAsyncSlots * sizeof(double), cudaHostAllocDefault));
   s->ea_stop = false;
-  s->ea_thread = std::thread(ea_worker, s);
+  for (int k = 0; k < s->ea_nw; ++k) s->ea_w[k].th = std::thread(ea_worker, s, k);
   return FM_OK;
 }
 
@@ -1209,8 +1243,18 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ee_S = (double*)(w + pl.ee_S); s->ee_max = (double*)(w + pl.ee_max); s->ee_sites = (int*)(w + pl.ee_sites);
   s->chk_cols = (z64*)(w + pl.chk_cols); s->chk_G = (z64*)(w + pl.chk_G);
   s->ea_M = (z64*)(w + pl.ea_M);
-  s->ea_vb = (z64*)(w + pl.ea_vb); s->ea_wb = (z64*)(w + pl.ea_wb); s->ea_pb = (z64*)(w + pl.ea_pb);
-  s->ea_d = (double*)(w + pl.ea_d); s->ea_e = (double*)(w + pl.ea_e); s->ea_lam = (double*)(w + pl.ea_lam);
+  s->ea_nw = pl.ea_workers;
+  for (int k = 0; k < s->ea_nw; ++k) {
+    fm_state::EaWorker& ew = s->ea_w[k];
+    const int64_t Nn = p->Lx * (int64_t)p->Ly / 2;
+    ew.vb = (z64*)(w + pl.ea_vb) + k * Nn;
+    ew.wb = (z64*)(w + pl.ea_wb) + k * Nn;
+    ew.pb = (z64*)(w + pl.ea_pb) + k * hermitian_entropy_pbuf((int)Nn);
+    ew.d = (double*)(w + pl.ea_d) + k * Nn;
+    ew.e = (double*)(w + pl.ea_e) + k * Nn;
+    ew.lam = (double*)(w + pl.ea_lam) + k * Nn;
+  }
+  s->ea_issued_flag.assign(kEaIssuedCap, 0);
   s->ea_S = (double*)(w + pl.ea_S);
   s->ea_st = s->hp_st = nullptr; s->hp_in = s->hp_out = nullptr; s->ea_host = nullptr; s->ea_next = 0;
   s->ea_ring = ea_ring_size(s->N);
@@ -1233,9 +1277,11 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
     const int Lh = p->Lx * p->Ly, Nh = Lh / 2;
     s->sk_snap = (c32*)(w + pl.sk_snap);
     s->sk_sync = sketch_layout(w + pl.sk_sync, Lh, Nh, s->sk_rmax);
-    s->sk_async = sketch_layout(w + pl.sk_async, Lh, Nh, s->sk_rmax);
+    const size_t skb = align256(sketch_scratch_bytes(Lh, Nh, s->sk_rmax));
+    for (int k = 0; k < s->ea_nw; ++k) s->ea_w[k].sk = sketch_layout(w + pl.sk_async + k * skb, Lh, Nh, s->sk_rmax);
   }
   s->sk_res = (double*)(w + pl.sk_res);
+  for (int k = 0; k < s->ea_nw; ++k) s->ea_w[k].chk = s->sk_res + 2 + k;
   s->sk_last_rank = 0; s->sk_last_chk = 0.0; s->sk_last_fallback = 0;
   s->ee_buf_ev = nullptr;
   {
@@ -1501,7 +1547,8 @@ fm_status fm_set_entropy_method(fm_state* s, int32_t method) {
   if (method != FM_EE_FULL && s->prm.precision != FM_MIXED)
     return fail(s, FM_EINVAL, "the entropy sketch needs a mixed-precision state");
   CK(cudaStreamSynchronize(s->st));
-  if (s->ea_st) CK(cudaStreamSynchronize(s->ea_st));
+  for (int k = 0; k < s->ea_nw; ++k)
+    if (s->ea_w[k].st) CK(cudaStreamSynchronize(s->ea_w[k].st));
   s->ee_method = method;
   return FM_OK;
 }
@@ -1882,10 +1929,14 @@ void fm_destroy(fm_state* s) {
       s->ea_stop = true;
     }
     s->ea_cv.notify_all();
-    if (s->ea_thread.joinable()) s->ea_thread.join();   // the thread drains its queue first
-    cudaStreamSynchronize(s->ea_st);
+    for (int k = 0; k < s->ea_nw; ++k)
+      if (s->ea_w[k].th.joinable()) s->ea_w[k].th.join();   // the threads drain the queue first
+    for (int k = 0; k < s->ea_nw; ++k)
+      if (s->ea_w[k].st) {
+        cudaStreamSynchronize(s->ea_w[k].st);
+        cudaStreamDestroy(s->ea_w[k].st);
+      }
     cudaStreamSynchronize(s->hp_st);
-    cudaStreamDestroy(s->ea_st);
     cudaStreamDestroy(s->hp_st);
     cudaEventDestroy(s->hp_in);
     cudaEventDestroy(s->hp_out);

@@ -11,6 +11,8 @@
 // Warp 0 issues TMA, warp 1 issues MMAs (one thread), warp 2 owns TMEM,
 // warps 4-7 drain TMEM into the mode's epilogue.  Every wait is bounded and
 // raises FM_DEVERR_TIMEOUT instead of hanging.
+#include <atomic>
+#include <mutex>
 #include <cudaTypedefs.h>
 
 #include <vector>
@@ -373,8 +375,11 @@ static cudaError_t set_smem() {
 // Shared-memory opt-in of every instantiation, done once before any launch (so
 // that no attribute call falls inside a stream capture).
 cudaError_t configure_all() {
-  static cudaError_t done = cudaErrorNotReady;
-  if (done == cudaSuccess) return done;
+  static std::atomic<bool> done{false};
+  static std::mutex mu;
+  if (done.load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.load(std::memory_order_relaxed)) return cudaSuccess;
   cudaError_t e;
   if ((e = set_smem<256, 0, MODE_PLAIN>()) || (e = set_smem<128, 0, MODE_PLAIN>()) ||
       (e = set_smem<128, 1, MODE_PLAIN>()) || (e = set_smem<256, 0, MODE_PROP>()) ||
@@ -383,8 +388,8 @@ cudaError_t configure_all() {
       (e = set_smem<128, 0, MODE_TRMM>()) || (e = set_smem<256, 0, MODE_TRMM>()) ||
       (e = set_smem<128, 0, MODE_ADDV>()) || (e = set_smem<256, 0, MODE_ADDV>()))
     return e;
-  done = cudaSuccess;
-  return done;
+  done.store(true, std::memory_order_release);
+  return cudaSuccess;
 }
 
 template <int BN, int CH, int MODE>
@@ -447,13 +452,12 @@ std::vector<int4> tile_list(int mtiles, int ntiles, int batch, int parts, bool u
 }
 
 int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, c = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    return c > 0 ? c : 1;
+  }();
   return n;
 }
 
