@@ -44,6 +44,16 @@ unsigned long long fmx_exact_gram_scratch_bytes(int nmax, int N);
  * same routine the mixed-precision entropy uses for m > 256. */
 int fmx_exact_gram(const void* X, int n, int N, void* M, void* d_scratch, void* stream);
 
+/* Cholesky factor and inverse of B Hermitian blocks on the CUDA cores, the leaf
+ * of the mixed-precision CholeskyQR's recursive factorisation (Sec. III,
+ * CholeskyQR2): G_b = R_b^dag R_b, R_b upper triangular with a real positive
+ * diagonal, T_b = R_b^-1.  G, R, T: complex64 (re, im float pairs), n x n
+ * column-major with leading dimension ld, block b at offset b * ld * n; only
+ * the upper triangle of G is read; R and T are written in full (zeros below
+ * the diagonal).  1 <= n <= 128.  A non-positive or non-finite pivot ORs 1
+ * into *d_status (device int) and the factorisation continues with pivot 1. */
+int fmx_chol_leaf(const void* G, int n, int ld, int B, void* R, void* T, int* d_status, void* stream);
+
 /* Host-only hooks of the continuous-time projective protocol (no device
  * needed).  fmx_poisson_draw: the draws of event e of trajectory traj under
  * seed, out[0] = u_wait, out[1] = site, out[2] = Born draw.  fmx_poisson_taps:

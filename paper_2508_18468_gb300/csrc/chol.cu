@@ -61,157 +61,233 @@ template cudaError_t cholesky_inverse<float>(cudaStream_t, c32*, c32*, c32*, c32
 
 // ------------------------------------------------------------------ one-CTA leaf
 // G = R^dag R and T = R^-1 for an n x n block (n <= 128) of every trajectory,
-// complex64, one CTA of 1024 threads per trajectory.  Thread (warp w, lane l)
-// keeps the elements (w + 32q, l + 32p), q, p = 0..3, of the upper triangle in
-// registers.
-//   Cholesky, right-looking with the rows left unscaled: step j reads the final
-//   row j and its pivot d_j from shared memory and updates every element r, c
-//   with j < r <= c by a_rc -= conj(a_jr) a_jc / d_j; the owners of row j + 1
-//   then store it (now final), one barrier per step.  Afterwards
-//   R_jc = a_jc / sqrt(d_j).
-//   Inverse, by rows from the bottom: W = 1; row j of T is W_j / R_jj once every
-//   row below it has been subtracted, W_i -= R_ij T_j (i < j).  T is kept
-//   transposed in the strict lower triangle of the same array, its diagonal
-//   apart; again one barrier per step.
-// R and T are written with zeros below the diagonal.  A non-positive pivot
-// raises FM_DEVERR_PIVOT and continues with pivot 1.
+// complex64, one CTA of 256 threads per trajectory, blocked by 32:
+//   for each diagonal block k: one warp factors it (lane c owns column c; step j
+//   scales row j by 1 / sqrt(pivot) and every lane updates its column with it)
+//   and inverts its triangle by columns; the
+//   CTA then forms the panel R_k,> = T_kk^dag G_k,> and the trailing update
+//   G_>,> -= R_k,>^dag R_k,> (upper triangle);
+//   then each block column j of T above the diagonal:
+//   T_<j,j = -(T_<j,<j R_<j,j) T_jj, the inner product kept in shared memory.
+// R is kept in the upper triangle of a shared array, T transposed in its strict
+// lower triangle and T's diagonal apart: 20 CTA barriers per 128 x 128 leaf
+// instead of one per row.  R and T are written with zeros below the diagonal.
+// A non-positive pivot raises FM_DEVERR_PIVOT and continues with pivot 1.
 namespace fm {
 
 constexpr int kLeafMax = 128;
 constexpr int kLeafLd = kLeafMax + 1;
-constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + 2 * kLeafMax) * sizeof(c32);
+constexpr int kLeafThreads = 256;
+constexpr int kLeafYLd = 33;
+constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + kLeafMax + 96 * kLeafYLd) * sizeof(c32) +
+                              kLeafMax * sizeof(float);
 
-__global__ void __launch_bounds__(1024) chol_inv_leaf_kernel(const c32* __restrict__ G, c32* R, c32* T, int n,
-                                                             int64_t ld, int64_t sNN, int* status) {
+// Factor and invert the m x m (m <= 32) diagonal block at D (row stride kLeafLd),
+// one warp, lane c owning column c: R into the upper triangle of D, T = R^-1
+// transposed into its strict lower triangle (row c of the lower triangle holds
+// column c of T, which only lane c touches), T's diagonal into Tdk, 1 / R_jj into
+// Rinv.  Loops stay rolled (a fully unrolled factorisation overflows the
+// instruction cache); the column updates go in chunks of 8 rows, loads first, so
+// that each chunk waits for shared memory once.  Returns true after a bad pivot.
+__device__ __forceinline__ bool leaf_diag_block(c32* D, c32* Tdk, float* Rinv, int m, int c) {
+  bool bad = false;
+  for (int j = 0; j < m; ++j) {
+    float piv = D[j * kLeafLd + j].re;
+    if (!(piv > 0.0f) || !isfinite(piv)) {
+      bad = true;
+      piv = 1.0f;
+    }
+    const float rs = sqrtf(piv), ri = __frcp_rn(rs);
+    if (c == 0) Rinv[j] = ri;
+    c32 rjc = cmk(0.0f, 0.0f);
+    if (c >= j && c < m) {
+      rjc = c == j ? cmk(rs, 0.0f) : cscale(D[j * kLeafLd + c], ri);
+      D[j * kLeafLd + c] = rjc;                 // row j of R is final
+    }
+    __syncwarp();
+    if (c > j && c < m) {
+      for (int r0 = j + 1; r0 <= c; r0 += 8) {
+        c32 x[8], y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r = min(r0 + u, 31);
+          x[u] = D[j * kLeafLd + r];            // R_jr: one address for the warp
+          y[u] = D[r * kLeafLd + c];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) y[u] = csub(y[u], cmul(cconj(x[u]), rjc));
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (r0 + u <= c) D[(r0 + u) * kLeafLd + c] = y[u];
+      }
+    }
+    __syncwarp();
+  }
+  // column c of T by back substitution R t = e_c, column-oriented: t_k = w_k / R_kk,
+  // then w_i -= R_ik t_k for i < k (every lane at the same k: R_ik is one address)
+  if (c < m) {
+    for (int i = 0; i < c; ++i) D[c * kLeafLd + i] = cmk(0.0f, 0.0f);
+    Tdk[c] = cmk(1.0f, 0.0f);
+  }
+  __syncwarp();
+  for (int k = m - 1; k >= 0; --k) {
+    if (c >= k && c < m) {
+      c32* wk = c == k ? &Tdk[c] : &D[c * kLeafLd + k];
+      const c32 t = cscale(*wk, Rinv[k]);
+      *wk = t;
+      for (int i0 = 0; i0 < k; i0 += 8) {
+        c32 x[8], y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = min(i0 + u, 31);
+          x[u] = D[i * kLeafLd + k];
+          y[u] = D[c * kLeafLd + i];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) y[u] = csub(y[u], cmul(x[u], t));
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u < k) D[c * kLeafLd + i0 + u] = y[u];
+      }
+    }
+  }
+  __syncwarp();
+  return bad;
+}
+
+__global__ void __launch_bounds__(kLeafThreads, 1) chol_inv_leaf_kernel(const c32* __restrict__ G, c32* R, c32* T,
+                                                                        int n, int64_t ld, int64_t sNN, int* status) {
   extern __shared__ c32 sm[];
   c32* A = sm;                                  // A[r * kLeafLd + c]
   c32* Td = sm + kLeafMax * kLeafLd;            // diagonal of T
-  float* Rd = (float*)(Td + kLeafMax);          // sqrt of the pivots
+  c32* Y = Td + kLeafMax;                       // panel staging (32 x 96), products of the inverse (96 x 32)
+  float* Rinv = (float*)(Y + 96 * kLeafYLd);    // 1 / R_jj
   const int64_t b = blockIdx.x;
   G += b * sNN;
   R += b * sNN;
   T += b * sNN;
-  const int tid = threadIdx.x, l = tid & 31, w = tid >> 5;
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int r = idx % n, c = idx / n;
-    if (r <= c) A[r * kLeafLd + c] = G[r + (int64_t)c * ld];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int base = tid; base < n * n; base += 8 * kLeafThreads) {   // 8 loads in flight per thread
+    c32 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * kLeafThreads, r = idx % n, c = idx / n;
+      v[u] = (idx < n * n && r <= c) ? G[r + (int64_t)c * ld] : cmk(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * kLeafThreads, r = idx % n, c = idx / n;
+      if (idx < n * n && r <= c) A[r * kLeafLd + c] = v[u];
+    }
   }
   __syncthreads();
-  c32 a[4][4];
+  const int nb = (n + 31) / 32;
+  bool bad = false;
+  for (int kb = 0; kb < nb; ++kb) {
+    const int o = 32 * kb, m = min(32, n - o), rest = n - o - m;   // rest > 0 implies m == 32
+    if (warp == 0) bad |= leaf_diag_block(A + o * kLeafLd + o, Td + o, Rinv + o, m, lane);
+    __syncthreads();
+    if (rest == 0) break;
+    // panel R_{o+r, c} = sum_{i <= r} conj(T_{o+i, o+r}) G_{o+i, c}: items (8 rows, column),
+    // staged in Y (32 x 96) until every item has read G
+    const int items = 4 * rest;
+    for (int e = tid; e < items; e += kLeafThreads) {
+      const int cidx = e % rest, r0 = 8 * (e / rest), cp = o + 32 + cidx;
+      c32 acc[8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+      for (int rr = 0; rr < 8; ++rr) acc[rr] = cmk(0.0f, 0.0f);
+      for (int i = 0; i < r0; ++i) {            // rows r0 .. r0 + 7 all below i
+        const c32 a = A[(o + i) * kLeafLd + cp];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int r = w + 32 * q, c = l + 32 * p;
-      a[q][p] = (r <= c && c < n) ? A[r * kLeafLd + c] : cmk(0.0f, 0.0f);
-    }
-  // ---- Cholesky (unscaled rows)
-  for (int j = 0; j + 1 < n; ++j) {
-    float d = A[j * kLeafLd + j].re;
-    if (!(d > 0.0f) || !isfinite(d)) {
-      if (tid == 0) atomicOr(status, FM_DEVERR_PIVOT);
-      d = 1.0f;
-    }
-    const float inv = 1.0f / d;
-    c32 pc[4];
+        for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], cconj(A[(o + r0 + rr) * kLeafLd + o + i]), a);
+      }
+      for (int i = r0; i < r0 + 8; ++i) {       // the 8 x 8 triangle
+        const c32 a = A[(o + i) * kLeafLd + cp];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int c = l + 32 * p;
-      pc[p] = (c > j && c < n) ? cscale(A[j * kLeafLd + c], inv) : cmk(0.0f, 0.0f);
-    }
-    // rows r = w + 32 q and column groups p are warp-uniform: skip the finished ones
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = w + 32 * q;
-      if (r > j && r < n) {
-        const c32 prc = cconj(A[j * kLeafLd + r]);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          if (32 * p + 31 >= r) {
-            const int c = l + 32 * p;
-            if (c >= r && c < n) a[q][p] = csub(a[q][p], cmul(prc, pc[p]));
-          }
+        for (int rr = 0; rr < 8; ++rr) {
+          const int r = r0 + rr;
+          if (r > i) cfma(acc[rr], cconj(A[(o + r) * kLeafLd + o + i]), a);
+          else if (r == i) cfma(acc[rr], cconj(Td[o + i]), a);
         }
       }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) Y[(r0 + rr) * 96 + cidx] = acc[rr];
     }
-    // row j + 1 is final: its owners store it
-    const int nr = j + 1;
-    if (w == (nr & 31)) {
-      const int q = nr >> 5;
+    __syncthreads();
+    for (int e = tid; e < 32 * rest; e += kLeafThreads) {
+      const int r = e / rest, cidx = e % rest;
+      A[(o + r) * kLeafLd + o + 32 + cidx] = Y[r * 96 + cidx];
+    }
+    __syncthreads();
+    // trailing update of the upper triangle: items (8 rows, column), rows <= column
+    int tot = 0;
+    for (int q = 0; 8 * q < rest; ++q) tot += rest - 8 * q;
+    for (int e = tid; e < tot; e += kLeafThreads) {
+      int q = 0, base = 0;
+      while (e >= base + rest - 8 * q) {
+        base += rest - 8 * q;
+        ++q;
+      }
+      const int ci = 8 * q + (e - base), c = o + 32 + ci, rb = o + 32 + 8 * q;
+      c32 s8[8];
 #pragma unroll
-      for (int qq = 0; qq < 4; ++qq)
-        if (qq == q)
+      for (int rr = 0; rr < 8; ++rr) s8[rr] = cmk(0.0f, 0.0f);
+#pragma unroll 2
+      for (int i = 0; i < 32; ++i) {
+        const c32 a = A[(o + i) * kLeafLd + c];
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int c = l + 32 * p;
-            if (c >= nr && c < n) A[nr * kLeafLd + c] = a[qq][p];
-          }
+        for (int rr = 0; rr < 8; ++rr) cfma(s8[rr], cconj(A[(o + i) * kLeafLd + rb + rr]), a);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr)
+        if (8 * q + rr <= ci) A[(rb + rr) * kLeafLd + c] = csub(A[(rb + rr) * kLeafLd + c], s8[rr]);
     }
     __syncthreads();
   }
-  // ---- R = rows scaled by 1 / sqrt(pivot)
-  for (int j = tid; j < n; j += blockDim.x) {
-    float d = A[j * kLeafLd + j].re;
-    if (!(d > 0.0f) || !isfinite(d)) {
-      atomicOr(status, FM_DEVERR_PIVOT);
-      d = 1.0f;
-    }
-    Rd[j] = sqrtf(d);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int c = idx % n, r = idx / n;
-    if (r < c) A[r * kLeafLd + c] = cscale(A[r * kLeafLd + c], 1.0f / Rd[r]);
-    else if (r == c) A[r * kLeafLd + r] = cmk(Rd[r], 0.0f);
-  }
-  __syncthreads();
-  // ---- T = R^-1 by rows from the bottom; W in registers
+  // T above the diagonal blocks, block column j: Y = T_<j,<j R_<j,j, then T_<j,j = -Y T_jj
+  for (int j = 1; j < nb; ++j) {
+    const int c0 = 32 * j, mj = min(32, n - c0), items = 4 * j * mj;
+    for (int e = tid; e < items; e += kLeafThreads) {
+      const int rq = e / mj, cc = e % mj, c = c0 + cc, rb = 8 * rq;
+      c32 acc[8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+      for (int rr = 0; rr < 8; ++rr) acc[rr] = cmk(0.0f, 0.0f);
+      for (int s = rb; s < rb + 8; ++s) {       // the 8 x 8 triangle of T_rs, s >= r
+        const c32 rsc = A[s * kLeafLd + c];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) a[q][p] = cmk((w + 32 * q == l + 32 * p) ? 1.0f : 0.0f, 0.0f);
-  if (tid == 0) Td[n - 1] = cmk(1.0f / Rd[n - 1], 0.0f);
-  __syncthreads();
-  for (int j = n - 1; j >= 1; --j) {
-    // T_jc for the owned columns c >= j, R_rj for the owned rows r < j (warp-uniform rows)
-    c32 t[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int c = l + 32 * p;
-      t[p] = (c > j && c < n) ? A[c * kLeafLd + j] : (c == j ? Td[j] : cmk(0.0f, 0.0f));
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = w + 32 * q;
-      if (r < j) {
-        const c32 rr = A[r * kLeafLd + j];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          if (32 * p + 31 >= j) {
-            const int c = l + 32 * p;
-            if (c >= j && c < n) a[q][p] = csub(a[q][p], cmul(rr, t[p]));
-          }
+        for (int rr = 0; rr < 8; ++rr) {
+          const int r = rb + rr;
+          if (s > r) cfma(acc[rr], A[s * kLeafLd + r], rsc);
+          else if (s == r) cfma(acc[rr], Td[r], rsc);
         }
       }
+      for (int s = rb + 8; s < c0; ++s) {
+        const c32 rsc = A[s * kLeafLd + c];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], A[s * kLeafLd + rb + rr], rsc);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) Y[(rb + rr) * kLeafYLd + cc] = acc[rr];
     }
-    // row j - 1 of W is final: T_{j-1, c} = W_{j-1, c} / R_{j-1, j-1}
-    const int nr = j - 1;
-    if (w == (nr & 31)) {
-      const int q = nr >> 5;
-      const float s = 1.0f / Rd[nr];
+    __syncthreads();
+    for (int e = tid; e < items; e += kLeafThreads) {
+      const int rq = e / mj, cc = e % mj, c = c0 + cc, rb = 8 * rq;
+      c32 acc[8];
+      const c32 tcc = Td[c];
 #pragma unroll
-      for (int qq = 0; qq < 4; ++qq)
-        if (qq == q)
+      for (int rr = 0; rr < 8; ++rr) acc[rr] = cmul(Y[(rb + rr) * kLeafYLd + cc], tcc);
+      for (int s = c0; s < c; ++s) {
+        const c32 tsc = A[c * kLeafLd + s];
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int c = l + 32 * p;
-            if (c == nr) Td[nr] = cscale(a[qq][p], s);
-            else if (c > nr && c < n) A[c * kLeafLd + nr] = cscale(a[qq][p], s);
-          }
+        for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], Y[(rb + rr) * kLeafYLd + s - c0], tsc);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) A[c * kLeafLd + rb + rr] = cmk(-acc[rr].re, -acc[rr].im);
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+  if (bad && lane == 0) atomicOr(status, FM_DEVERR_PIVOT);
+  for (int idx = tid; idx < n * n; idx += kLeafThreads) {
     const int r = idx % n, c = idx / n;
     const int64_t o = r + (int64_t)c * ld;
     if (r < c) {
@@ -236,8 +312,14 @@ cudaError_t chol_inv_leaf(cudaStream_t st, const c32* G, c32* R, c32* T, int n, 
     attr = cudaFuncSetAttribute(chol_inv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmem);
   });
   if (attr != cudaSuccess) return attr;
-  chol_inv_leaf_kernel<<<B, 1024, kLeafSmem, st>>>(G, R, T, n, ld, sNN, status);
+  chol_inv_leaf_kernel<<<B, kLeafThreads, kLeafSmem, st>>>(G, R, T, n, ld, sNN, status);
   return cudaGetLastError();
 }
 
 }  // namespace fm
+
+extern "C" int fmx_chol_leaf(const void* G, int n, int ld, int B, void* R, void* T, int* d_status, void* stream) {
+  if (n < 1 || n > fm::kLeafMax || ld < n || B < 1 || !d_status) return (int)cudaErrorInvalidValue;
+  return (int)fm::chol_inv_leaf((cudaStream_t)stream, (const c32*)G, (c32*)R, (c32*)T, n, ld,
+                                (int64_t)ld * n, B, d_status);
+}
