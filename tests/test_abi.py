@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point of include/fm.h (CPU only)."""
+"""The C-ABI library loads and exports every entry point declared in include/*.h (CPU only)."""
 import ctypes
 import os
 import re
@@ -8,10 +8,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "fm.h")).read()
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fm_[A-Za-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fmx?_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -23,10 +23,13 @@ def fm():
 
 
 def test_every_declared_symbol_is_exported(fm):
-    names = _declared()
-    assert len(names) >= 19
-    for n in names:
-        assert hasattr(fm.lib, n), n
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert "fm.h" in headers and "fm_testing.h" in headers
+    names = {h: _declared(h) for h in headers}
+    assert len(names["fm.h"]) >= 19 and len(names["fm_testing.h"]) >= 8
+    for h, ns in names.items():
+        for n in ns:
+            assert hasattr(fm.lib, n), "%s: %s" % (h, n)
 
 
 def test_struct_layouts(fm):
