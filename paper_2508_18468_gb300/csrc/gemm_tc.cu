@@ -124,10 +124,20 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
   }
 }
 
+// K-blocks [x, y) of a tile; the host guarantees x < y for every tile that is not skipped.
 template <int BN>
-__device__ __forceinline__ int kblocks_of(const Params& p, const TileInfo& ti) {
-  if (p.tri_k) return min(p.kblocks, (ti.nt + 1) * BN / BK);
-  return p.kblocks;
+__device__ __forceinline__ int2 krange(const Params& p, const TileInfo& ti) {
+  int lo = 0, hi = p.kblocks;
+  if (p.tri_k) hi = min(hi, (ti.nt + 1) * BN / BK);
+  const int mr = p.mt_mod > 0 ? ti.mt % p.mt_mod : ti.mt;
+  if (p.kb_lo_mt) lo = mr * p.kb_lo_mt;
+  if (p.kb_hi_mt) hi = min(hi, (mr + 1) * p.kb_hi_mt);
+  if (p.kb_hi_nt) hi = min(hi, (ti.nt + 1) * p.kb_hi_nt);
+  return make_int2(lo, hi);
+}
+
+__device__ __forceinline__ bool tile_skipped(const Params& p, const TileInfo& ti) {
+  return p.herm_upper && ti.mt % p.mt_mod > ti.nt;
 }
 
 template <int BN, int CHUNKED, int MODE>
@@ -178,10 +188,11 @@ __global__ void __launch_bounds__(256, 1)
       uint32_t issued_mask = 0, last_phase = 0;
       for (int t = blockIdx.x; t < p.ntiles && !*abort_flag; t += gridDim.x) {
         const TileInfo ti = decode(p, t);
-        const int kbn = kblocks_of<BN>(p, ti);
+        if (tile_skipped(p, ti)) continue;
+        const int2 kr = krange<BN>(p, ti);
         const int arow = ti.b * p.a_rows_per_b + ti.mt * BM;
         const int brow = ti.b * p.b_rows_per_b + ti.nt * BN;
-        for (int kb = 0; kb < kbn; ++kb) {
+        for (int kb = kr.x; kb < kr.y; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
           const int kx = kb * BK;
           int kxb = kx;
@@ -218,10 +229,11 @@ __global__ void __launch_bounds__(256, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
         const TileInfo ti = decode(p, t);
-        const int kbn = kblocks_of<BN>(p, ti);
-        const int ckb = CHUNKED ? p.chunk_kb : kbn;
-        for (int k0 = 0; k0 < kbn && ok; k0 += ckb, ++cbuf) {
-          const int k1 = min(kbn, k0 + ckb);
+        if (tile_skipped(p, ti)) continue;
+        const int2 kr = krange<BN>(p, ti);
+        const int ckb = CHUNKED ? p.chunk_kb : kr.y - kr.x;
+        for (int k0 = kr.x; k0 < kr.y && ok; k0 += ckb, ++cbuf) {
+          const int k1 = min(kr.y, k0 + ckb);
           const int buf = (int)(cbuf % C::NBUF);
           const uint32_t bpar = (cbuf / C::NBUF) & 1u;
           if (!mbar_wait(&tmem_empty[buf], bpar ^ 1, abort_flag)) { ok = false; break; }
@@ -266,14 +278,15 @@ __global__ void __launch_bounds__(256, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const TileInfo ti = decode(p, t);
-      const int kbn = kblocks_of<BN>(p, ti);
+      if (tile_skipped(p, ti)) continue;
+      const int2 kr = krange<BN>(p, ti);
       double rowsum = 0.0;
       if (CHUNKED) {
         // running fp32 sums of the whole tile row, fed chunk by chunk (round to nearest)
         float S[BN];
 #pragma unroll
         for (int j = 0; j < BN; ++j) S[j] = 0.0f;
-        for (int k0 = 0; k0 < kbn; k0 += p.chunk_kb, ++cbuf) {
+        for (int k0 = kr.x; k0 < kr.y; k0 += p.chunk_kb, ++cbuf) {
           const int buf = (int)(cbuf % C::NBUF);
           const uint32_t bpar = (cbuf / C::NBUF) & 1u;
           if (!mbar_wait(&tmem_full[buf], bpar, abort_flag)) { ok = false; break; }

@@ -32,6 +32,12 @@ struct Params {
   const float* in_f;   // TRMM: if set, out = in + D (D = U (T - 1)); ADDV: the array D is added to
   int kblocks;         // K / BK
   int tri_k;           // limit K-blocks to (nt+1) BN / BK (triangular B)
+  // K-block bounds by tile for triangular operands (0: off), with mr = mt % mt_mod:
+  int kb_lo_mt;        //   start at mr kb_lo_mt (A upper triangular)
+  int kb_hi_mt;        //   end at (mr + 1) kb_hi_mt (A lower triangular)
+  int kb_hi_nt;        //   end at (nt + 1) kb_hi_nt (B^T upper triangular)
+  int mt_mod;          //   row tiles per block of A rows (the complex embedding stacks Re and Im rows)
+  int herm_upper;      // skip the tiles with mr > nt (a Hermitian product's lower tiles)
   int a_rows_per_b;    // A row offset per batch item
   int b_rows_per_b;    // B row offset per batch item
   int k_shift;         // part 1 of the Gram: B read at (k + k_shift) mod kdim, negated past the wrap

@@ -169,9 +169,12 @@ __global__ void __launch_bounds__(256) build_ttilde_kernel(const c32* __restrict
 }
 
 // Planes of the real embedding of op(X) (m x k complex; op: 0 = none, 2 = conjugate
-// transpose): A (2m x 2k, row-major) = [[Re, -Im], [Im, Re]].  32 x 32 tiles of
-// op(X) staged in shared memory so both the read and the writes are coalesced;
-// m and k multiples of 32.  Grid (m / 32, k / 32, B), block (32, 8).
+// transpose): A (2m x 2k, row-major) = [[Re, -Im], [Im, Re]], the K axis interleaved
+// by groups of 32 (complex column kk, part s at 64 (kk / 32) + 32 s + kk % 32), so that
+// one 64-wide K-block holds both parts of 32 complex columns and a triangular operand
+// spans a contiguous range of K-blocks.  32 x 32 tiles of op(X) staged in shared
+// memory so both the read and the writes are coalesced; m and k multiples of 32.
+// Grid (m / 32, k / 32, B), block (32, 8).
 __global__ void __launch_bounds__(256) embed_a_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op,
                                                       int m, int k, __half* Ah, __half* Al) {
   __shared__ c32 t[32][33];                       // t[row][col] of op(X)
@@ -193,20 +196,21 @@ __global__ void __launch_bounds__(256) embed_a_kernel(const c32* __restrict__ X,
   const int64_t base = b * 4 * (int64_t)m * k;
   for (int q = ty; q < 32; q += 8) {
     const c32 x = t[q][tx];
-    const int64_t top = base + (int64_t)(r0 + q) * k2 + c0 + tx;
+    const int64_t top = base + (int64_t)(r0 + q) * k2 + 2 * c0 + tx;
     const int64_t bot = top + (int64_t)m * k2;
     __half h, lo;
     split16_f(x.re, h, lo);
-    Ah[top] = h; Al[top] = lo; Ah[bot + k] = h; Al[bot + k] = lo;
+    Ah[top] = h; Al[top] = lo; Ah[bot + 32] = h; Al[bot + 32] = lo;
     split16_f(-x.im, h, lo);
-    Ah[top + k] = h; Al[top + k] = lo;
+    Ah[top + 32] = h; Al[top + 32] = lo;
     split16_f(x.im, h, lo);
     Ah[bot] = h; Al[bot] = lo;
   }
 }
 
-// Planes of B (n x 2k, row-major): row j = [Re op(Y)[:, j], Im op(Y)[:, j]].
-// Grid (k / 32, n / 32, B), block (32, 8); k and n multiples of 32.
+// Planes of B (n x 2k, row-major): row j = the Re and Im parts of op(Y)[:, j], K
+// interleaved by groups of 32 as in embed_a_kernel.  Grid (k / 32, n / 32, B),
+// block (32, 8); k and n multiples of 32.
 __global__ void __launch_bounds__(256) embed_b_kernel(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int op,
                                                       int k, int n, __half* Bh, __half* Bl) {
   __shared__ c32 t[32][33];                       // t[j][kk] = op(Y)[kk][j]
@@ -228,22 +232,24 @@ __global__ void __launch_bounds__(256) embed_b_kernel(const c32* __restrict__ Y,
   const int64_t base = b * 2 * (int64_t)k * n;
   for (int q = ty; q < 32; q += 8) {
     const c32 y = t[q][tx];
-    const int64_t o = base + (int64_t)(j0 + q) * k2 + k0 + tx;
+    const int64_t o = base + (int64_t)(j0 + q) * k2 + 2 * k0 + tx;
     __half h, lo;
     split16_f(y.re, h, lo);
     Bh[o] = h; Bl[o] = lo;
     split16_f(y.im, h, lo);
-    Bh[o + k] = h; Bl[o + k] = lo;
+    Bh[o + 32] = h; Bl[o + 32] = lo;
   }
 }
 
 // C = alpha (D_re + i D_im) + beta C, D = [D_re; D_im] (2m x n, column-major, per
-// trajectory).  Grid (ceil(m / 256), n, B).
+// trajectory).  upper != 0: only the 128 x 128 tiles on or above the diagonal (the
+// ones a Hermitian product computes); C keeps its other entries.
+// Grid (ceil(m / 256), n, B).
 __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ D, int m, int n, float alpha,
-                                                      float beta, c32* C, int64_t ldc, int64_t sC) {
+                                                      float beta, c32* C, int64_t ldc, int64_t sC, int upper) {
   const int64_t b = blockIdx.z;
   const int r = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (r >= m) return;
+  if (r >= m || (upper && (r >> 7) > (j >> 7))) return;
   const float* Dj = D + b * 2 * (int64_t)m * n + (int64_t)j * 2 * m;
   c32* c = C + b * sC + r + (int64_t)j * ldc;
   c32 out = cmk(alpha * Dj[r], alpha * Dj[m + r]);
@@ -489,6 +495,9 @@ namespace {
     c->launches += 1;                                               \
   } while (0)
 
+// Operand shapes of cgemm_tc.
+enum { CG_A_UPPER = 1, CG_A_LOWER = 2, CG_B_UPPER = 4, CG_HERM = 8 };
+
 tc::Params base_params(MixedCtx* c, MixedHost* h) {
   tc::Params p;
   memset(&p, 0, sizeof(p));
@@ -504,11 +513,16 @@ tc::Params base_params(MixedCtx* c, MixedHost* h) {
 // k of 32.  The product runs as the real GEMM [[Re, -Im], [Im, Re]] (op X) x [Re; Im] (op Y).
 // (Measured: even the 128-cubed products at the bottom of the recursion take ~7 us here
 // plus their layout kernels, less than a CUDA-core complex64 GEMM of the same size.)
+// shape: CG_A_UPPER / CG_A_LOWER (op(X) triangular, m == k) and CG_B_UPPER (op(Y) upper
+// triangular, n == k) skip the K-blocks of zeros; CG_HERM (m == n, the result Hermitian)
+// computes and writes only the tiles on or above the diagonal.  The skipped products are
+// exact zeros, so the result is the full product's.
 int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int64_t sX, int opY, const c32* Y,
              int64_t ldy, int64_t sY, int m, int n, int k, float alpha, float beta, c32* C, int64_t ldc,
-             int64_t sC) {
+             int64_t sC, int shape) {
   const int B = c->B;
-  if (m % 32 || k % 32 || n % 128) {
+  if (m % 128 || k % 32 || n % 128 || ((shape & (CG_A_UPPER | CG_A_LOWER)) && m != k) ||
+      ((shape & CG_B_UPPER) && n != k) || ((shape & CG_HERM) && m != n)) {
     c->err = "cgemm sizes";
     return FM_EINVAL;
   }
@@ -537,8 +551,15 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
   p.out_f = h->cd;
   p.ld_out = 2 * (int64_t)m;
   p.out_batch_stride = 2 * (int64_t)m * n;
+  // K-block = 32 complex columns; a 128-row (column) tile spans 4 of them
+  p.mt_mod = m / tc::BM;
+  p.kb_lo_mt = (shape & CG_A_UPPER) ? 4 : 0;
+  p.kb_hi_mt = (shape & CG_A_LOWER) ? 4 : 0;
+  p.kb_hi_nt = (shape & CG_B_UPPER) ? 4 : 0;
+  p.herm_upper = (shape & CG_HERM) ? 1 : 0;
   MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, tc::sm_count()));
-  combine_kernel<<<dim3(FM_CEIL_DIV(m, 256), n, B), 256, 0, c->st>>>(h->cd, m, n, alpha, beta, C, ldc, sC);
+  combine_kernel<<<dim3(FM_CEIL_DIV(m, 256), n, B), 256, 0, c->st>>>(h->cd, m, n, alpha, beta, C, ldc, sC,
+                                                                     p.herm_upper);
   MCK(cudaGetLastError());
   return FM_OK;
 }
@@ -548,7 +569,9 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
 // reach of the second, float64-factored pass):
 //   R11, T11 <- block(off, h);  R12 = T11^dag G12;  G22 -= R12^dag R12;
 //   R22, T22 <- block(off + h, n - h);  T12 = -T11 (R12 T22).
-// Blocks of <= 128 are factored on the CUDA cores; the products run on the tensor cores.
+// Blocks of <= 128 are factored on the CUDA cores; the products run on the tensor cores,
+// each skipping the zero half of its triangular operand, and the Hermitian update of
+// G22 computes its upper tiles only (nothing reads below the diagonal of G).
 int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   const int N = c->N;
   const int64_t sNN = (int64_t)N * N;
@@ -566,11 +589,17 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   int r;
   const int64_t sXS = (int64_t)h->md * h->md;  // batch stride of the xs scratch
   if ((r = chol_inv_rec(h, c, off, hh))) return r;
-  if ((r = cgemm_tc(h, c, 2, T + d0, N, sNN, 0, G + o12, N, sNN, hh, m2, hh, 1.f, 0.f, R + o12, N, sNN))) return r;
-  if ((r = cgemm_tc(h, c, 2, R + o12, N, sNN, 0, R + o12, N, sNN, m2, m2, hh, -1.f, 1.f, G + d1, N, sNN))) return r;
+  if ((r = cgemm_tc(h, c, 2, T + d0, N, sNN, 0, G + o12, N, sNN, hh, m2, hh, 1.f, 0.f, R + o12, N, sNN,
+                    CG_A_LOWER)))
+    return r;
+  if ((r = cgemm_tc(h, c, 2, R + o12, N, sNN, 0, R + o12, N, sNN, m2, m2, hh, -1.f, 1.f, G + d1, N, sNN, CG_HERM)))
+    return r;
   if ((r = chol_inv_rec(h, c, off + hh, m2))) return r;
-  if ((r = cgemm_tc(h, c, 0, R + o12, N, sNN, 0, T + d1, N, sNN, hh, m2, m2, 1.f, 0.f, h->xs, hh, sXS))) return r;
-  if ((r = cgemm_tc(h, c, 0, T + d0, N, sNN, 0, h->xs, hh, sXS, hh, m2, hh, -1.f, 0.f, T + o12, N, sNN))) return r;
+  if ((r = cgemm_tc(h, c, 0, R + o12, N, sNN, 0, T + d1, N, sNN, hh, m2, m2, 1.f, 0.f, h->xs, hh, sXS, CG_B_UPPER)))
+    return r;
+  if ((r = cgemm_tc(h, c, 0, T + d0, N, sNN, 0, h->xs, hh, sXS, hh, m2, hh, -1.f, 0.f, T + o12, N, sNN,
+                    CG_A_UPPER)))
+    return r;
   return FM_OK;
 }
 
