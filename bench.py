@@ -105,13 +105,34 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing (CPU)
-def oracle_step_seconds(L_sample, nsteps, seed):
-    """Wall time per oracle homodyne step at L_sample (FP64, numpy on all host cores)."""
+def oracle_sample(wl):
+    """The oracle's bounded sample of a workload: (Lx, Ly, protocol, gamma) of the lattice it times.
+    The workload's own lattice when L <= ORACLE_SAMPLE_L, else a ring of ORACLE_SAMPLE_L sites or a
+    square torus of that many; the workload's protocol (homodyne for the torus workload that runs
+    both, and for the served mix) at its mean rate."""
+    if "Lx" not in wl:                                   # the served mix: its largest ring
+        Lx, Ly, prot, gam = max(wl["sizes"]), 1, "homodyne", sum(wl["gamma_range"]) / 2
+    else:
+        Lx, Ly = wl["Lx"], wl["Ly"]
+        prot = "projective" if wl["protocol"] == "projective" else "homodyne"
+        gam = sum(wl["gammas"]) / len(wl["gammas"])
+    if Lx * Ly > ORACLE_SAMPLE_L:
+        if Ly == 1:
+            Lx = ORACLE_SAMPLE_L
+        else:
+            Lx = Ly = int(round(ORACLE_SAMPLE_L ** 0.5))
+    return Lx, Ly, prot, gam
+
+
+def oracle_step_seconds(sample, nsteps, seed):
+    """Wall time per oracle step of one trajectory on the sample lattice (FP64, numpy on all host cores)."""
     import numpy as np  # noqa: F401
     from oracle import lattice, trajectory
-    prm = trajectory.Params(Lx=L_sample, gamma=1.0, protocol=trajectory.HOMODYNE, seed=seed)
-    P = lattice.propagator(L_sample, 1, prm.J, prm.dt)
-    U = lattice.initial_orbitals(L_sample)
+    Lx, Ly, prot, gam = sample
+    prm = trajectory.Params(Lx=Lx, Ly=Ly, gamma=gam, seed=seed,
+                            protocol=trajectory.PROJECTIVE if prot == "projective" else trajectory.HOMODYNE)
+    P = lattice.propagator(Lx, Ly, prm.J, prm.dt)
+    U = lattice.initial_orbitals(Lx, Ly)
     U, _ = trajectory.step(U, P, prm, 0)       # one untimed step (first touch)
     t0 = time.perf_counter()
     for s in range(1, 1 + nsteps):
@@ -126,12 +147,28 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def cpu_baseline_line(L_target, seed, nsteps=3):
-    t = oracle_step_seconds(ORACLE_SAMPLE_L, nsteps, seed)
-    scale = (L_target / ORACLE_SAMPLE_L) ** 3
+def workload_sites(wl):
+    return wl["Lx"] * wl["Ly"] if "Lx" in wl else max(wl["sizes"])
+
+
+def describe_sample(sample, nsteps, L_target, per):
+    Lx, Ly, prot, gam = sample
+    lat = "L=%d" % Lx if Ly == 1 else "%dx%d torus" % (Lx, Ly)
+    text = "%d %s oracle steps (gamma %.2f) at %s (numpy FP64, %.3g s/step)" % (nsteps, prot, gam, lat, per)
+    if Lx * Ly != L_target:
+        text += ", scaled by (%d/%d)^3" % (L_target, Lx * Ly)
+    return text
+
+
+def cpu_baseline_line(wl, seed, nsteps=3):
+    """The oracle timed on a bounded sample of the workload (one trajectory-step costs ~L^3 for the
+    dense propagation and CholeskyQR, so a smaller lattice is scaled by the cube of the site ratio)."""
+    sample = oracle_sample(wl)
+    L_target = workload_sites(wl)
+    t = oracle_step_seconds(sample, nsteps, seed)
+    scale = (L_target / (sample[0] * sample[1])) ** 3
     return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": "%d homodyne oracle steps at L=%d (numpy FP64, %.2f s/step), scaled by (%d/%d)^3"
-                      % (nsteps, ORACLE_SAMPLE_L, t, L_target, ORACLE_SAMPLE_L)}
+            "sample": describe_sample(sample, nsteps, L_target, t)}
 
 
 # ---------------------------------------------------------------- helpers
@@ -194,21 +231,23 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     wl = workloads.WORKLOADS[args.workload]
-    L = wl["Lx"] * wl["Ly"]
+    L = workload_sites(wl)
     seed = workloads.seed_of(args.workload)
+    sample = oracle_sample(wl)
     for s in range(args.warmup):
-        oracle_step_seconds(ORACLE_SAMPLE_L, 1, seed + s)
-    per = oracle_step_seconds(ORACLE_SAMPLE_L, args.steps, seed)
-    scale = (L / ORACLE_SAMPLE_L) ** 3
+        oracle_step_seconds(sample, 1, seed + s)
+    per = oracle_step_seconds(sample, args.steps, seed)
+    scale = (L / (sample[0] * sample[1])) ** 3
     value = 1.0 / (per * scale)
     metric = METRIC if args.workload == WORKLOAD else "trajectory steps/s (%s)" % args.workload
+    config = {"workload": args.workload, "L": L, "N": L // 2}
+    if "protocol" in wl:
+        config["protocol"] = wl["protocol"]
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * scale * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "L": L, "N": L // 2, "protocol": wl["protocol"]},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference", "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                             "sample": "%d oracle steps at L=%d scaled by (%d/%d)^3" % (
-                                 args.steps, ORACLE_SAMPLE_L, L, ORACLE_SAMPLE_L)},
+                             "sample": describe_sample(sample, args.steps, L, per)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -373,7 +412,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline_line(L, seed)
+        line["cpu_baseline"] = cpu_baseline_line(wl, seed)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
