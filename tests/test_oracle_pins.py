@@ -516,3 +516,109 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         return np.exp(np.sqrt(gamma * dt) * xi + (n - 1.0) * gamma * dt)[:, None] * U
     prm_h = Params(Lx=8, gamma=1.0, protocol=HOMODYNE, seed=99, traj_id=3)
     assert _pin_fails(lambda: _compare_homodyne(prm_h, 10, weight=bad_weight))
+
+
+def _rejected(pin, *args):
+    """True when the pin (a test function above) fails on the planted oracle."""
+    try:
+        pin(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def test_pins_catch_planted_mistakes_in_observables_and_lattice(monkeypatch):
+    """Slips in the entropy, mutual information, Eq. (2), Eq. (GAB), the Runge-Kutta stages,
+    the initial state and the hopping bonds: each is rejected by a pin above, and the pins
+    pass again once the slip is removed."""
+    good_terms = observables.binary_entropy_terms
+
+    # (e) the entropy without its (1 - lambda) ln(1 - lambda) half
+    def terms_half(lam):
+        lam = np.clip(np.asarray(lam, dtype=np.float64), 0.0, 1.0)
+        out = np.zeros_like(lam)
+        inner = lam > 0.0
+        out[inner] = lam[inner] * np.log(lam[inner])
+        return out
+    monkeypatch.setattr(observables, "binary_entropy_terms", terms_half)
+    assert _rejected(test_entropy_of_half_filled_random_state_matches_schmidt)
+    monkeypatch.undo()
+
+    # (e') the entropy in bits instead of nats
+    monkeypatch.setattr(observables, "binary_entropy_terms", lambda lam: good_terms(lam) / np.log(2.0))
+    assert _rejected(test_entropy_of_half_filled_random_state_matches_schmidt)
+    monkeypatch.undo()
+
+    # (f) mutual information with the joint entropy added instead of subtracted
+    def mi_plus(U, A, B):
+        return (observables.entanglement_entropy(U, list(A)) + observables.entanglement_entropy(U, list(B))
+                + observables.entanglement_entropy(U, sorted(list(A) + list(B))))
+    monkeypatch.setattr(observables, "mutual_information", mi_plus)
+    # (I(A, Abar) = 2 S(A) and I >= 0 still hold for a pure state: S(A u Abar) = 0)
+    assert not _rejected(test_invariants_along_a_projective_trajectory)
+    assert _rejected(test_homodyne_matches_brute_force, 8, 1, 1.0)
+    monkeypatch.undo()
+
+    # (g) Eq. (2) with the partner site one further than the displacement
+    def corr_shifted(U, Lx, Ly=1):
+        L = Lx * Ly
+        C2 = np.abs(observables.correlation(U)) ** 2
+        site = np.arange(L)
+        x, y = site % Lx, site // Lx
+        out = np.zeros(L)
+        for dy in range(Ly):
+            for dx in range(Lx):
+                d = dx + Lx * dy
+                if d:
+                    j = (x + dx + 1) % Lx + Lx * ((y + dy) % Ly)
+                    out[d] = -float(np.mean(C2[site, j]))
+        return out
+    monkeypatch.setattr(observables, "displacement_correlation", corr_shifted)
+    assert _rejected(test_density_correlations_match_occupation_statistics, 10, 1, 5)
+    monkeypatch.undo()
+
+    # (g') Eq. (GAB) summing C_ij instead of |C_ij|^2
+    def cov_linear(U, A, B):
+        A, B = list(A), list(B)
+        return float(np.real(np.sum(U[A, :] @ np.conj(U[B, :]).T)))
+    monkeypatch.setattr(observables, "particle_covariance", cov_linear)
+    assert _rejected(test_density_correlations_match_occupation_statistics, 4, 3, 6)
+    monkeypatch.undo()
+
+    # (h) a Runge-Kutta stage taken over the full step instead of half of it
+    def rk4_bad(U, H, xi, gamma, dt):
+        n = trajectory.occupations(U)
+        A = -1j * H + np.diag((np.sqrt(gamma * dt) * xi + (2.0 * n - 1.0) * gamma * dt) / dt)
+        k1 = A @ U
+        k2 = A @ (U + 0.5 * dt * k1)
+        k3 = A @ (U + dt * k2)
+        k4 = A @ (U + dt * k3)
+        return U + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    monkeypatch.setattr(trajectory, "step_rk4", rk4_bad)
+    assert _rejected(test_rk4_step_is_the_quartic_taylor_polynomial_and_close_to_expm)
+    monkeypatch.undo()
+
+    # (i) the Neel start on the odd sites (|0101...>, Sec. II's printing) instead of App. A's
+    monkeypatch.setattr(lattice, "occupied_sites",
+                        lambda Lx, Ly=1: np.arange(1, Lx, 2) if Ly == 1 else
+                        np.array([x + Lx * y for y in range(Ly) for x in range(Lx) if (x + y) % 2 == 1]))
+    assert _rejected(test_unmonitored_density_closed_form, 64, 1, 200)
+    monkeypatch.undo()
+
+    # (j) the ring without its wrap-around bond (open chain)
+    good_hop = lattice.hopping_matrix
+
+    def hop_open(Lx, Ly=1, J=1.0):
+        H = good_hop(Lx, Ly, J).copy()
+        if Ly == 1:
+            H[0, Lx - 1] = H[Lx - 1, 0] = 0.0
+        return H
+    monkeypatch.setattr(lattice, "hopping_matrix", hop_open)
+    assert _rejected(test_propagator_is_expm_of_hopping, 12, 1)
+    monkeypatch.undo()
+
+    # the pins pass on the real oracle
+    test_entropy_of_half_filled_random_state_matches_schmidt()
+    test_density_correlations_match_occupation_statistics(10, 1, 5)
+    test_rk4_step_is_the_quartic_taylor_polynomial_and_close_to_expm()
+    test_propagator_is_expm_of_hopping(12, 1)
