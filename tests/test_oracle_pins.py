@@ -30,6 +30,23 @@ def test_philox_known_answers():
         assert [int(o) for o in out] == v[6:10]
 
 
+def test_uniform53_is_the_53_bit_grid():
+    """u = k 2^-53 with k the 27 high bits of the first word over the 26 high bits of the
+    second: every value on the 53-bit grid of [0, 1) is reachable, 0 and 1 - 2^-53 at the ends,
+    and the low bits of the words do not matter."""
+    top = np.uint64(0xFFFFFFFF)
+    assert philox.uniform53(0, 0) == 0.0
+    assert philox.uniform53(top, top) == 1.0 - 2.0 ** -53
+    assert philox.uniform53(0, 1 << 6) == 2.0 ** -53                 # lowest bit kept from wb
+    assert philox.uniform53(0, (1 << 6) - 1) == 0.0                  # the 6 bits below are dropped
+    assert philox.uniform53(1 << 5, 0) == 2.0 ** -27                 # lowest bit kept from wa
+    assert philox.uniform53((1 << 5) - 1, 0) == 0.0
+    assert philox.uniform53(1 << 31, 0) == 0.5
+    ks = np.array([0x12345678, 0xDEADBEEF], dtype=np.uint64)
+    u = philox.uniform53(ks[0], ks[1])
+    assert u * 2.0 ** 53 == float((0x12345678 >> 5) * (1 << 26) + (0xDEADBEEF >> 6))
+
+
 def test_uniform_and_normal_draws():
     u_sel, u_out = philox.measure_draws(seed=12345, traj_id=7, step=3, L=200000)
     for u in (u_sel, u_out):
