@@ -75,3 +75,21 @@ def test_null_state_calls_fail_cleanly(fm):
     assert fm.lib.fm_step(None, 1) == fm.FM_EINVAL
     assert fm.lib.fm_kernel_launches(None) == 0
     fm.lib.fm_destroy(None)
+
+
+def test_binding_without_the_library_raises():
+    """The binding refuses to import when libfm.so is absent: no fallback implementation."""
+    src_path = os.path.join(ROOT, "paper_2508_18468_gb300", "fm.py")
+    src = open(src_path).read()
+    ns = {"__file__": os.path.join(ROOT, "no_such_directory", "fm.py"), "__name__": "fm_without_library"}
+    with pytest.raises(ImportError, match="no non-CUDA fallback"):
+        exec(compile(src, src_path, "exec"), ns)
+
+
+def test_trajectories_fail_loudly_without_a_gpu(fm):
+    """On a host without a CUDA device the product path raises instead of computing anything."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(RuntimeError):
+        fm.Trajectories(fm.make_params(64))
