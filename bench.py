@@ -105,22 +105,23 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing (CPU)
-def oracle_sample(wl):
+def oracle_sample(wl, cap=None):
     """The oracle's bounded sample of a workload: (Lx, Ly, protocol, gamma) of the lattice it times.
-    The workload's own lattice when L <= ORACLE_SAMPLE_L, else a ring of ORACLE_SAMPLE_L sites or a
+    The workload's own lattice when L <= cap (default ORACLE_SAMPLE_L), else a ring of cap sites or a
     square torus of that many; the workload's protocol (homodyne for the torus workload that runs
     both, and for the served mix) at its mean rate."""
+    cap = ORACLE_SAMPLE_L if cap is None else cap
     if "Lx" not in wl:                                   # the served mix: its largest ring
         Lx, Ly, prot, gam = max(wl["sizes"]), 1, "homodyne", sum(wl["gamma_range"]) / 2
     else:
         Lx, Ly = wl["Lx"], wl["Ly"]
         prot = "projective" if wl["protocol"] == "projective" else "homodyne"
         gam = sum(wl["gammas"]) / len(wl["gammas"])
-    if Lx * Ly > ORACLE_SAMPLE_L:
+    if Lx * Ly > cap:
         if Ly == 1:
-            Lx = ORACLE_SAMPLE_L
+            Lx = cap
         else:
-            Lx = Ly = int(round(ORACLE_SAMPLE_L ** 0.5))
+            Lx = Ly = int(round(cap ** 0.5))
     return Lx, Ly, prot, gam
 
 
@@ -160,6 +161,32 @@ def describe_sample(sample, nsteps, L_target, per):
     return text
 
 
+SINGLE_CORE_SAMPLE_L = 1024
+
+
+def oracle_single_core(wl, seed, nsteps=2):
+    """The oracle held to one thread (BLAS and OpenMP pools of size 1, in a child process so the
+    setting takes effect before numpy loads), on at most SINGLE_CORE_SAMPLE_L sites, scaled by the
+    cube of the site ratio like the multi-core figure.  Returns a dict; on any failure its value is
+    None and it says why."""
+    sample = oracle_sample(wl, SINGLE_CORE_SAMPLE_L)
+    L_target = workload_sites(wl)
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_step_seconds(%r, %d, %d)))" % (ROOT, tuple(sample), nsteps, seed))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        if out.returncode != 0:
+            raise RuntimeError(out.stderr.strip().splitlines()[-1] if out.stderr.strip() else "exit %d" % out.returncode)
+        per = float(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the bench line is printed either way
+        return {"value": None, "threads": 1, "error": str(e)[:200]}
+    scale = (L_target / (sample[0] * sample[1])) ** 3
+    return {"value": 1.0 / (per * scale), "unit": UNIT, "threads": 1,
+            "sample": describe_sample(sample, nsteps, L_target, per)}
+
+
 def cpu_baseline_line(wl, seed, nsteps=3):
     """The oracle timed on a bounded sample of the workload (one trajectory-step costs ~L^3 for the
     dense propagation and CholeskyQR, so a smaller lattice is scaled by the cube of the site ratio)."""
@@ -168,7 +195,8 @@ def cpu_baseline_line(wl, seed, nsteps=3):
     t = oracle_step_seconds(sample, nsteps, seed)
     scale = (L_target / (sample[0] * sample[1])) ** 3
     return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": describe_sample(sample, nsteps, L_target, t)}
+            "sample": describe_sample(sample, nsteps, L_target, t),
+            "single_core": oracle_single_core(wl, seed)}
 
 
 # ---------------------------------------------------------------- helpers

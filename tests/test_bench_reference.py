@@ -59,3 +59,17 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_single_core_oracle_figure():
+    """cpu_baseline carries the oracle held to one thread as well (a child process with every
+    thread pool of size 1), on the same kind of sample, capped at 1024 sites."""
+    import bench
+    from paper_2508_18468_gb300 import workloads
+    W = workloads.WORKLOADS
+    assert bench.oracle_sample(W["ring16384_homodyne"], bench.SINGLE_CORE_SAMPLE_L)[:2] == (1024, 1)
+    assert bench.oracle_sample(W["torus160_both"], bench.SINGLE_CORE_SAMPLE_L)[:2] == (32, 32)
+    cb = bench.cpu_baseline_line(W["ring64_projective"], 1, nsteps=1)
+    sc = cb["single_core"]
+    assert sc["threads"] == 1 and sc.get("value") and sc["value"] > 0, sc
+    assert "projective" in sc["sample"] and "scaled" not in sc["sample"]
