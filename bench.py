@@ -176,7 +176,7 @@ def oracle_single_core(wl, seed, nsteps=2):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     try:
-        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
         if out.returncode != 0:
             raise RuntimeError(out.stderr.strip().splitlines()[-1] if out.stderr.strip() else "exit %d" % out.returncode)
         per = float(out.stdout.strip().splitlines()[-1])
