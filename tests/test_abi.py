@@ -93,3 +93,27 @@ def test_trajectories_fail_loudly_without_a_gpu(fm):
         pytest.skip("a CUDA device is present")
     with pytest.raises(RuntimeError):
         fm.Trajectories(fm.make_params(64))
+
+
+def test_init_state_validates_arguments_before_touching_the_device(fm):
+    """fm_init_state rejects a missing out pointer, invalid parameters, a null or misaligned
+    workspace (FM_EINVAL) and a workspace smaller than fm_workspace_bytes (FM_ENOMEM) before any
+    device access; calls on a null state return FM_EINVAL."""
+    lib = fm.lib
+    p = fm.make_params(64)
+    need = fm.fm_workspace_bytes(p)
+    out = ctypes.c_void_p(12345)
+    fake = 1 << 20                                     # aligned, never dereferenced on these paths
+    assert lib.fm_init_state(ctypes.byref(p), ctypes.c_void_p(fake), need, None, None) == fm.FM_EINVAL
+    bad = fm.make_params(63)
+    assert lib.fm_init_state(ctypes.byref(bad), ctypes.c_void_p(fake), need, None, ctypes.byref(out)) == fm.FM_EINVAL
+    assert out.value is None                           # *out cleared on failure
+    assert lib.fm_init_state(ctypes.byref(p), None, need, None, ctypes.byref(out)) == fm.FM_EINVAL
+    assert lib.fm_init_state(ctypes.byref(p), ctypes.c_void_p(fake + 8), need, None,
+                             ctypes.byref(out)) == fm.FM_EINVAL
+    assert lib.fm_init_state(ctypes.byref(p), ctypes.c_void_p(fake), need - 1, None,
+                             ctypes.byref(out)) == fm.FM_ENOMEM
+    assert out.value is None
+    assert lib.fm_step(None, 1) == fm.FM_EINVAL
+    assert lib.fm_last_error(None) == b"null state"
+    lib.fm_destroy(None)
