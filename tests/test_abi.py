@@ -117,3 +117,29 @@ def test_init_state_validates_arguments_before_touching_the_device(fm):
     assert lib.fm_step(None, 1) == fm.FM_EINVAL
     assert lib.fm_last_error(None) == b"null state"
     lib.fm_destroy(None)
+
+
+def test_test_hooks_reject_invalid_sizes_before_any_launch(fm):
+    """The tensor-core and leaf hooks of include/fm_testing.h return cudaErrorInvalidValue (1) for
+    sizes their kernels do not take, before touching any pointer."""
+    lib = fm.lib
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.fmx_tc_gemm.restype = i32
+    lib.fmx_tc_gemm.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, i32, i32, i32, i32, vp, vp]
+    lib.fmx_tc_gram.restype = i32
+    lib.fmx_tc_gram.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
+    lib.fmx_chol_leaf.restype = i32
+    lib.fmx_chol_leaf.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
+    INVALID = 1
+    gemm = lambda M, N, K, BN, chunk=0: lib.fmx_tc_gemm(None, None, None, None, M, N, K, None, BN, 0, chunk, 1,
+                                                         None, None)
+    assert gemm(100, 128, 64, 128) == INVALID          # M not a multiple of 128
+    assert gemm(128, 128, 64, 64) == INVALID           # BN neither 128 nor 256
+    assert gemm(128, 128, 64, 256) == INVALID          # N not a multiple of BN
+    assert gemm(128, 128, 32, 128) == INVALID          # K not a multiple of 64
+    assert gemm(128, 256, 64, 256, chunk=2) == INVALID  # register drain only with BN = 128
+    assert lib.fmx_tc_gram(None, None, 64, 96, 1, None, 128, None, None) == INVALID
+    dummy = ctypes.c_void_p(1 << 20)
+    for n, ld, B in ((0, 1, 1), (129, 129, 1), (64, 63, 1), (64, 64, 0)):
+        assert lib.fmx_chol_leaf(dummy, n, ld, B, dummy, dummy, dummy, None) == INVALID
+    assert lib.fmx_chol_leaf(dummy, 64, 64, 1, dummy, dummy, None, None) == INVALID   # no status word
