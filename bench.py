@@ -54,6 +54,12 @@ def parse():
                          "method), the sketch, or the full eigen-decomposition of C_A")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the short measurements of the other workloads (ring64, ring1024 x 256, torus "
+                         "160 x 160, served mix) added to the line")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the all-FP64 GPU path (one trajectory, beside the mixed path on the same "
+                         "trajectory) for the speedup and the accuracy of the mixed path; 0 skips it")
     return ap.parse_args()
 
 
@@ -253,6 +259,153 @@ def replica_traj_id(rank, batch):
     return rank * batch
 
 
+def fp64_side_by_side(fm, wl, seed, traj, gamma, nsteps, ee_sites, ee_method):
+    """The all-FP64 GPU path (complex128 state, FP64 GEMMs and Cholesky, the workload's reorth
+    interval) on one trajectory of the workload, timed with CUDA events over nsteps steps from the
+    Neel start, and the mixed path on the same trajectory (same Philox draws) for the same steps;
+    then the half-chain entropy of both (FP64: the full eigen-decomposition; mixed: the bench's
+    entropy method), max|C_mixed - C_fp64| on the first 512 rows and the orthonormality of both."""
+    import numpy as np
+    import torch
+    Lx, Ly = wl["Lx"], wl["Ly"]
+    protocol = fm.FM_HOMODYNE if wl["protocol"] == "homodyne" else fm.FM_PROJECTIVE
+    kw = dict(batch=1, protocol=protocol, reorth_interval=wl["reorth_interval"], gamma=gamma, seed=seed,
+              traj_id=traj)
+    stream = torch.cuda.current_stream()
+    gd = fm.Trajectories(fm.make_params(Lx, Ly, precision=fm.FM_FP64, **kw))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gd.step(nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    gm = fm.Trajectories(fm.make_params(Lx, Ly, precision=fm.FM_MIXED, tile_config=wl.get("tile_config", 0), **kw))
+    if ee_method != "full":
+        gm.set_entropy_method(fm.FM_EE_SKETCH if ee_method == "sketch" else fm.FM_EE_AUTO)
+    gm.step(nsteps)
+    Sd, Sm = gd.entropy(ee_sites), gm.entropy(ee_sites)
+    rows = 512
+    Ud, Um = gd.copy_U()[:rows], gm.copy_U()[:rows]
+    dc = float(np.max(np.abs(Um @ Um.conj().T - Ud @ Ud.conj().T)))
+    cols = list(range(0, gd.N, max(1, gd.N // 64)))[:64]
+    od, om = gd.orthonormality_error(cols), gm.orthonormality_error(cols)
+    gd.close()
+    gm.close()
+    del gd, gm
+    torch.cuda.empty_cache()
+    return {"fp64_gpu": {"value": nsteps / t, "unit": UNIT, "steps": nsteps, "trajectories": 1,
+                         "ms_per_step": t * 1e3 / nsteps, "gamma": gamma, "traj_id": traj,
+                         "what": "complex128 state, FP64 dense propagation GEMM, FP64 CholeskyQR2 "
+                                 "(reorth interval %d), CUDA events" % wl["reorth_interval"]},
+            "accuracy": {"steps": nsteps, "S_fp64": Sd, "S_mixed": Sm,
+                         "ee_rel_err": abs(Sm - Sd) / max(abs(Sd), 1.0),
+                         "max_abs_dC_512_rows": dc, "ortho_fp64": od, "ortho_mixed": om,
+                         "ee_method_mixed": ee_method}}
+
+
+def timed_steps(fm, g, nsteps, stream):
+    """Device time (s) of nsteps steps of g with CUDA events, and its phase split."""
+    import torch
+    g.step(1)                                       # warm-up (and first-use set-up)
+    torch.cuda.synchronize()
+    g.phase_times()
+    g.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ph = g.phase_times()
+    g.set_timing(False)
+    return e0.elapsed_time(e1) / 1e3, ph
+
+
+def prop_roofline(ph, L, N, B, peaks):
+    ms, n = ph["propagate"]
+    if n == 0:
+        return None
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / 3.0
+    ach = 8.0 * L * L * N * B / (ms / n / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "kernel": "tc_gemm_kernel (propagation)", "ms_per_launch": ms / n}
+
+
+def other_workloads(fm, peaks):
+    """Short measurements of the other workloads, one GPU, CUDA events on the stepping stream:
+    ring L = 64 projective (FP64, 200 steps, half-chain entropy every 10 steps); ring L = 1024
+    projective, 256 trajectories (mixed, 20 steps); the 160 x 160 torus, 8 trajectories of each
+    protocol (mixed, 2 steps); a bounded served mix (64 Poisson requests of 100 steps, L in
+    {256 .. 4096}, arrivals at the workload's rate)."""
+    import torch
+    from paper_2508_18468_gb300 import serve, workloads
+    stream = torch.cuda.current_stream()
+    out = {}
+    # c1: ring 64, FP64, 200 steps with 20 half-chain entropies
+    wl = workloads.WORKLOADS["ring64_projective"]
+    g = fm.Trajectories(fm.make_params(64, protocol=fm.FM_PROJECTIVE, precision=fm.FM_FP64, gamma=0.5,
+                                       seed=workloads.seed_of("ring64_projective")))
+    g.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        g.step(10)
+        g.entropy(workloads.half_chain(64))
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["ring64_projective"] = {"value": 200 / t, "unit": UNIT, "steps": 200, "trajectories": 1,
+                                "precision": "fp64", "what": "200 steps and 20 half-chain entropies, wall "
+                                "time (launch-latency bound)"}
+    g.close()
+    # c2: ring 1024 x 256 projective, mixed
+    wl = workloads.WORKLOADS["ring1024_projective_batch"]
+    gam = wl["gammas"]
+    g = fm.Trajectories(fm.make_params(1024, batch=len(gam), protocol=fm.FM_PROJECTIVE, precision=fm.FM_MIXED,
+                                       seed=workloads.seed_of("ring1024_projective_batch")))
+    g.set_gammas(gam)
+    t, ph = timed_steps(fm, g, 20, stream)
+    out["ring1024_projective_batch"] = {"value": len(gam) * 20 / t, "unit": UNIT, "steps": 20,
+                                        "trajectories": len(gam), "precision": "mixed",
+                                        "ms_per_step": t * 1e3 / 20,
+                                        "phases_ms": {k: round(v[0], 3) for k, v in ph.items()},
+                                        "roofline": prop_roofline(ph, 1024, 512, len(gam), peaks)}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    # c4: torus 160 x 160, 8 trajectories per protocol
+    wl = workloads.WORKLOADS["torus160_both"]
+    gam = wl["gammas"]
+    for name, prot in (("homodyne", fm.FM_HOMODYNE), ("projective", fm.FM_PROJECTIVE)):
+        g = fm.Trajectories(fm.make_params(160, 160, batch=len(gam), protocol=prot, precision=fm.FM_MIXED,
+                                           seed=workloads.seed_of("torus160_both")))
+        g.set_gammas(gam)
+        t, ph = timed_steps(fm, g, 2, stream)
+        out["torus160_" + name] = {"value": len(gam) * 2 / t, "unit": UNIT, "steps": 2,
+                                   "trajectories": len(gam), "precision": "mixed", "ms_per_step": t * 1e3 / 2,
+                                   "phases_ms": {k: round(v[0], 3) for k, v in ph.items()},
+                                   "roofline": prop_roofline(ph, 25600, 12800, len(gam), peaks)}
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    # c5: a bounded served mix in real time
+    reqs = serve.served_mix_requests(64, 100)
+    srv = serve.Server(slots=8)
+    res, st = srv.run(reqs, realtime=True)
+    for gs in srv.groups.values():
+        for gg in gs:
+            gg.close()
+    torch.cuda.empty_cache()
+    out["served_mix"] = {"value": st["steps_per_s"], "unit": UNIT, "requests": st["requests"],
+                         "steps_per_request": 100, "arrivals": "Poisson, 50/s",
+                         "step_latency_ms_p50": st["step_latency_ms_p50"],
+                         "step_latency_ms_p99": st["step_latency_ms_p99"], "wall_s": st["wall_s"],
+                         "groups": st["groups"], "what": "64 of the workload's 256 requests, 100 of its 500 "
+                         "steps each; latency per request step"}
+    return out
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     from paper_2508_18468_gb300 import workloads
@@ -383,13 +536,28 @@ def run_ours(args, world, rank, local):
         e2e = {"value": world * B * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * B,
                "d2h_bytes_per_step": 8 * B * L + 8 * B // ee_every}
 
+    guard = g.reorth_stats() if precision == fm.FM_MIXED else None
+    # the batch's workspace is no longer needed: free it before the side measurements
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    side = None
+    if args.fp64_steps > 0 and precision == fm.FM_MIXED and rank == 0:
+        hard = max(range(B), key=lambda b: gam[b])        # the trajectory with the largest rate
+        side = fp64_side_by_side(fm, wl, seed, replica_traj_id(rank, B) + hard, gam[hard], args.fp64_steps,
+                                 ee_sites, ee_method)
+
+    peaks, peak_src = load_peaks()
+    others = None
+    if not args.no_others and rank == 0 and args.workload == WORKLOAD:
+        others = other_workloads(fm, peaks)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
 
-    peaks, peak_src = load_peaks()
     prop_ms, prop_n = phases["propagate"]
     prop_flops = 8.0 * L * L * N * B                        # algorithmic complex GEMM flops per launch
     if precision == fm.FM_MIXED:
@@ -439,6 +607,17 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if guard is not None:
+        line["reorth_guard"] = {"second_passes": guard[0], "extra_passes": guard[1],
+                                "max_diag_E": guard[2][0], "max_offdiag_E": guard[2][1],
+                                "note": "E = U^dag U - 1 measured by each second CholeskyQR pass"}
+    if others is not None:
+        line["other_workloads"] = others
+    if side is not None:
+        line["fp64_gpu"] = side["fp64_gpu"]
+        line["speedup_vs_fp64"] = value / side["fp64_gpu"]["value"]
+        line["ee_rel_err_vs_fp64"] = side["accuracy"]["ee_rel_err"]
+        line["accuracy_vs_fp64"] = side["accuracy"]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_line(wl, seed)
     print(json.dumps(line), flush=True)

@@ -165,7 +165,13 @@ fm_status fm_reset_trajectory(fm_state* s, int32_t b, uint64_t traj_id, double g
 fm_status fm_steps_done(fm_state* s, int32_t b, int64_t* out);
 
 /* S_A (nats) of trajectory b, A = host array of n distinct sites.  FP64
- * Householder tridiagonalisation + bisection on the GPU.  Synchronises. */
+ * Householder tridiagonalisation + bisection on the GPU.  Synchronises.
+ * Mixed precision with reorth_interval k > 1: between second CholeskyQR passes
+ * U is orthonormal only to ~1e-6..1e-5, so this call, fm_entropy_async,
+ * fm_mutual_info, fm_density_correlation, fm_particle_covariance and fm_copy_U
+ * first run the pending second pass when the step count is not a multiple of
+ * k (span(U) -- the state -- is unchanged; U becomes orthonormal to < 1e-7).
+ * fm_occupations, fm_orthonormality_error and fm_save read U as it is. */
 fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, double* S_out);
 
 /* Asynchronous S_A of trajectory b at the current point of the step sequence.
@@ -186,6 +192,10 @@ fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, do
  * buffer the state allocates on first use.  A launch error of the library
  * thread is reported by fm_entropy_wait (FM_ECUDA, sticky). */
 fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t n, int64_t* ticket);
+
+/* *ready = 1 if the entropy of `ticket` is ready (fm_entropy_wait then returns
+ * without waiting for it), else 0.  Never blocks. */
+fm_status fm_entropy_ready(fm_state* s, int64_t ticket, int32_t* ready);
 
 /* Block until the entropy of `ticket` is ready and return it. */
 fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out);
@@ -253,6 +263,22 @@ fm_status fm_orthonormality_error(fm_state* s, int32_t b, const int32_t* cols, i
  * last call.  Synchronises. */
 fm_status fm_take_events(fm_state* s, fm_event* out, int32_t cap, int32_t* count, int64_t* dropped);
 
+/* Replay mode for the fixed-step projective protocol (App. A, Born rule and Eqs.
+ * (A1), (A2)): from the next fm_step on, the measurement of site `site` by trajectory
+ * `traj` at step index `step` (t/dt before the step, as in fm_event) takes the listed
+ * `outcome` (0 or 1) instead of comparing its Philox draw with the Born weight.  Which
+ * sites are measured still follows the Philox selection draws; listed measurements
+ * that the selection does not make are ignored.  The u and p fields of the entries
+ * are ignored, so the events another state logged (fm_take_events) can be passed
+ * straight in, e.g. to hold a mixed-precision run on the outcome sequence of an FP64
+ * run through near ties.  A forced measurement is logged with u = -1 (a forced click)
+ * or u = 2 (a forced no-click).  Forcing an outcome of Born weight 0 (a click where
+ * C_jj = 0, a no-click where C_jj = 1) is undefined and ends in FM_ENUMERIC.
+ * events: host array of n <= fm_params.event_capacity entries (the list is kept in
+ * the workspace), 0 <= step < 2^31, each (step, traj, site) at most once; n = 0
+ * clears the list.  FM_EINVAL for other protocols.  Synchronises. */
+fm_status fm_force_outcomes(fm_state* s, const fm_event* events, int32_t n);
+
 /* Checkpoint: U (as stored), step counters, rates and ids to / from a file.
  * Philox is counter based, so a restored run continues bit-identically. */
 fm_status fm_save(fm_state* s, const char* path);
@@ -278,14 +304,32 @@ enum { FM_PH_PROPAGATE = 0, FM_PH_MEASURE = 1, FM_PH_GRAM = 2, FM_PH_CHOLESKY = 
 fm_status fm_set_timing(fm_state* s, int32_t enable);
 fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts);
 
+/* The guard of the mixed-precision second CholeskyQR pass (App. A, "QR after each
+ * step").  The second pass factors G = U^dag U = 1 + E to first order (T = 1 - F, F
+ * the strict upper part of E plus half its diagonal, E measured in float64 on the
+ * diagonal); that leaves U^dag U - 1 = -(F^dag F + F^2 + F^dag^2) + O(E^3), whose
+ * entries are at most 3 (N o^2 + o d) + (3/4) d^2 with d, o the largest diagonal and
+ * off-diagonal |E|.  The Gram's epilogue records d and o per trajectory; when that
+ * bound exceeds 1e-7 for any trajectory of the batch, one more closed-form pass runs
+ * (decided on the device, so graphs replay it too); if the E it then measures still
+ * exceeds the bound, the state fails with FM_ENUMERIC rather than continue less
+ * orthonormal than 1e-6.
+ * *checks: second passes run since init; *extra_passes: of which needed the extra
+ * pass; maxima[0..3] (host array of 4, may be NULL): the largest d and o seen by the
+ * second passes, then by the extra passes, since the previous call (reset by the
+ * call).  FP64 states (a float64 Cholesky every pass) report zeros.  Synchronises. */
+fm_status fm_reorth_stats(fm_state* s, int64_t* checks, int64_t* extra_passes, double* maxima);
+
 /* Result of fm_autotune. */
 typedef struct {
   int32_t tile_config;      /* best fm_params.tile_config */
   int32_t reorth_interval;  /* best fm_params.reorth_interval */
   double ms_per_step;       /* its device time per step of the whole batch */
-  double ortho_err;         /* its largest max|U^dag U - 1| seen on the checked steps */
+  double ortho_err;         /* its largest max|U^dag U - 1| after the checked steps that end a
+                               period (a second CholeskyQR pass) */
   int32_t tried;            /* configurations timed */
   int32_t rejected;         /* of which over the orthonormality tolerance */
+  double ortho_mid;         /* the same after the checked steps inside a period (first pass only) */
 } fm_tuning;
 
 /* Pick tile_config and reorth_interval for the workload *p by measurement
@@ -300,7 +344,10 @@ typedef struct {
  * graphs when use_graphs != 0), then 2 * reorth_interval single steps after
  * each of which max|U^dag U - 1| over 64 sampled columns of the first and
  * last trajectory is measured.  The fastest candidate whose error stays
- * <= ortho_tol wins; if none does, the fastest with reorth_interval = 1.
+ * <= ortho_tol after the steps that end a period (second pass done) and
+ * <= 100 ortho_tol after the others wins (observables first complete a
+ * period that is still open, see fm_entropy); if none does, the fastest with
+ * reorth_interval = 1.
  * Synchronises; the workspace holds nothing useful afterwards. */
 fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, void* cuda_stream,
                       int32_t steps, int32_t max_reorth, double ortho_tol, int32_t use_graphs,
@@ -327,8 +374,11 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
  * that first call before any stream capture.  All calls share the array:
  * calls whose work overlaps on the GPU (other streams, other threads) race and
  * must be serialised by the caller.  Each call writes every scratch word it
- * reads, so nothing carries over from the previous call.  The same FP64
- * Householder + bisection method as fm_entropy. */
+ * reads, so nothing carries over from the previous call.  The site list is
+ * copied into the gather kernel's launch parameters, so `sites` may be freed
+ * as soon as the call returns, and the call makes no host-to-device copy.
+ * n == 0 writes S = 0.  The same FP64 Householder + bisection method as
+ * fm_entropy. */
 fm_status fm_entropy_noalloc(const void* d_U, int32_t L, int32_t N, const int32_t* sites, int32_t n,
                              double* d_S, void* cuda_stream);
 

@@ -4,10 +4,12 @@ Each ``csrc/*.cu`` is compiled to an object in parallel, then linked into one
 shared library with the CUDA runtime linked statically, so the library loads
 (and exports its C ABI) on machines without a GPU driver.
 """
+import hashlib
 import os
 import shutil
 import subprocess
 import sys
+import time
 from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
@@ -34,21 +36,47 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale(srcs, target):
-    if not os.path.exists(target):
-        return True
-    t = os.path.getmtime(target)
+def _inputs_digest(srcs, extra_flags=()):
+    """SHA-256 of every source, header and flag the library is built from."""
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
     deps.append(os.path.abspath(__file__))
-    return any(os.path.getmtime(d) > t for d in deps)
+    h = hashlib.sha256()
+    for d in sorted(deps):
+        h.update(os.path.relpath(d, ROOT).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(_flags() + list(extra_flags)).encode())
+    return h.hexdigest()
+
+
+STAMP = os.path.join(BUILD, "inputs.sha256")
+
+
+def _stale(digest):
+    """The library is rebuilt unless it exists and was linked from exactly these inputs (a
+    content hash, not file times: a copied tree keeps no trustworthy times)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return True
+    with open(STAMP) as f:
+        return f.read().strip() != digest
+
+
+last_build = {}
 
 
 def build(verbose=False, force=False, extra_flags=()):
-    """Compile and link; returns the path of the library."""
+    """Compile and link unless the library was built from the same inputs; returns the
+    path of the library.  ``last_build`` records whether this call compiled and how long
+    it took."""
     srcs = sources()
-    if not force and not _stale(srcs, LIB):
+    digest = _inputs_digest(srcs, extra_flags)
+    if not force and not _stale(digest):
+        last_build.update(compiled=False, seconds=0.0, digest=digest[:16])
+        if verbose:
+            sys.stderr.write("libfm.so up to date (inputs %s)\n" % digest[:16])
         return LIB
+    t0 = time.time()
     os.makedirs(BUILD, exist_ok=True)
     nvcc = nvcc_path()
 
@@ -70,6 +98,12 @@ def build(verbose=False, force=False, extra_flags=()):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(digest + "\n")
+    last_build.update(compiled=True, seconds=time.time() - t0, digest=digest[:16])
+    if verbose:
+        sys.stderr.write("libfm.so compiled from %d sources in %.1f s (inputs %s)\n"
+                         % (len(srcs), last_build["seconds"], digest[:16]))
     return LIB
 
 

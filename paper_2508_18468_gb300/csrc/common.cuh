@@ -56,6 +56,29 @@ FM_DEVFN philox_out philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_
 enum { FM_TAG_MEASURE = 1, FM_TAG_NOISE = 2 };
 
 // Draw for (site, step, trajectory, tag) under `seed`.
+// Replay of projective outcomes (fm_force_outcomes): f holds n entries (step, trajectory,
+// site, outcome) sorted by (step, trajectory, site).  Returns the forced outcome of the
+// measurement of `site` by trajectory b at `step`, or -1 if it is not listed.
+FM_DEVFN int fm_forced_outcome(const int4* f, int n, int64_t step, int b, int site) {
+  if (n <= 0 || step > 0x7fffffff) return -1;
+  const int st = (int)step;
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int4 e = f[mid];
+    const bool less = e.x < st || (e.x == st && (e.y < b || (e.y == b && e.z < site)));
+    if (less) lo = mid + 1; else hi = mid;
+  }
+  if (lo < n) {
+    const int4 e = f[lo];
+    if (e.x == st && e.y == b && e.z == site) return e.w;
+  }
+  return -1;
+}
+// The outcome draw that makes the rule "outcome 1 iff u < p" (p clamped to [0, 1]) give
+// the forced outcome: -1 forces a click, 2 a no-click.
+FM_DEVFN double fm_forced_u(int outcome) { return outcome ? -1.0 : 2.0; }
+
 FM_DEVFN philox_out fm_draw(uint64_t seed, uint64_t traj, int64_t step, int site, uint32_t tag) {
   return philox4x32_10((uint32_t)site, (uint32_t)step, (uint32_t)(traj & 0xFFFFFFFFu),
                        tag | ((uint32_t)(traj >> 32) << 8),
@@ -77,7 +100,8 @@ FM_DEVFN double fm_normal(philox_out o) {
 // ------------------------------------------------------------------ device error flags
 // Bit flags written by kernels into the state's status word; read by the host
 // at synchronisation points.
-enum { FM_DEVERR_PIVOT = 1, FM_DEVERR_NONFINITE = 2, FM_DEVERR_TIMEOUT = 4, FM_DEVERR_BOUNDS = 8 };
+enum { FM_DEVERR_PIVOT = 1, FM_DEVERR_NONFINITE = 2, FM_DEVERR_TIMEOUT = 4, FM_DEVERR_BOUNDS = 8,
+       FM_DEVERR_REORTH = 16 };
 
 // ------------------------------------------------------------------ host helpers
 #define FM_CEIL_DIV(a, b) (((a) + (b) - 1) / (b))

@@ -63,7 +63,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Plan {
   size_t total = 0;
   // offsets
-  size_t gamma, traj, step, status, occ, log_count, log, part, nocc, w, xbuf, vbuf;
+  size_t gamma, traj, step, status, occ, log_count, log, force, part, nocc, w, xbuf, vbuf;
   size_t U, U2, P, G, R, T, Dinv, X;                  // FP64 path (G, R, T, Dinv, X also mixed)
   size_t V, V2, Vh, Vl, Ah, Al, Th, Tl, aux;           // mixed path
   size_t ee_vb, ee_wb, ee_pb, ee_d, ee_e, ee_lam, ee_S, ee_sites, ee_max;
@@ -129,6 +129,7 @@ Plan make_plan(const fm_params& p) {
   pl.occ = pl.take(N * 4);
   pl.log_count = pl.take(16);
   pl.log = pl.take((size_t)p.event_capacity * sizeof(fm_event));
+  pl.force = pl.take((size_t)p.event_capacity * 16);
   pl.part = pl.take(B * kMaxChunks * L * 8);
   pl.nocc = pl.take(B * L * 8);
   pl.w = pl.take(B * L * 8);
@@ -208,6 +209,7 @@ struct fm_state {
   // common
   double* gamma_d; uint64_t* traj_d; int64_t* step_d; int* status_d; int* occ_d;
   unsigned long long* log_count_d; fm_event* log_d;
+  int4* force_d; int force_n;   // forced projective outcomes (fm_force_outcomes), sorted
   double *part_d, *nocc_d, *w_d;
   void *xbuf_d, *vbuf_d;
   z64 *G, *R, *T, *Dinv, *X;
@@ -310,6 +312,7 @@ struct fm_state {
   std::vector<uint64_t> traj_h;
   std::vector<int64_t> step_h;
   int64_t global_steps;
+  int64_t settled_step;       // global step at which the pending second pass last ran early (-1: never)
   int sticky;
   std::string err;
   int64_t launches;
@@ -350,6 +353,9 @@ fm_status sync_and_check(fm_state* s) {
     if (st & FM_DEVERR_TIMEOUT) return fail(s, FM_ETIMEOUT, "a bounded device wait gave up");
     if (st & FM_DEVERR_PIVOT) return fail(s, FM_ENUMERIC, "non-positive Cholesky pivot (U lost rank)");
     if (st & FM_DEVERR_NONFINITE) return fail(s, FM_ENUMERIC, "non-finite values in U");
+    if (st & FM_DEVERR_REORTH)
+      return fail(s, FM_ENUMERIC, "re-orthonormalisation did not converge (U^dag U - 1 still above the "
+                                  "first-order pass's reach after the extra pass)");
     return fail(s, FM_ENUMERIC, "device error flag " + std::to_string(st));
   }
   return FM_OK;
@@ -523,6 +529,27 @@ fm_status check_state(fm_state* s) {
   return FM_OK;
 }
 
+// A mixed-precision state whose step period is not complete (reorth_interval k > 1 and
+// the last step not a multiple of k) has had only the first CholeskyQR pass since its
+// last second pass: U^dag U - 1 is then ~1e-6..1e-5 instead of < 1e-7.  Observables
+// that read U first run that pending second pass now (in place: the buffers a captured
+// step graph uses stay put); span(U), the state itself, does not change.  The steps that
+// follow continue the usual k-step schedule.
+fm_status settle(fm_state* s) {
+  if (!s->mh || s->prm.reorth_interval <= 1 || s->global_steps % s->prm.reorth_interval == 0 ||
+      s->settled_step == s->global_steps)
+    return FM_OK;
+  MixedCtx& c = s->mc;
+  c.st = s->st;
+  c.V = s->V; c.V2 = s->V2;
+  c.launches = 0;
+  fm_status r = (fm_status)mixed_settle(s->mh, &c);
+  s->launches += c.launches;
+  if (r) return fail(s, r, c.err);
+  s->settled_step = s->global_steps;
+  return FM_OK;
+}
+
 // ------------------------------------------------------------------ FP64 CholeskyQR pass
 // G = U^dag U ; G = R^dag R ; T = R^-1 ; U <- U T
 fm_status cholqr_f64(fm_state* s) {
@@ -612,6 +639,7 @@ fm_status step_f64(fm_state* s) {
     a.xbuf = s->xbuf_d; a.vbuf = s->vbuf_d;
     a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
     a.dev_status = s->status_d;
+    a.force = s->force_d; a.force_n = s->force_n;
     s->timer.begin(FM_PH_MEASURE);
     if (pm_use_wide(L, N, B)) CK(pm_measure_wide(s->st, a, s->pmw, &s->launches));
     else CKL(pm_measure(s->st, a), 1);
@@ -667,6 +695,7 @@ fm_status step_poisson(fm_state* s) {
   a.xbuf = s->xbuf_d; a.vbuf = s->vbuf_d;
   a.log = s->log_d; a.log_count = (int64_t*)s->log_count_d; a.log_capacity = s->prm.event_capacity;
   a.dev_status = s->status_d;
+  a.force = nullptr; a.force_n = 0;
   const int nchx = band_chunks(s->Lx, s->Ly, N, B, 0, a.layout), nchy = band_chunks(s->Lx, s->Ly, N, B, 1, a.layout);
   std::vector<z64> taps;
   std::vector<int> list, cnt(B);
@@ -1015,6 +1044,7 @@ fm_status retune(fm_state* s, int tile_config, int reorth) {
     CKL(neel_init_v(s->st, s->V, s->Vh, s->Vl, L, N, B, s->occ_d), 1);
   }
   s->global_steps = 0;
+  s->settled_step = -1;
   for (int b = 0; b < B; ++b) s->step_h[b] = 0;
   if (s->prm.protocol == FM_PROJECTIVE_POISSON)
     for (int b = 0; b < B; ++b) poisson_sync(s, b);
@@ -1229,10 +1259,12 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->ws = (char*)d_workspace; s->ws_bytes = ws_bytes; s->pl = pl;
   s->global_steps = 0; s->sticky = 0; s->launches = 0;
   s->graphs_on = false; s->cap_st = nullptr; s->graph_exec = nullptr; s->graph_period = 0;
+  s->settled_step = -1;
   char* w = s->ws;
   s->gamma_d = (double*)(w + pl.gamma); s->traj_d = (uint64_t*)(w + pl.traj); s->step_d = (int64_t*)(w + pl.step);
   s->status_d = (int*)(w + pl.status); s->occ_d = (int*)(w + pl.occ);
   s->log_count_d = (unsigned long long*)(w + pl.log_count); s->log_d = (fm_event*)(w + pl.log);
+  s->force_d = (int4*)(w + pl.force); s->force_n = 0;
   s->part_d = (double*)(w + pl.part); s->nocc_d = (double*)(w + pl.nocc); s->w_d = (double*)(w + pl.w);
   s->xbuf_d = w + pl.xbuf; s->vbuf_d = w + pl.vbuf;
   s->G = (z64*)(w + pl.G); s->R = (z64*)(w + pl.R); s->T = (z64*)(w + pl.T);
@@ -1389,6 +1421,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
       c.gamma = s->gamma_d; c.traj = s->traj_d; c.step = s->step_d; c.status = s->status_d;
       c.part = s->part_d; c.nocc = s->nocc_d; c.w = s->w_d; c.xbuf = s->xbuf_d; c.vbuf = s->vbuf_d;
       c.log = s->log_d; c.log_count = (int64_t*)s->log_count_d; c.log_capacity = p->event_capacity;
+      c.force = s->force_d; c.force_n = 0;
       c.extra = s->mixed_extra; c.launches = 0; c.timer = &s->timer; c.pmw = s->pmw;
       c.prop_banded = 0;
       c.band_tx = s->band_tx; c.band_ty = s->band_ty; c.band_ox = s->band_ox; c.band_oy = s->band_oy;
@@ -1463,6 +1496,40 @@ fm_status fm_set_propagation(fm_state* s, int32_t mode) {
   return FM_OK;
 }
 
+fm_status fm_force_outcomes(fm_state* s, const fm_event* events, int32_t n) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (s->prm.protocol != FM_PROJECTIVE)
+    return fail(s, FM_EINVAL, "forced outcomes apply to the fixed-step projective protocol");
+  if (n < 0 || (n > 0 && !events)) return fail(s, FM_EINVAL, "bad forced-outcome list");
+  if (n > s->prm.event_capacity) return fail(s, FM_EINVAL, "more forced outcomes than event_capacity");
+  std::vector<int4> f(n);
+  for (int i = 0; i < n; ++i) {
+    const fm_event& e = events[i];
+    if (e.step < 0 || e.step > 0x7fffffff || e.traj < 0 || e.traj >= s->B || e.site < 0 || e.site >= s->L ||
+        (e.outcome != 0 && e.outcome != 1))
+      return fail(s, FM_EINVAL, "forced outcome " + std::to_string(i) + " out of range");
+    f[i] = make_int4((int)e.step, e.traj, e.site, e.outcome);
+  }
+  std::sort(f.begin(), f.end(), [](const int4& a, const int4& b) {
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+  });
+  for (int i = 1; i < n; ++i)
+    if (f[i].x == f[i - 1].x && f[i].y == f[i - 1].y && f[i].z == f[i - 1].z)
+      return fail(s, FM_EINVAL, "a measurement is listed twice");
+  CK(cudaStreamSynchronize(s->st));
+  if (n > 0) CK(cudaMemcpy(s->force_d, f.data(), sizeof(int4) * (size_t)n, cudaMemcpyHostToDevice));
+  s->force_n = n;
+  if (s->prm.precision != FM_FP64) s->mc.force_n = n;
+  if (s->graph_exec) {                 // the captured period holds the previous list's length
+    cudaGraphExecDestroy(s->graph_exec);
+    s->graph_exec = nullptr;
+  }
+  return FM_OK;
+}
+
 fm_status fm_set_gammas(fm_state* s, const double* gammas) {
   fm_status r = check_state(s);
   if (r) return r;
@@ -1512,6 +1579,7 @@ fm_status fm_entropy(fm_state* s, int32_t b, const int32_t* sites, int32_t n, do
   fm_status r = check_state(s);
   if (r) return r;
   if (!S_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  if ((r = settle(s))) return r;
   r = validate_sites(s, sites, n);
   if (r) return r;
   return entropy_impl(s, b, sites, n, S_out);
@@ -1521,9 +1589,28 @@ fm_status fm_entropy_async(fm_state* s, int32_t b, const int32_t* sites, int32_t
   fm_status r = check_state(s);
   if (r) return r;
   if (!ticket || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or ticket");
+  if ((r = settle(s))) return r;
   r = validate_sites(s, sites, n);
   if (r) return r;
   return entropy_async_impl(s, b, sites, n, ticket);
+}
+
+fm_status fm_entropy_ready(fm_state* s, int64_t ticket, int32_t* ready) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  if (!ready || ticket < 0 || ticket >= s->ea_next || ticket < s->ea_next - kAsyncSlots)
+    return fail(s, FM_EINVAL, "unknown or expired ticket");
+  if ((r = ea_check(s))) return r;
+  *ready = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->ea_mu);
+    if (s->ea_issued < ticket + 1) return FM_OK;
+  }
+  const cudaError_t e = cudaEventQuery(s->ea_done[(int)(ticket % kAsyncSlots)]);
+  if (e == cudaSuccess) *ready = 1;
+  else if (e != cudaErrorNotReady) return fail(s, FM_ECUDA, std::string("entropy event: ") + cudaGetErrorString(e));
+  else (void)cudaGetLastError();
+  return FM_OK;
 }
 
 fm_status fm_entropy_wait(fm_state* s, int64_t ticket, double* S_out) {
@@ -1566,6 +1653,7 @@ fm_status fm_density_correlation(fm_state* s, int32_t b, double* c_out) {
   fm_status r = check_state(s);
   if (r) return r;
   if (!c_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  if ((r = settle(s))) return r;
   const int L = s->L, N = s->N;
   const int S = std::max(1, L / 2);               // stripe width: the stripe fits the scratch next to U
   double* bins = s->obs;
@@ -1603,6 +1691,7 @@ fm_status fm_particle_covariance(fm_state* s, int32_t b, const int32_t* A, int32
   fm_status r = check_state(s);
   if (r) return r;
   if (!G_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  if ((r = settle(s))) return r;
   if ((r = validate_sites(s, A, nA)) || (r = validate_sites(s, B, nB))) return r;
   std::vector<int32_t> AB(A, A + nA);
   AB.insert(AB.end(), B, B + nB);
@@ -1638,6 +1727,7 @@ fm_status fm_mutual_info(fm_state* s, int32_t b, const int32_t* A, int32_t nA, c
   fm_status r = check_state(s);
   if (r) return r;
   if (!I_out || b < 0 || b >= s->B) return fail(s, FM_EINVAL, "bad trajectory index or output");
+  if ((r = settle(s))) return r;
   if ((r = validate_sites(s, A, nA)) || (r = validate_sites(s, B, nB))) return r;
   std::vector<int32_t> AB(A, A + nA);
   AB.insert(AB.end(), B, B + nB);
@@ -1656,6 +1746,7 @@ fm_status fm_copy_U(fm_state* s, int32_t b, void* host_c128, int64_t ld) {
   fm_status r = check_state(s);
   if (r) return r;
   if (b < 0 || b >= s->B || !host_c128 || ld < s->L) return fail(s, FM_EINVAL, "bad copy_U arguments");
+  if ((r = settle(s))) return r;
   const z64* src;
   BufGuard guard(s, s->st);                       // s->aux
   if (s->prm.precision == FM_FP64) src = s->U + (int64_t)b * s->L * s->N;
@@ -1794,6 +1885,7 @@ fm_status fm_load(fm_state* s, const char* path) {
     return fail(s, FM_EINVAL, "checkpoint does not match this state's parameters");
   CK(cudaStreamSynchronize(s->st));
   s->gamma_h = g; s->traj_h = t; s->step_h = st; s->global_steps = gsteps;
+  s->settled_step = -1;
   if (s->prm.protocol == FM_PROJECTIVE_POISSON)
     for (int b = 0; b < s->B; ++b) poisson_sync(s, b);
   CK(cudaMemcpy(s->gamma_d, g.data(), 8 * s->B, cudaMemcpyHostToDevice));
@@ -1820,6 +1912,21 @@ fm_status fm_phase_times(fm_state* s, double* ms, int64_t* counts) {
   fm_status r = check_state(s);
   if (r) return r;
   if (!s->timer.collect(ms, counts)) return fail(s, FM_ECUDA, "event timing failed");
+  return FM_OK;
+}
+
+fm_status fm_reorth_stats(fm_state* s, int64_t* checks, int64_t* extra_passes, double* maxima) {
+  fm_status r = check_state(s);
+  if (r) return r;
+  int64_t cnt[2] = {0, 0};
+  double mx[4] = {0.0, 0.0, 0.0, 0.0};
+  if (s->mh) {
+    if (mixed_guard_stats(s->mh, s->st, cnt, mx) != FM_OK) return fail(s, FM_ECUDA, "guard statistics readback");
+  }
+  if (checks) *checks = cnt[0];
+  if (extra_passes) *extra_passes = cnt[1];
+  if (maxima)
+    for (int i = 0; i < 4; ++i) maxima[i] = mx[i];
   return FM_OK;
 }
 
@@ -1866,7 +1973,7 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
   std::vector<int> cols;
   for (int i = 0; i < std::min(s->N, 64); ++i) cols.push_back((int)((int64_t)i * s->N / std::min(s->N, 64)));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  fm_tuning best{0, 1, 0.0, 0.0, 0, 0}, best1{0, 1, 0.0, 0.0, 0, 0};
+  fm_tuning best{0, 1, 0.0, 0.0, 0, 0, 0.0}, best1{0, 1, 0.0, 0.0, 0, 0, 0.0};
   bool have = false, have1 = false;
   int tried = 0, rejected = 0;
   do {
@@ -1887,20 +1994,26 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
         if ((r = sync_and_check(s))) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        double worst = 0.0;
+        // orthonormality after each of 2k single steps: at the period ends (after a second
+        // pass) against ortho_tol; in between (first pass only; observables settle such a
+        // state first, fm_entropy etc.) against 100 ortho_tol, where the next step's
+        // occupations, the only other reader, move by <= 1e-4 relative
+        double worst = 0.0, worst_mid = 0.0;
         for (int i = 0; i < period && r == FM_OK; ++i) {
           if ((r = fm_step(s, 1))) break;
+          const bool end = s->global_steps % k == 0;
           for (int b : {0, s->B - 1}) {
             double e = 0.0;
             if ((r = fm_orthonormality_error(s, b, cols.data(), (int)cols.size(), &e))) break;
-            worst = std::max(worst, e);
+            if (end) worst = std::max(worst, e);
+            else worst_mid = std::max(worst_mid, e);
           }
         }
         if (r) break;
-        fm_tuning cand{tc, k, (double)ms / nt, worst, 0, 0};
+        fm_tuning cand{tc, k, (double)ms / nt, worst, 0, 0, worst_mid};
         ++tried;
         if (k == 1 && (!have1 || cand.ms_per_step < best1.ms_per_step)) { best1 = cand; have1 = true; }
-        if (worst <= ortho_tol) {
+        if (worst <= ortho_tol && worst_mid <= 100.0 * ortho_tol) {
           if (!have || cand.ms_per_step < best.ms_per_step) { best = cand; have = true; }
         } else {
           ++rejected;

@@ -87,6 +87,14 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
                                  (int64_t)(n0 + c0) * p.Ntraj) + ti.part;
 #pragma unroll
     for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.Ntraj] = d[j];
+    if (p.estat) {
+      // largest off-diagonal |entry| of this row's slab (rowsum carries the running max)
+      float mx = (float)rowsum;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (m0 + r != n0 + c0 + j) mx = fmaxf(mx, fabsf(d[j]));
+      rowsum = (double)mx;
+    }
   } else if (MODE == MODE_ADDV) {
     // all 32 loads before the first store: the stores could alias the loads as far as
     // the compiler knows, so interleaving them would serialise on memory latency
@@ -146,6 +154,7 @@ __global__ void __launch_bounds__(256, 1)
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                    const Params p) {
   using C = Cfg<BN, CHUNKED>;
+  if (p.cond && *(volatile const int*)p.cond == 0) return;   // uniform: before any barrier or TMEM
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
@@ -332,6 +341,10 @@ __global__ void __launch_bounds__(256, 1)
         tc_fence_before();
         if (lane == 0) mbar_arrive(&tmem_empty[buf]);
         ++cbuf;
+      }
+      if (MODE == MODE_GRAM && p.estat) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint((float)rowsum));
+        if (lane == 0) atomicMax(&p.estat[2 * ti.b + 1], m);
       }
       if (MODE == MODE_PROP) {
         const int R = ti.mt * BM + r;

@@ -50,6 +50,12 @@ struct Params {
   int64_t ld_out;
   int L, Ntraj, C;
   int* status;
+  // GRAM: if set, per batch item b the largest |G_kl| over the off-diagonal entries the
+  // launch computes, atomically max-ed into estat[2 b + 1] as float bits (G is then a
+  // Gram of nearly orthonormal columns, so these are the entries of E = G - 1)
+  unsigned* estat;
+  // if set and *cond == 0 the launch does nothing (a conditional pass decided on the device)
+  const int* cond;
 };
 
 bool make_kmajor_map(CUtensorMap* m, const __half* base, uint64_t K, uint64_t rows, uint64_t ld, uint32_t box_rows);

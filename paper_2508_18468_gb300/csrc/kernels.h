@@ -50,6 +50,7 @@ struct pm_args {
   void* xbuf; void* vbuf;            // scratch: batch*N and batch*L complex (T of the layout)
   fm_event* log; int64_t* log_count; int log_capacity;
   int* dev_status;
+  const int4* force; int force_n;    // forced outcomes (fm_force_outcomes), sorted; n = 0: none
 };
 cudaError_t pm_measure(cudaStream_t st, const pm_args& a);
 // the same measurements as grid-wide kernels per event, all trajectories at once

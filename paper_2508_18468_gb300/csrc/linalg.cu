@@ -225,36 +225,62 @@ FM_DEVFN void split16(float x, __half& h, __half& l) {
   l = __float2half_rn((x - __half2float(h)) * 2048.0f);
 }
 
-// rows: blockIdx.x * 256 + tid of the 2L rows; columns: 8 consecutive of the B*N
-// (N is a multiple of 8 on this path, so a group never spans two trajectories).
-__global__ void scale_rows_v_kernel(float* V, __half* Vh, __half* Vl, int L, int N, int64_t ngroups,
-                                    const double* __restrict__ w) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= 2 * L) return;
+// One thread scales 4 consecutive rows (of the 2L) of a run of columns: 16-byte loads
+// and stores of V, 8-byte stores of each fp16 plane, the 4 weights reloaded only when
+// the run enters the next trajectory; 4 columns' loads are issued before their stores.
+// Grid (2L / 1024 row blocks, column runs); 2L is a multiple of 4 (L even).
+__global__ void __launch_bounds__(256) scale_rows_v_kernel(float* __restrict__ V, __half* __restrict__ Vh,
+                                                           __half* __restrict__ Vl, int L, int N, int64_t ncols,
+                                                           int64_t run, const double* __restrict__ w) {
+  const int r0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (r0 >= 2 * L) return;
   const int64_t L2 = 2 * (int64_t)L;
-  for (int64_t g = blockIdx.y; g < ngroups; g += gridDim.y) {
-    const int64_t c0 = g * 8;
-    const int64_t b = c0 / N;
-    const float s = (float)w[b * L + (r < L ? r : r - L)];
+  const int64_t c0 = blockIdx.y * run, c1 = min(ncols, c0 + run);
+  int64_t bcur = -1;
+  float s[4];
+  for (int64_t c = c0; c < c1; c += 4) {
+    const int nc = (int)(c1 - c < 4 ? c1 - c : 4);
+    float4 x[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int64_t idx = r + (c0 + q) * L2;
-      const float x = V[idx] * s;
-      V[idx] = x;
-      __half h, l;
-      split16(x, h, l);
-      Vh[idx] = h;
-      Vl[idx] = l;
+    for (int q = 0; q < 4; ++q)
+      if (q < nc) x[q] = *(const float4*)(V + r0 + (c + q) * L2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= nc) break;
+      const int64_t b = (c + q) / N;
+      if (b != bcur) {
+        bcur = b;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = r0 + e;
+          s[e] = (float)w[b * L + (r < L ? r : r - L)];
+        }
+      }
+      float4 y = x[q];
+      y.x *= s[0]; y.y *= s[1]; y.z *= s[2]; y.w *= s[3];
+      const int64_t idx = r0 + (c + q) * L2;
+      *(float4*)(V + idx) = y;
+      __align__(8) __half h[4], l[4];
+      split16(y.x, h[0], l[0]);
+      split16(y.y, h[1], l[1]);
+      split16(y.z, h[2], l[2]);
+      split16(y.w, h[3], l[3]);
+      *(uint2*)(Vh + idx) = *(const uint2*)h;
+      *(uint2*)(Vl + idx) = *(const uint2*)l;
     }
   }
 }
 
 cudaError_t scale_rows_v(cudaStream_t st, float* V, __half* Vh, __half* Vl, int L, int N, int batch,
                          const double* w) {
-  if (N % 8) return cudaErrorInvalidValue;
-  const int64_t ngroups = (int64_t)batch * N / 8;
-  dim3 grid(FM_CEIL_DIV(2 * L, 256), (unsigned)std::min<int64_t>(ngroups, 65535));
-  scale_rows_v_kernel<<<grid, 256, 0, st>>>(V, Vh, Vl, L, N, ngroups, w);
+  if (L % 2) return cudaErrorInvalidValue;
+  const int64_t ncols = (int64_t)batch * N;
+  const unsigned rblocks = (unsigned)FM_CEIL_DIV(2 * (int64_t)L, 1024);
+  // about 8 resident blocks per SM in total, each over a run of columns
+  const int64_t want = std::max<int64_t>(1, (int64_t)152 * 8 / rblocks);
+  const int64_t run = std::max<int64_t>(4, ((ncols + want - 1) / want + 3) / 4 * 4);
+  const unsigned cruns = (unsigned)FM_CEIL_DIV(ncols, run);
+  scale_rows_v_kernel<<<dim3(rblocks, cruns), 256, 0, st>>>(V, Vh, Vl, L, N, ncols, run, w);
   return cudaGetLastError();
 }
 
@@ -347,6 +373,10 @@ __global__ void __launch_bounds__(1024) pm_kernel(pm_args a) {
       philox_out o = fm_draw(a.seed, traj, step, j, FM_TAG_MEASURE);
       s = fm_u53(o.w[0], o.w[1]) < pmeas;
       uo = fm_u53(o.w[2], o.w[3]);
+      if (s && a.force_n > 0) {
+        const int fo = fm_forced_outcome(a.force, a.force_n, step, b, j);
+        if (fo >= 0) uo = fm_forced_u(fo);
+      }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, s);
     if (lane == 0) warp_cnt[warp] = __popc(bal);
@@ -427,7 +457,8 @@ struct PmEvent {
 
 __global__ void __launch_bounds__(1024) pm_select_kernel(const double* gamma, double dt, const uint64_t* traj,
                                                          const int64_t* step, uint64_t seed, int L, int* list,
-                                                         double* ulist, int* count) {
+                                                         double* ulist, int* count, const int4* force,
+                                                         int force_n) {
   const int b = blockIdx.x;
   const double pmeas = 1.0 - exp(-gamma[b] * dt);
   __shared__ int warp_cnt[33];
@@ -443,6 +474,10 @@ __global__ void __launch_bounds__(1024) pm_select_kernel(const double* gamma, do
       philox_out o = fm_draw(seed, traj[b], step[b], j, FM_TAG_MEASURE);
       sel = fm_u53(o.w[0], o.w[1]) < pmeas;
       uo = fm_u53(o.w[2], o.w[3]);
+      if (sel && force_n > 0) {
+        const int fo = fm_forced_outcome(force, force_n, step[b], b, j);
+        if (fo >= 0) uo = fm_forced_u(fo);
+      }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, sel);
     if (lane == 0) warp_cnt[warp] = __popc(bal);
@@ -559,7 +594,8 @@ __global__ void pm_update_kernel(void* Ub, int L, int N, int kchunk, const void*
 }
 
 cudaError_t pm_select(cudaStream_t st, const pm_args& a, int* list, double* ulist, int* count) {
-  pm_select_kernel<<<a.batch, 1024, 0, st>>>(a.gamma, a.dt, a.traj, a.step, a.seed, a.L, list, ulist, count);
+  pm_select_kernel<<<a.batch, 1024, 0, st>>>(a.gamma, a.dt, a.traj, a.step, a.seed, a.L, list, ulist, count,
+                                             a.force, a.force_n);
   return cudaGetLastError();
 }
 
@@ -573,7 +609,8 @@ cudaError_t pm_measure_wide(cudaStream_t st, const pm_args& a, void* scratch, in
   int* count = (int*)s;
   s += (((int64_t)a.batch * 4) + 255) & ~(int64_t)255;
   PmEvent* ev = (PmEvent*)s;
-  pm_select_kernel<<<a.batch, 1024, 0, st>>>(a.gamma, a.dt, a.traj, a.step, a.seed, a.L, list, ulist, count);
+  pm_select_kernel<<<a.batch, 1024, 0, st>>>(a.gamma, a.dt, a.traj, a.step, a.seed, a.L, list, ulist, count,
+                                             a.force, a.force_n);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   ++*launches;

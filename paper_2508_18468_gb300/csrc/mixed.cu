@@ -37,6 +37,29 @@ int pick_gm(int tile_config) {
   return g ? (1 << (g + 1)) : 8;
 }
 
+// Second-pass guard, in device memory: per trajectory b the largest |diag E| and
+// off-diagonal |E| (float bits, E = G - 1 of the second pass's Gram) in e2[2b], e2[2b+1];
+// the same for the conditional extra pass in e3; the extra-pass flag; counters (second
+// passes checked, extra passes run); the running maxima since the last query (e2 diag,
+// e2 off-diagonal, e3 diag, e3 off-diagonal, float bits).
+struct GuardPtrs {
+  unsigned *e2, *e3;
+  int* flag;
+  unsigned long long* counters;
+  unsigned* seen;
+};
+size_t guard_bytes(int B) { return (size_t)16 * B + 64; }
+GuardPtrs guard_ptrs(void* base, int B) {
+  GuardPtrs g;
+  char* p = (char*)base;
+  g.counters = (unsigned long long*)p;          // [0] checks, [1] extra passes
+  g.seen = (unsigned*)(p + 16);                 // [4]
+  g.flag = (int*)(p + 32);
+  g.e2 = (unsigned*)(p + 64);
+  g.e3 = g.e2 + 2 * B;
+  return g;
+}
+
 struct Scratch {
   size_t total = 0;
   size_t tiles_prop, tiles_gram, tiles_trmm, tiles_trmm2, urm_h, urm_l;
@@ -46,6 +69,7 @@ struct Scratch {
   int pb_kc = 0;
   size_t ca_h, ca_l, cb_h, cb_l, cd, xs;   // complex tensor GEMM helper (Cholesky recursion)
   size_t gf, rf, tf, dinvf, xf, diag;     // complex64 Gram / factor / inverse, FP64 Gram diagonal
+  size_t guard;                           // second-pass guard (ReorthGuard layout)
   size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
 };
 
@@ -83,6 +107,7 @@ Scratch scratch_plan(int Lx, int Ly, int B, int protocol) {
   s.dinvf = s.take((int64_t)B * ((N + 31) / 32) * 32 * 32 * 8);
   s.xf = s.take((int64_t)B * N * 32 * 8);
   s.diag = s.take((int64_t)B * N * 8);
+  s.guard = s.take(guard_bytes(B));
   if (uses_pm_block(protocol, (int)L, B)) {
     const int64_t Kc = pmb_capacity((int)L);
     s.pb_kc = (int)Kc;
@@ -129,7 +154,8 @@ FM_DEVFN void split16_f(float v, __half& h, __half& l) {
 // One block per row (b, c) of Z~ (2N halves), eight K positions per thread and
 // pass, written as 16-byte stores of each plane.
 __global__ void __launch_bounds__(256) build_ttilde_kernel(const c32* __restrict__ Z, const double* __restrict__ diag,
-                                                           int mode, int N, __half* Th, __half* Tl) {
+                                                           int mode, int N, __half* Th, __half* Tl, const int* cond) {
+  if (cond && *cond == 0) return;
   const int N2 = 2 * N;
   const int64_t row = blockIdx.x;
   const int64_t b = row / N2;
@@ -266,7 +292,8 @@ __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ 
 // Grid (L / 64, 2N / 64, B), block (32, 8).
 __global__ void __launch_bounds__(256) transpose_planes_kernel(const __half* __restrict__ Vh,
                                                                const __half* __restrict__ Vl, int L, int N,
-                                                               __half* Uh, __half* Ul) {
+                                                               __half* Uh, __half* Ul, const int* cond) {
+  if (cond && *cond == 0) return;
   __shared__ __half2 sh[64][33];                  // [c][i pair]
   __shared__ __half2 sl[64][33];
   const int i0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
@@ -294,7 +321,10 @@ __global__ void __launch_bounds__(256) transpose_planes_kernel(const __half* __r
 // double) and the same value on the diagonal of the complex64 Gram.  Replaces
 // the tensor-core diagonal, whose fp32 accumulator loses up to one ulp per
 // 16-deep MMA, biased toward zero on these all-positive sums.
-__global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int B, double* diag, c32* G) {
+// estat (second pass): the largest |diag_b[k] - 1| into estat[2b] as float bits.
+__global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int B, double* diag, c32* G,
+                                 unsigned* estat, const int* cond) {
+  if (cond && *cond == 0) return;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)B * N) return;
@@ -318,7 +348,56 @@ __global__ void gram_diag_kernel(const float* __restrict__ V, int L, int N, int 
   if (lane == 0) {
     diag[b * N + k] = acc;
     G[b * (int64_t)N * N + k + k * (int64_t)N] = cmk((float)acc, 0.0f);
+    if (estat) atomicMax(&estat[2 * b], __float_as_uint((float)fabs(acc - 1.0)));
   }
+}
+
+// The guard of the first-order second pass.  With G = 1 + E (E Hermitian), S the strict
+// upper part of E and D its diagonal, the closed-form factor T = 1 - S - D/2 leaves
+//   T^dag G T - 1 = -(F^dag F + F^2 + F^dag^2) + O(E^3),   F = S + D/2,
+// whose entries are bounded by 3 (N o^2 + o d) + (3/4) d^2 (o = max |S|, d = max |D|).
+// final == 0 (the second pass): flag = 1 when that bound exceeds tau for any trajectory,
+// so the conditional extra pass runs; final != 0 (the extra pass, which measured the E
+// the second pass left): a bound above tau means two closed-form passes were not enough
+// (U ill-conditioned beyond the float Gram's reach), reported as FM_DEVERR_REORTH.
+// Clears the statistics it read.  One warp.
+__global__ void reorth_guard_kernel(unsigned* e, int B, int N, float tau, int final, int* flag,
+                                    unsigned long long* counters, unsigned* seen, int* status) {
+  const int lane = threadIdx.x;
+  unsigned dmax = 0u, omax = 0u;
+  int over = 0;
+  for (int b = lane; b < B; b += 32) {
+    const float d = __uint_as_float(e[2 * b]), o = __uint_as_float(e[2 * b + 1]);
+    e[2 * b] = 0u;
+    e[2 * b + 1] = 0u;
+    const float bound = 3.0f * ((float)N * o * o + o * d) + 0.75f * d * d;
+    over |= (bound > tau || !(bound == bound)) ? 1 : 0;
+    dmax = max(dmax, __float_as_uint(d));
+    omax = max(omax, __float_as_uint(o));
+  }
+  over = __any_sync(0xffffffffu, over);
+  dmax = __reduce_max_sync(0xffffffffu, dmax);
+  omax = __reduce_max_sync(0xffffffffu, omax);
+  if (lane == 0) {
+    const int k = final ? 2 : 0;
+    seen[k] = max(seen[k], dmax);
+    seen[k + 1] = max(seen[k + 1], omax);
+    if (!final) {
+      counters[0] += 1ull;
+      if (over) counters[1] += 1ull;
+      *flag = over;
+    } else if (over && status) {
+      atomicOr(status, FM_DEVERR_REORTH);
+    }
+  }
+}
+
+// dst = src (float4 words) unless cond is set and *cond == 0.
+__global__ void copy_cond_kernel(const float4* __restrict__ src, float4* __restrict__ dst, int64_t n4,
+                                 const int* cond) {
+  if (cond && *cond == 0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 }  // namespace
@@ -334,6 +413,7 @@ struct MixedHost {
   int64_t md;        // largest block dimension of the Cholesky recursion products
   c32 *gf, *rf, *tf, *dinvf, *xf;
   double* diag;
+  GuardPtrs guard;
   CUtensorMap prop_Ah, prop_Al, prop_Bh, prop_Bl;
   CUtensorMap gram_Ah, gram_Al, gram_Bh, gram_Bl;
   CUtensorMap trmm_Ah, trmm_Al, trmm_Bh, trmm_Bl;
@@ -407,6 +487,7 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   h->dinvf = (c32*)(base + sp.dinvf);
   h->xf = (c32*)(base + sp.xf);
   h->diag = (double*)(base + sp.diag);
+  h->guard = guard_ptrs(base + sp.guard, B);
   h->pmb = uses_pm_block(c->protocol, L, B);
   if (h->pmb) {
     const int64_t Kc = sp.pb_kc;
@@ -462,6 +543,7 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
             cudaMemcpyAsync(h->tiles_trmm, tt.data(), tt.size() * 16, cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
             cudaMemcpyAsync(h->tiles_trmm2, tt2.data(), tt2.size() * 16, cudaMemcpyHostToDevice, c->st) ==
                 cudaSuccess &&
+            cudaMemsetAsync(base + sp.guard, 0, guard_bytes(B), c->st) == cudaSuccess &&
             cudaStreamSynchronize(c->st) == cudaSuccess;
   if (!ok) { *why = "tile upload"; delete h; return nullptr; }
   const uint64_t L2 = 2 * (uint64_t)L, N2 = 2 * (uint64_t)N;
@@ -603,14 +685,30 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   return FM_OK;
 }
 
+// Target of the second-pass guard: the bound on the entries of U^dag U - 1 that the
+// first-order factor may leave (a tenth of the 1e-6 orthonormality bar).
+constexpr float kReorthTau = 1e-7f;
+
 // One CholeskyQR pass on V: Gram (tensor) -> inverse factor -> U <- U + U (T - 1) (tensor).
 // first == true: T = R^-1 from the recursive factorisation (G far from 1), and
 //   the product accumulates in fp32 registers every 2 K-blocks;
 // first == false: G = 1 + E with |E| small after a full pass, T = 1 - F to first
-//   order (O(|E|^2) error), F built from G with its float64 diagonal.
-int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired) {
+//   order (O(|E|^2) error), F built from G with its float64 diagonal; the Gram's
+//   epilogue and diagonal kernel record the largest entries of E for the guard
+//   (reorth_guard_kernel).
+// how a pass leaves the state: PASS_SWAP the product in V2, then V and V2 swap (host
+// pointers); PASS_EXTRA a closed-form pass run only when the guard's device flag is set
+// (every launch returns at once when it is clear), the product copied back into V;
+// PASS_INPLACE the product copied back into V unconditionally.  The last two keep the
+// buffers where a captured step graph expects them.
+enum PassMode { PASS_SWAP = 0, PASS_EXTRA = 1, PASS_INPLACE = 2 };
+
+int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired, int mode = PASS_SWAP) {
   const int L = c->L, N = c->N, B = c->B, BN = h->BN;
   const int grid = tc::sm_count();
+  const bool extra = mode == PASS_EXTRA;
+  const int* cond = extra ? h->guard.flag : nullptr;
+  unsigned* estat = first ? nullptr : (extra ? h->guard.e3 : h->guard.e2);
   tc::Params p = base_params(c, h);
   p.mode = tc::MODE_GRAM;
   p.ntiles = h->n_gram;
@@ -621,10 +719,18 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired) {
   p.k_shift = L;
   p.kdim = 2 * L;
   p.out_gf = (float*)h->gf;
+  p.estat = estat;
+  p.cond = cond;
   c->timer->begin(FM_PH_GRAM);
   MCK(tc::launch(c->st, BN, h->gram_Ah, h->gram_Al, h->gram_Bh, h->gram_Bl, p, grid));
-  gram_diag_kernel<<<FM_CEIL_DIV((int64_t)B * N * 32, 256), 256, 0, c->st>>>(c->V, L, N, B, h->diag, h->gf);
+  gram_diag_kernel<<<FM_CEIL_DIV((int64_t)B * N * 32, 256), 256, 0, c->st>>>(c->V, L, N, B, h->diag, h->gf, estat,
+                                                                             cond);
   MCK(cudaGetLastError());
+  if (!first) {
+    reorth_guard_kernel<<<1, 32, 0, c->st>>>(estat, B, N, kReorthTau, extra ? 1 : 0, h->guard.flag,
+                                             h->guard.counters, h->guard.seen, c->status);
+    MCK(cudaGetLastError());
+  }
   c->timer->end(FM_PH_GRAM);
   c->timer->begin(FM_PH_CHOLESKY);
   if (first) {
@@ -632,10 +738,10 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired) {
     if (r) return r;
   }
   build_ttilde_kernel<<<(unsigned)(2 * (int64_t)B * N), 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag,
-                                                                          first ? 0 : 1, N, c->Th, c->Tl);
+                                                                          first ? 0 : 1, N, c->Th, c->Tl, cond);
   MCK(cudaGetLastError());
   transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
-                                                                                  h->urm_l);
+                                                                                  h->urm_l, cond);
   MCK(cudaGetLastError());
   c->timer->end(FM_PH_CHOLESKY);
   // first pass: 128-wide tiles (fp32 register accumulation every 2 K-blocks when no
@@ -654,6 +760,7 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired) {
   p.out_h = c->Vh;
   p.out_l = c->Vl;
   p.in_f = c->V;
+  p.cond = cond;
   // the first pass drains TMEM into fp32 registers every 2 K-blocks when its result
   // stays the state until the next step (the fp32 TMEM accumulators round toward zero:
   // up to ~1e-4 relative over 16384 terms); when the second pass follows at once it
@@ -662,9 +769,22 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired) {
   c->timer->begin(FM_PH_TRMM);
   if (wide2) MCK(tc::launch(c->st, 256, h->trmm_Ah, h->trmm_Al, h->trmm2_Bh, h->trmm2_Bl, p, grid));
   else MCK(tc::launch(c->st, 128, h->trmm_Ah, h->trmm_Al, h->trmm_Bh, h->trmm_Bl, p, grid));
+  if (mode != PASS_SWAP) {
+    const int64_t n4 = (int64_t)B * 2 * L * N / 4;
+    copy_cond_kernel<<<(unsigned)std::min<int64_t>(FM_CEIL_DIV(n4, 256), 8 * grid), 256, 0, c->st>>>(
+        (const float4*)c->V2, (float4*)c->V, n4, cond);
+    MCK(cudaGetLastError());
+  }
   c->timer->end(FM_PH_TRMM);
-  std::swap(c->V, c->V2);
+  if (mode == PASS_SWAP) std::swap(c->V, c->V2);
   return FM_OK;
+}
+
+// The second (closed-form) pass and, when its guard asks for it, one more.
+int second_pass(MixedHost* h, MixedCtx* c, int mode = PASS_SWAP) {
+  int r = qr_pass(h, c, false, true, mode);
+  if (r) return r;
+  return qr_pass(h, c, false, true, PASS_EXTRA);
 }
 
 // Tensor-core product D = A B^T of K-major fp16 planes (raster tile order, one
@@ -710,6 +830,7 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   pm_args a;
   a.U = c->V; a.L = L; a.N = N; a.batch = B; a.layout = 1;
   a.gamma = c->gamma; a.dt = c->dt; a.traj = c->traj; a.step = c->step; a.seed = c->seed;
+  a.force = c->force; a.force_n = c->force_n;
   MCK(pm_select(c->st, a, h->pb_list, h->pb_ulist, h->pb_count));
   int* hc = h->pb_hcount.data();
   MCK(cudaMemcpyAsync(hc, h->pb_count, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st));
@@ -727,7 +848,7 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   // propagation writes the float state only, so its planes are made here)
   MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
   transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
-                                                                                  h->urm_l);
+                                                                                  h->urm_l, nullptr);
   MCK(cudaGetLastError());
   MCK(pmb_setup(c->st, h->pb_list, h->pb_count, L, B, kmax, h->pb_pos));
   MCK(cudaMemsetAsync(m.C, 0, sizeof(c32) * 7 * (size_t)B * m.sM, c->st));
@@ -765,12 +886,36 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
 
 }  // namespace
 
+int mixed_guard_stats(MixedHost* h, cudaStream_t st, int64_t* counts, double* maxima) {
+  unsigned char buf[32];
+  if (cudaMemcpyAsync(buf, h->guard.counters, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FM_ECUDA;
+  unsigned long long cnt[2];
+  unsigned seen[4];
+  memcpy(cnt, buf, 16);
+  memcpy(seen, buf + 16, 16);
+  counts[0] = (int64_t)cnt[0];
+  counts[1] = (int64_t)cnt[1];
+  for (int i = 0; i < 4; ++i) {
+    float f;
+    memcpy(&f, &seen[i], 4);
+    maxima[i] = (double)f;
+  }
+  // the maxima restart from zero; the counters keep counting
+  if (cudaMemsetAsync(h->guard.seen, 0, 16, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return FM_ECUDA;
+  return FM_OK;
+}
+
+int mixed_settle(MixedHost* h, MixedCtx* c) { return second_pass(h, c, PASS_INPLACE); }
+
 int mixed_reorth(MixedHost* h, MixedCtx* c) {
   const int L = c->L, N = c->N, B = c->B;
   MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
   int r = qr_pass(h, c, true, true);
   if (r) return r;
-  return qr_pass(h, c, false, true);
+  return second_pass(h, c);
 }
 
 int mixed_step(MixedHost* h, MixedCtx* c) {
@@ -795,7 +940,7 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     const bool second = (c->global_step + 1) % c->reorth_interval == 0;
     int r = qr_pass(h, c, true, second);
     if (r) return r;
-    if (second && (r = qr_pass(h, c, false, true))) return r;
+    if (second && (r = second_pass(h, c))) return r;
     MCK(bump_steps(c->st, c->step, B));
     return FM_OK;
   }
@@ -838,7 +983,7 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     int r = qr_pass(h, c, true, second);
     if (r) return r;
     if (second) {
-      r = qr_pass(h, c, false, true);
+      r = second_pass(h, c);
       if (r) return r;
     }
   } else {
@@ -848,6 +993,7 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     a.xbuf = c->xbuf; a.vbuf = c->vbuf;
     a.log = c->log; a.log_count = c->log_count; a.log_capacity = c->log_capacity;
     a.dev_status = c->status;
+    a.force = c->force; a.force_n = c->force_n;
     c->timer->begin(FM_PH_MEASURE);
     bool done = false;
     if (h->pmb) {
@@ -868,7 +1014,7 @@ int mixed_step(MixedHost* h, MixedCtx* c) {
     if ((c->global_step + 1) % k == 0) {
       int r = qr_pass(h, c, true, true);
       if (r) return r;
-      r = qr_pass(h, c, false, true);
+      r = second_pass(h, c);
       if (r) return r;
     }
   }

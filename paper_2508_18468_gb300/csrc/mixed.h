@@ -27,6 +27,7 @@ struct MixedCtx {
   double *part, *nocc, *w;
   void *xbuf, *vbuf;
   fm_event* log; int64_t* log_count; int log_capacity;
+  const int4* force; int force_n;   // forced projective outcomes (sorted), n = 0: none
   void* extra;             // mixed_scratch_bytes() of device scratch
   PhaseTimer* timer;       // phase events (may be off)
   void* pmw;               // scratch of the grid-wide projective update
@@ -47,5 +48,12 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why);   // uploads tile lists,
 void mixed_free(MixedHost* h);
 int mixed_step(MixedHost* h, MixedCtx* c);               // returns an fm_status value
 int mixed_reorth(MixedHost* h, MixedCtx* c);             // fp16 planes of V, then both CholeskyQR passes
+// the second CholeskyQR pass (and its guard's extra pass) on the current state, the
+// product written back into V (the buffers stay put): completes a step period early
+int mixed_settle(MixedHost* h, MixedCtx* c);
+// second-pass guard: counts[0] passes checked, counts[1] extra passes run (since init);
+// maxima[0..3] the largest |diag E|, |offdiag E| measured by the second passes and by the
+// extra passes since the previous call (which then restart from zero).  Synchronises st.
+int mixed_guard_stats(MixedHost* h, cudaStream_t st, int64_t* counts, double* maxima);
 
 }  // namespace fm

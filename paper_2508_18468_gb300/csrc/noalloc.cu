@@ -6,6 +6,7 @@
 // synchronisation that freeing memory implies.  For them, the scratch of this
 // entry point lives in one fixed array in the library's static device memory,
 // which every GPU that loads the library keeps until the process exits.
+#include <algorithm>
 #include <mutex>
 
 #include "fm.h"
@@ -26,12 +27,29 @@ constexpr size_t kPbOff = kWbOff + al((size_t)kMaxM * 16);
 constexpr size_t kDOff = kPbOff + al((size_t)fm::hermitian_entropy_pbuf(kMaxM) * 16);
 constexpr size_t kEOff = kDOff + al((size_t)kMaxM * 8);
 constexpr size_t kLamOff = kEOff + al((size_t)kMaxM * 8);
-constexpr size_t kSitesOff = kLamOff + al((size_t)kMaxM * 8);
-constexpr size_t kTotal = kSitesOff + al((size_t)kMaxRows * 4);
+constexpr size_t kTotal = kLamOff + al((size_t)kMaxM * 8);
 
 // The scratch itself.  In host code this name is only a stand-in, never a
 // device address; the address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char fm_noalloc_scratch[kTotal];
+
+// The subsystem's sites travel inside the gather kernel's parameters (4 KB, within the
+// 32 KB parameter space of current GPUs), so the call makes no host-to-device copy.
+struct SiteList {
+  int32_t s[kMaxRows];
+};
+
+// rows[a + k n] = U[site_a + k L]: the rows of A, n x N column-major.
+__global__ void gather_sites_kernel(const z64* __restrict__ U, int L, int N, const SiteList sl, int n,
+                                    z64* __restrict__ rows) {
+  const int64_t tot = (int64_t)n * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % n);
+    const int64_t k = idx / n;
+    rows[idx] = U[sl.s[a] + k * L];
+  }
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -82,11 +100,14 @@ extern "C" fm_status fm_entropy_noalloc(const void* d_U, int32_t L, int32_t N, c
   double* d = (double*)(base + kDOff);
   double* e = (double*)(base + kEOff);
   double* lam = (double*)(base + kLamOff);
-  int* dsites = (int*)(base + kSitesOff);
   // Every scratch word read below is written first in the same call, so no
   // clearing is needed between calls.
-  if (cudaMemcpyAsync(dsites, sites, sizeof(int) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return FM_ECUDA;
-  if (gather_rows_z(st, (const z64*)d_U, L, N, dsites, n, rows) != cudaSuccess) return FM_ECUDA;
+  SiteList sl;
+  for (int i = 0; i < n; ++i) sl.s[i] = sites[i];
+  const int64_t tot = (int64_t)n * N;
+  const unsigned grid = (unsigned)std::min<int64_t>((tot + 255) / 256, 4 * 152);
+  gather_sites_kernel<<<grid, 256, 0, st>>>((const z64*)d_U, L, N, sl, n, rows);
+  if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
   const z64 one = {1.0, 0.0}, zero = {0.0, 0.0};
   const int m = n <= N ? n : N;
   cudaError_t ce = (n <= N)

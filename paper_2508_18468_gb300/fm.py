@@ -39,7 +39,7 @@ class fm_event(ctypes.Structure):
 class fm_tuning(ctypes.Structure):
     _fields_ = [("tile_config", ctypes.c_int32), ("reorth_interval", ctypes.c_int32),
                 ("ms_per_step", ctypes.c_double), ("ortho_err", ctypes.c_double),
-                ("tried", ctypes.c_int32), ("rejected", ctypes.c_int32)]
+                ("tried", ctypes.c_int32), ("rejected", ctypes.c_int32), ("ortho_mid", ctypes.c_double)]
 
 
 class FmError(RuntimeError):
@@ -67,6 +67,7 @@ def _load():
         "fm_mutual_info": (i32, [vp, i32, P(i32), i32, P(i32), i32, P(dbl)]),
         "fm_entropy_async": (i32, [vp, i32, P(i32), i32, P(i64)]),
         "fm_entropy_wait": (i32, [vp, i64, P(dbl)]),
+        "fm_entropy_ready": (i32, [vp, i64, P(i32)]),
         "fm_copy_U": (i32, [vp, i32, vp, i64]),
         "fm_set_U": (i32, [vp, i32, vp, i64]),
         "fm_occupations": (i32, [vp, i32, P(dbl)]),
@@ -88,6 +89,8 @@ def _load():
         "fm_particle_covariance": (i32, [vp, i32, P(i32), i32, P(i32), i32, P(dbl)]),
         "fm_set_entropy_method": (i32, [vp, i32]),
         "fm_entropy_sketch_info": (i32, [vp, P(i32), P(dbl), P(i32)]),
+        "fm_reorth_stats": (i32, [vp, P(i64), P(i64), P(dbl)]),
+        "fm_force_outcomes": (i32, [vp, P(fm_event), i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -147,8 +150,8 @@ def autotune(params, steps=4, max_reorth=4, ortho_tol=1e-6, use_graphs=True, dev
     if code != FM_OK:
         raise FmError(code, "fm_autotune failed")
     return {"tile_config": out.tile_config, "reorth_interval": out.reorth_interval,
-            "ms_per_step": out.ms_per_step, "ortho_err": out.ortho_err, "tried": out.tried,
-            "rejected": out.rejected}
+            "ms_per_step": out.ms_per_step, "ortho_err": out.ortho_err, "ortho_mid": out.ortho_mid,
+            "tried": out.tried, "rejected": out.rejected}
 
 
 class Trajectories:
@@ -230,6 +233,12 @@ class Trajectories:
         self._check(lib.fm_entropy_wait(self._h, int(ticket), ctypes.byref(out)))
         return out.value
 
+    def entropy_ready(self, ticket):
+        """True if entropy_wait(ticket) would return at once."""
+        out = ctypes.c_int32()
+        self._check(lib.fm_entropy_ready(self._h, int(ticket), ctypes.byref(out)))
+        return bool(out.value)
+
     def mutual_info(self, A, B, b=0):
         a, pa = _i32_array(A)
         c, pb = _i32_array(B)
@@ -298,6 +307,15 @@ class Trajectories:
               for i in range(count.value)]
         return ev, dropped.value
 
+    def force_outcomes(self, events):
+        """Replay: events as (traj, step, site, outcome) tuples (the first, second, third and last
+        fields of take_events() entries also fit); an empty list clears the replay."""
+        events = list(events)
+        buf = (fm_event * max(1, len(events)))()
+        for i, e in enumerate(events):
+            buf[i].traj, buf[i].step, buf[i].site, buf[i].outcome = int(e[0]), int(e[1]), int(e[2]), int(e[-1])
+        self._check(lib.fm_force_outcomes(self._h, buf, len(events)))
+
     def save(self, path):
         self._check(lib.fm_save(self._h, str(path).encode()))
 
@@ -316,6 +334,15 @@ class Trajectories:
         cnt = (ctypes.c_int64 * len(PHASES))()
         self._check(lib.fm_phase_times(self._h, ms, cnt))
         return {name: (ms[i], cnt[i]) for i, name in enumerate(PHASES)}
+
+    def reorth_stats(self):
+        """Second-pass guard of the mixed path: (checks, extra_passes, [d2, o2, d3, o3]) -- the
+        largest diagonal / off-diagonal |U^dag U - 1| measured by the second passes and the extra
+        passes since the previous call."""
+        c, e = ctypes.c_int64(), ctypes.c_int64()
+        mx = (ctypes.c_double * 4)()
+        self._check(lib.fm_reorth_stats(self._h, ctypes.byref(c), ctypes.byref(e), mx))
+        return c.value, e.value, list(mx)
 
     @property
     def kernel_launches(self):

@@ -319,3 +319,36 @@ def test_continuous_time_projective_checkpoint_and_graph_request(fm, tmp_path):
     c.step(10)
     for t in range(2):
         assert np.array_equal(a.copy_U(t), c.copy_U(t))
+
+
+def test_forced_outcomes_replay_oracle(fm):
+    """fm_force_outcomes against the oracle's forced replay: in five of steps 2-11 the first
+    measurement with 0.05 < p < 0.95 gets the outcome opposite to the natural one; every
+    other measurement is decided by its draw.  Outcomes and C = U U^dag equal the oracle's
+    run with the same forced outcomes, and the forced measurements are logged with u = -1
+    (click) or 2 (no-click)."""
+    po, g = pair(fm, 64, gamma=2.0, events=100000, seed=91, traj_id=5)
+    natural = trajectory.run(po, 12)["events"]
+    forced = {}
+    for s in range(2, 12):
+        for (st, j, u, p, o) in natural:
+            if st == s and 0.05 < p < 0.95 and len(forced) < 5:
+                forced[s] = {j: 1 - o}
+                break
+    assert len(forced) == 5
+    ref = trajectory.run(po, 12, forced=forced)
+    g.force_outcomes([(0, s, j, o) for s, d in forced.items() for j, o in d.items()])
+    g.step(12)
+    ev, dropped = g.take_events()
+    assert dropped == 0
+    assert cdiff(g.copy_U(), ref["U"]) <= C_TOL
+    assert sorted((e[1], e[2], e[5]) for e in ev) == sorted((s, j, o) for (s, j, u, p, o) in ref["events"])
+    flagged = {(e[1], e[2]): e[3] for e in ev if not (0.0 <= e[3] <= 1.0)}
+    assert flagged == {(s, j): (-1.0 if o else 2.0) for s, d in forced.items() for j, o in d.items()}
+    # the same list on a second state, then cleared: natural outcomes again
+    g2 = pair(fm, 64, gamma=2.0, events=100000, seed=91, traj_id=5)[1]
+    g2.force_outcomes([(0, s, j, o) for s, d in forced.items() for j, o in d.items()])
+    g2.force_outcomes([])
+    g2.step(12)
+    ev2, _ = g2.take_events()
+    assert sorted((e[1], e[2], e[5]) for e in ev2) == sorted((s, j, o) for (s, j, u, p, o) in natural)

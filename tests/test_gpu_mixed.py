@@ -246,3 +246,27 @@ def test_continuous_time_projective_mixed(fm, Lx, Ly, reorth):
           % (Lx, Ly, len(ev), dc, srel(S, S_ref)))
     assert dc <= PER_STEP_C * n
     assert srel(S, S_ref) <= S_REL
+
+
+def test_projective_ring1024_forced_to_oracle_over_200_steps(fm):
+    """The mixed path held on the oracle's outcome sequence (fm_force_outcomes) for 200
+    projective steps at L = 1024, gamma = 0.5: no near tie can branch the two runs, so the
+    states stay comparable for the whole run; C within the per-step bound and the
+    half-chain entropy within the method's bar."""
+    n = 200
+    prm = Params(Lx=1024, gamma=0.5, protocol=PROJECTIVE, seed=0x2508184689)
+    half = list(range(512))
+    ref = trajectory.run(prm, n)
+    forced = [(0, s, j, o) for (s, j, u, p, o) in ref["events"]]
+    g = mixed(fm, 1024, protocol=fm.FM_PROJECTIVE, gamma=0.5, seed=0x2508184689, event_capacity=1 << 16)
+    g.force_outcomes(forced)
+    g.step(n)
+    ev, dropped = g.take_events()
+    assert dropped == 0
+    assert sorted((e[1], e[2], e[5]) for e in ev) == sorted((s, j, o) for (s, j, u, p, o) in ref["events"])
+    dc = cdiff(g.copy_U(), ref["U"])
+    S, S_ref = g.entropy(half), observables.entanglement_entropy(ref["U"], half)
+    print("forced replay, L=1024, %d steps, %d events: max|dC| %.2e, S %.9f vs %.9f (rel %.2e)"
+          % (n, len(ev), dc, S, S_ref, srel(S, S_ref)))
+    assert dc <= PER_STEP_C * n
+    assert srel(S, S_ref) <= S_REL

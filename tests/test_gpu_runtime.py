@@ -55,6 +55,30 @@ def test_served_mix_equals_each_request_alone(fm):
         assert ra.S == r.S, (q, ra.S, r.S)
 
 
+def test_served_poisson_arrivals_in_real_time_equal_each_request_alone(fm):
+    """Requests arriving as a Poisson stream in real time (mean gap 4 ms) while other
+    groups run: admitted into free slots of idle groups or new groups, answered by
+    asynchronous entropies; each answer equals the request served alone, bit for bit."""
+    from paper_2508_18468_gb300 import serve
+    rng = np.random.default_rng(5)
+    kinds = [(256, "homodyne"), (512, "projective"), (1024, "homodyne"), (256, "projective")]
+    t = np.cumsum(rng.exponential(0.004, size=10))
+    reqs = [serve.Request(rid=i, L=kinds[i % 4][0], protocol=kinds[i % 4][1], gamma=0.2 + 0.15 * i,
+                          traj_id=200 + i, steps=10 + (i % 3), arrival=float(t[i])) for i in range(10)]
+    srv = serve.Server(slots=2, memory_budget=16 << 30)
+    res, st = srv.run(reqs, realtime=True)
+    assert sorted(r.rid for r in res) == list(range(10))
+    assert st["latency_samples"] == st["trajectory_steps"] == sum(q.steps for q in reqs)
+    assert st["step_latency_ms_p99"] >= st["step_latency_ms_p50"] > 0
+    for r in res:
+        q = reqs[r.rid]
+        assert r.steps == q.steps
+        alone = serve.Server(slots=1, memory_budget=8 << 30)
+        (ra,), _ = alone.run([serve.Request(rid=0, L=q.L, protocol=q.protocol, gamma=q.gamma, traj_id=q.traj_id,
+                                            steps=q.steps)], realtime=False)
+        assert ra.S == r.S, (q, ra.S, r.S)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_async_entropy_sees_the_state_when_requested(fm, precision):
     L = 512 if precision else 96
