@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(fm):
 def test_struct_layouts(fm):
     assert ctypes.sizeof(fm.fm_params) == 72
     assert ctypes.sizeof(fm.fm_event) == 40
-    assert ctypes.sizeof(fm.fm_tuning) == 32
+    assert ctypes.sizeof(fm.fm_tuning) == 40
     assert fm.fm_version().startswith("fm ")
 
 
@@ -47,6 +47,9 @@ def test_workspace_bytes_validates_parameters(fm):
                 fm.make_params(64, gamma=-1.0), fm.make_params(64, reorth_interval=0),
                 fm.make_params(5, Ly=4), fm.make_params(64, protocol=7), fm.make_params(1)):
         assert fm.fm_workspace_bytes(bad) == 0
+    # the event log and the forced-outcome list both scale with event_capacity
+    base = fm.fm_workspace_bytes(fm.make_params(64, event_capacity=0))
+    assert fm.fm_workspace_bytes(fm.make_params(64, event_capacity=4096)) - base >= 4096 * (40 + 16)
 
 
 def test_tile_config_is_validated(fm):
