@@ -215,18 +215,26 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def profiled_traffic(name):
-    """dram bytes per launch recorded in profiles/<name>.md ('dram_bytes_per_launch: X'), if present."""
-    path = os.path.join(ROOT, "profiles", name + ".md")
+def profiled_traffic(L, B):
+    """DRAM bytes (read + write) of one propagation launch at ring L with B trajectories, from the
+    ncu capture at ring L = 4096, B = 4 (profiles/prop_gemm_ring4096.md, line
+    'dram_bytes_per_launch_propagation: X'), scaled by (L / 4096)^3 (B / 4): the operand re-reads
+    grow with the number of tile waves (~L^2 B) times the operand bytes of a wave (~L).  Returns
+    (bytes, source) or (None, why)."""
+    path = os.path.join(ROOT, "profiles", "prop_gemm_ring4096.md")
     if not os.path.exists(path):
-        return None
+        return None, "no capture"
     for line in open(path):
-        if line.strip().startswith("dram_bytes_per_launch:"):
+        if line.strip().startswith("dram_bytes_per_launch_propagation:"):
             try:
-                return float(line.split(":", 1)[1].split()[0])
+                x = float(line.split(":", 1)[1].split()[0])
             except ValueError:
-                return None
-    return None
+                return None, "unreadable capture line"
+            scale = (L / 4096.0) ** 3 * (B / 4.0)
+            return x * scale, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of tc_gemm_kernel<128,0,1> "
+                               "at ring L=4096, B=4 (profiles/prop_gemm_ring4096.md) x (L/4096)^3 (B/4) = "
+                               "x %.0f" % scale)
+    return None, "no propagation line in the capture summary"
 
 
 def setup_distributed(args):
@@ -389,6 +397,40 @@ def other_workloads(fm, peaks):
         g.close()
         del g
         torch.cuda.empty_cache()
+    # c5 as one batch: the served mix's lattice sizes, 8 homodyne trajectories each, advanced by one
+    # CUDA graph per period (fm_group: the batches' kernels overlap) against stepping the batches in turn
+    sizes = workloads.WORKLOADS["served_mix"]["sizes"]
+    states = [fm.Trajectories(fm.make_params(Lm, batch=8, protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED,
+                                             gamma=1.0, seed=workloads.seed_of("served_mix"), traj_id=8 * i))
+              for i, Lm in enumerate(sizes)]
+    grp = fm.Group(states)
+    nst = 10 * grp.period
+    grp.step(grp.period)                           # capture and warm-up
+    times = {}
+    for mode in ("one_graph", "batches_in_turn"):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if mode == "one_graph":
+            grp.step(nst)
+        else:
+            for g in states:
+                g.step(nst)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[mode] = e0.elapsed_time(e1) / 1e3
+    ntraj = 8 * len(sizes)
+    out["batched_mix_one_graph"] = {"value": ntraj * nst / times["one_graph"], "unit": UNIT, "steps": nst,
+                                    "trajectories": ntraj, "lattices": sizes,
+                                    "batches_in_turn_value": ntraj * nst / times["batches_in_turn"],
+                                    "what": "8 homodyne trajectories of each L, one fm_group graph launch per "
+                                            "period vs each batch's own eager steps, CUDA events"}
+    grp.close()
+    for g in states:
+        g.close()
+    del states
+    torch.cuda.empty_cache()
     # c5: a bounded served mix in real time
     reqs = serve.served_mix_requests(64, 100)
     srv = serve.Server(slots=8)
@@ -458,7 +500,8 @@ def run_ours(args, world, rank, local):
     protocol = fm.FM_HOMODYNE if wl["protocol"] == "homodyne" else fm.FM_PROJECTIVE
     prm = fm.make_params(Lx, Ly, batch=B, protocol=protocol, precision=precision,
                          reorth_interval=wl["reorth_interval"], gamma=gam[0], seed=seed,
-                         traj_id=replica_traj_id(rank, B))
+                         traj_id=replica_traj_id(rank, B),
+                         tile_config=wl.get("tile_config", 0) if precision == fm.FM_MIXED else 0)
     g = fm.Trajectories(prm)
     g.set_gammas(gam)
     if args.propagation == "banded":
@@ -577,13 +620,14 @@ def run_ours(args, world, rank, local):
         nbytes = passes * 2.0 * B * L * N * elem
         achieved = nbytes / (prop_ms / prop_n / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "band_prop_kernel (propagation)",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "band_x4_kernel (stencil propagation)",
                 "ms_per_launch": prop_ms / prop_n, "peak_note": "%s copy bandwidth" % peak_src}
     elif prop_n > 0:
         achieved = prop_flops / (prop_ms / prop_n / 1e3) / 1e12
-        traffic = profiled_traffic("prop_gemm_ring16384") if precision == fm.FM_MIXED else None
+        traffic, tsrc = profiled_traffic(L, B) if (precision == fm.FM_MIXED and Ly == 1) else (None, "not captured")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "tc_gemm_kernel (propagation, split-fp16 tcgen05)",
+                "traffic": traffic, "traffic_source": tsrc,
+                "kernel": "tc_gemm_kernel (propagation, split-fp16 tcgen05)",
                 "ms_per_launch": prop_ms / prop_n, "peak_note": peak_note}
     line = {
         "metric": METRIC if args.workload == WORKLOAD else "trajectory steps/s (%s)" % args.workload,
@@ -596,6 +640,7 @@ def run_ours(args, world, rank, local):
                    "ee_sites": "half chain (%d sites), FP64, started every %d steps and overlapped" % (L // 2, ee_every),
                    "ee_method": ee_method,
                    "precision": args.precision, "propagation": args.propagation,
+                   "reorth_interval": wl["reorth_interval"], "tile_config": wl.get("tile_config", 0),
                    "l2": "inputs larger than L2 (state %.1f GB, propagator %.1f GB per GPU)" % (
                        B * 2 * L * N * 4 / 1e9, 4 * L * L * 4 / 1e9),
                    "parallelism": "replicas x%d" % world},

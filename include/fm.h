@@ -289,9 +289,10 @@ fm_status fm_load(fm_state* s, const char* path);
  * the remaining steps run eagerly), removing per-kernel launch overhead.
  * The first replay captures the graph (on a library-owned stream) and
  * synchronises.  Results are bit-identical to eager stepping.  Phase timing
- * is not recorded inside graphs.  Projective states whose measurements run as
- * grid-wide per-event kernels (few trajectories or L > 2048: the per-step
- * event count is read back to size the launches) always step eagerly. */
+ * is not recorded inside graphs.  Projective states whose measurements read
+ * the step's event count back to size their launches -- the grid-wide FP64
+ * per-event kernels (few trajectories or L > 2048) and the mixed-precision
+ * block update -- and continuous-time states always step eagerly. */
 fm_status fm_set_graphs(fm_state* s, int32_t enable);
 
 /* Phase timing (tracing).  When enabled, each phase of fm_step and fm_entropy
@@ -381,6 +382,36 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
  * fm_entropy. */
 fm_status fm_entropy_noalloc(const void* d_U, int32_t L, int32_t N, const int32_t* sites, int32_t n,
                              double* d_S, void* cuda_stream);
+
+/* Several states in one CUDA graph (App. A's step, batched across lattice sizes).
+ * A group captures one period of every member state -- P steps, P the least common
+ * multiple of the members' 2 * reorth_interval -- into a single graph in which each
+ * state's kernels form their own branch, so that the batches of different L (and
+ * protocol or precision) advance together in one cudaGraphLaunch and their kernels
+ * overlap on the device.  The states keep their workspaces and streams; the group
+ * owns only its streams, events and graph.  Member states must be graph-capable:
+ * not FM_PROJECTIVE_POISSON, and no projective state whose measurements read event
+ * counts back (mixed precision, or the grid-wide FP64 path: fewer than 64
+ * trajectories or L > 2048); P <= 256.  FM_EINVAL otherwise, or for a state listed
+ * twice.  cuda_stream: the stream the graph replays on (cudaStream_t or NULL). */
+typedef struct fm_group fm_group;
+fm_status fm_group_create(fm_state* const* states, int32_t n, void* cuda_stream, fm_group** out);
+
+/* Advance every member by nsteps, a multiple of the group period, from a step count
+ * that is a multiple of it (FM_EINVAL otherwise).  The first call, and the first after
+ * a member's propagation, forced outcomes or tuning changed, captures the graph
+ * (synchronising the members' streams); later calls only replay it, nsteps / P
+ * launches.  The caller's stream first waits for every member's stream, and every
+ * member's stream then waits for the replays, so other calls on a member stay in
+ * order.  Results are bit-identical to stepping each state alone.  Asynchronous. */
+fm_status fm_group_step(fm_group* g, int32_t nsteps);
+
+/* The group period P (0 for NULL); the last error message of the group. */
+int32_t fm_group_period(const fm_group* g);
+const char* fm_group_last_error(const fm_group* g);
+
+/* Synchronise the replay stream and free the group (not its states).  NULL is allowed. */
+void fm_group_destroy(fm_group* g);
 
 /* Launches of library kernels issued on this state since init. */
 int64_t fm_kernel_launches(const fm_state* s);

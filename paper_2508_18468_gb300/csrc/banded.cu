@@ -112,6 +112,172 @@ __global__ void __launch_bounds__(256) band_x_kernel(const void* __restrict__ in
   if (partial && pos < Lx) partial[(b * nch + c) * L + i] = s;
 }
 
+// The x stencil of the float state (mixed precision), 4 consecutive sites per thread.
+// A block stages, for kB4Cols columns at a time, the input runs of RB rows (one row
+// segment of S = min(Lx, 1024) sites plus the stencil's halo each; RB = 256 / (S / 4)
+// rows when rows are short, as on the torus) in shared memory as separate Re and Im
+// arrays; each thread then slides a 4-wide window down its run, one new input per tap,
+// so a tap costs 2 shared loads and 16 FMAs for 4 outputs (the generic kernel above
+// spends 2 complex loads per output and tap).  Outputs go out as float4 where the 4 sites
+// are consecutive and aligned.  Grid (segments per row x row groups, column chunks, B).
+constexpr int kB4Seg = 1024;
+constexpr int kB4Cols = 2;
+constexpr int kB4Cap = 1344;                       // staged floats per column and plane
+constexpr int kB4Loads = (kB4Cap + 255) / 256;
+
+struct B4Shape {
+  int S, tpr, RB, segs, groups;
+};
+inline B4Shape band4_shape(int Lx, int Ly) {
+  B4Shape g;
+  g.S = Lx < kB4Seg ? Lx : kB4Seg;
+  g.tpr = (g.S + 3) / 4;
+  g.RB = 256 / g.tpr;
+  if (g.RB < 1) g.RB = 1;
+  if (g.RB > Ly) g.RB = Ly;
+  g.segs = (Lx + g.S - 1) / g.S;
+  g.groups = (Ly + g.RB - 1) / g.RB;
+  return g;
+}
+
+__global__ void __launch_bounds__(256, 3) band_x4_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                         int L, int N, int Lx, int Ly, int S, int tpr, int RB, int segs,
+                                                         const z64* __restrict__ taps, const int* __restrict__ off,
+                                                         int ntap, int per, double* partial, int nch, int tap_stride) {
+  __shared__ float sre[kB4Cols][kB4Cap];
+  __shared__ float sim[kB4Cols][kB4Cap];
+  __shared__ float tre[kBandMaxTaps], tim[kBandMaxTaps];
+  const int64_t b = blockIdx.z;
+  taps += b * tap_stride;
+  const int tid = threadIdx.x;
+  if (tid < ntap) {
+    tre[tid] = (float)taps[tid].re;
+    tim[tid] = (float)taps[tid].im;
+  }
+  const int seg = blockIdx.x % segs, rg = blockIdx.x / segs;
+  const int x0 = seg * S;
+  const int run = S + ntap - 1;                    // staged inputs per row
+  const int offmax = off[0] + ntap - 1;
+  const int tot = RB * run;
+  const int64_t L2 = 2 * (int64_t)L;
+  const float* inb = in + b * L2 * N;
+  float* outb = out + b * L2 * N;
+  // source sites of this thread's staged elements (the same for every column)
+  int src[kB4Loads];
+#pragma unroll
+  for (int u = 0; u < kB4Loads; ++u) {
+    const int q = tid + 256 * u;
+    src[u] = -1;
+    if (q < tot) {
+      const int r = q / run, e = q - r * run, y = rg * RB + r;
+      if (y < Ly) {
+        int x = (x0 - offmax + e) % Lx;
+        if (x < 0) x += Lx;
+        src[u] = x + Lx * y;
+      }
+    }
+  }
+  // this thread's outputs: row r, sites x0 + 4 g .. x0 + 4 g + 3 of it
+  const int r = tid / tpr, g = tid - r * tpr, y = rg * RB + r;
+  const int xs = x0 + 4 * g;
+  const int nval = (r < RB && y < Ly) ? max(0, min(4, min(x0 + S, Lx) - xs)) : 0;
+  const int site0 = xs + Lx * y;
+  const bool vec = nval == 4 && (site0 % 4) == 0 && (L % 4) == 0;
+  const int base = r * run + 4 * g + ntap - 1;     // staged index of the input for output 0 at tap 0
+  const int c = blockIdx.y;
+  const int k0 = c * per, k1 = min(N, k0 + per);
+  double acc2[4] = {0.0, 0.0, 0.0, 0.0};
+  // software pipeline: the next stage's columns are loaded into registers while the current
+  // stage is computed from shared memory
+  float vr[kB4Cols][kB4Loads], vi[kB4Cols][kB4Loads];
+  auto load_stage = [&](int kb) {
+    const int nk = min(kB4Cols, k1 - kb);
+#pragma unroll
+    for (int kk = 0; kk < kB4Cols; ++kk)
+#pragma unroll
+      for (int u = 0; u < kB4Loads; ++u)
+        if (kk < nk && src[u] >= 0) {
+          const float* col = inb + (int64_t)(kb + kk) * L2;
+          vr[kk][u] = __ldg(col + src[u]);
+          vi[kk][u] = __ldg(col + L + src[u]);
+        }
+  };
+  auto store_stage = [&](int kb) {
+    const int nk = min(kB4Cols, k1 - kb);
+#pragma unroll
+    for (int kk = 0; kk < kB4Cols; ++kk)
+#pragma unroll
+      for (int u = 0; u < kB4Loads; ++u)
+        if (kk < nk && src[u] >= 0) {
+          sre[kk][tid + 256 * u] = vr[kk][u];
+          sim[kk][tid + 256 * u] = vi[kk][u];
+        }
+  };
+  if (k0 < k1) {
+    load_stage(k0);
+    __syncthreads();                               // the taps are in shared memory
+    store_stage(k0);
+    __syncthreads();
+  }
+  for (int kb = k0; kb < k1; kb += kB4Cols) {
+    const int nk = min(kB4Cols, k1 - kb);
+    const bool more = kb + kB4Cols < k1;
+    if (more) load_stage(kb + kB4Cols);
+    if (nval > 0)
+      for (int kk = 0; kk < nk; ++kk) {
+        const float* ar = sre[kk];
+        const float* ai = sim[kk];
+        float wr[4], wi[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {               // a short last group reads only its own run
+          wr[e] = e < nval ? ar[base + e] : 0.f;
+          wi[e] = e < nval ? ai[base + e] : 0.f;
+        }
+        float orr[4] = {0.f, 0.f, 0.f, 0.f}, oii[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int t = 0; t < ntap; ++t) {
+          const float pr = tre[t], pi = tim[t];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            orr[e] = fmaf(pr, wr[e], orr[e]);
+            orr[e] = fmaf(-pi, wi[e], orr[e]);
+            oii[e] = fmaf(pr, wi[e], oii[e]);
+            oii[e] = fmaf(pi, wr[e], oii[e]);
+          }
+          // slide the window one input down: inputs base - t - 1 .. base - t + 2
+#pragma unroll
+          for (int e = 3; e > 0; --e) {
+            wr[e] = wr[e - 1];
+            wi[e] = wi[e - 1];
+          }
+          if (t + 1 < ntap) {
+            wr[0] = ar[base - t - 1];
+            wi[0] = ai[base - t - 1];
+          }
+        }
+        float* col = outb + (int64_t)(kb + kk) * L2;
+        if (vec) {
+          *(float4*)(col + site0) = make_float4(orr[0], orr[1], orr[2], orr[3]);
+          *(float4*)(col + L + site0) = make_float4(oii[0], oii[1], oii[2], oii[3]);
+        } else {
+          for (int e = 0; e < nval; ++e) {
+            col[site0 + e] = orr[e];
+            col[L + site0 + e] = oii[e];
+          }
+        }
+        if (partial)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc2[e] += (double)(orr[e] * orr[e] + oii[e] * oii[e]);
+      }
+    if (more) {
+      __syncthreads();                             // every thread is done with this stage
+      store_stage(kb + kB4Cols);
+      __syncthreads();
+    }
+  }
+  if (partial)
+    for (int e = 0; e < nval; ++e) partial[(b * nch + c) * L + site0 + e] = acc2[e];
+}
+
 template <typename T, int LAYOUT, int SEGY>
 __global__ void __launch_bounds__(256) band_y_kernel(const void* __restrict__ in, void* out, int L, int N, int Lx,
                                                      int Ly, const z64* __restrict__ taps,
@@ -184,9 +350,22 @@ int clamp_chunks(int64_t blocks, int N) {
 }
 }  // namespace
 
+// the x stencil of the float state takes band_x4_kernel when its staged runs fit
+bool use_band4(int Lx, int Ly, int layout, int ntap) {
+  if (layout != 1) return false;
+  const B4Shape g = band4_shape(Lx, Ly);
+  return g.RB * (g.S + ntap - 1) <= kB4Cap;
+}
+
 int band_chunks(int Lx, int Ly, int N, int B, int dir, int layout) {
-  const int64_t blocks = dir == 0 ? (int64_t)FM_CEIL_DIV(Lx, kBandSegX) * Ly * B
-                                  : (int64_t)FM_CEIL_DIV(Lx, 32) * FM_CEIL_DIV(Ly, seg_y(layout)) * B;
+  int64_t blocks;
+  if (dir == 0 && layout == 1) {
+    const B4Shape g = band4_shape(Lx, Ly);
+    blocks = (int64_t)g.segs * g.groups * B;
+  } else {
+    blocks = dir == 0 ? (int64_t)FM_CEIL_DIV(Lx, kBandSegX) * Ly * B
+                      : (int64_t)FM_CEIL_DIV(Lx, 32) * FM_CEIL_DIV(Ly, seg_y(layout)) * B;
+  }
   return clamp_chunks(blocks, N);
 }
 
@@ -197,7 +376,12 @@ cudaError_t band_propagate(cudaStream_t st, int layout, const void* in, void* ou
                            int tap_stride) {
   if (ntap < 1 || ntap > kBandMaxTaps || nch < 1 || Lx * Ly != L) return cudaErrorInvalidValue;
   const int per = FM_CEIL_DIV(N, nch);
-  if (dir == 0) {
+  if (dir == 0 && use_band4(Lx, Ly, layout, ntap)) {
+    const B4Shape g = band4_shape(Lx, Ly);
+    const dim3 grid(g.segs * g.groups, nch, B);
+    band_x4_kernel<<<grid, 256, 0, st>>>((const float*)in, (float*)out, L, N, Lx, Ly, g.S, g.tpr, g.RB, g.segs, taps,
+                                         off, ntap, per, partial, nch, tap_stride);
+  } else if (dir == 0) {
     const dim3 grid(FM_CEIL_DIV(Lx, kBandSegX) * Ly, nch, B);
     if (layout == 0)
       band_x_kernel<double, 0><<<grid, 256, 0, st>>>(in, out, L, N, Lx, taps, off, ntap, per, partial, nch,

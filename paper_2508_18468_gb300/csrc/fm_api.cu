@@ -313,6 +313,7 @@ struct fm_state {
   std::vector<int64_t> step_h;
   int64_t global_steps;
   int64_t settled_step;       // global step at which the pending second pass last ran early (-1: never)
+  int64_t config_gen;         // bumped whenever captured step graphs of this state go stale
   int sticky;
   std::string err;
   int64_t launches;
@@ -947,12 +948,18 @@ fm_status step_once(fm_state* s) {
   return FM_OK;
 }
 
-// Capture one period of steps into s->graph_exec (state pointers return to
-// their starting buffers after a period, so the graph can be replayed).
-fm_status capture_period(fm_state* s) {
-  const int P = s->graph_period;
-  if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
-  CK(cudaStreamSynchronize(s->st));
+// Whether the steps of s can be captured into a graph: host-scheduled steps (event
+// counts read back: the grid-wide projective path and the mixed-precision projective
+// block; events drawn on the host: the continuous-time protocol) cannot.
+bool graph_capable(const fm_state* s) {
+  if (s->prm.protocol == FM_PROJECTIVE_POISSON) return false;
+  if (s->prm.protocol == FM_PROJECTIVE && (s->mh || pm_use_wide(s->L, s->N, s->B))) return false;
+  return true;
+}
+
+// Issue P steps of s on stream cs (which is being captured); nothing executes, so the
+// host bookkeeping is restored afterwards.  *per: the launches of the P steps.
+fm_status issue_period(fm_state* s, cudaStream_t cs, int P, int64_t* per) {
   cudaStream_t user = s->st;
   const int64_t g0 = s->global_steps;
   const int64_t l0 = s->launches;
@@ -961,27 +968,37 @@ fm_status capture_period(fm_state* s) {
   float* V0 = s->V;
   const bool timing = s->timer.on;
   s->timer.on = false;
-  s->st = s->cap_st;
-  s->timer.st = s->cap_st;
+  s->st = cs;
+  s->timer.st = cs;
   fm_status r = FM_OK;
-  cudaGraph_t graph = nullptr;
-  if (cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    r = fail(s, FM_ECUDA, "cudaStreamBeginCapture");
-  } else {
-    for (int i = 0; i < P && r == FM_OK; ++i) r = step_once(s);
-    cudaError_t e = cudaStreamEndCapture(s->cap_st, &graph);
-    if (r == FM_OK && e != cudaSuccess) r = fail(s, FM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-  }
+  for (int i = 0; i < P && r == FM_OK; ++i) r = step_once(s);
   s->st = user;
   s->timer.st = user;
   s->timer.on = timing;
   if (s->prm.precision != FM_FP64) s->mc.st = user;
-  // capturing did not execute anything: restore the host bookkeeping
-  const int64_t per_period = s->launches - l0;
+  *per = s->launches - l0;
   s->global_steps = g0;
   s->step_h = steps0;
   s->launches = l0;
   if (r == FM_OK && (s->U != U0 || s->V != V0)) r = fail(s, FM_ECUDA, "graph period does not return the state buffers");
+  return r;
+}
+
+// Capture one period of steps into s->graph_exec (state pointers return to
+// their starting buffers after a period, so the graph can be replayed).
+fm_status capture_period(fm_state* s) {
+  if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(s->st));
+  fm_status r = FM_OK;
+  cudaGraph_t graph = nullptr;
+  int64_t per_period = 0;
+  if (cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    r = fail(s, FM_ECUDA, "cudaStreamBeginCapture");
+  } else {
+    r = issue_period(s, s->cap_st, s->graph_period, &per_period);
+    cudaError_t e = cudaStreamEndCapture(s->cap_st, &graph);
+    if (r == FM_OK && e != cudaSuccess) r = fail(s, FM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+  }
   if (r == FM_OK) {
     if (cudaGraphInstantiate(&s->graph_exec, graph, 0) != cudaSuccess) r = fail(s, FM_ECUDA, "cudaGraphInstantiate");
   }
@@ -995,10 +1012,7 @@ fm_status capture_period(fm_state* s) {
 fm_status step_many(fm_state* s, int32_t nsteps) {
   fm_status r;
   int i = 0;
-  // host-scheduled steps (event counts read back, or drawn on the host) do not replay
-  const bool graph_ok = !(s->prm.protocol == FM_PROJECTIVE && pm_use_wide(s->L, s->N, s->B)) &&
-                        s->prm.protocol != FM_PROJECTIVE_POISSON;
-  if (s->graphs_on && graph_ok) {
+  if (s->graphs_on && graph_capable(s)) {
     const int P = s->graph_period;
     while (i < nsteps && (s->global_steps % P) != 0) {
       if ((r = step_once(s))) return r;
@@ -1045,6 +1059,7 @@ fm_status retune(fm_state* s, int tile_config, int reorth) {
   }
   s->global_steps = 0;
   s->settled_step = -1;
+  s->config_gen += 1;
   for (int b = 0; b < B; ++b) s->step_h[b] = 0;
   if (s->prm.protocol == FM_PROJECTIVE_POISSON)
     for (int b = 0; b < B; ++b) poisson_sync(s, b);
@@ -1260,6 +1275,7 @@ fm_status fm_init_state(const fm_params* p, void* d_workspace, size_t ws_bytes, 
   s->global_steps = 0; s->sticky = 0; s->launches = 0;
   s->graphs_on = false; s->cap_st = nullptr; s->graph_exec = nullptr; s->graph_period = 0;
   s->settled_step = -1;
+  s->config_gen = 0;
   char* w = s->ws;
   s->gamma_d = (double*)(w + pl.gamma); s->traj_d = (uint64_t*)(w + pl.traj); s->step_d = (int64_t*)(w + pl.step);
   s->status_d = (int*)(w + pl.status); s->occ_d = (int*)(w + pl.occ);
@@ -1489,6 +1505,7 @@ fm_status fm_set_propagation(fm_state* s, int32_t mode) {
   CK(cudaStreamSynchronize(s->st));
   s->prop_mode = mode;
   if (s->prm.precision != FM_FP64) s->mc.prop_banded = mode == FM_PROP_BANDED;
+  s->config_gen += 1;
   if (s->graph_exec) {                 // the captured period used the other propagation
     cudaGraphExecDestroy(s->graph_exec);
     s->graph_exec = nullptr;
@@ -1523,6 +1540,7 @@ fm_status fm_force_outcomes(fm_state* s, const fm_event* events, int32_t n) {
   if (n > 0) CK(cudaMemcpy(s->force_d, f.data(), sizeof(int4) * (size_t)n, cudaMemcpyHostToDevice));
   s->force_n = n;
   if (s->prm.precision != FM_FP64) s->mc.force_n = n;
+  s->config_gen += 1;
   if (s->graph_exec) {                 // the captured period holds the previous list's length
     cudaGraphExecDestroy(s->graph_exec);
     s->graph_exec = nullptr;
@@ -2028,6 +2046,171 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
   out->tried = tried;
   out->rejected = rejected;
   return FM_OK;
+}
+
+// ------------------------------------------------------------------ several states in one graph
+struct fm_group {
+  std::vector<fm_state*> s;
+  cudaStream_t st = nullptr;            // the caller's stream the graph replays on
+  cudaStream_t origin = nullptr;        // capture origin
+  std::vector<cudaStream_t> br;         // one capture branch per state
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join, in;
+  cudaGraphExec_t exec = nullptr;
+  int period = 0;
+  std::vector<int64_t> per;             // launches of one period, per state
+  std::vector<int64_t> gen;             // config_gen of each state at capture
+  std::string err;
+};
+
+namespace {
+int64_t gcd64(int64_t a, int64_t b) { return b ? gcd64(b, a % b) : a; }
+
+void group_release(fm_group* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  for (cudaStream_t b : g->br)
+    if (b) cudaStreamDestroy(b);
+  g->br.clear();
+  if (g->origin) cudaStreamDestroy(g->origin);
+  for (cudaEvent_t e : g->join)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : g->in)
+    if (e) cudaEventDestroy(e);
+  g->join.clear();
+  g->in.clear();
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->done) cudaEventDestroy(g->done);
+}
+
+// One period of every state, each on its own branch of one graph (forked from the origin
+// stream, joined back into it), so that the states' kernels overlap on the device.
+fm_status group_capture(fm_group* g) {
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  for (fm_state* s : g->s)
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) return FM_ECUDA;
+  cudaGraph_t graph = nullptr;
+  fm_status r = FM_OK;
+  if (cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FM_ECUDA;
+  cudaError_t e = cudaEventRecord(g->fork, g->origin);
+  for (size_t i = 0; i < g->s.size() && r == FM_OK && e == cudaSuccess; ++i) {
+    e = cudaStreamWaitEvent(g->br[i], g->fork, 0);
+    if (e == cudaSuccess) r = issue_period(g->s[i], g->br[i], g->period, &g->per[i]);
+    if (r == FM_OK && e == cudaSuccess) e = cudaEventRecord(g->join[i], g->br[i]);
+    if (r == FM_OK && e == cudaSuccess) e = cudaStreamWaitEvent(g->origin, g->join[i], 0);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(g->origin, &graph);
+  if (r == FM_OK && (e != cudaSuccess || e2 != cudaSuccess)) {
+    g->err = std::string("group capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+    r = FM_ECUDA;
+  } else if (r != FM_OK) {
+    g->err = "group capture: a state failed (see its fm_last_error)";
+  }
+  if (r == FM_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+    g->err = "group graph instantiation";
+    r = FM_ECUDA;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  for (size_t i = 0; i < g->s.size(); ++i) g->gen[i] = g->s[i]->config_gen;
+  return r;
+}
+}  // namespace
+
+fm_status fm_group_create(fm_state* const* states, int32_t n, void* cuda_stream, fm_group** out) {
+  if (!out || !states || n < 1 || n > 4096) return FM_EINVAL;
+  *out = nullptr;
+  int64_t P = 1;
+  for (int i = 0; i < n; ++i) {
+    fm_state* s = states[i];
+    if (!s || check_state(s) != FM_OK || !graph_capable(s)) return FM_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (states[j] == s) return FM_EINVAL;
+    const int64_t q = 2 * (int64_t)s->prm.reorth_interval;
+    P = P / gcd64(P, q) * q;
+    if (P > 256) return FM_EINVAL;
+  }
+  fm_group* g = new fm_group();
+  g->s.assign(states, states + n);
+  g->st = (cudaStream_t)cuda_stream;
+  g->period = (int)P;
+  g->per.assign(n, 0);
+  g->gen.assign(n, -1);
+  bool ok = cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) == cudaSuccess;
+  g->br.assign(n, nullptr);
+  g->join.assign(n, nullptr);
+  g->in.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&g->br[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g->in[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    group_release(g);
+    delete g;
+    return FM_ECUDA;
+  }
+  *out = g;
+  return FM_OK;
+}
+
+fm_status fm_group_step(fm_group* g, int32_t nsteps) {
+  if (!g) return FM_EINVAL;
+  if (nsteps < 0 || nsteps % g->period) {
+    g->err = "nsteps must be a multiple of the group period " + std::to_string(g->period);
+    return FM_EINVAL;
+  }
+  for (fm_state* s : g->s) {
+    if (check_state(s) != FM_OK) {
+      g->err = "a state holds an error";
+      return FM_ESTATE;
+    }
+    if (s->global_steps % g->period) {
+      g->err = "every state must stand at a multiple of the group period";
+      return FM_EINVAL;
+    }
+  }
+  if (nsteps == 0) return FM_OK;
+  bool stale = !g->exec;
+  for (size_t i = 0; i < g->s.size(); ++i) stale |= g->gen[i] != g->s[i]->config_gen;
+  if (stale) {
+    const fm_status r = group_capture(g);
+    if (r) return r;
+  }
+  // the caller's stream waits for every state's stream, replays, and every state's stream
+  // then waits for it (so later calls on a state see the steps)
+  for (size_t i = 0; i < g->s.size(); ++i)
+    if (cudaEventRecord(g->in[i], g->s[i]->st) != cudaSuccess || cudaStreamWaitEvent(g->st, g->in[i], 0) != cudaSuccess)
+      return FM_ECUDA;
+  const int reps = nsteps / g->period;
+  for (int k = 0; k < reps; ++k)
+    if (cudaGraphLaunch(g->exec, g->st) != cudaSuccess) {
+      g->err = "cudaGraphLaunch";
+      return FM_ECUDA;
+    }
+  if (cudaEventRecord(g->done, g->st) != cudaSuccess) return FM_ECUDA;
+  for (size_t i = 0; i < g->s.size(); ++i) {
+    fm_state* s = g->s[i];
+    if (cudaStreamWaitEvent(s->st, g->done, 0) != cudaSuccess) return FM_ECUDA;
+    s->global_steps += nsteps;
+    for (int b = 0; b < s->B; ++b) s->step_h[b] += nsteps;
+    s->launches += reps * g->per[i];
+  }
+  return FM_OK;
+}
+
+int32_t fm_group_period(const fm_group* g) { return g ? g->period : 0; }
+
+const char* fm_group_last_error(const fm_group* g) { return g ? g->err.c_str() : "null group"; }
+
+void fm_group_destroy(fm_group* g) {
+  if (!g) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  group_release(g);
+  delete g;
 }
 
 int64_t fm_kernel_launches(const fm_state* s) { return s ? s->launches + s->ea_launches.load() : 0; }

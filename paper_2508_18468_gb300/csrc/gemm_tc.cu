@@ -111,6 +111,21 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
       p.out_h[o] = h;
       p.out_l[o] = __float2half_rn((v - __half2float(h)) * 2048.0f);
     }
+  } else if (MODE == MODE_CPLX) {
+    // row tile mt < mt_mod: real parts of rows mt BM .. ; mt >= mt_mod: imaginary parts
+    const int part = ti.mt >= p.mt_mod ? 1 : 0;
+    const int64_t row = (int64_t)(ti.mt - part * p.mt_mod) * BM + r;
+    float* out = p.out_c + 2 * ((int64_t)ti.b * p.out_batch_stride + row + (int64_t)(n0 + c0) * p.ld_out) + part;
+    if (p.beta != 0.0f) {
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = out[2 * (int64_t)j * p.ld_out];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.ld_out] = p.alpha * d[j] + p.beta * x[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[2 * (int64_t)j * p.ld_out] = p.alpha * d[j];
+    }
   } else {  // MODE_TRMM: column c of the L x 2N view -> V_b[(c&1) L + i + (c>>1) 2L]
     const int64_t base = (int64_t)ti.b * 2 * p.L * p.Ntraj + (m0 + r);
     float x[32];                              // loads first (see MODE_ADDV)
@@ -412,7 +427,8 @@ cudaError_t configure_all() {
       (e = set_smem<128, 0, MODE_PROP>()) || (e = set_smem<256, 0, MODE_GRAM>()) ||
       (e = set_smem<128, 0, MODE_GRAM>()) || (e = set_smem<128, 1, MODE_TRMM>()) ||
       (e = set_smem<128, 0, MODE_TRMM>()) || (e = set_smem<256, 0, MODE_TRMM>()) ||
-      (e = set_smem<128, 0, MODE_ADDV>()) || (e = set_smem<256, 0, MODE_ADDV>()))
+      (e = set_smem<128, 0, MODE_ADDV>()) || (e = set_smem<256, 0, MODE_ADDV>()) ||
+      (e = set_smem<128, 0, MODE_CPLX>()))
     return e;
   done.store(true, std::memory_order_release);
   return cudaSuccess;
@@ -452,6 +468,9 @@ cudaError_t launch(cudaStream_t st, int BN, const CUtensorMap& Ah, const CUtenso
       if (ch) return cudaErrorInvalidValue;
       return BN == 256 ? launch_one<256, 0, MODE_ADDV>(st, Ah, Al, Bh, Bl, p, grid)
                        : launch_one<128, 0, MODE_ADDV>(st, Ah, Al, Bh, Bl, p, grid);
+    case MODE_CPLX:
+      if (ch || BN != 128) return cudaErrorInvalidValue;
+      return launch_one<128, 0, MODE_CPLX>(st, Ah, Al, Bh, Bl, p, grid);
     case MODE_TRMM:
       if (ch) return launch_one<128, 1, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid);
       return BN == 256 ? launch_one<256, 0, MODE_TRMM>(st, Ah, Al, Bh, Bl, p, grid)

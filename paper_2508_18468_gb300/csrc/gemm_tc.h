@@ -19,7 +19,9 @@ enum Mode {
   MODE_PROP = 1,   // propagation: out_f as PLAIN + per-row sums of D^2 into partial
   MODE_GRAM = 2,   // Gram: D into the real (part 0) / imaginary (part 1) half of complex64 G_b
   MODE_TRMM = 3,   // U R^-1: D into V_b (fp32) and its fp16 planes
-  MODE_ADDV = 4    // out_f[b stride + m + n ld_out] = in_f[same] + D, and its fp16 planes out_h, out_l
+  MODE_ADDV = 4,   // out_f[b stride + m + n ld_out] = in_f[same] + D, and its fp16 planes out_h, out_l
+  MODE_CPLX = 5    // complex C = alpha D + beta C: the A rows stack the real (row tiles < mt_mod) and
+                   // imaginary parts; out_c complex64, ld_out / out_batch_stride in complex elements
 };
 
 struct Params {
@@ -56,6 +58,8 @@ struct Params {
   unsigned* estat;
   // if set and *cond == 0 the launch does nothing (a conditional pass decided on the device)
   const int* cond;
+  float* out_c;        // CPLX: complex64 C (interleaved re, im)
+  float alpha, beta;   // CPLX
 };
 
 bool make_kmajor_map(CUtensorMap* m, const __half* base, uint64_t K, uint64_t rows, uint64_t ld, uint32_t box_rows);

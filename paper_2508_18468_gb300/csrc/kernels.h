@@ -83,9 +83,10 @@ cudaError_t pmb_gather_w(cudaStream_t st, const __half* urm_h, const __half* urm
                          const int* count, int B, int K, __half* wt_h, __half* wt_l);
 cudaError_t pmb_gather_c(cudaStream_t st, const float* Dp, int64_t sD, int L, int K, int B, const int* list,
                          const int* count, const PmbMats& m);
-cudaError_t pmb_event(cudaStream_t st, int i, int Kc, int L, int B, const int* count, const int* list,
-                      const double* ulist, const int64_t* step, const PmbMats& m, fm_event* log,
-                      unsigned long long* log_count, int log_capacity, int nmax);
+// every event of the step in one launch (one CTA per trajectory, the events in order)
+cudaError_t pmb_events(cudaStream_t st, int Kc, int L, int B, const int* count, const int* list, const double* ulist,
+                       const int64_t* step, const PmbMats& m, fm_event* log, unsigned long long* log_count,
+                       int log_capacity);
 cudaError_t pmb_ttilde(cudaStream_t st, const PmbMats& m, int K, int B, __half* th, __half* tl);
 cudaError_t pmb_split(cudaStream_t st, const float* x, int64_t n, __half* h, __half* l);
 cudaError_t pmb_atilde(cudaStream_t st, const float* Ap, int L, int K, int B, const int* pos, const PmbMats& m,

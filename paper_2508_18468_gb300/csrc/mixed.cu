@@ -67,7 +67,7 @@ struct Scratch {
   size_t pb_list, pb_ulist, pb_count, pb_pos, pb_wt_h, pb_wt_l, pb_dp, pb_dph, pb_dpl, pb_ap, pb_ath, pb_atl;
   size_t pb_tth, pb_ttl, pb_xth, pb_xtl, pb_mats, pb_vecs, pb_ev, pb_wc, pb_x;
   int pb_kc = 0;
-  size_t ca_h, ca_l, cb_h, cb_l, cd, xs;   // complex tensor GEMM helper (Cholesky recursion)
+  size_t ca_h, ca_l, cb_h, cb_l, xs;       // complex tensor GEMM helper (Cholesky recursion)
   size_t gf, rf, tf, dinvf, xf, diag;     // complex64 Gram / factor / inverse, FP64 Gram diagonal
   size_t guard;                           // second-pass guard (ReorthGuard layout)
   size_t take(size_t b) { size_t o = total; total += (b + 255) & ~(size_t)255; return o; }
@@ -99,7 +99,6 @@ Scratch scratch_plan(int Lx, int Ly, int B, int protocol) {
   s.ca_l = s.take((int64_t)B * 4 * md * md * 2);
   s.cb_h = s.take((int64_t)B * 2 * md * md * 2);
   s.cb_l = s.take((int64_t)B * 2 * md * md * 2);
-  s.cd = s.take((int64_t)B * 2 * md * md * 4);
   s.xs = s.take((int64_t)B * md * md * 8);
   s.gf = s.take((int64_t)B * N * N * 8);
   s.rf = s.take((int64_t)B * N * N * 8);
@@ -234,6 +233,80 @@ __global__ void __launch_bounds__(256) embed_a_kernel(const c32* __restrict__ X,
   }
 }
 
+// The same planes as embed_a_kernel for k a multiple of 64: a 32 x 64 tile of op(X)
+// staged in shared memory, then each thread writes the 8 K positions of one row and one
+// group of 8 complex columns as 16-byte stores (Re, -Im on the top row, Im, Re on the
+// bottom row, both planes).  Grid (m / 32, k / 64, B), 256 threads.
+__global__ void __launch_bounds__(256) embed_a64_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op,
+                                                        int m, int k, __half* Ah, __half* Al) {
+  __shared__ c32 t[32][65];                       // t[row][col] of op(X)
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 64;
+  const int64_t b = blockIdx.z;
+  const c32* Xb = X + b * sX;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  if (op == 2) {
+    for (int q = ty; q < 32; q += 8) {            // lanes along the columns of op(X) (rows of X)
+      c32 x0 = Xb[(c0 + tx) + (int64_t)(r0 + q) * ldx];
+      c32 x1 = Xb[(c0 + 32 + tx) + (int64_t)(r0 + q) * ldx];
+      x0.im = -x0.im;
+      x1.im = -x1.im;
+      t[q][tx] = x0;
+      t[q][32 + tx] = x1;
+    }
+  } else {
+    for (int q = ty; q < 64; q += 8) t[tx][q] = Xb[(r0 + tx) + (int64_t)(c0 + q) * ldx];
+  }
+  __syncthreads();
+  const int r = tid >> 3, g = tid & 7;
+  const int kk0 = c0 + 8 * g;                     // 8 complex columns inside one group of 32
+  const int64_t k2 = 2 * (int64_t)k;
+  const int64_t top = b * 4 * (int64_t)m * k + (int64_t)(r0 + r) * k2 + 64 * (kk0 / 32) + (kk0 % 32);
+  const int64_t bot = top + (int64_t)m * k2;
+  __align__(16) __half hre[8], lre[8], him[8], lim[8], hni[8], lni[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const c32 x = t[r][8 * g + e];
+    split16_f(x.re, hre[e], lre[e]);
+    split16_f(x.im, him[e], lim[e]);
+    split16_f(-x.im, hni[e], lni[e]);
+  }
+  *(uint4*)(Ah + top) = *(const uint4*)hre;
+  *(uint4*)(Al + top) = *(const uint4*)lre;
+  *(uint4*)(Ah + top + 32) = *(const uint4*)hni;
+  *(uint4*)(Al + top + 32) = *(const uint4*)lni;
+  *(uint4*)(Ah + bot) = *(const uint4*)him;
+  *(uint4*)(Al + bot) = *(const uint4*)lim;
+  *(uint4*)(Ah + bot + 32) = *(const uint4*)hre;
+  *(uint4*)(Al + bot + 32) = *(const uint4*)lre;
+}
+
+// The planes of embed_b_kernel for op(Y) = Y and k a multiple of 64, without staging:
+// each thread reads 8 consecutive entries of one column of Y (64 bytes) and writes their
+// Re and Im halves as 16-byte stores.  Grid (k / 64, n / 32, B), 256 threads.
+__global__ void __launch_bounds__(256) embed_b64_kernel(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int k,
+                                                        int n, __half* Bh, __half* Bl) {
+  const int tid = threadIdx.x, g = tid & 7, jj = tid >> 3;
+  const int kk0 = blockIdx.x * 64 + 8 * g, j = blockIdx.y * 32 + jj;
+  const int64_t b = blockIdx.z;
+  const float4* src = (const float4*)(Y + b * sY + kk0 + (int64_t)j * ldy);
+  float4 v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = src[q];
+  __align__(16) __half hre[8], lre[8], him[8], lim[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    split16_f(v[q].x, hre[2 * q], lre[2 * q]);
+    split16_f(v[q].y, him[2 * q], lim[2 * q]);
+    split16_f(v[q].z, hre[2 * q + 1], lre[2 * q + 1]);
+    split16_f(v[q].w, him[2 * q + 1], lim[2 * q + 1]);
+  }
+  const int64_t o = b * 2 * (int64_t)k * n + (int64_t)j * 2 * k + 64 * (kk0 / 32) + (kk0 % 32);
+  *(uint4*)(Bh + o) = *(const uint4*)hre;
+  *(uint4*)(Bl + o) = *(const uint4*)lre;
+  *(uint4*)(Bh + o + 32) = *(const uint4*)him;
+  *(uint4*)(Bl + o + 32) = *(const uint4*)lim;
+}
+
 // Planes of B (n x 2k, row-major): row j = the Re and Im parts of op(Y)[:, j], K
 // interleaved by groups of 32 as in embed_a_kernel.  Grid (k / 32, n / 32, B),
 // block (32, 8); k and n multiples of 32.
@@ -267,53 +340,42 @@ __global__ void __launch_bounds__(256) embed_b_kernel(const c32* __restrict__ Y,
   }
 }
 
-// C = alpha (D_re + i D_im) + beta C, D = [D_re; D_im] (2m x n, column-major, per
-// trajectory).  upper != 0: only the 128 x 128 tiles on or above the diagonal (the
-// ones a Hermitian product computes); C keeps its other entries.
-// Grid (ceil(m / 256), n, B).
-__global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ D, int m, int n, float alpha,
-                                                      float beta, c32* C, int64_t ldc, int64_t sC, int upper) {
-  const int64_t b = blockIdx.z;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (r >= m || (upper && (r >> 7) > (j >> 7))) return;
-  const float* Dj = D + b * 2 * (int64_t)m * n + (int64_t)j * 2 * m;
-  c32* c = C + b * sC + r + (int64_t)j * ldc;
-  c32 out = cmk(alpha * Dj[r], alpha * Dj[m + r]);
-  if (beta != 0.0f) {
-    const c32 old = *c;
-    out.re += beta * old.re;
-    out.im += beta * old.im;
-  }
-  *c = out;
-}
-
 // Urm[(b L + i) 2N + c] = plane_b[i + L c] (V_b read as the L x 2N column-major
-// matrix U~), both planes.  64 x 64 tiles, half2 reads along i and writes along c.
-// Grid (L / 64, 2N / 64, B), block (32, 8).
+// matrix U~), both planes.  64 x 64 tiles: 16-byte loads along i and 16-byte stores
+// along c.  In shared memory element (c, i) sits at column i ^ 8 (c >> 3) of row c, so
+// the stores of a row's 8-element chunks and the gathers of 8 rows c = 8v .. 8v + 7 at
+// one i both spread over all banks.  Grid (L / 64, 2N / 64, B), 256 threads.
 __global__ void __launch_bounds__(256) transpose_planes_kernel(const __half* __restrict__ Vh,
                                                                const __half* __restrict__ Vl, int L, int N,
                                                                __half* Uh, __half* Ul, const int* cond) {
   if (cond && *cond == 0) return;
-  __shared__ __half2 sh[64][33];                  // [c][i pair]
-  __shared__ __half2 sl[64][33];
+  __shared__ __align__(16) __half sh[64][64];
+  __shared__ __align__(16) __half sl[64][64];
   const int i0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
   const int64_t b = blockIdx.z;
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = threadIdx.x;
   const int64_t vb = b * 2 * (int64_t)L * N;
-  for (int cc = ty; cc < 64; cc += 8) {
-    const int64_t o = vb + (int64_t)(c0 + cc) * L + i0 + 2 * tx;
-    sh[cc][tx] = *(const __half2*)(Vh + o);
-    sl[cc][tx] = *(const __half2*)(Vl + o);
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int q = tid + 256 * hh, u = q & 7, c = q >> 3;
+    const int64_t o = vb + (int64_t)(c0 + c) * L + i0 + 8 * u;
+    const int col = (8 * u) ^ (8 * (c >> 3));
+    *(uint4*)&sh[c][col] = *(const uint4*)(Vh + o);
+    *(uint4*)&sl[c][col] = *(const uint4*)(Vl + o);
   }
   __syncthreads();
-  for (int ii = ty; ii < 64; ii += 8) {
-    const int64_t o = (b * L + i0 + ii) * 2 * (int64_t)N + c0 + 2 * tx;
-    const __half2 h0 = sh[2 * tx][ii >> 1], h1 = sh[2 * tx + 1][ii >> 1];
-    const __half2 l0 = sl[2 * tx][ii >> 1], l1 = sl[2 * tx + 1][ii >> 1];
-    *(__half2*)(Uh + o) = (ii & 1) ? __halves2half2(__high2half(h0), __high2half(h1))
-                                   : __halves2half2(__low2half(h0), __low2half(h1));
-    *(__half2*)(Ul + o) = (ii & 1) ? __halves2half2(__high2half(l0), __high2half(l1))
-                                   : __halves2half2(__low2half(l0), __low2half(l1));
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int q = tid + 256 * hh, v = q & 7, i = q >> 3;
+    __align__(16) __half oh[8], ol[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      oh[e] = sh[8 * v + e][i ^ (8 * v)];
+      ol[e] = sl[8 * v + e][i ^ (8 * v)];
+    }
+    const int64_t o = (b * L + i0 + i) * 2 * (int64_t)N + c0 + 8 * v;
+    *(uint4*)(Uh + o) = *(const uint4*)oh;
+    *(uint4*)(Ul + o) = *(const uint4*)ol;
   }
 }
 
@@ -408,7 +470,6 @@ struct MixedHost {
   int4 *tiles_prop, *tiles_gram, *tiles_trmm, *tiles_trmm2;
   __half *urm_h, *urm_l;
   __half *ca_h, *ca_l, *cb_h, *cb_l;
-  float* cd;
   c32* xs;
   int64_t md;        // largest block dimension of the Cholesky recursion products
   c32 *gf, *rf, *tf, *dinvf, *xf;
@@ -478,7 +539,6 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   h->ca_l = (__half*)(base + sp.ca_l);
   h->cb_h = (__half*)(base + sp.cb_h);
   h->cb_l = (__half*)(base + sp.cb_l);
-  h->cd = (float*)(base + sp.cd);
   h->xs = (c32*)(base + sp.xs);
   h->md = N / 2 + 128;
   h->gf = (c32*)(base + sp.gf);
@@ -608,9 +668,18 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
     c->err = "cgemm sizes";
     return FM_EINVAL;
   }
-  embed_a_kernel<<<dim3(m / 32, k / 32, B), dim3(32, 8), 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+  const bool y_aligned = ((uintptr_t)Y % 16 == 0) && (ldy % 2 == 0) && (sY % 2 == 0);
+  if (k % 64 == 0) {
+    embed_a64_kernel<<<dim3(m / 32, k / 64, B), 256, 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+  } else {
+    embed_a_kernel<<<dim3(m / 32, k / 32, B), dim3(32, 8), 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+  }
   MCK(cudaGetLastError());
-  embed_b_kernel<<<dim3(k / 32, n / 32, B), dim3(32, 8), 0, c->st>>>(Y, ldy, sY, opY, k, n, h->cb_h, h->cb_l);
+  if (k % 64 == 0 && opY == 0 && y_aligned) {
+    embed_b64_kernel<<<dim3(k / 64, n / 32, B), 256, 0, c->st>>>(Y, ldy, sY, k, n, h->cb_h, h->cb_l);
+  } else {
+    embed_b_kernel<<<dim3(k / 32, n / 32, B), dim3(32, 8), 0, c->st>>>(Y, ldy, sY, opY, k, n, h->cb_h, h->cb_l);
+  }
   MCK(cudaGetLastError());
   CUtensorMap ah, al, bh, bl;
   const uint64_t K2 = 2 * (uint64_t)k;
@@ -622,7 +691,6 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
     return FM_ECUDA;
   }
   tc::Params p = base_params(c, h);
-  p.mode = tc::MODE_PLAIN;
   p.tiles = nullptr;
   p.mtiles = 2 * m / tc::BM;
   p.ntiles_n = n / 128;
@@ -630,9 +698,14 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
   p.kblocks = 2 * k / tc::BK;
   p.a_rows_per_b = 2 * m;
   p.b_rows_per_b = n;
-  p.out_f = h->cd;
-  p.ld_out = 2 * (int64_t)m;
-  p.out_batch_stride = 2 * (int64_t)m * n;
+  // the epilogue writes C = alpha (D_re + i D_im) + beta C itself (tiles below the diagonal
+  // of a Hermitian product are neither computed nor written)
+  p.mode = tc::MODE_CPLX;
+  p.out_c = (float*)C;
+  p.ld_out = ldc;
+  p.out_batch_stride = sC;
+  p.alpha = alpha;
+  p.beta = beta;
   // K-block = 32 complex columns; a 128-row (column) tile spans 4 of them
   p.mt_mod = m / tc::BM;
   p.kb_lo_mt = (shape & CG_A_UPPER) ? 4 : 0;
@@ -640,9 +713,6 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
   p.kb_hi_nt = (shape & CG_B_UPPER) ? 4 : 0;
   p.herm_upper = (shape & CG_HERM) ? 1 : 0;
   MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, tc::sm_count()));
-  combine_kernel<<<dim3(FM_CEIL_DIV(m, 256), n, B), 256, 0, c->st>>>(h->cd, m, n, alpha, beta, C, ldc, sC,
-                                                                     p.herm_upper);
-  MCK(cudaGetLastError());
   return FM_OK;
 }
 
@@ -740,7 +810,7 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired, int mode = PASS_
   build_ttilde_kernel<<<(unsigned)(2 * (int64_t)B * N), 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag,
                                                                           first ? 0 : 1, N, c->Th, c->Tl, cond);
   MCK(cudaGetLastError());
-  transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
+  transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), 256, 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
                                                                                   h->urm_l, cond);
   MCK(cudaGetLastError());
   c->timer->end(FM_PH_CHOLESKY);
@@ -847,7 +917,7 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
   // U~ planes (L x 2N per trajectory, K-major) of the propagated state (the
   // propagation writes the float state only, so its planes are made here)
   MCK(split_planes(c->st, c->V, c->Vh, c->Vl, (int64_t)B * 2 * L * N));
-  transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), dim3(32, 8), 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
+  transpose_planes_kernel<<<dim3(L / 64, 2 * N / 64, B), 256, 0, c->st>>>(c->Vh, c->Vl, L, N, h->urm_h,
                                                                                   h->urm_l, nullptr);
   MCK(cudaGetLastError());
   MCK(pmb_setup(c->st, h->pb_list, h->pb_count, L, B, kmax, h->pb_pos));
@@ -858,12 +928,9 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
                      h->pb_dp, 2 * K, sD, nullptr, nullptr, nullptr);
   if (r) return r;
   MCK(pmb_gather_c(c->st, h->pb_dp, sD, L, K, B, h->pb_list, h->pb_count, m));
-  // the events, in order
-  for (int i = 0; i < kmax; ++i) {
-    MCK(pmb_event(c->st, i, Kc, L, B, h->pb_count, h->pb_list, h->pb_ulist, c->step, m, c->log,
-                  (unsigned long long*)c->log_count, c->log_capacity, kmax));
-    c->launches += i > 0 ? 3 : 2;                 // with the one MCK counts: 4 (3 for the first event)
-  }
+  // the events, in order: one launch for all of them (one CTA per trajectory)
+  MCK(pmb_events(c->st, Kc, L, B, h->pb_count, h->pb_list, h->pb_ulist, c->step, m, c->log,
+                 (unsigned long long*)c->log_count, c->log_capacity));
   // B^dag = T_B^dag W
   MCK(pmb_gather_wc(c->st, c->V, L, N, K, B, h->pb_list, h->pb_count, m));
   const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};

@@ -109,146 +109,150 @@ __global__ void pmb_gather_c_kernel(const float* Dp, int64_t sD, int L, int K, i
   C[b * sC + r + (int64_t)c * Kc] = v;
 }
 
-// ------------------------------------------------------------------ one event (i), all trajectories
-// E1: rho = e_i + T_B conj(a), y = C[:, i] + (C T_B) conj(a), a = row i of (C T_A + T_E);
-// warp per row r.
-__global__ void pmb_rho_kernel(int i, int Kc, const int* count, const c32* C, const c32* TBr, const c32* CTB,
-                               const c32* CTA, const c32* TE, int64_t sM, c32* rho, c32* y) {
-  const int b = blockIdx.z;
-  const int n = count[b];
-  if (i >= n) return;
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (r >= n) return;
-  const int64_t o = b * sM;
-  const c32* arow_a = CTA + o + (int64_t)i * Kc;
-  const c32* arow_e = TE + o + (int64_t)i * Kc;
-  c32 sr = cmk(0.0f, 0.0f), sy = cmk(0.0f, 0.0f);
-  for (int l = lane; l < i; l += 32) {
-    const c32 a = cconj(cadd(arow_a[l], arow_e[l]));
-    if (l >= r) cfmaf(sr, TBr[o + (int64_t)r * Kc + l], a);
-    cfmaf(sy, CTB[o + (int64_t)r * Kc + l], a);
-  }
-  sr = warp_csum(sr);
-  sy = warp_csum(sy);
-  if (lane == 0) {
-    if (r == i) sr.re += 1.0f;
-    rho[b * Kc + r] = r <= i ? sr : cmk(0.0f, 0.0f);
-    y[b * Kc + r] = cadd(sy, C[o + r + (int64_t)i * Kc]);
-  }
-}
+// ------------------------------------------------------------------ all events of a step, one launch
+// Every event i < count[b] of trajectory b in one CTA of 512 threads (trajectories are
+// independent; the events of one are sequential), in phases separated by CTA barriers:
+//   E1  rho = e_i + T_B conj(a), y = C[:, i] + (C T_B) conj(a), a = row i of (C T_A + T_E)
+//       (a warp per row, lane-strided terms);
+//   E3  the Born weight p = Re rho^dag y (the first 8 warps, fixed order), the outcome, the
+//       event log, then t_i = rho / sqrt(p) into T_B and ys = y / sqrt(p) = C t_i into C T_B;
+//   E4  g_l = sum_{r <= l} conj(T_B[r, l]) ys_r for l < i (a warp per column);
+//   E5  column i of T_A, C T_A and T_E (a warp per row).
+// One launch per step instead of four per event (the events were launch-latency bound).
+constexpr int kEvThreads = 512;          // two CTAs per SM (46 registers a thread)
 
-// E3: Born weight, outcome, t_i and C t_i; one CTA per trajectory.
-__global__ void __launch_bounds__(256) pmb_decide_kernel(int i, int Kc, int L, const int* count, const int* list,
-                                                         const double* ulist, const int64_t* step, const c32* rho,
-                                                         const c32* y, c32* TBr, c32* TBc, c32* CTB, int64_t sM,
-                                                         c32* ys, PmbEvent* ev, fm_event* log,
-                                                         unsigned long long* log_count, int log_capacity) {
+__global__ void __launch_bounds__(kEvThreads) pmb_events_kernel(int Kc, int L, const int* count, const int* list,
+                                                                 const double* ulist, const int64_t* step,
+                                                                 PmbMats m, fm_event* log,
+                                                                 unsigned long long* log_count, int log_capacity) {
   const int b = blockIdx.x;
   const int n = count[b];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kEvThreads >> 5;
+  const int64_t o = b * m.sM;
+  c32* rho = m.rho + b * Kc;
+  c32* y = m.y + b * Kc;
+  c32* ys = m.ys + b * Kc;
+  c32* g = m.g + b * Kc;
   __shared__ double red[33];
-  __shared__ double sp_sh;
+  __shared__ double sp_sh, c_sh, dsel_sh;
   __shared__ int act_sh;
-  if (i >= n) {
-    if (threadIdx.x == 0) ev[b].active = 0;
-    return;
-  }
-  double part = 0.0;
-  for (int r = threadIdx.x; r <= i; r += blockDim.x) {
-    const c32 a = rho[b * Kc + r], c = y[b * Kc + r];
-    part += (double)a.re * c.re + (double)a.im * c.im;
-  }
-  // fixed-order block sum
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double p = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) p += red[w];
-    p = fmin(fmax(p, 0.0), 1.0);
-    const int j = list[(int64_t)b * L + i];
-    const double u = ulist[(int64_t)b * L + i];
-    PmbEvent e;
-    e.outcome = (u < p) ? 1 : 0;
-    e.active = (p >= 1e-300) ? 1 : 0;
-    e.sp = sqrt(p);
-    e.c = e.outcome ? -1.0 : 1.0 / sqrt(1.0 - p) - 1.0;
-    e.dsel = e.outcome ? 1.0 : -e.sp / sqrt(1.0 - p);
-    ev[b] = e;
-    sp_sh = e.sp;
-    act_sh = e.active;
-    if (log && log_capacity > 0) {
-      const unsigned long long slot = atomicAdd(log_count, 1ull);
-      if (slot < (unsigned long long)log_capacity) {
-        fm_event le;
-        le.step = step[b]; le.traj = b; le.site = j; le.u = u; le.p = p; le.outcome = e.outcome; le.pad = 0;
-        log[slot] = le;
+  for (int i = 0; i < n; ++i) {
+    // E1: rho, y (warp per row)
+    const c32* arow_a = m.CTA + o + (int64_t)i * Kc;
+    const c32* arow_e = m.TE + o + (int64_t)i * Kc;
+    for (int r = warp; r < n; r += nwarps) {
+      c32 sr = cmk(0.0f, 0.0f), sy = cmk(0.0f, 0.0f);
+      for (int l = lane; l < i; l += 32) {
+        const c32 a = cconj(cadd(arow_a[l], arow_e[l]));
+        if (l >= r) cfmaf(sr, m.TBr[o + (int64_t)r * Kc + l], a);
+        cfmaf(sy, m.CTB[o + (int64_t)r * Kc + l], a);
+      }
+      sr = warp_csum(sr);
+      sy = warp_csum(sy);
+      if (lane == 0) {
+        if (r == i) sr.re += 1.0f;
+        rho[r] = r <= i ? sr : cmk(0.0f, 0.0f);
+        y[r] = cadd(sy, m.C[o + r + (int64_t)i * Kc]);
       }
     }
-  }
-  __syncthreads();
-  if (!act_sh) return;
-  const float inv = (float)(1.0 / sp_sh);
-  const int64_t o = b * sM;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const c32 yr = cscale(y[b * Kc + r], inv);
-    ys[b * Kc + r] = yr;
-    CTB[o + (int64_t)r * Kc + i] = yr;
-    if (r <= i) {
-      const c32 t = cscale(rho[b * Kc + r], inv);
-      TBr[o + (int64_t)r * Kc + i] = t;
-      TBc[o + r + (int64_t)i * Kc] = t;
+    __syncthreads();
+    // E3: Born weight by the first 256 threads (the per-phase kernel's order), outcome
+    if (tid < 256) {
+      double part = 0.0;
+      for (int r = tid; r <= i; r += 256) {
+        const c32 a = rho[r], c = y[r];
+        part += (double)a.re * c.re + (double)a.im * c.im;
+      }
+      for (int w = 16; w > 0; w >>= 1) part += __shfl_xor_sync(0xffffffffu, part, w);
+      if (lane == 0) red[warp] = part;
     }
+    __syncthreads();
+    if (tid == 0) {
+      double p = 0.0;
+      for (int w = 0; w < 8; ++w) p += red[w];
+      p = fmin(fmax(p, 0.0), 1.0);
+      const int j = list[(int64_t)b * L + i];
+      const double u = ulist[(int64_t)b * L + i];
+      PmbEvent e;
+      e.outcome = (u < p) ? 1 : 0;
+      e.active = (p >= 1e-300) ? 1 : 0;
+      e.sp = sqrt(p);
+      e.c = e.outcome ? -1.0 : 1.0 / sqrt(1.0 - p) - 1.0;
+      e.dsel = e.outcome ? 1.0 : -e.sp / sqrt(1.0 - p);
+      m.ev[b] = e;
+      sp_sh = e.sp;
+      c_sh = e.c;
+      dsel_sh = e.dsel;
+      act_sh = e.active;
+      if (log && log_capacity > 0) {
+        const unsigned long long slot = atomicAdd(log_count, 1ull);
+        if (slot < (unsigned long long)log_capacity) {
+          fm_event le;
+          le.step = step[b]; le.traj = b; le.site = j; le.u = u; le.p = p; le.outcome = e.outcome; le.pad = 0;
+          log[slot] = le;
+        }
+      }
+    }
+    __syncthreads();
+    if (!act_sh) continue;                         // no weight on the site: nothing changes
+    const float inv = (float)(1.0 / sp_sh);
+    for (int r = tid; r < n; r += kEvThreads) {
+      const c32 yr = cscale(y[r], inv);
+      ys[r] = yr;
+      m.CTB[o + (int64_t)r * Kc + i] = yr;
+      if (r <= i) {
+        const c32 t = cscale(rho[r], inv);
+        m.TBr[o + (int64_t)r * Kc + i] = t;
+        m.TBc[o + r + (int64_t)i * Kc] = t;
+      }
+    }
+    __syncthreads();
+    // E4: g (warp per column l < i)
+    for (int l = warp; l < i; l += nwarps) {
+      const c32* col = m.TBc + o + (int64_t)l * Kc;
+      c32 sg = cmk(0.0f, 0.0f);
+      for (int r = lane; r <= l; r += 32) cfmaf(sg, cconj(col[r]), ys[r]);
+      sg = warp_csum(sg);
+      if (lane == 0) g[l] = sg;
+    }
+    __syncthreads();
+    // E5: column i of T_A, C T_A, T_E (warp per row)
+    const float c = (float)c_sh;
+    for (int r = warp; r < n; r += nwarps) {
+      const int64_t orow = o + (int64_t)r * Kc;
+      c32 tau = cmk(0.0f, 0.0f), ctau = cmk(0.0f, 0.0f), eps = cmk(0.0f, 0.0f);
+      for (int l = lane; l < i; l += 32) {
+        const c32 gl = g[l];
+        if (l >= r) {
+          cfmaf(tau, m.TA[orow + l], gl);
+          cfmaf(eps, m.TE[orow + l], gl);
+        }
+        cfmaf(ctau, m.CTA[orow + l], gl);
+      }
+      tau = warp_csum(tau);
+      ctau = warp_csum(ctau);
+      eps = warp_csum(eps);
+      if (lane == 0) {
+        if (r <= i) {
+          tau = cadd(tau, m.TBr[orow + i]);
+          m.TA[orow + i] = cscale(tau, c);
+          c32 te = cscale(eps, c);
+          if (r == i) te.re += (float)dsel_sh;
+          m.TE[orow + i] = te;
+        }
+        ctau = cadd(ctau, ys[r]);
+        m.CTA[orow + i] = cscale(ctau, c);
+      }
+    }
+    __syncthreads();
   }
 }
 
-// E4: g_l = sum_{r <= l} conj(T_B[r, l]) ys_r for l < i; warp per column.
-__global__ void pmb_g_kernel(int i, int Kc, const int* count, const PmbEvent* ev, const c32* TBc, int64_t sM,
-                             const c32* ys, c32* g) {
-  const int b = blockIdx.z;
-  if (i >= count[b] || !ev[b].active) return;
-  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (l >= i) return;
-  const c32* col = TBc + b * sM + (int64_t)l * Kc;
-  c32 s = cmk(0.0f, 0.0f);
-  for (int r = lane; r <= l; r += 32) cfmaf(s, cconj(col[r]), ys[b * Kc + r]);
-  s = warp_csum(s);
-  if (lane == 0) g[b * Kc + l] = s;
-}
-
-// E5: column i of T_A, C T_A and T_E; warp per row.
-__global__ void pmb_update_kernel(int i, int Kc, const int* count, const PmbEvent* ev, c32* TA, c32* CTA, c32* TE,
-                                  const c32* TBr, int64_t sM, const c32* ys, const c32* g) {
-  const int b = blockIdx.z;
-  const int n = count[b];
-  if (i >= n || !ev[b].active) return;
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (r >= n) return;
-  const int64_t o = b * sM + (int64_t)r * Kc;
-  c32 tau = cmk(0.0f, 0.0f), ctau = cmk(0.0f, 0.0f), eps = cmk(0.0f, 0.0f);
-  for (int l = lane; l < i; l += 32) {
-    const c32 gl = g[b * Kc + l];
-    if (l >= r) {
-      cfmaf(tau, TA[o + l], gl);
-      cfmaf(eps, TE[o + l], gl);
-    }
-    cfmaf(ctau, CTA[o + l], gl);
-  }
-  tau = warp_csum(tau);
-  ctau = warp_csum(ctau);
-  eps = warp_csum(eps);
-  if (lane == 0) {
-    const PmbEvent e = ev[b];
-    const float c = (float)e.c;
-    if (r <= i) {
-      tau = cadd(tau, TBr[o + i]);
-      TA[o + i] = cscale(tau, c);
-      c32 te = cscale(eps, c);
-      if (r == i) te.re += (float)e.dsel;
-      TE[o + i] = te;
-    }
-    ctau = cadd(ctau, ys[b * Kc + r]);
-    CTA[o + i] = cscale(ctau, c);
-  }
+cudaError_t pmb_events(cudaStream_t st, int Kc, int L, int B, const int* count, const int* list, const double* ulist,
+                       const int64_t* step, const PmbMats& m, fm_event* log, unsigned long long* log_count,
+                       int log_capacity) {
+  pmb_events_kernel<<<B, kEvThreads, 0, st>>>(Kc, L, count, list, ulist, step, m, log, log_count, log_capacity);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ operands of the final products
@@ -392,22 +396,6 @@ cudaError_t pmb_gather_wc(cudaStream_t st, const float* V, int L, int N, int K, 
 
 cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int B, int N, __half* xh, __half* xl) {
   pmb_xtilde_kernel<<<dim3(FM_CEIL_DIV(K, 256), N, B), 256, 0, st>>>(m.X, m.sW, K, m.Kc, N, xh, xl);
-  return cudaGetLastError();
-}
-
-cudaError_t pmb_event(cudaStream_t st, int i, int Kc, int L, int B, const int* count, const int* list,
-                      const double* ulist, const int64_t* step, const PmbMats& m, fm_event* log,
-                      unsigned long long* log_count, int log_capacity, int nmax) {
-  const int warps = 8;
-  const dim3 rows(FM_CEIL_DIV(nmax, warps), 1, B);
-  pmb_rho_kernel<<<rows, 32 * warps, 0, st>>>(i, Kc, count, m.C, m.TBr, m.CTB, m.CTA, m.TE, m.sM, m.rho, m.y);
-  pmb_decide_kernel<<<B, 256, 0, st>>>(i, Kc, L, count, list, ulist, step, m.rho, m.y, m.TBr, m.TBc, m.CTB, m.sM,
-                                       m.ys, m.ev, log, log_count, log_capacity);
-  if (i > 0) {
-    const dim3 cols(FM_CEIL_DIV(i, warps), 1, B);
-    pmb_g_kernel<<<cols, 32 * warps, 0, st>>>(i, Kc, count, m.ev, m.TBc, m.sM, m.ys, m.g);
-  }
-  pmb_update_kernel<<<rows, 32 * warps, 0, st>>>(i, Kc, count, m.ev, m.TA, m.CTA, m.TE, m.TBr, m.sM, m.ys, m.g);
   return cudaGetLastError();
 }
 

@@ -91,6 +91,11 @@ def _load():
         "fm_entropy_sketch_info": (i32, [vp, P(i32), P(dbl), P(i32)]),
         "fm_reorth_stats": (i32, [vp, P(i64), P(i64), P(dbl)]),
         "fm_force_outcomes": (i32, [vp, P(fm_event), i32]),
+        "fm_group_create": (i32, [P(vp), i32, vp, P(vp)]),
+        "fm_group_step": (i32, [vp, i32]),
+        "fm_group_period": (i32, [vp]),
+        "fm_group_last_error": (ctypes.c_char_p, [vp]),
+        "fm_group_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -350,3 +355,40 @@ class Trajectories:
 
     def last_error(self):
         return lib.fm_last_error(self._h).decode()
+
+
+class Group:
+    """Several Trajectories objects advanced together by one CUDA graph (fm_group_*)."""
+
+    def __init__(self, members, stream=None):
+        import torch
+        self.members = list(members)              # keep the states alive
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        code = lib.fm_group_create(arr, len(self.members), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if code != FM_OK:
+            raise FmError(code, "fm_group_create failed")
+        self._h = h
+
+    @property
+    def period(self):
+        return int(lib.fm_group_period(self._h))
+
+    def step(self, nsteps):
+        code = lib.fm_group_step(self._h, int(nsteps))
+        if code != FM_OK:
+            raise FmError(code, lib.fm_group_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fm_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

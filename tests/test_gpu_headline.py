@@ -7,8 +7,9 @@ settings that change its result only at the 1e-14 level and make long runs affor
 the propagation as stencils of the circulant propagator (every tap above 1e-15 kept;
 equal to the dense product to that level, test_gpu_fp64.py) and one FP64 CholeskyQR pass
 per step (a float64 pass leaves U^dag U - 1 at ~kappa^2 1e-16; the test checks <= 1e-12).
-The mixed side runs exactly as the benchmark does: dense split-fp16 propagation, both
-CholeskyQR passes every step.
+The mixed side runs as the benchmark does at L = 16384 (dense split-fp16 propagation, the first
+CholeskyQR pass every step, the second every reorth_interval steps of the workload) and with
+the second pass every step elsewhere unless the test says otherwise.
 
 Bars (the method's): half-chain entropy relative error |dS| / max(S, 1) <= 1e-3;
 C = U U^dag on a block of rows within 2e-6 per step (the per-step bound of the mixed
@@ -75,9 +76,11 @@ def test_ring16384_mixed_vs_fp64(fm):
     smaller lattice reaches.  Both entropy methods of the mixed path (the sketch the
     benchmark uses at this size, and the full eigen-decomposition) against FP64."""
     L, n = 16384, 8
+    wl = workloads.WORKLOADS["ring16384_homodyne"]
     seed = workloads.seed_of("ring16384_homodyne")
     kw = dict(protocol=fm.FM_HOMODYNE, gamma=1.0, seed=seed, traj_id=2)
-    gm = fm.Trajectories(fm.make_params(L, precision=fm.FM_MIXED, **kw))
+    gm = fm.Trajectories(fm.make_params(L, precision=fm.FM_MIXED, reorth_interval=wl["reorth_interval"],
+                                        tile_config=wl["tile_config"], **kw))
     gm.step(n)
     gd = fp64_reference(fm, L, **kw)
     gd.step(n)
@@ -91,7 +94,32 @@ def test_ring16384_mixed_vs_fp64(fm):
     checks, extra, mx = gm.reorth_stats()
     print("second-pass guard: %d checks, %d extra passes, max |diag E| %.2e, max |offdiag E| %.2e"
           % (checks, extra, mx[0], mx[1]))
-    assert checks == n
+    assert checks == n // wl["reorth_interval"]
+
+
+def test_ring16384_tuned_interval_against_every_step_over_100_steps(fm):
+    """The benchmark's second-pass interval (every 8 steps, fm_autotune's choice for this batch)
+    against the second pass every step, ring L = 16384, gamma = 1.0: the half-chain entropy every
+    25 steps up to 100 within the method's bar, and U^dag U = 1 to 1e-6 at the end."""
+    L = 16384
+    wl = workloads.WORKLOADS["ring16384_homodyne"]
+    k = wl["reorth_interval"]
+    assert k > 1
+    kw = dict(protocol=fm.FM_HOMODYNE, precision=fm.FM_MIXED, gamma=1.0, seed=workloads.seed_of("ring16384_homodyne"),
+              traj_id=2)
+    ga = fm.Trajectories(fm.make_params(L, reorth_interval=k, tile_config=wl["tile_config"], **kw))
+    gb = fm.Trajectories(fm.make_params(L, reorth_interval=1, **kw))
+    half = workloads.half_chain(L)
+    for g in (ga, gb):
+        g.set_entropy_method(fm.FM_EE_AUTO)
+    for t in range(25, 101, 25):
+        ga.step(25)
+        gb.step(25)
+        Sa, Sb = ga.entropy(half), gb.entropy(half)
+        print("ring L=16384 step %d: S (second pass every %d) %.9f, every step %.9f, rel %.2e"
+              % (t, k, Sa, Sb, srel(Sa, Sb)))
+        assert srel(Sa, Sb) <= S_REL
+    assert ga.orthonormality_error(sample_cols(L // 2)) <= ORTHO
 
 
 def test_ring8192_mixed_vs_fp64_over_100_steps(fm):

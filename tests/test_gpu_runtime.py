@@ -165,3 +165,46 @@ def test_graphs_with_banded_propagation_equal_eager(fm):
     b.step(9)
     for t in range(2):
         assert np.array_equal(a.copy_U(t), b.copy_U(t))
+
+
+def test_group_graph_advances_uneven_lattices_bit_identically(fm):
+    """Batches of different L, protocol and precision advanced by one CUDA graph (fm_group):
+    after two replays of the group period each state equals a twin stepped alone, bit for
+    bit; the period is the lcm of the members' 2 reorth_interval; a step count that is not a
+    multiple of it is refused; a member's propagation change re-captures the graph."""
+    specs = [dict(Lx=256, batch=2, protocol=1, precision=1, reorth_interval=1, gamma=0.7, seed=61),
+             dict(Lx=512, batch=3, protocol=1, precision=1, reorth_interval=2, gamma=1.1, seed=62),
+             dict(Lx=1024, batch=1, protocol=2, precision=1, reorth_interval=1, gamma=0.5, seed=63),
+             dict(Lx=64, batch=64, protocol=0, precision=0, reorth_interval=1, gamma=0.9, seed=64)]
+
+    def make(sp):
+        sp = dict(sp)
+        return fm.Trajectories(fm.make_params(sp.pop("Lx"), **sp))
+    members = [make(sp) for sp in specs]
+    twins = [make(sp) for sp in specs]
+    grp = fm.Group(members)
+    assert grp.period == 4
+    with pytest.raises(fm.FmError):
+        grp.step(6)
+    for g in members + twins:
+        g.step(4)
+    l0 = [m.kernel_launches for m in members]
+    grp.step(8)
+    for t in twins:
+        t.step(8)
+    for m, t, sp in zip(members, twins, specs):
+        assert m.steps_done(0) == t.steps_done(0) == 12
+        assert m.kernel_launches > l0[members.index(m)]
+        for b in range(sp["batch"] if sp["batch"] < 4 else 2):
+            assert np.array_equal(m.copy_U(b), t.copy_U(b)), sp
+    # a member's configuration changes: the group graph is captured again
+    members[0].set_propagation(fm.FM_PROP_BANDED)
+    twins[0].set_propagation(fm.FM_PROP_BANDED)
+    grp.step(4)
+    twins[0].step(4)
+    assert np.array_equal(members[0].copy_U(1), twins[0].copy_U(1))
+    grp.close()
+    # a state whose steps read counts back cannot join a group
+    bad = fm.Trajectories(fm.make_params(256, batch=2, protocol=0, precision=1, gamma=0.5, seed=65))
+    with pytest.raises(fm.FmError):
+        fm.Group([bad])
