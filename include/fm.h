@@ -107,13 +107,18 @@ typedef struct {
 /* fm_params.tile_config of the mixed-precision path: bits 0-1 the output tile
  * width of the propagation and Gram products (0 automatic: 128 up to N = 8192,
  * 256 beyond when N % 256 == 0; 1: 128; 2: 256, needs N % 256 == 0); bits 2-4 g
- * the height of the tile raster groups, 2^(g+1) row tiles (0: 8).  Any other
- * bit set is FM_EINVAL.  Results do not depend on it beyond float rounding
- * order inside a tile (none: each output is one fixed-order sum per tile). */
+ * the height of the tile raster groups, 2^(g+1) row tiles (0: 8); bits 5-6 d:
+ * with reorth_interval > 1, the first CholeskyQR product of the steps that no
+ * second pass follows drains its fp32 tensor-memory accumulators (which round
+ * toward zero) into registers every 2^(d+1) K-blocks of 64 (0: 2; 3 is invalid).
+ * Any other bit set is FM_EINVAL.  Bits 0-4 do not change a single result (each
+ * output is one fixed-order sum per tile); bits 5-6 change the rounding of U
+ * between second passes (U^dag U - 1 stays ~1e-6 there). */
 #define FM_TILE_BN_AUTO 0
 #define FM_TILE_BN_128 1
 #define FM_TILE_BN_256 2
 #define FM_TILE_GROUP(g) ((g) << 2)
+#define FM_TILE_DRAIN(d) ((d) << 5)
 
 /* One projective measurement: trajectory b of the batch, step index (t/dt
  * before the step), site, the outcome draw u, Born probability p, outcome. */

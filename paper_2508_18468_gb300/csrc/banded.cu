@@ -124,6 +124,10 @@ constexpr int kB4Seg = 1024;
 constexpr int kB4Cols = 2;
 constexpr int kB4Cap = 1344;                       // staged floats per column and plane
 constexpr int kB4Loads = (kB4Cap + 255) / 256;
+// staged element q sits at q + q / 32 in shared memory: each lane's window starts 4 words
+// after its neighbour's, which without the padding word would put lanes 8 apart on one bank
+constexpr int kB4Pad = kB4Cap + kB4Cap / 32;
+FM_DEVFN int b4pos(int q) { return q + (q >> 5); }
 
 struct B4Shape {
   int S, tpr, RB, segs, groups;
@@ -144,8 +148,8 @@ __global__ void __launch_bounds__(256, 3) band_x4_kernel(const float* __restrict
                                                          int L, int N, int Lx, int Ly, int S, int tpr, int RB, int segs,
                                                          const z64* __restrict__ taps, const int* __restrict__ off,
                                                          int ntap, int per, double* partial, int nch, int tap_stride) {
-  __shared__ float sre[kB4Cols][kB4Cap];
-  __shared__ float sim[kB4Cols][kB4Cap];
+  __shared__ float sre[kB4Cols][kB4Pad];
+  __shared__ float sim[kB4Cols][kB4Pad];
   __shared__ float tre[kBandMaxTaps], tim[kBandMaxTaps];
   const int64_t b = blockIdx.z;
   taps += b * tap_stride;
@@ -209,8 +213,8 @@ __global__ void __launch_bounds__(256, 3) band_x4_kernel(const float* __restrict
 #pragma unroll
       for (int u = 0; u < kB4Loads; ++u)
         if (kk < nk && src[u] >= 0) {
-          sre[kk][tid + 256 * u] = vr[kk][u];
-          sim[kk][tid + 256 * u] = vi[kk][u];
+          sre[kk][b4pos(tid + 256 * u)] = vr[kk][u];
+          sim[kk][b4pos(tid + 256 * u)] = vi[kk][u];
         }
   };
   if (k0 < k1) {
@@ -230,8 +234,8 @@ __global__ void __launch_bounds__(256, 3) band_x4_kernel(const float* __restrict
         float wr[4], wi[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {               // a short last group reads only its own run
-          wr[e] = e < nval ? ar[base + e] : 0.f;
-          wi[e] = e < nval ? ai[base + e] : 0.f;
+          wr[e] = e < nval ? ar[b4pos(base + e)] : 0.f;
+          wi[e] = e < nval ? ai[b4pos(base + e)] : 0.f;
         }
         float orr[4] = {0.f, 0.f, 0.f, 0.f}, oii[4] = {0.f, 0.f, 0.f, 0.f};
         for (int t = 0; t < ntap; ++t) {
@@ -250,8 +254,8 @@ __global__ void __launch_bounds__(256, 3) band_x4_kernel(const float* __restrict
             wi[e] = wi[e - 1];
           }
           if (t + 1 < ntap) {
-            wr[0] = ar[base - t - 1];
-            wi[0] = ai[base - t - 1];
+            wr[0] = ar[b4pos(base - t - 1)];
+            wi[0] = ai[b4pos(base - t - 1)];
           }
         }
         float* col = outb + (int64_t)(kb + kk) * L2;

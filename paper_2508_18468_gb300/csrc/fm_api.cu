@@ -1996,8 +1996,13 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
   int tried = 0, rejected = 0;
   do {
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { r = FM_ECUDA; break; }
-    for (int k = 1; k <= max_reorth && r == FM_OK; k *= 2)
-      for (int tc : tiles) {
+    // candidates: every tile configuration x interval, then (mixed precision, interval > 1)
+    // the drain intervals of the first-pass product for the fastest accepted one
+    std::vector<std::pair<int, int>> cands;
+    for (int k = 1; k <= max_reorth; k *= 2)
+      for (int tc : tiles) cands.push_back({tc, k});
+    for (size_t ci = 0; ci < cands.size() && r == FM_OK; ++ci) {
+        const int tc = cands[ci].first, k = cands[ci].second;
         if ((r = retune(s, tc, k))) break;
         if ((r = fm_set_graphs(s, use_graphs ? 1 : 0))) break;
         const int period = 2 * k;
@@ -2036,7 +2041,9 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
         } else {
           ++rejected;
         }
-      }
+        if (ci + 1 == cands.size() && mixed && have && best.reorth_interval > 1 && !(best.tile_config >> 5))
+          for (int d = 1; d <= 2; ++d) cands.push_back({best.tile_config | (d << 5), best.reorth_interval});
+    }
   } while (0);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -83,6 +83,12 @@ cudaError_t pmb_gather_w(cudaStream_t st, const __half* urm_h, const __half* urm
                          const int* count, int B, int K, __half* wt_h, __half* wt_l);
 cudaError_t pmb_gather_c(cudaStream_t st, const float* Dp, int64_t sD, int L, int K, int B, const int* list,
                          const int* count, const PmbMats& m);
+// one event i of the step, all trajectories (four launches, each spread over the GPU)
+cudaError_t pmb_event(cudaStream_t st, int i, int Kc, int L, int B, const int* count, const int* list,
+                      const double* ulist, const int64_t* step, const PmbMats& m, fm_event* log,
+                      unsigned long long* log_count, int log_capacity, int nmax);
+// whether pmb_events suits B trajectories with at most kmax events each
+bool pmb_events_fit(int B, int kmax);
 // every event of the step in one launch (one CTA per trajectory, the events in order)
 cudaError_t pmb_events(cudaStream_t st, int Kc, int L, int B, const int* count, const int* list, const double* ulist,
                        const int64_t* step, const PmbMats& m, fm_event* log, unsigned long long* log_count,

@@ -466,6 +466,7 @@ __global__ void copy_cond_kernel(const float4* __restrict__ src, float4* __restr
 
 struct MixedHost {
   int BN;
+  int drain_kb;      // K-blocks between TMEM drains of the first-pass product that no second pass follows
   int n_prop, n_gram, n_trmm, n_trmm2;
   int4 *tiles_prop, *tiles_gram, *tiles_trmm, *tiles_trmm2;
   __half *urm_h, *urm_l;
@@ -496,7 +497,7 @@ bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* wh
     *why = "mixed precision needs L = Lx*Ly divisible by 256 (N a multiple of 128)";
     return false;
   }
-  if ((tile_config & ~0x1f) || (tile_config & 3) == 3) {
+  if ((tile_config & ~0x7f) || (tile_config & 3) == 3 || ((tile_config >> 5) & 3) == 3) {
     *why = "unknown tile_config bits";
     return false;
   }
@@ -525,6 +526,7 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   MixedHost* h = new MixedHost();
   const int L = c->L, N = c->N, B = c->B;
   h->BN = pick_bn(N, c->tile_config);
+  h->drain_kb = 2 << ((c->tile_config >> 5) & 3);
   const int BN = h->BN;
   const int GM = pick_gm(c->tile_config);
   Scratch sp = scratch_plan(c->Lx, c->Ly, B, c->protocol);
@@ -831,11 +833,12 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired, int mode = PASS_
   p.out_l = c->Vl;
   p.in_f = c->V;
   p.cond = cond;
-  // the first pass drains TMEM into fp32 registers every 2 K-blocks when its result
-  // stays the state until the next step (the fp32 TMEM accumulators round toward zero:
-  // up to ~1e-4 relative over 16384 terms); when the second pass follows at once it
-  // removes that error with the rest (to O(|E|^2) ~ 1e-8), so the plain kernel serves
-  p.chunk_kb = (first && !paired) ? 2 : 0;
+  // the first pass drains TMEM into fp32 registers every drain_kb K-blocks (2 by default,
+  // fm_params.tile_config bits 5-6) when its result stays the state until the next step
+  // (the fp32 TMEM accumulators round toward zero: up to ~1e-4 relative over 16384 terms);
+  // when the second pass follows at once it removes that error with the rest (to
+  // O(|E|^2) ~ 1e-8), so the plain kernel serves
+  p.chunk_kb = (first && !paired) ? h->drain_kb : 0;
   c->timer->begin(FM_PH_TRMM);
   if (wide2) MCK(tc::launch(c->st, 256, h->trmm_Ah, h->trmm_Al, h->trmm2_Bh, h->trmm2_Bl, p, grid));
   else MCK(tc::launch(c->st, 128, h->trmm_Ah, h->trmm_Al, h->trmm_Bh, h->trmm_Bl, p, grid));
@@ -928,9 +931,18 @@ int pm_block_step(MixedHost* h, MixedCtx* c, bool* done) {
                      h->pb_dp, 2 * K, sD, nullptr, nullptr, nullptr);
   if (r) return r;
   MCK(pmb_gather_c(c->st, h->pb_dp, sD, L, K, B, h->pb_list, h->pb_count, m));
-  // the events, in order: one launch for all of them (one CTA per trajectory)
-  MCK(pmb_events(c->st, Kc, L, B, h->pb_count, h->pb_list, h->pb_ulist, c->step, m, c->log,
-                 (unsigned long long*)c->log_count, c->log_capacity));
+  // the events, in order: many trajectories or few events in one launch (one CTA per
+  // trajectory); else one launch per phase of each event, spread over the GPU
+  if (pmb_events_fit(B, kmax)) {
+    MCK(pmb_events(c->st, Kc, L, B, h->pb_count, h->pb_list, h->pb_ulist, c->step, m, c->log,
+                   (unsigned long long*)c->log_count, c->log_capacity));
+  } else {
+    for (int i = 0; i < kmax; ++i) {
+      MCK(pmb_event(c->st, i, Kc, L, B, h->pb_count, h->pb_list, h->pb_ulist, c->step, m, c->log,
+                    (unsigned long long*)c->log_count, c->log_capacity, kmax));
+      c->launches += i > 0 ? 3 : 2;               // with the one MCK counts: 4 (3 for the first event)
+    }
+  }
   // B^dag = T_B^dag W
   MCK(pmb_gather_wc(c->st, c->V, L, N, K, B, h->pb_list, h->pb_count, m));
   const c32 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};

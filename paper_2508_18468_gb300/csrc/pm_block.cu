@@ -109,6 +109,148 @@ __global__ void pmb_gather_c_kernel(const float* Dp, int64_t sD, int L, int K, i
   C[b * sC + r + (int64_t)c * Kc] = v;
 }
 
+// ------------------------------------------------------------------ one event (i), all trajectories
+// E1: rho = e_i + T_B conj(a), y = C[:, i] + (C T_B) conj(a), a = row i of (C T_A + T_E);
+// warp per row r.
+__global__ void pmb_rho_kernel(int i, int Kc, const int* count, const c32* C, const c32* TBr, const c32* CTB,
+                               const c32* CTA, const c32* TE, int64_t sM, c32* rho, c32* y) {
+  const int b = blockIdx.z;
+  const int n = count[b];
+  if (i >= n) return;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const int64_t o = b * sM;
+  const c32* arow_a = CTA + o + (int64_t)i * Kc;
+  const c32* arow_e = TE + o + (int64_t)i * Kc;
+  c32 sr = cmk(0.0f, 0.0f), sy = cmk(0.0f, 0.0f);
+  for (int l = lane; l < i; l += 32) {
+    const c32 a = cconj(cadd(arow_a[l], arow_e[l]));
+    if (l >= r) cfmaf(sr, TBr[o + (int64_t)r * Kc + l], a);
+    cfmaf(sy, CTB[o + (int64_t)r * Kc + l], a);
+  }
+  sr = warp_csum(sr);
+  sy = warp_csum(sy);
+  if (lane == 0) {
+    if (r == i) sr.re += 1.0f;
+    rho[b * Kc + r] = r <= i ? sr : cmk(0.0f, 0.0f);
+    y[b * Kc + r] = cadd(sy, C[o + r + (int64_t)i * Kc]);
+  }
+}
+
+// E3: Born weight, outcome, t_i and C t_i; one CTA per trajectory.
+__global__ void __launch_bounds__(256) pmb_decide_kernel(int i, int Kc, int L, const int* count, const int* list,
+                                                         const double* ulist, const int64_t* step, const c32* rho,
+                                                         const c32* y, c32* TBr, c32* TBc, c32* CTB, int64_t sM,
+                                                         c32* ys, PmbEvent* ev, fm_event* log,
+                                                         unsigned long long* log_count, int log_capacity) {
+  const int b = blockIdx.x;
+  const int n = count[b];
+  __shared__ double red[33];
+  __shared__ double sp_sh;
+  __shared__ int act_sh;
+  if (i >= n) {
+    if (threadIdx.x == 0) ev[b].active = 0;
+    return;
+  }
+  double part = 0.0;
+  for (int r = threadIdx.x; r <= i; r += blockDim.x) {
+    const c32 a = rho[b * Kc + r], c = y[b * Kc + r];
+    part += (double)a.re * c.re + (double)a.im * c.im;
+  }
+  // fixed-order block sum
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double p = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) p += red[w];
+    p = fmin(fmax(p, 0.0), 1.0);
+    const int j = list[(int64_t)b * L + i];
+    const double u = ulist[(int64_t)b * L + i];
+    PmbEvent e;
+    e.outcome = (u < p) ? 1 : 0;
+    e.active = (p >= 1e-300) ? 1 : 0;
+    e.sp = sqrt(p);
+    e.c = e.outcome ? -1.0 : 1.0 / sqrt(1.0 - p) - 1.0;
+    e.dsel = e.outcome ? 1.0 : -e.sp / sqrt(1.0 - p);
+    ev[b] = e;
+    sp_sh = e.sp;
+    act_sh = e.active;
+    if (log && log_capacity > 0) {
+      const unsigned long long slot = atomicAdd(log_count, 1ull);
+      if (slot < (unsigned long long)log_capacity) {
+        fm_event le;
+        le.step = step[b]; le.traj = b; le.site = j; le.u = u; le.p = p; le.outcome = e.outcome; le.pad = 0;
+        log[slot] = le;
+      }
+    }
+  }
+  __syncthreads();
+  if (!act_sh) return;
+  const float inv = (float)(1.0 / sp_sh);
+  const int64_t o = b * sM;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const c32 yr = cscale(y[b * Kc + r], inv);
+    ys[b * Kc + r] = yr;
+    CTB[o + (int64_t)r * Kc + i] = yr;
+    if (r <= i) {
+      const c32 t = cscale(rho[b * Kc + r], inv);
+      TBr[o + (int64_t)r * Kc + i] = t;
+      TBc[o + r + (int64_t)i * Kc] = t;
+    }
+  }
+}
+
+// E4: g_l = sum_{r <= l} conj(T_B[r, l]) ys_r for l < i; warp per column.
+__global__ void pmb_g_kernel(int i, int Kc, const int* count, const PmbEvent* ev, const c32* TBc, int64_t sM,
+                             const c32* ys, c32* g) {
+  const int b = blockIdx.z;
+  if (i >= count[b] || !ev[b].active) return;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (l >= i) return;
+  const c32* col = TBc + b * sM + (int64_t)l * Kc;
+  c32 s = cmk(0.0f, 0.0f);
+  for (int r = lane; r <= l; r += 32) cfmaf(s, cconj(col[r]), ys[b * Kc + r]);
+  s = warp_csum(s);
+  if (lane == 0) g[b * Kc + l] = s;
+}
+
+// E5: column i of T_A, C T_A and T_E; warp per row.
+__global__ void pmb_update_kernel(int i, int Kc, const int* count, const PmbEvent* ev, c32* TA, c32* CTA, c32* TE,
+                                  const c32* TBr, int64_t sM, const c32* ys, const c32* g) {
+  const int b = blockIdx.z;
+  const int n = count[b];
+  if (i >= n || !ev[b].active) return;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const int64_t o = b * sM + (int64_t)r * Kc;
+  c32 tau = cmk(0.0f, 0.0f), ctau = cmk(0.0f, 0.0f), eps = cmk(0.0f, 0.0f);
+  for (int l = lane; l < i; l += 32) {
+    const c32 gl = g[b * Kc + l];
+    if (l >= r) {
+      cfmaf(tau, TA[o + l], gl);
+      cfmaf(eps, TE[o + l], gl);
+    }
+    cfmaf(ctau, CTA[o + l], gl);
+  }
+  tau = warp_csum(tau);
+  ctau = warp_csum(ctau);
+  eps = warp_csum(eps);
+  if (lane == 0) {
+    const PmbEvent e = ev[b];
+    const float c = (float)e.c;
+    if (r <= i) {
+      tau = cadd(tau, TBr[o + i]);
+      TA[o + i] = cscale(tau, c);
+      c32 te = cscale(eps, c);
+      if (r == i) te.re += (float)e.dsel;
+      TE[o + i] = te;
+    }
+    ctau = cadd(ctau, ys[b * Kc + r]);
+    CTA[o + i] = cscale(ctau, c);
+  }
+}
+
 // ------------------------------------------------------------------ all events of a step, one launch
 // Every event i < count[b] of trajectory b in one CTA of 512 threads (trajectories are
 // independent; the events of one are sequential), in phases separated by CTA barriers:
@@ -118,7 +260,9 @@ __global__ void pmb_gather_c_kernel(const float* Dp, int64_t sD, int L, int K, i
 //       event log, then t_i = rho / sqrt(p) into T_B and ys = y / sqrt(p) = C t_i into C T_B;
 //   E4  g_l = sum_{r <= l} conj(T_B[r, l]) ys_r for l < i (a warp per column);
 //   E5  column i of T_A, C T_A and T_E (a warp per row).
-// One launch per step instead of four per event (the events were launch-latency bound).
+// One launch per step instead of four per event: the choice when many trajectories keep the
+// SMs busy or the events are few (pmb_events_fit); the per-phase kernels above spread one
+// event's rows over the whole GPU, which long event lists of a few trajectories need.
 constexpr int kEvThreads = 512;          // two CTAs per SM (46 registers a thread)
 
 __global__ void __launch_bounds__(kEvThreads) pmb_events_kernel(int Kc, int L, const int* count, const int* list,
@@ -247,6 +391,8 @@ __global__ void __launch_bounds__(kEvThreads) pmb_events_kernel(int Kc, int L, c
     __syncthreads();
   }
 }
+
+bool pmb_events_fit(int B, int kmax) { return B >= 64 || kmax <= 128; }
 
 cudaError_t pmb_events(cudaStream_t st, int Kc, int L, int B, const int* count, const int* list, const double* ulist,
                        const int64_t* step, const PmbMats& m, fm_event* log, unsigned long long* log_count,
@@ -396,6 +542,22 @@ cudaError_t pmb_gather_wc(cudaStream_t st, const float* V, int L, int N, int K, 
 
 cudaError_t pmb_xtilde(cudaStream_t st, const PmbMats& m, int K, int B, int N, __half* xh, __half* xl) {
   pmb_xtilde_kernel<<<dim3(FM_CEIL_DIV(K, 256), N, B), 256, 0, st>>>(m.X, m.sW, K, m.Kc, N, xh, xl);
+  return cudaGetLastError();
+}
+
+cudaError_t pmb_event(cudaStream_t st, int i, int Kc, int L, int B, const int* count, const int* list,
+                      const double* ulist, const int64_t* step, const PmbMats& m, fm_event* log,
+                      unsigned long long* log_count, int log_capacity, int nmax) {
+  const int warps = 8;
+  const dim3 rows(FM_CEIL_DIV(nmax, warps), 1, B);
+  pmb_rho_kernel<<<rows, 32 * warps, 0, st>>>(i, Kc, count, m.C, m.TBr, m.CTB, m.CTA, m.TE, m.sM, m.rho, m.y);
+  pmb_decide_kernel<<<B, 256, 0, st>>>(i, Kc, L, count, list, ulist, step, m.rho, m.y, m.TBr, m.TBc, m.CTB, m.sM,
+                                       m.ys, m.ev, log, log_count, log_capacity);
+  if (i > 0) {
+    const dim3 cols(FM_CEIL_DIV(i, warps), 1, B);
+    pmb_g_kernel<<<cols, 32 * warps, 0, st>>>(i, Kc, count, m.ev, m.TBc, m.sM, m.ys, m.g);
+  }
+  pmb_update_kernel<<<rows, 32 * warps, 0, st>>>(i, Kc, count, m.ev, m.TA, m.CTA, m.TE, m.TBr, m.sM, m.ys, m.g);
   return cudaGetLastError();
 }
 
