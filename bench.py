@@ -232,8 +232,8 @@ def profiled_traffic(L, B):
                 return None, "unreadable capture line"
             scale = (L / 4096.0) ** 3 * (B / 4.0)
             return x * scale, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of tc_gemm_kernel<128,0,1> "
-                               "at ring L=4096, B=4 (profiles/prop_gemm_ring4096.md) x (L/4096)^3 (B/4) = "
-                               "x %.0f" % scale)
+                               "(the benchmark's tile configuration) at ring L=4096, B=4 "
+                               "(profiles/prop_gemm_ring4096.md) x (L/4096)^3 (B/4) = x %.0f" % scale)
     return None, "no propagation line in the capture summary"
 
 

@@ -489,6 +489,9 @@ struct MixedHost {
   float *pb_dp, *pb_ap;
   PmbMats pm;
   std::vector<int> pb_hcount;
+  // second stream of the first-pass Cholesky (two halves of the batch side by side)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* why) {
@@ -516,7 +519,16 @@ size_t mixed_scratch_bytes(int Lx, int Ly, int batch, int protocol) {
   return scratch_plan(Lx, Ly, batch, protocol).total;
 }
 
-void mixed_free(MixedHost* h) { delete h; }
+void mixed_free(MixedHost* h) {
+  if (!h) return;
+  if (h->st2) {
+    cudaStreamSynchronize(h->st2);
+    cudaStreamDestroy(h->st2);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
+  delete h;
+}
 
 MixedHost* mixed_create(MixedCtx* c, std::string* why) {
   if (tc::configure_all() != cudaSuccess) {
@@ -592,6 +604,13 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
     m.X = (c32*)(base + sp.pb_x);
     h->pb_hcount.assign(B, 0);
   }
+  if (B >= 2 && (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)) {
+    *why = "Cholesky stream";
+    mixed_free(h);
+    return nullptr;
+  }
   std::vector<int4> tp = tc::tile_list(2 * L / tc::BM, B * N / BN, 1, 1, false, BN, GM);
   std::vector<int4> tg = tc::tile_list(N / tc::BM, N / BN, B, 2, true, BN, GM);
   std::vector<int4> tt = tc::tile_list(L / tc::BM, 2 * N / 128, B, 1, false, 128, GM);
@@ -607,7 +626,7 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
                 cudaSuccess &&
             cudaMemsetAsync(base + sp.guard, 0, guard_bytes(B), c->st) == cudaSuccess &&
             cudaStreamSynchronize(c->st) == cudaSuccess;
-  if (!ok) { *why = "tile upload"; delete h; return nullptr; }
+  if (!ok) { *why = "tile upload"; mixed_free(h); return nullptr; }
   const uint64_t L2 = 2 * (uint64_t)L, N2 = 2 * (uint64_t)N;
   ok = tc::make_kmajor_map(&h->prop_Ah, c->Ah, L2, L2, L2, tc::BM) &&
        tc::make_kmajor_map(&h->prop_Al, c->Al, L2, L2, L2, tc::BM) &&
@@ -623,7 +642,7 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
        tc::make_kmajor_map(&h->trmm_Bl, c->Tl, N2, (uint64_t)B * N2, N2, 128) &&
        tc::make_kmajor_map(&h->trmm2_Bh, c->Th, N2, (uint64_t)B * N2, N2, 256) &&
        tc::make_kmajor_map(&h->trmm2_Bl, c->Tl, N2, (uint64_t)B * N2, N2, 256);
-  if (!ok) { *why = "cuTensorMapEncodeTiled failed"; delete h; return nullptr; }
+  if (!ok) { *why = "cuTensorMapEncodeTiled failed"; mixed_free(h); return nullptr; }
   return h;
 }
 
@@ -757,6 +776,49 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   return FM_OK;
 }
 
+// The first-pass factorisation of the whole batch as two halves side by side: the halves'
+// recursions are independent, so one half's latency-bound leaves (a CTA per trajectory)
+// run while the other half's products fill the GPU.  The second half works on the second
+// halves of the factor and operand scratch (per-trajectory strides), on a library stream
+// forked from the step's stream and joined back into it (a captured graph holds both).
+int chol_two_halves(MixedHost* h, MixedCtx* c) {
+  const int B = c->B;
+  if (B < 2 || !h->st2) return chol_inv_rec(h, c, 0, c->N);
+  const int B1 = B / 2, B2 = B - B1;
+  const int64_t sNN = (int64_t)c->N * c->N, md2 = h->md * h->md;
+  MixedHost h2 = *h;
+  h2.gf += B1 * sNN;
+  h2.rf += B1 * sNN;
+  h2.tf += B1 * sNN;
+  h2.ca_h += B1 * 4 * md2;
+  h2.ca_l += B1 * 4 * md2;
+  h2.cb_h += B1 * 2 * md2;
+  h2.cb_l += B1 * 2 * md2;
+  h2.xs += B1 * md2;
+  h2.st2 = nullptr;
+  h2.fork = h2.join = nullptr;                 // the copy owns nothing
+  MixedCtx c1 = *c, c2 = *c;
+  c1.B = B1;
+  c2.B = B2;
+  c2.st = h->st2;
+  c1.launches = c2.launches = 0;
+  if (cudaEventRecord(h->fork, c->st) != cudaSuccess || cudaStreamWaitEvent(h->st2, h->fork, 0) != cudaSuccess) {
+    c->err = "Cholesky stream fork";
+    return FM_ECUDA;
+  }
+  const int r1 = chol_inv_rec(h, &c1, 0, c->N);
+  const int r2 = r1 ? r1 : chol_inv_rec(&h2, &c2, 0, c->N);
+  h2.pb_hcount.clear();
+  c->launches += c1.launches + c2.launches;
+  // join even after an error, so that the step's stream never runs ahead of the second half
+  const bool joined = cudaEventRecord(h->join, h->st2) == cudaSuccess &&
+                      cudaStreamWaitEvent(c->st, h->join, 0) == cudaSuccess;
+  if (r1) { c->err = c1.err; return r1; }
+  if (r2) { c->err = c2.err; return r2; }
+  if (!joined) { c->err = "Cholesky stream join"; return FM_ECUDA; }
+  return FM_OK;
+}
+
 // Target of the second-pass guard: the bound on the entries of U^dag U - 1 that the
 // first-order factor may leave (a tenth of the 1e-6 orthonormality bar).
 constexpr float kReorthTau = 1e-7f;
@@ -806,7 +868,7 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired, int mode = PASS_
   c->timer->end(FM_PH_GRAM);
   c->timer->begin(FM_PH_CHOLESKY);
   if (first) {
-    int r = chol_inv_rec(h, c, 0, N);
+    int r = chol_two_halves(h, c);
     if (r) return r;
   }
   build_ttilde_kernel<<<(unsigned)(2 * (int64_t)B * N), 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag,

@@ -1,11 +1,11 @@
 """Profiling helpers: workloads to run under ncu, and a launch-list summary.
 
-    python -m paper_2508_18468_gb300.profiling steps L B K [protocol] [propagation] [reorth]
+    python -m paper_2508_18468_gb300.profiling steps L B K [protocol] [propagation] [reorth] [tile_config]
         L-site ring (or Lx x Ly torus written "LxxLy"), B trajectories, mixed precision:
         warm-up steps up to a whole step period, then K steps inside the NVTX range "steps"
         (capture them with ncu --nvtx --nvtx-include "steps/").  protocol: homodyne (default),
         projective, poisson, rk4; propagation: dense (default) or banded; reorth: the
-        reorth_interval (default 1).  Prints one JSON line.
+        reorth_interval (default 1); tile_config (default 0).  Prints one JSON line.
     python -m paper_2508_18468_gb300.profiling entropy L [full|sketch] [steps]
         `steps` steps (default 1) of a single homodyne trajectory, then the half-chain
         entropy by the given method (default full) inside the NVTX range "entropy".
@@ -50,7 +50,7 @@ def _lattice(spec):
     return int(spec), 1
 
 
-def steps(spec, B, K, protocol="homodyne", propagation="dense", reorth=1):
+def steps(spec, B, K, protocol="homodyne", propagation="dense", reorth=1, tile_config=0):
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -60,7 +60,8 @@ def steps(spec, B, K, protocol="homodyne", propagation="dense", reorth=1):
             "rk4": fm.FM_HOMODYNE_RK4}[protocol]
     reorth = int(reorth)
     g = fm.Trajectories(fm.make_params(Lx, Ly, batch=B, protocol=prot, precision=fm.FM_MIXED, gamma=1.0,
-                                       seed=workloads.seed_of("ring16384_homodyne"), reorth_interval=reorth))
+                                       seed=workloads.seed_of("ring16384_homodyne"), reorth_interval=reorth,
+                                       tile_config=int(tile_config)))
     g.set_gammas(([0.3, 0.3, 1.0, 1.0] * B)[:B])
     if propagation == "banded":
         g.set_propagation(fm.FM_PROP_BANDED)
@@ -74,7 +75,7 @@ def steps(spec, B, K, protocol="homodyne", propagation="dense", reorth=1):
     t = time.perf_counter() - t0
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"Lx": Lx, "Ly": Ly, "B": B, "steps": K, "protocol": protocol, "propagation": propagation,
-                      "reorth_interval": reorth, "s_per_step": t / K,
+                      "reorth_interval": reorth, "tile_config": int(tile_config), "s_per_step": t / K,
                       "launches_per_step": (g.kernel_launches - l0) / K}))
 
 
@@ -101,7 +102,7 @@ def entropy(L, method="full", nsteps=1):
 if __name__ == "__main__":
     cmd = sys.argv[1]
     if cmd == "steps":
-        steps(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), *sys.argv[5:8])
+        steps(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), *sys.argv[5:9])
     elif cmd == "entropy":
         entropy(int(sys.argv[2]), *(sys.argv[3:4]), *[int(x) for x in sys.argv[4:5]])
     elif cmd == "summary":

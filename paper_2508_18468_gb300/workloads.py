@@ -30,9 +30,10 @@ WORKLOADS = {
     # 1d ring L = 16384, homodyne, gamma in {0.3, 1.0} x 2 trajectories, 1000 steps,
     # half-chain EE every 100 steps.  reorth_interval and tile_config: what fm_autotune picks for
     # this batch (max_reorth 8, orthonormality bar 1e-6): the second CholeskyQR pass every 8
-    # steps; tile_config 9 = 128-wide tiles in raster groups of 8 row tiles (the defaults)
+    # steps; tile_config 77 = 128-wide tiles in raster groups of 16 row tiles, the first-pass
+    # product drained every 8 K-blocks between second passes
     "ring16384_homodyne": dict(index=2, Lx=16384, Ly=1, protocol="homodyne", gammas=[0.3, 0.3, 1.0, 1.0],
-                               steps=1000, ee_every=100, ee_sizes=[8192], reorth_interval=8, tile_config=9,
+                               steps=1000, ee_every=100, ee_sizes=[8192], reorth_interval=8, tile_config=77,
                                precision="mixed"),
     # profiling size of the same step (a few GB on the device): 1d ring L = 4096, homodyne, 4 trajectories
     "ring4096_homodyne": dict(index=5, Lx=4096, Ly=1, protocol="homodyne", gammas=[0.3, 0.3, 1.0, 1.0],
