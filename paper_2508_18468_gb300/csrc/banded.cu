@@ -195,7 +195,11 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
   const int base = r * run + 4 * g + ntap - 1;     // staged index of the input for output 0 at tap 0
   const int c = blockIdx.y;
   const int k0 = c * per, k1 = min(N, k0 + per);
+  // row sums of |out|^2: float over up to 16 columns, then into double (GB300's FP64 rate is
+  // ~1/60 of FP32: a double add per output bounded the whole pass)
   double acc2[4] = {0.0, 0.0, 0.0, 0.0};
+  float accf[4] = {0.f, 0.f, 0.f, 0.f};
+  int nacc = 0;
   // software pipeline: the next stage's columns are loaded into registers while the current
   // stage is computed from shared memory
   float vr[kB4Cols][kB4Loads], vi[kB4Cols][kB4Loads];
@@ -270,9 +274,18 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
             col[L + site0 + e] = oii[e];
           }
         }
-        if (partial)
+        if (partial) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc2[e] += (double)(orr[e] * orr[e] + oii[e] * oii[e]);
+          for (int e = 0; e < 4; ++e) accf[e] = fmaf(orr[e], orr[e], fmaf(oii[e], oii[e], accf[e]));
+          if (++nacc == 16) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              acc2[e] += (double)accf[e];
+              accf[e] = 0.f;
+            }
+            nacc = 0;
+          }
+        }
       }
     } else if (nval > 0)
       for (int kk = 0; kk < nk; ++kk) {
@@ -315,9 +328,18 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
             col[L + site0 + e] = oii[e];
           }
         }
-        if (partial)
+        if (partial) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc2[e] += (double)(orr[e] * orr[e] + oii[e] * oii[e]);
+          for (int e = 0; e < 4; ++e) accf[e] = fmaf(orr[e], orr[e], fmaf(oii[e], oii[e], accf[e]));
+          if (++nacc == 16) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              acc2[e] += (double)accf[e];
+              accf[e] = 0.f;
+            }
+            nacc = 0;
+          }
+        }
       }
     if (more) {
       __syncthreads();                             // every thread is done with this stage
@@ -326,7 +348,7 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
     }
   }
   if (partial)
-    for (int e = 0; e < nval; ++e) partial[(b * nch + c) * L + site0 + e] = acc2[e];
+    for (int e = 0; e < nval; ++e) partial[(b * nch + c) * L + site0 + e] = acc2[e] + (double)accf[e];
 }
 
 template <typename T, int LAYOUT, int SEGY>
@@ -348,9 +370,15 @@ __global__ void __launch_bounds__(256) band_y_kernel(const void* __restrict__ in
   const int h = SEGY + ntap - 1;
   const int c = blockIdx.y;
   const int k0 = c * per, k1 = min(N, k0 + per);
+  // row sums of |out|^2 (see band_x4_kernel): in T over up to 16 columns, then double
   double s[SEGY / 8];
+  T sf[SEGY / 8];
 #pragma unroll
-  for (int r = 0; r < SEGY / 8; ++r) s[r] = 0.0;
+  for (int r = 0; r < SEGY / 8; ++r) {
+    s[r] = 0.0;
+    sf[r] = (T)0;
+  }
+  int nacc = 0;
   // staged rows of one column: h <= SEGY + kBandMaxTaps - 1, at most RY per thread, loaded
   // into registers before any is stored
   constexpr int RY = (H + 7) / 8;
@@ -382,15 +410,23 @@ __global__ void __launch_bounds__(256) band_y_kernel(const void* __restrict__ in
             acc.im += tp[t].re * u.im + tp[t].im * u.re;
           }
           band_io<T, LAYOUT>::st(out, b, L, N, x + Lx * y, k, acc);
-          if (partial) s[r] += (double)(acc.re * acc.re + acc.im * acc.im);
+          if (partial) sf[r] += acc.re * acc.re + acc.im * acc.im;
         }
       }
+    if (partial && ++nacc == 16) {
+#pragma unroll
+      for (int r = 0; r < SEGY / 8; ++r) {
+        s[r] += (double)sf[r];
+        sf[r] = (T)0;
+      }
+      nacc = 0;
+    }
   }
   if (partial && x < Lx)
 #pragma unroll
     for (int r = 0; r < SEGY / 8; ++r) {
       const int y = y0 + ty + 8 * r;
-      if (y < Ly) partial[(b * nch + c) * L + x + Lx * y] = s[r];
+      if (y < Ly) partial[(b * nch + c) * L + x + Lx * y] = s[r] + (double)sf[r];
     }
 }
 

@@ -75,12 +75,15 @@ __device__ __forceinline__ void emit(const Params& p, const TileInfo& ti, int r,
 #pragma unroll
     for (int j = 0; j < 32; ++j) out[(int64_t)j * p.ld_out] = d[j];
   } else if (MODE == MODE_PROP) {
+    // row sums of squares: float over the slab's 32 columns (fixed order), then one double add
     float* out = p.out_f + (int64_t)(m0 + r) + (int64_t)(n0 + c0) * p.ld_out;
+    float part = 0.0f;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       out[(int64_t)j * p.ld_out] = d[j];
-      rowsum += (double)d[j] * (double)d[j];
+      part = fmaf(d[j], d[j], part);
     }
+    rowsum += (double)part;
   } else if (MODE == MODE_GRAM) {
     // complex64 G_b[k1 + k2 N], real or imaginary part
     float* out = p.out_gf + 2 * ((int64_t)ti.b * p.Ntraj * p.Ntraj + (int64_t)(m0 + r) +
