@@ -124,10 +124,10 @@ constexpr int kB4Seg = 1024;
 constexpr int kB4Cols = 2;
 constexpr int kB4Cap = 1344;                       // staged floats per column and plane
 constexpr int kB4Loads = (kB4Cap + 255) / 256;
-// staged element q sits at q + q / 32 in shared memory: each lane's window starts 4 words
-// after its neighbour's, which without the padding word would put lanes 8 apart on one bank
-constexpr int kB4Pad = kB4Cap + kB4Cap / 32;
-FM_DEVFN int b4pos(int q) { return q + (q >> 5); }
+// staged rows are runp = run rounded up to 4 floats apart, so that each thread's window (which
+// starts at its first output's site minus the stencil's reach) is 16-byte aligned and loads as
+// float4s: 8 lanes then read 128 contiguous bytes, conflict-free
+constexpr int kB4Pad = kB4Cap + 3 * 8;
 
 struct B4Shape {
   int S, tpr, RB, segs, groups;
@@ -149,12 +149,12 @@ inline B4Shape band4_shape(int Lx, int Ly) {
 // inner loop is NT x 16 FMAs with static indices; NT = 0: any tap count, a window sliding one
 // input per tap.
 template <int NT>
-__global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const float* __restrict__ in, float* __restrict__ out,
+__global__ void __launch_bounds__(256, 2) band_x4_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                          int L, int N, int Lx, int Ly, int S, int tpr, int RB, int segs,
                                                          const z64* __restrict__ taps, const int* __restrict__ off,
                                                          int ntap, int per, double* partial, int nch, int tap_stride) {
-  __shared__ float sre[kB4Cols][kB4Pad];
-  __shared__ float sim[kB4Cols][kB4Pad];
+  __shared__ __align__(16) float sre[kB4Cols][kB4Pad];
+  __shared__ __align__(16) float sim[kB4Cols][kB4Pad];
   __shared__ float tre[kBandMaxTaps], tim[kBandMaxTaps];
   const int64_t b = blockIdx.z;
   taps += b * tap_stride;
@@ -166,19 +166,22 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
   const int seg = blockIdx.x % segs, rg = blockIdx.x / segs;
   const int x0 = seg * S;
   const int run = S + ntap - 1;                    // staged inputs per row
+  const int runp = (run + 3) & ~3;                 // their row pitch in shared memory
   const int offmax = off[0] + ntap - 1;
   const int tot = RB * run;
   const int64_t L2 = 2 * (int64_t)L;
   const float* inb = in + b * L2 * N;
   float* outb = out + b * L2 * N;
   // source sites of this thread's staged elements (the same for every column)
-  int src[kB4Loads];
+  int src[kB4Loads], dst[kB4Loads];
 #pragma unroll
   for (int u = 0; u < kB4Loads; ++u) {
     const int q = tid + 256 * u;
     src[u] = -1;
+    dst[u] = 0;
     if (q < tot) {
       const int r = q / run, e = q - r * run, y = rg * RB + r;
+      dst[u] = r * runp + e;
       if (y < Ly) {
         int x = (x0 - offmax + e) % Lx;
         if (x < 0) x += Lx;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
   const int nval = (r < RB && y < Ly) ? max(0, min(4, min(x0 + S, Lx) - xs)) : 0;
   const int site0 = xs + Lx * y;
   const bool vec = nval == 4 && (site0 % 4) == 0 && (L % 4) == 0;
-  const int base = r * run + 4 * g + ntap - 1;     // staged index of the input for output 0 at tap 0
+  const int base = r * runp + 4 * g + ntap - 1;    // staged index of the input for output 0 at tap 0
   const int c = blockIdx.y;
   const int k0 = c * per, k1 = min(N, k0 + per);
   // row sums of |out|^2: float over up to 16 columns, then into double (GB300's FP64 rate is
@@ -222,8 +225,8 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
 #pragma unroll
       for (int u = 0; u < kB4Loads; ++u)
         if (kk < nk && src[u] >= 0) {
-          sre[kk][b4pos(tid + 256 * u)] = vr[kk][u];
-          sim[kk][b4pos(tid + 256 * u)] = vi[kk][u];
+          sre[kk][dst[u]] = vr[kk][u];
+          sim[kk][dst[u]] = vi[kk][u];
         }
   };
   if (k0 < k1) {
@@ -246,12 +249,17 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
       for (int kk = 0; kk < nk; ++kk) {
         const float* ar = sre[kk];
         const float* ai = sim[kk];
-        // x[q] = input base - (NT - 1) + q; output e at tap t reads x[NT - 1 + e - t]
-        float xr[NT + 3], xi[NT + 3];
+        // x[q] = input base - (NT - 1) + q (a 16-byte aligned run: base - (NT - 1) = r runp + 4 g);
+        // output e at tap t reads x[NT - 1 + e - t]
+        constexpr int NV = (NT + 3 + 3) / 4;
+        float xr[4 * NV], xi[4 * NV];
+        const float4* wr4 = (const float4*)(ar + base - (NT - 1));
+        const float4* wi4 = (const float4*)(ai + base - (NT - 1));
 #pragma unroll
-        for (int q = 0; q < NT + 3; ++q) {
-          xr[q] = ar[b4pos(base - (NT - 1) + q)];
-          xi[q] = ai[b4pos(base - (NT - 1) + q)];
+        for (int v = 0; v < NV; ++v) {
+          const float4 a = wr4[v], bb = wi4[v];
+          xr[4 * v] = a.x; xr[4 * v + 1] = a.y; xr[4 * v + 2] = a.z; xr[4 * v + 3] = a.w;
+          xi[4 * v] = bb.x; xi[4 * v + 1] = bb.y; xi[4 * v + 2] = bb.z; xi[4 * v + 3] = bb.w;
         }
         float orr[4] = {0.f, 0.f, 0.f, 0.f}, oii[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -294,8 +302,8 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
         float wr[4], wi[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {               // a short last group reads only its own run
-          wr[e] = e < nval ? ar[b4pos(base + e)] : 0.f;
-          wi[e] = e < nval ? ai[b4pos(base + e)] : 0.f;
+          wr[e] = e < nval ? ar[base + e] : 0.f;
+          wi[e] = e < nval ? ai[base + e] : 0.f;
         }
         float orr[4] = {0.f, 0.f, 0.f, 0.f}, oii[4] = {0.f, 0.f, 0.f, 0.f};
         for (int t = 0; t < ntap; ++t) {
@@ -314,8 +322,8 @@ __global__ void __launch_bounds__(256, NT > 0 ? 2 : 3) band_x4_kernel(const floa
             wi[e] = wi[e - 1];
           }
           if (t + 1 < ntap) {
-            wr[0] = ar[b4pos(base - t - 1)];
-            wi[0] = ai[b4pos(base - t - 1)];
+            wr[0] = ar[base - t - 1];
+            wi[0] = ai[base - t - 1];
           }
         }
         float* col = outb + (int64_t)(kb + kk) * L2;
@@ -441,7 +449,8 @@ int clamp_chunks(int64_t blocks, int N) {
 bool use_band4(int Lx, int Ly, int layout, int ntap) {
   if (layout != 1) return false;
   const B4Shape g = band4_shape(Lx, Ly);
-  return g.RB * (g.S + ntap - 1) <= kB4Cap;
+  const int runp = (g.S + ntap - 1 + 3) & ~3;
+  return g.RB * runp + 4 <= kB4Pad;
 }
 
 int band_chunks(int Lx, int Ly, int N, int B, int dir, int layout) {
