@@ -585,14 +585,14 @@ def run_ours(args, world, rank, local):
     del g
     torch.cuda.empty_cache()
     side = None
-    if args.fp64_steps > 0 and precision == fm.FM_MIXED and rank == 0:
+    if args.fp64_steps > 0 and precision == fm.FM_MIXED and world == 1:
         hard = max(range(B), key=lambda b: gam[b])        # the trajectory with the largest rate
         side = fp64_side_by_side(fm, wl, seed, replica_traj_id(rank, B) + hard, gam[hard], args.fp64_steps,
                                  ee_sites, ee_method)
 
     peaks, peak_src = load_peaks()
     others = None
-    if not args.no_others and rank == 0 and args.workload == WORKLOAD:
+    if not args.no_others and world == 1 and args.workload == WORKLOAD:
         others = other_workloads(fm, peaks)
 
     if rank != 0:

@@ -85,71 +85,66 @@ constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + kLeafMax + 96 * kLeaf
 // Factor and invert the m x m (m <= 32) diagonal block at D (row stride kLeafLd),
 // one warp, lane c owning column c: R into the upper triangle of D, T = R^-1
 // transposed into its strict lower triangle (row c of the lower triangle holds
-// column c of T, which only lane c touches), T's diagonal into Tdk, 1 / R_jj into
-// Rinv.  Loops stay rolled (a fully unrolled factorisation overflows the
-// instruction cache); the column updates go in chunks of 8 rows, loads first, so
-// that each chunk waits for shared memory once.  Returns true after a bad pivot.
+// column c of T), T's diagonal into Tdk, 1 / R_jj into Rinv.  Returns true after a
+// bad pivot (which is then taken as 1).
+//   Factor: lane c keeps the rest of its column of the Schur complement in registers,
+//   rotated so that the pivot row is always col[0]; step j takes G_jj from lane j,
+//   forms R_jc = G_jc / R_jj and subtracts conj(R_jr) R_jc from rows r = j + 1 .. c,
+//   R_jr arriving by a shuffle from lane r.
+//   Inverse: column c of T by back substitution, R t = e_c from row c up; the entries
+//   t_{i+1} .. already found sit rotated in registers, row i of R comes from shared
+//   memory (one address for the whole warp).
 __device__ __forceinline__ bool leaf_diag_block(c32* D, c32* Tdk, float* Rinv, int m, int c) {
   bool bad = false;
+  c32 col[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) col[q] = (c < m && q <= c) ? D[q * kLeafLd + c] : cmk(0.0f, 0.0f);
   for (int j = 0; j < m; ++j) {
-    float piv = D[j * kLeafLd + j].re;
+    float piv = __shfl_sync(0xffffffffu, col[0].re, j);
     if (!(piv > 0.0f) || !isfinite(piv)) {
       bad = true;
       piv = 1.0f;
     }
     const float rs = sqrtf(piv), ri = __frcp_rn(rs);
+    const c32 rj = (c == j) ? cmk(rs, 0.0f) : cscale(col[0], ri);   // R_jc (lanes c >= j)
+    if (c >= j && c < m) D[j * kLeafLd + c] = rj;
     if (c == 0) Rinv[j] = ri;
-    c32 rjc = cmk(0.0f, 0.0f);
-    if (c >= j && c < m) {
-      rjc = c == j ? cmk(rs, 0.0f) : cscale(D[j * kLeafLd + c], ri);
-      D[j * kLeafLd + c] = rjc;                 // row j of R is final
+#pragma unroll
+    for (int q = 1; q < 32; ++q) {
+      const int lr = (j + q) & 31;
+      const c32 x = cmk(__shfl_sync(0xffffffffu, rj.re, lr), __shfl_sync(0xffffffffu, rj.im, lr));   // R_{j, j+q}
+      if (j + q <= c) col[q] = csub(col[q], cmul(cconj(x), rj));
     }
-    __syncwarp();
-    if (c > j && c < m) {
-      for (int r0 = j + 1; r0 <= c; r0 += 8) {
-        c32 x[8], y[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int r = min(r0 + u, 31);
-          x[u] = D[j * kLeafLd + r];            // R_jr: one address for the warp
-          y[u] = D[r * kLeafLd + c];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) y[u] = csub(y[u], cmul(cconj(x[u]), rjc));
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (r0 + u <= c) D[(r0 + u) * kLeafLd + c] = y[u];
-      }
-    }
-    __syncwarp();
+    for (int q = 0; q < 31; ++q) col[q] = col[q + 1];
+    col[31] = cmk(0.0f, 0.0f);
   }
-  // column c of T by back substitution R t = e_c, column-oriented: t_k = w_k / R_kk,
-  // then w_i -= R_ik t_k for i < k (every lane at the same k: R_ik is one address)
-  if (c < m) {
-    for (int i = 0; i < c; ++i) D[c * kLeafLd + i] = cmk(0.0f, 0.0f);
-    Tdk[c] = cmk(1.0f, 0.0f);
-  }
-  __syncwarp();
-  for (int k = m - 1; k >= 0; --k) {
-    if (c >= k && c < m) {
-      c32* wk = c == k ? &Tdk[c] : &D[c * kLeafLd + k];
-      const c32 t = cscale(*wk, Rinv[k]);
-      *wk = t;
-      for (int i0 = 0; i0 < k; i0 += 8) {
-        c32 x[8], y[8];
+  __syncwarp();                                   // rows of R visible to the whole warp
+  // s[q] = t_{i+1+q}, column c of T (zero beyond row c)
+  c32 sv[32];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = min(i0 + u, 31);
-          x[u] = D[i * kLeafLd + k];
-          y[u] = D[c * kLeafLd + i];
-        }
+  for (int q = 0; q < 32; ++q) sv[q] = cmk(0.0f, 0.0f);
+  for (int i = m - 1; i >= 0; --i) {
+    // four partial sums (k = i + 1 + q, q mod 4), so that the multiply-adds do not wait on
+    // one another, then added in a fixed order
+    c32 acc[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) y[u] = csub(y[u], cmul(x[u], t));
+    for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0f, 0.0f);
+    const c32* Ri = D + i * kLeafLd;
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (i0 + u < k) D[c * kLeafLd + i0 + u] = y[u];
-      }
+    for (int q = 0; q < 31; ++q) {
+      const int k = i + 1 + q;
+      if (k <= c && k < m) cfma(acc[q & 3], Ri[k], sv[q]);
     }
+    const c32 sum = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+    const c32 ti = cscale(cmk((c == i ? 1.0f : 0.0f) - sum.re, -sum.im), Rinv[i]);
+    if (c < m) {
+      if (i < c) D[c * kLeafLd + i] = ti;
+      else if (i == c) Tdk[c] = ti;
+    }
+#pragma unroll
+    for (int q = 31; q > 0; --q) sv[q] = sv[q - 1];
+    sv[0] = ti;
   }
   __syncwarp();
   return bad;
