@@ -62,15 +62,17 @@ template cudaError_t cholesky_inverse<float>(cudaStream_t, c32*, c32*, c32*, c32
 // ------------------------------------------------------------------ one-CTA leaf
 // G = R^dag R and T = R^-1 for an n x n block (n <= 128) of every trajectory,
 // complex64, one CTA of 256 threads per trajectory, blocked by 32:
-//   for each diagonal block k: one warp factors it (lane c owns column c; step j
-//   scales row j by 1 / sqrt(pivot) and every lane updates its column with it)
-//   and inverts its triangle by columns; the
+//   for each diagonal block k: one warp factors and inverts it in one sweep (lane c
+//   owns column c; step j scales row j by 1 / sqrt(pivot) and every lane updates its
+//   column and its column of the inverse with it); the
 //   CTA then forms the panel R_k,> = T_kk^dag G_k,> and the trailing update
 //   G_>,> -= R_k,>^dag R_k,> (upper triangle);
-//   then each block column j of T above the diagonal:
-//   T_<j,j = -(T_<j,<j R_<j,j) T_jj, the inner product kept in shared memory.
+//   each block column j of T above the diagonal, T_<j,j = -(T_<j,<j R_<j,j) T_jj,
+//   is formed by the other seven warps while warp 0 factors the next diagonal
+//   blocks: the inner product beside block j, the product with T_jj beside block
+//   j + 1 (the last block column's after the loop).
 // R is kept in the upper triangle of a shared array, T transposed in its strict
-// lower triangle and T's diagonal apart: 20 CTA barriers per 128 x 128 leaf
+// lower triangle and T's diagonal apart: 14 CTA barriers per 128 x 128 leaf
 // instead of one per row.  R and T are written with zeros below the diagonal.
 // A non-positive pivot raises FM_DEVERR_PIVOT and continues with pivot 1.
 namespace fm {
@@ -79,75 +81,116 @@ constexpr int kLeafMax = 128;
 constexpr int kLeafLd = kLeafMax + 1;
 constexpr int kLeafThreads = 256;
 constexpr int kLeafYLd = 33;
-constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + kLeafMax + 96 * kLeafYLd) * sizeof(c32) +
-                              kLeafMax * sizeof(float);
+constexpr size_t kLeafSmem = ((size_t)kLeafMax * kLeafLd + kLeafMax + 2 * 96 * kLeafYLd) * sizeof(c32);
 
-// Factor and invert the m x m (m <= 32) diagonal block at D (row stride kLeafLd),
-// one warp, lane c owning column c: R into the upper triangle of D, T = R^-1
-// transposed into its strict lower triangle (row c of the lower triangle holds
-// column c of T), T's diagonal into Tdk, 1 / R_jj into Rinv.  Returns true after a
-// bad pivot (which is then taken as 1).
-//   Factor: lane c keeps the rest of its column of the Schur complement in registers,
-//   rotated so that the pivot row is always col[0]; step j takes G_jj from lane j,
-//   forms R_jc = G_jc / R_jj and subtracts conj(R_jr) R_jc from rows r = j + 1 .. c,
-//   R_jr arriving by a shuffle from lane r.
-//   Inverse: column c of T by back substitution, R t = e_c from row c up; the entries
-//   t_{i+1} .. already found sit rotated in registers, row i of R comes from shared
-//   memory (one address for the whole warp).
-__device__ __forceinline__ bool leaf_diag_block(c32* D, c32* Tdk, float* Rinv, int m, int c) {
-  bool bad = false;
-  c32 col[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) col[q] = (c < m && q <= c) ? D[q * kLeafLd + c] : cmk(0.0f, 0.0f);
-  for (int j = 0; j < m; ++j) {
-    float piv = __shfl_sync(0xffffffffu, col[0].re, j);
+// Steps j0 .. j1 - 1 of the diagonal-block sweep below, with b[] holding rows j .. j + QN - 1
+// of lane c's column (every row still live when j >= 32 - QN).  Rolled, with constant
+// indices into b[]: the quarter-sized copies keep the code small enough to stay in the
+// instruction cache, and shrink the updates and the rotation as the block is consumed.
+template <int QN>
+__device__ __forceinline__ void leaf_diag_steps(c32 (&b)[32], c32* D, c32* Tdk, int j0, int j1, int m, int c,
+                                                bool& bad) {
+  const c32 zero = cmk(0.0f, 0.0f);
+  for (int j = j0; j < j1; ++j) {
+    float piv = __shfl_sync(0xffffffffu, b[0].re, j);
     if (!(piv > 0.0f) || !isfinite(piv)) {
       bad = true;
       piv = 1.0f;
     }
     const float rs = sqrtf(piv), ri = __frcp_rn(rs);
-    const c32 rj = (c == j) ? cmk(rs, 0.0f) : cscale(col[0], ri);   // R_jc (lanes c >= j)
-    if (c >= j && c < m) D[j * kLeafLd + c] = rj;
-    if (c == 0) Rinv[j] = ri;
+    const c32 s = cscale(b[0], ri);
+    const c32 rj = (c > j) ? s : (c == j ? cmk(rs, 0.0f) : zero);   // R_jc
+    const c32 tj = (c < j) ? s : (c == j ? cmk(ri, 0.0f) : zero);   // (R^-dag)_jc
+    if (c < m) D[j * kLeafLd + c] = (c < j) ? cconj(s) : rj;
+    if (c == j) Tdk[j] = cmk(ri, 0.0f);
+    __syncwarp();
+    const c32* Dj = D + j * kLeafLd + j;
+    // every lane runs every update (masked rather than branched: branches here cost more
+    // than the multiply-adds they would skip)
 #pragma unroll
-    for (int q = 1; q < 32; ++q) {
-      const int lr = (j + q) & 31;
-      const c32 x = cmk(__shfl_sync(0xffffffffu, rj.re, lr), __shfl_sync(0xffffffffu, rj.im, lr));   // R_{j, j+q}
-      if (j + q <= c) col[q] = csub(col[q], cmul(cconj(x), rj));
+    for (int q = 1; q < QN; ++q) {
+      const c32 x = (j + q < m) ? Dj[q] : zero;                     // R_{j, j+q}
+      const c32 f = (j + q <= c) ? rj : tj;
+      b[q] = csub(b[q], cmul(cconj(x), f));
     }
 #pragma unroll
-    for (int q = 0; q < 31; ++q) col[q] = col[q + 1];
-    col[31] = cmk(0.0f, 0.0f);
+    for (int q = 0; q < QN - 1; ++q) b[q] = b[q + 1];
+    b[QN - 1] = zero;
   }
-  __syncwarp();                                   // rows of R visible to the whole warp
-  // s[q] = t_{i+1+q}, column c of T (zero beyond row c)
-  c32 sv[32];
+}
+
+// Factor and invert the m x m (m <= 32) diagonal block at D (row stride kLeafLd) in one
+// sweep, one warp, lane c owning column c: R into the upper triangle of D, T = R^-1
+// transposed into its strict lower triangle (row j of the lower triangle holds column j
+// of T), T's diagonal into Tdk.  Returns true after a bad pivot (which is then taken as 1).
+//   The row operations that take G to R (step j: row j scaled by 1 / sqrt(pivot), then
+//   conj(R_jr) times it subtracted from every row r > j) take the identity to R^-dag when
+//   applied to it alongside.  Lane c keeps one array b[], rotated so that b[0] is row j:
+//   rows <= c hold its column of the Schur complement, rows > c its column of the
+//   transformed identity (whose row c is 1 until step c and whose rows above c stay 0,
+//   so neither is stored).  Step j writes row j (R_jc for c >= j, T_cj = conj of
+//   (R^-dag)_jc for c < j) to shared memory, and every lane takes R_jr, r > j, from there
+//   (one address for the whole warp).
+__device__ __forceinline__ bool leaf_diag_block(c32* D, c32* Tdk, int m, int c) {
+  bool bad = false;
+  c32 b[32];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) sv[q] = cmk(0.0f, 0.0f);
-  for (int i = m - 1; i >= 0; --i) {
-    // four partial sums (k = i + 1 + q, q mod 4), so that the multiply-adds do not wait on
-    // one another, then added in a fixed order
-    c32 acc[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) acc[a] = cmk(0.0f, 0.0f);
-    const c32* Ri = D + i * kLeafLd;
-#pragma unroll
-    for (int q = 0; q < 31; ++q) {
-      const int k = i + 1 + q;
-      if (k <= c && k < m) cfma(acc[q & 3], Ri[k], sv[q]);
-    }
-    const c32 sum = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
-    const c32 ti = cscale(cmk((c == i ? 1.0f : 0.0f) - sum.re, -sum.im), Rinv[i]);
-    if (c < m) {
-      if (i < c) D[c * kLeafLd + i] = ti;
-      else if (i == c) Tdk[c] = ti;
-    }
-#pragma unroll
-    for (int q = 31; q > 0; --q) sv[q] = sv[q - 1];
-    sv[0] = ti;
-  }
+  for (int q = 0; q < 32; ++q) b[q] = (c < m && q <= c) ? D[q * kLeafLd + c] : cmk(0.0f, 0.0f);
+  leaf_diag_steps<32>(b, D, Tdk, 0, min(m, 8), m, c, bad);
+  leaf_diag_steps<24>(b, D, Tdk, 8, min(m, 16), m, c, bad);
+  leaf_diag_steps<16>(b, D, Tdk, 16, min(m, 24), m, c, bad);
+  leaf_diag_steps<8>(b, D, Tdk, 24, m, m, c, bad);
   __syncwarp();
   return bad;
+}
+
+// Block column j of T above the diagonal, in two halves run by threads t0 .. t0 + nt - 1:
+//   first:  Z = T_<j,<j R_<j,j   (needs T up to block column j - 1 and the panels above j;
+//                                 not T_jj, so it can run beside the factorisation of block j)
+//   second: T_<j,j = -Z T_jj     (needs block j factored)
+// Z (96 x 33) is the inverse's own staging; items are (8 rows, one column).
+__device__ __forceinline__ void leaf_tcol_first(const c32* A, const c32* Td, c32* Z, int n, int j, int t, int nt) {
+  const int c0 = 32 * j, mj = min(32, n - c0), items = 4 * j * mj;
+  for (int e = t; e < items; e += nt) {
+    const int rq = e / mj, cc = e % mj, c = c0 + cc, rb = 8 * rq;
+    c32 acc[8];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = cmk(0.0f, 0.0f);
+    for (int s = rb; s < rb + 8; ++s) {         // the 8 x 8 triangle of T_rs, s >= r
+      const c32 rsc = A[s * kLeafLd + c];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const int r = rb + rr;
+        if (s > r) cfma(acc[rr], A[s * kLeafLd + r], rsc);
+        else if (s == r) cfma(acc[rr], Td[r], rsc);
+      }
+    }
+    for (int s = rb + 8; s < c0; ++s) {
+      const c32 rsc = A[s * kLeafLd + c];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], A[s * kLeafLd + rb + rr], rsc);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) Z[(rb + rr) * kLeafYLd + cc] = acc[rr];
+  }
+}
+
+__device__ __forceinline__ void leaf_tcol_second(c32* A, const c32* Td, const c32* Z, int n, int j, int t, int nt) {
+  const int c0 = 32 * j, mj = min(32, n - c0), items = 4 * j * mj;
+  for (int e = t; e < items; e += nt) {
+    const int rq = e / mj, cc = e % mj, c = c0 + cc, rb = 8 * rq;
+    c32 acc[8];
+    const c32 tcc = Td[c];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = cmul(Z[(rb + rr) * kLeafYLd + cc], tcc);
+    for (int s = c0; s < c; ++s) {
+      const c32 tsc = A[c * kLeafLd + s];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], Z[(rb + rr) * kLeafYLd + s - c0], tsc);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) A[c * kLeafLd + rb + rr] = cmk(-acc[rr].re, -acc[rr].im);
+  }
 }
 
 __global__ void __launch_bounds__(kLeafThreads, 1) chol_inv_leaf_kernel(const c32* __restrict__ G, c32* R, c32* T,
@@ -155,24 +198,26 @@ __global__ void __launch_bounds__(kLeafThreads, 1) chol_inv_leaf_kernel(const c3
   extern __shared__ c32 sm[];
   c32* A = sm;                                  // A[r * kLeafLd + c]
   c32* Td = sm + kLeafMax * kLeafLd;            // diagonal of T
-  c32* Y = Td + kLeafMax;                       // panel staging (32 x 96), products of the inverse (96 x 32)
-  float* Rinv = (float*)(Y + 96 * kLeafYLd);    // 1 / R_jj
+  c32* Y = Td + kLeafMax;                       // panel staging (32 x 96)
+  c32* Z = Y + 96 * kLeafYLd;                   // products of the inverse (96 x 32)
   const int64_t b = blockIdx.x;
   G += b * sNN;
   R += b * sNN;
   T += b * sNN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int base = tid; base < n * n; base += 8 * kLeafThreads) {   // 8 loads in flight per thread
-    c32 v[8];
+  // the upper triangle, a warp per column and a lane per row, 16 loads in flight per thread
+  // (one SM alone: the bytes in flight set the rate)
+  for (int c0 = warp; c0 < n; c0 += 4 * (kLeafThreads / 32)) {
+    c32 v[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * kLeafThreads, r = idx % n, c = idx / n;
-      v[u] = (idx < n * n && r <= c) ? G[r + (int64_t)c * ld] : cmk(0.0f, 0.0f);
+    for (int u = 0; u < 16; ++u) {
+      const int c = c0 + (u >> 2) * (kLeafThreads / 32), r = lane + 32 * (u & 3);
+      v[u] = (c < n && r <= c) ? G[r + (int64_t)c * ld] : cmk(0.0f, 0.0f);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * kLeafThreads, r = idx % n, c = idx / n;
-      if (idx < n * n && r <= c) A[r * kLeafLd + c] = v[u];
+    for (int u = 0; u < 16; ++u) {
+      const int c = c0 + (u >> 2) * (kLeafThreads / 32), r = lane + 32 * (u & 3);
+      if (c < n && r <= c) A[r * kLeafLd + c] = v[u];
     }
   }
   __syncthreads();
@@ -180,7 +225,18 @@ __global__ void __launch_bounds__(kLeafThreads, 1) chol_inv_leaf_kernel(const c3
   bool bad = false;
   for (int kb = 0; kb < nb; ++kb) {
     const int o = 32 * kb, m = min(32, n - o), rest = n - o - m;   // rest > 0 implies m == 32
-    if (warp == 0) bad |= leaf_diag_block(A + o * kLeafLd + o, Td + o, Rinv + o, m, lane);
+    if (warp == 0) {
+      bad |= leaf_diag_block(A + o * kLeafLd + o, Td + o, m, lane);
+    } else if (kb >= 1) {
+      // meanwhile, the other warps: the second half of block column kb - 1 of T, then the
+      // first half of block column kb (neither touches block kb, which warp 0 is factoring)
+      const int t = tid - 32, nt = kLeafThreads - 32;
+      if (kb >= 2) {
+        leaf_tcol_second(A, Td, Z, n, kb - 1, t, nt);
+        asm volatile("bar.sync 1, %0;" ::"n"(kLeafThreads - 32) : "memory");
+      }
+      leaf_tcol_first(A, Td, Z, n, kb, t, nt);
+    }
     __syncthreads();
     if (rest == 0) break;
     // panel R_{o+r, c} = sum_{i <= r} conj(T_{o+i, o+r}) G_{o+i, c}: items (8 rows, column),
@@ -239,61 +295,23 @@ __global__ void __launch_bounds__(kLeafThreads, 1) chol_inv_leaf_kernel(const c3
     }
     __syncthreads();
   }
-  // T above the diagonal blocks, block column j: Y = T_<j,<j R_<j,j, then T_<j,j = -Y T_jj
-  for (int j = 1; j < nb; ++j) {
-    const int c0 = 32 * j, mj = min(32, n - c0), items = 4 * j * mj;
-    for (int e = tid; e < items; e += kLeafThreads) {
-      const int rq = e / mj, cc = e % mj, c = c0 + cc, rb = 8 * rq;
-      c32 acc[8];
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) acc[rr] = cmk(0.0f, 0.0f);
-      for (int s = rb; s < rb + 8; ++s) {       // the 8 x 8 triangle of T_rs, s >= r
-        const c32 rsc = A[s * kLeafLd + c];
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-          const int r = rb + rr;
-          if (s > r) cfma(acc[rr], A[s * kLeafLd + r], rsc);
-          else if (s == r) cfma(acc[rr], Td[r], rsc);
-        }
-      }
-      for (int s = rb + 8; s < c0; ++s) {
-        const c32 rsc = A[s * kLeafLd + c];
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], A[s * kLeafLd + rb + rr], rsc);
-      }
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) Y[(rb + rr) * kLeafYLd + cc] = acc[rr];
-    }
-    __syncthreads();
-    for (int e = tid; e < items; e += kLeafThreads) {
-      const int rq = e / mj, cc = e % mj, c = c0 + cc, rb = 8 * rq;
-      c32 acc[8];
-      const c32 tcc = Td[c];
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) acc[rr] = cmul(Y[(rb + rr) * kLeafYLd + cc], tcc);
-      for (int s = c0; s < c; ++s) {
-        const c32 tsc = A[c * kLeafLd + s];
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) cfma(acc[rr], Y[(rb + rr) * kLeafYLd + s - c0], tsc);
-      }
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) A[c * kLeafLd + rb + rr] = cmk(-acc[rr].re, -acc[rr].im);
-    }
+  // the second half of the last block column of T (the others ran beside the factorisation)
+  if (nb >= 2) {
+    leaf_tcol_second(A, Td, Z, n, nb - 1, tid, kLeafThreads);
     __syncthreads();
   }
   if (bad && lane == 0) atomicOr(status, FM_DEVERR_PIVOT);
-  for (int idx = tid; idx < n * n; idx += kLeafThreads) {
-    const int r = idx % n, c = idx / n;
-    const int64_t o = r + (int64_t)c * ld;
-    if (r < c) {
-      R[o] = A[r * kLeafLd + c];
-      T[o] = A[c * kLeafLd + r];
-    } else if (r == c) {
-      R[o] = A[r * kLeafLd + r];
-      T[o] = Td[r];
-    } else {
-      R[o] = cmk(0.0f, 0.0f);
-      T[o] = cmk(0.0f, 0.0f);
+  // R and T with their zeros, a warp per column and a lane per row
+  for (int c = warp; c < n; c += kLeafThreads / 32) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = lane + 32 * u;
+      if (r < n) {
+        const int64_t o = r + (int64_t)c * ld;
+        const c32 zero = cmk(0.0f, 0.0f);
+        R[o] = (r <= c) ? A[r * kLeafLd + c] : zero;
+        T[o] = (r < c) ? A[c * kLeafLd + r] : (r == c ? Td[r] : zero);
+      }
     }
   }
 }
