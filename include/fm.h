@@ -110,15 +110,19 @@ typedef struct {
  * the height of the tile raster groups, 2^(g+1) row tiles (0: 8); bits 5-6 d:
  * with reorth_interval > 1, the first CholeskyQR product of the steps that no
  * second pass follows drains its fp32 tensor-memory accumulators (which round
- * toward zero) into registers every 2^(d+1) K-blocks of 64 (0: 2; 3 is invalid).
- * Any other bit set is FM_EINVAL.  Bits 0-4 do not change a single result (each
- * output is one fixed-order sum per tile); bits 5-6 change the rounding of U
- * between second passes (U^dag U - 1 stays ~1e-6 there). */
+ * toward zero) into registers every 2^(d+1) K-blocks of 64 (0: 2; 3 is invalid);
+ * bit 7: the first CholeskyQR factorisation of a batch of three or more runs as one
+ * chain of launches per trajectory (up to four streams) instead of two halves of
+ * the batch.  Any other bit set is FM_EINVAL.  Bits 0-4 and 7 do not change a
+ * single result (each output is one fixed-order sum per tile, each factor one
+ * trajectory's); bits 5-6 change the rounding of U between second passes
+ * (U^dag U - 1 stays ~1e-6 there). */
 #define FM_TILE_BN_AUTO 0
 #define FM_TILE_BN_128 1
 #define FM_TILE_BN_256 2
 #define FM_TILE_GROUP(g) ((g) << 2)
 #define FM_TILE_DRAIN(d) ((d) << 5)
+#define FM_TILE_CHOL_CHAINS (1 << 7)
 
 /* One projective measurement: trajectory b of the batch, step index (t/dt
  * before the step), site, the outcome draw u, Born probability p, outcome. */
@@ -353,7 +357,9 @@ typedef struct {
  * <= ortho_tol after the steps that end a period (second pass done) and
  * <= 100 ortho_tol after the others wins (observables first complete a
  * period that is still open, see fm_entropy); if none does, the fastest with
- * reorth_interval = 1.
+ * reorth_interval = 1.  Mixed precision then also measures, against the winner,
+ * its first-pass drain intervals of 4 and 8 K-blocks (reorth_interval > 1) and
+ * then one Cholesky chain per trajectory (batches of three or more).
  * Synchronises; the workspace holds nothing useful afterwards. */
 fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, void* cuda_stream,
                       int32_t steps, int32_t max_reorth, double ortho_tol, int32_t use_graphs,

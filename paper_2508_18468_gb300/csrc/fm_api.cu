@@ -1997,8 +1997,10 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
   do {
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { r = FM_ECUDA; break; }
     // candidates: every tile configuration x interval, then (mixed precision, interval > 1)
-    // the drain intervals of the first-pass product for the fastest accepted one
+    // the drain intervals of the first-pass product for the fastest accepted one, then
+    // (batches of three or more) the fastest with one Cholesky chain per trajectory
     std::vector<std::pair<int, int>> cands;
+    int stage = 0;
     for (int k = 1; k <= max_reorth; k *= 2)
       for (int tc : tiles) cands.push_back({tc, k});
     for (size_t ci = 0; ci < cands.size() && r == FM_OK; ++ci) {
@@ -2041,8 +2043,17 @@ fm_status fm_autotune(const fm_params* p, void* d_workspace, size_t ws_bytes, vo
         } else {
           ++rejected;
         }
-        if (ci + 1 == cands.size() && mixed && have && best.reorth_interval > 1 && !(best.tile_config >> 5))
-          for (int d = 1; d <= 2; ++d) cands.push_back({best.tile_config | (d << 5), best.reorth_interval});
+        if (ci + 1 == cands.size() && mixed && have) {
+          if (stage == 0) {
+            stage = 1;
+            if (best.reorth_interval > 1 && !(best.tile_config >> 5))
+              for (int d = 1; d <= 2; ++d) cands.push_back({best.tile_config | (d << 5), best.reorth_interval});
+          }
+          if (stage == 1 && ci + 1 == cands.size()) {
+            stage = 2;
+            if (s->B >= 3) cands.push_back({best.tile_config | FM_TILE_CHOL_CHAINS, best.reorth_interval});
+          }
+        }
     }
   } while (0);
   if (e0) cudaEventDestroy(e0);

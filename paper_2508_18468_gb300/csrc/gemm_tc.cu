@@ -50,6 +50,62 @@ __device__ __forceinline__ TileInfo decode(const Params& p, int t) {
     ti.mt = v.x; ti.nt = v.y; ti.b = v.z; ti.part = v.w;
     return ti;
   }
+  if (p.order == ORDER_PAIRS_A || p.order == ORDER_PAIRS_B) {
+    // units = pairs of tiles; rounds 2k and 2k + 1 of the persistent loop take the two
+    // members of the same G units in the same CTA order (the last, partial round pair:
+    // its members side by side)
+    const int G = gridDim.x, U = p.ntiles >> 1;
+    const int kp = t / (2 * G), full = U / G, rem = U - full * G;
+    const int rr = t - kp * 2 * G;
+    const int which = kp < full ? rr / G : rr / rem;
+    const int u = kp * G + (kp < full ? rr - which * G : rr - which * rem);
+    const int M = p.mt_mod;
+    if (p.order == ORDER_PAIRS_A) {
+      const int P2 = M >> 1, pr = u % P2;
+      int rest = u / P2;
+      ti.nt = rest % p.ntiles_n;
+      rest /= p.ntiles_n;
+      const bool high = (which == 0) == (p.kb_hi_mt != 0);   // the heavier member first
+      ti.mt = (rest & 1) * M + (high ? M - 1 - pr : pr);
+      ti.b = rest >> 1;
+    } else {
+      const int P2 = p.ntiles_n >> 1, pn = u % P2;
+      const int rest = u / P2;
+      ti.mt = rest % p.mtiles;
+      ti.b = rest / p.mtiles;
+      ti.nt = which == 0 ? p.ntiles_n - 1 - pn : pn;
+    }
+    ti.part = 0;
+    return ti;
+  }
+  if (p.order == ORDER_HERM) {
+    // the upper tiles of each (batch item, Re / Im half): groups of 16 row tiles, each
+    // sweeping its columns nt >= its first row (column j of a group holds min(16, j + 1) rows)
+    const int M = p.mt_mod, T = M * (M + 1) / 2;
+    const int bp = t / T;
+    int r = t - bp * T, g0 = 0;
+    for (;;) {
+      const int w = M - g0;
+      const int size = w <= 16 ? w * (w + 1) / 2 : 136 + (w - 16) * 16;
+      if (r < size) break;
+      r -= size;
+      g0 += 16;
+    }
+    int j, ro;
+    if (r < 136 || M - g0 <= 16) {
+      j = 0;
+      while ((j + 1) * (j + 2) / 2 <= r) ++j;
+      ro = r - j * (j + 1) / 2;
+    } else {
+      j = 16 + (r - 136) / 16;
+      ro = (r - 136) % 16;
+    }
+    ti.mt = (bp & 1) * M + g0 + ro;
+    ti.nt = g0 + j;
+    ti.b = bp >> 1;
+    ti.part = 0;
+    return ti;
+  }
   // grouped raster: 16 consecutive m-tiles sweep all n-tiles
   const int per_b = p.mtiles * p.ntiles_n;
   ti.b = t / per_b;

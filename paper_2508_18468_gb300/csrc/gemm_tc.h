@@ -24,8 +24,21 @@ enum Mode {
                    // imaginary parts; out_c complex64, ld_out / out_batch_stride in complex elements
 };
 
+// Tile orders when Params::tiles is NULL (each a bijection onto the launch's tiles):
+enum Order {
+  ORDER_RASTER = 0,   // groups of 16 row tiles sweep all column tiles
+  ORDER_PAIRS_A = 1,  // triangular A (kb_lo_mt / kb_hi_mt): row blocks mr and mt_mod - 1 - mr, whose
+                      //   K ranges add up to a constant, fall to one CTA in consecutive rounds
+                      //   (mt_mod even)
+  ORDER_PAIRS_B = 2,  // triangular B (kb_hi_nt): the same with column tiles nt and ntiles_n - 1 - nt
+                      //   (ntiles_n even)
+  ORDER_HERM = 3      // herm_upper: only the tiles mr <= nt (ntiles = batch 2 mt_mod (mt_mod + 1) / 2),
+                      //   groups of 16 row tiles sweeping their columns
+};
+
 struct Params {
   int mode;
+  int order;           // Order (with tiles == NULL)
   int ntiles;
   const int4* tiles;   // (mt, nt, b, part) per tile, device memory; NULL: grouped raster over
   int mtiles, ntiles_n;  //   mtiles x ntiles_n tiles per batch item (batch = ntiles / (mtiles ntiles_n))

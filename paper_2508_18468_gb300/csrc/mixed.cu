@@ -489,9 +489,12 @@ struct MixedHost {
   float *pb_dp, *pb_ap;
   PmbMats pm;
   std::vector<int> pb_hcount;
-  // second stream of the first-pass Cholesky (two halves of the batch side by side)
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // library streams of the first-pass Cholesky (parts of the batch side by side, the
+  // first part on the step's stream)
+  int nchains = 1;
+  cudaStream_t cst[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
 };
 
 bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* why) {
@@ -500,7 +503,7 @@ bool mixed_supported(int Lx, int Ly, int batch, int tile_config, std::string* wh
     *why = "mixed precision needs L = Lx*Ly divisible by 256 (N a multiple of 128)";
     return false;
   }
-  if ((tile_config & ~0x7f) || (tile_config & 3) == 3 || ((tile_config >> 5) & 3) == 3) {
+  if ((tile_config & ~0xff) || (tile_config & 3) == 3 || ((tile_config >> 5) & 3) == 3) {
     *why = "unknown tile_config bits";
     return false;
   }
@@ -521,12 +524,14 @@ size_t mixed_scratch_bytes(int Lx, int Ly, int batch, int protocol) {
 
 void mixed_free(MixedHost* h) {
   if (!h) return;
-  if (h->st2) {
-    cudaStreamSynchronize(h->st2);
-    cudaStreamDestroy(h->st2);
+  for (int i = 0; i < 3; ++i) {
+    if (h->cst[i]) {
+      cudaStreamSynchronize(h->cst[i]);
+      cudaStreamDestroy(h->cst[i]);
+    }
+    if (h->join[i]) cudaEventDestroy(h->join[i]);
   }
   if (h->fork) cudaEventDestroy(h->fork);
-  if (h->join) cudaEventDestroy(h->join);
   delete h;
 }
 
@@ -604,10 +609,15 @@ MixedHost* mixed_create(MixedCtx* c, std::string* why) {
     m.X = (c32*)(base + sp.pb_x);
     h->pb_hcount.assign(B, 0);
   }
-  if (B >= 2 && (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
-                 cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
-                 cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)) {
-    *why = "Cholesky stream";
+  // chains of the first-pass Cholesky: two halves of the batch, or one trajectory per
+  // chain up to four (tile_config bit 7, batches of three or more)
+  h->nchains = B < 2 ? 1 : ((c->tile_config & FM_TILE_CHOL_CHAINS) && B >= 3 ? std::min(B, 4) : 2);
+  bool streams_ok = h->nchains == 1 || cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; streams_ok && i + 1 < h->nchains; ++i)
+    streams_ok = cudaStreamCreateWithFlags(&h->cst[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!streams_ok) {
+    *why = "Cholesky streams";
     mixed_free(h);
     return nullptr;
   }
@@ -733,6 +743,17 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
   p.kb_hi_mt = (shape & CG_A_LOWER) ? 4 : 0;
   p.kb_hi_nt = (shape & CG_B_UPPER) ? 4 : 0;
   p.herm_upper = (shape & CG_HERM) ? 1 : 0;
+  // balanced orders for the triangular and Hermitian shapes (their tiles' K ranges or
+  // counts differ by row or column; the plain raster left CTAs up to 1.4 x the mean)
+  const int M = m / tc::BM;
+  if ((shape & (CG_A_UPPER | CG_A_LOWER)) && M % 2 == 0) {
+    p.order = tc::ORDER_PAIRS_A;
+  } else if ((shape & CG_B_UPPER) && p.ntiles_n % 2 == 0) {
+    p.order = tc::ORDER_PAIRS_B;
+  } else if (shape & CG_HERM) {
+    p.order = tc::ORDER_HERM;
+    p.ntiles = B * M * (M + 1);
+  }
   MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, tc::sm_count()));
   return FM_OK;
 }
@@ -776,46 +797,60 @@ int chol_inv_rec(MixedHost* h, MixedCtx* c, int off, int n) {
   return FM_OK;
 }
 
-// The first-pass factorisation of the whole batch as two halves side by side: the halves'
-// recursions are independent, so one half's latency-bound leaves (a CTA per trajectory)
-// run while the other half's products fill the GPU.  The second half works on the second
-// halves of the factor and operand scratch (per-trajectory strides), on a library stream
-// forked from the step's stream and joined back into it (a captured graph holds both).
-int chol_two_halves(MixedHost* h, MixedCtx* c) {
-  const int B = c->B;
-  if (B < 2 || !h->st2) return chol_inv_rec(h, c, 0, c->N);
-  const int B1 = B / 2, B2 = B - B1;
+// The first-pass factorisation of the whole batch as parts side by side (two halves, or
+// one trajectory per part up to four): the parts' recursions are independent, so one
+// part's latency-bound leaves (a CTA per trajectory) and small products run while the
+// others' products fill the GPU.  Part i works on its trajectories' slices of the factor
+// and operand scratch (per-trajectory strides), part 0 on the step's stream and the others
+// on library streams forked from it and joined back into it (a captured graph holds all).
+// Every tile and every leaf is one trajectory's, so the split changes no result.
+int chol_chains(MixedHost* h, MixedCtx* c) {
+  const int B = c->B, P = std::min(h->nchains, B);
+  if (P < 2) return chol_inv_rec(h, c, 0, c->N);
   const int64_t sNN = (int64_t)c->N * c->N, md2 = h->md * h->md;
-  MixedHost h2 = *h;
-  h2.gf += B1 * sNN;
-  h2.rf += B1 * sNN;
-  h2.tf += B1 * sNN;
-  h2.ca_h += B1 * 4 * md2;
-  h2.ca_l += B1 * 4 * md2;
-  h2.cb_h += B1 * 2 * md2;
-  h2.cb_l += B1 * 2 * md2;
-  h2.xs += B1 * md2;
-  h2.st2 = nullptr;
-  h2.fork = h2.join = nullptr;                 // the copy owns nothing
-  MixedCtx c1 = *c, c2 = *c;
-  c1.B = B1;
-  c2.B = B2;
-  c2.st = h->st2;
-  c1.launches = c2.launches = 0;
-  if (cudaEventRecord(h->fork, c->st) != cudaSuccess || cudaStreamWaitEvent(h->st2, h->fork, 0) != cudaSuccess) {
+  if (cudaEventRecord(h->fork, c->st) != cudaSuccess) {
     c->err = "Cholesky stream fork";
     return FM_ECUDA;
   }
-  const int r1 = chol_inv_rec(h, &c1, 0, c->N);
-  const int r2 = r1 ? r1 : chol_inv_rec(&h2, &c2, 0, c->N);
-  h2.pb_hcount.clear();
-  c->launches += c1.launches + c2.launches;
-  // join even after an error, so that the step's stream never runs ahead of the second half
-  const bool joined = cudaEventRecord(h->join, h->st2) == cudaSuccess &&
-                      cudaStreamWaitEvent(c->st, h->join, 0) == cudaSuccess;
-  if (r1) { c->err = c1.err; return r1; }
-  if (r2) { c->err = c2.err; return r2; }
-  if (!joined) { c->err = "Cholesky stream join"; return FM_ECUDA; }
+  for (int i = 1; i < P; ++i)
+    if (cudaStreamWaitEvent(h->cst[i - 1], h->fork, 0) != cudaSuccess) {
+      c->err = "Cholesky stream fork";
+      return FM_ECUDA;
+    }
+  int r = FM_OK, b0 = 0;
+  for (int i = 0; i < P; ++i) {
+    const int nb = B / P + (i < B % P ? 1 : 0);
+    MixedHost hp = *h;                         // the copy owns nothing
+    hp.gf += b0 * sNN;
+    hp.rf += b0 * sNN;
+    hp.tf += b0 * sNN;
+    hp.ca_h += b0 * 4 * md2;
+    hp.ca_l += b0 * 4 * md2;
+    hp.cb_h += b0 * 2 * md2;
+    hp.cb_l += b0 * 2 * md2;
+    hp.xs += b0 * md2;
+    hp.pb_hcount.clear();
+    MixedCtx cp = *c;
+    cp.B = nb;
+    cp.st = i == 0 ? c->st : h->cst[i - 1];
+    cp.launches = 0;
+    if (r == FM_OK) {
+      r = chol_inv_rec(&hp, &cp, 0, c->N);
+      if (r) c->err = cp.err;
+    }
+    c->launches += cp.launches;
+    b0 += nb;
+  }
+  // join even after an error, so that the step's stream never runs ahead of a part
+  bool joined = true;
+  for (int i = 1; i < P; ++i)
+    joined = cudaEventRecord(h->join[i - 1], h->cst[i - 1]) == cudaSuccess &&
+             cudaStreamWaitEvent(c->st, h->join[i - 1], 0) == cudaSuccess && joined;
+  if (r) return r;
+  if (!joined) {
+    c->err = "Cholesky stream join";
+    return FM_ECUDA;
+  }
   return FM_OK;
 }
 
@@ -868,7 +903,7 @@ int qr_pass(MixedHost* h, MixedCtx* c, bool first, bool paired, int mode = PASS_
   c->timer->end(FM_PH_GRAM);
   c->timer->begin(FM_PH_CHOLESKY);
   if (first) {
-    int r = chol_two_halves(h, c);
+    int r = chol_chains(h, c);
     if (r) return r;
   }
   build_ttilde_kernel<<<(unsigned)(2 * (int64_t)B * N), 256, 0, c->st>>>(first ? h->tf : h->gf, h->diag,

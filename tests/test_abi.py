@@ -61,7 +61,8 @@ def test_tile_config_is_validated(fm):
     assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=3, **mixed)) == 0
     assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=1 << 5, **mixed)) > 0     # drain every 4 K-blocks
     assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=3 << 5, **mixed)) == 0
-    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=1 << 7, **mixed)) == 0
+    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=1 << 7, **mixed)) > 0      # a Cholesky chain per trajectory
+    assert fm.fm_workspace_bytes(fm.make_params(512, tile_config=1 << 8, **mixed)) == 0
     # the workspace does not depend on the tile configuration
     assert (fm.fm_workspace_bytes(fm.make_params(1024, tile_config=1, **mixed)) ==
             fm.fm_workspace_bytes(fm.make_params(1024, tile_config=2, **mixed)))

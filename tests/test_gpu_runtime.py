@@ -140,6 +140,20 @@ def test_tile_configurations_give_identical_states(fm):
             assert np.array_equal(g.copy_U(t), ref.copy_U(t)), tc
 
 
+def test_cholesky_chains_give_identical_states(fm):
+    """One first-pass Cholesky chain per trajectory (tile_config bit 7, three streams here)
+    against two halves of the batch: every factor is one trajectory's and every product
+    tile one fixed-order sum in any tile order, so not a bit changes (N = 1024: the
+    recursion's products of 512 and 256 run in the paired and Hermitian tile orders)."""
+    kw = dict(batch=3, protocol=1, precision=1, gamma=0.8, seed=9, reorth_interval=2)
+    ref = fm.Trajectories(fm.make_params(2048, **kw))
+    ref.step(5)
+    g = fm.Trajectories(fm.make_params(2048, tile_config=1 << 7, **kw))
+    g.step(5)
+    for t in range(3):
+        assert np.array_equal(g.copy_U(t), ref.copy_U(t)), t
+
+
 def test_autotune_picks_a_configuration_that_meets_the_bar(fm):
     p = fm.make_params(512, batch=2, protocol=1, precision=1, gamma=1.0, seed=3)
     res = fm.autotune(p, steps=2, max_reorth=2, ortho_tol=1e-6)
