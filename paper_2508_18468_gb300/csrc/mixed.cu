@@ -236,12 +236,11 @@ __global__ void __launch_bounds__(256) embed_a_kernel(const c32* __restrict__ X,
 // The same planes as embed_a_kernel for k a multiple of 64: a 32 x 64 tile of op(X)
 // staged in shared memory, then each thread writes the 8 K positions of one row and one
 // group of 8 complex columns as 16-byte stores (Re, -Im on the top row, Im, Re on the
-// bottom row, both planes).  Grid (m / 32, k / 64, B), 256 threads.
-__global__ void __launch_bounds__(256) embed_a64_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op,
-                                                        int m, int k, __half* Ah, __half* Al) {
+// bottom row, both planes).  Block (bx, by, b) of a grid (m / 32, k / 64, B), 256 threads.
+__device__ __forceinline__ void embed_a64_block(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op, int m,
+                                                int k, __half* Ah, __half* Al, int bx, int by, int64_t b) {
   __shared__ c32 t[32][65];                       // t[row][col] of op(X)
-  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 64;
-  const int64_t b = blockIdx.z;
+  const int r0 = bx * 32, c0 = by * 64;
   const c32* Xb = X + b * sX;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   if (op == 2) {
@@ -282,12 +281,12 @@ __global__ void __launch_bounds__(256) embed_a64_kernel(const c32* __restrict__ 
 
 // The planes of embed_b_kernel for op(Y) = Y and k a multiple of 64, without staging:
 // each thread reads 8 consecutive entries of one column of Y (64 bytes) and writes their
-// Re and Im halves as 16-byte stores.  Grid (k / 64, n / 32, B), 256 threads.
-__global__ void __launch_bounds__(256) embed_b64_kernel(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int k,
-                                                        int n, __half* Bh, __half* Bl) {
+// Re and Im halves as 16-byte stores.  Block (bx, by, b) of a grid (k / 64, n / 32, B),
+// 256 threads.
+__device__ __forceinline__ void embed_b64_block(const c32* __restrict__ Y, int64_t ldy, int64_t sY, int k, int n,
+                                                __half* Bh, __half* Bl, int bx, int by, int64_t b) {
   const int tid = threadIdx.x, g = tid & 7, jj = tid >> 3;
-  const int kk0 = blockIdx.x * 64 + 8 * g, j = blockIdx.y * 32 + jj;
-  const int64_t b = blockIdx.z;
+  const int kk0 = bx * 64 + 8 * g, j = by * 32 + jj;
   const float4* src = (const float4*)(Y + b * sY + kk0 + (int64_t)j * ldy);
   float4 v[4];
 #pragma unroll
@@ -305,6 +304,28 @@ __global__ void __launch_bounds__(256) embed_b64_kernel(const c32* __restrict__ 
   *(uint4*)(Bl + o) = *(const uint4*)lre;
   *(uint4*)(Bh + o + 32) = *(const uint4*)him;
   *(uint4*)(Bl + o + 32) = *(const uint4*)lim;
+}
+
+__global__ void __launch_bounds__(256) embed_a64_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op,
+                                                        int m, int k, __half* Ah, __half* Al) {
+  embed_a64_block(X, ldx, sX, op, m, k, Ah, Al, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Both operands' planes of one product in one launch: blocks [0, nA) of the flattened
+// grid run embed_a64_block over (m / 32) x (k / 64) tiles, the rest embed_b64_block
+// over (k / 64) x (n / 32); blockIdx.y is the trajectory.
+__global__ void __launch_bounds__(256) embed_ab64_kernel(const c32* __restrict__ X, int64_t ldx, int64_t sX, int op,
+                                                         const c32* __restrict__ Y, int64_t ldy, int64_t sY, int m,
+                                                         int n, int k, __half* Ah, __half* Al, __half* Bh,
+                                                         __half* Bl) {
+  const int nAx = m / 32, nA = nAx * (k / 64), nBx = k / 64;
+  const int i = blockIdx.x;
+  if (i < nA) {
+    embed_a64_block(X, ldx, sX, op, m, k, Ah, Al, i % nAx, i / nAx, blockIdx.y);
+  } else {
+    const int j = i - nA;
+    embed_b64_block(Y, ldy, sY, k, n, Bh, Bl, j % nBx, j / nBx, blockIdx.y);
+  }
 }
 
 // Planes of B (n x 2k, row-major): row j = the Re and Im parts of op(Y)[:, j], K
@@ -700,18 +721,21 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
     return FM_EINVAL;
   }
   const bool y_aligned = ((uintptr_t)Y % 16 == 0) && (ldy % 2 == 0) && (sY % 2 == 0);
-  if (k % 64 == 0) {
-    embed_a64_kernel<<<dim3(m / 32, k / 64, B), 256, 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
-  } else {
-    embed_a_kernel<<<dim3(m / 32, k / 32, B), dim3(32, 8), 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
-  }
-  MCK(cudaGetLastError());
   if (k % 64 == 0 && opY == 0 && y_aligned) {
-    embed_b64_kernel<<<dim3(k / 64, n / 32, B), 256, 0, c->st>>>(Y, ldy, sY, k, n, h->cb_h, h->cb_l);
+    const int nblk = (m / 32) * (k / 64) + (k / 64) * (n / 32);
+    embed_ab64_kernel<<<dim3(nblk, B), 256, 0, c->st>>>(X, ldx, sX, opX, Y, ldy, sY, m, n, k, h->ca_h, h->ca_l,
+                                                        h->cb_h, h->cb_l);
+    MCK(cudaGetLastError());
   } else {
+    if (k % 64 == 0) {
+      embed_a64_kernel<<<dim3(m / 32, k / 64, B), 256, 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+    } else {
+      embed_a_kernel<<<dim3(m / 32, k / 32, B), dim3(32, 8), 0, c->st>>>(X, ldx, sX, opX, m, k, h->ca_h, h->ca_l);
+    }
+    MCK(cudaGetLastError());
     embed_b_kernel<<<dim3(k / 32, n / 32, B), dim3(32, 8), 0, c->st>>>(Y, ldy, sY, opY, k, n, h->cb_h, h->cb_l);
+    MCK(cudaGetLastError());
   }
-  MCK(cudaGetLastError());
   CUtensorMap ah, al, bh, bl;
   const uint64_t K2 = 2 * (uint64_t)k;
   if (!tc::make_kmajor_map(&ah, h->ca_h, K2, (uint64_t)B * 2 * m, K2, tc::BM) ||
