@@ -778,7 +778,12 @@ int cgemm_tc(MixedHost* h, MixedCtx* c, int opX, const c32* X, int64_t ldx, int6
     p.order = tc::ORDER_HERM;
     p.ntiles = B * M * (M + 1);
   }
-  MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, tc::sm_count()));
+  // with the batch factored as parts side by side, a product that fills the GPU leaves 8 SMs
+  // to the other parts' latency-bound leaves and small products (its CTAs hold their SMs
+  // for the whole launch)
+  const int sms = tc::sm_count();
+  const int grid = h->nchains >= 2 && p.ntiles > sms && sms > 32 ? sms - 8 : sms;
+  MCK(tc::launch(c->st, 128, ah, al, bh, bl, p, grid));
   return FM_OK;
 }
 
