@@ -65,6 +65,21 @@ int fmx_poisson_draw(unsigned long long seed, unsigned long long traj, long long
 int fmx_poisson_taps(int n, int w, double J, double tau, double* out);
 int fmx_poisson_width(int n, double J, double dt);
 
+/* Host-only hook of the tensor-core GEMM's tile orders (no device needed): the
+ * tiles (row tile, column tile, batch item) of one launch in the order its
+ * persistent loop takes them, CTA i taking positions i, i + G, i + 2G, ... of
+ * a grid of G = min(grid, tiles) CTAs.  The launch has `batch` items of
+ * 2 mt_mod row tiles (the real and imaginary halves of a complex product's
+ * rows, mt_mod tiles each) by ntiles_n column tiles.  order: 0 grouped raster
+ * (16 row tiles sweep the columns); 1 the row blocks r and mt_mod - 1 - r of a
+ * triangular A paired in consecutive rounds (lower != 0: A lower triangular,
+ * else upper; mt_mod even); 2 the column tiles c and ntiles_n - 1 - c of a
+ * triangular B paired (ntiles_n even); 3 only the tiles on or above the
+ * diagonal of a Hermitian product (ntiles_n == mt_mod).  out[3 t .. 3 t + 2]
+ * for each position t; cap: entries of out / 3.  Returns the number of tiles,
+ * or -1 on invalid arguments. */
+int fmx_tile_order(int order, int mt_mod, int ntiles_n, int batch, int lower, int grid, int* out, int cap);
+
 #ifdef __cplusplus
 }
 #endif

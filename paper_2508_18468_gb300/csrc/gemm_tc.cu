@@ -12,6 +12,7 @@
 // warps 4-7 drain TMEM into the mode's epilogue.  Every wait is bounded and
 // raises FM_DEVERR_TIMEOUT instead of hanging.
 #include <atomic>
+#include <cstring>
 #include <mutex>
 #include <cudaTypedefs.h>
 
@@ -43,18 +44,15 @@ struct TileInfo {
   int mt, nt, b, part;
 };
 
-__device__ __forceinline__ TileInfo decode(const Params& p, int t) {
+// The tile at position t of the persistent loop of a launch of G CTAs (CTA i takes the
+// positions i, i + G, ...); host and device (the host side serves fmx_tile_order).
+__host__ __device__ __forceinline__ TileInfo decode_order(const Params& p, int t, int G) {
   TileInfo ti;
-  if (p.tiles) {
-    const int4 v = p.tiles[t];
-    ti.mt = v.x; ti.nt = v.y; ti.b = v.z; ti.part = v.w;
-    return ti;
-  }
   if (p.order == ORDER_PAIRS_A || p.order == ORDER_PAIRS_B) {
     // units = pairs of tiles; rounds 2k and 2k + 1 of the persistent loop take the two
     // members of the same G units in the same CTA order (the last, partial round pair:
     // its members side by side)
-    const int G = gridDim.x, U = p.ntiles >> 1;
+    const int U = p.ntiles >> 1;
     const int kp = t / (2 * G), full = U / G, rem = U - full * G;
     const int rr = t - kp * 2 * G;
     const int which = kp < full ? rr / G : rr / rem;
@@ -113,12 +111,22 @@ __device__ __forceinline__ TileInfo decode(const Params& p, int t) {
   const int GM = 16;
   const int group = t / (GM * p.ntiles_n);
   const int first_m = group * GM;
-  const int gsz = min(GM, p.mtiles - first_m);
+  const int gsz = p.mtiles - first_m < GM ? p.mtiles - first_m : GM;
   const int r = t - group * GM * p.ntiles_n;
   ti.mt = first_m + r % gsz;
   ti.nt = r / gsz;
   ti.part = 0;
   return ti;
+}
+
+__device__ __forceinline__ TileInfo decode(const Params& p, int t) {
+  if (p.tiles) {
+    const int4 v = p.tiles[t];
+    TileInfo ti;
+    ti.mt = v.x; ti.nt = v.y; ti.b = v.z; ti.part = v.w;
+    return ti;
+  }
+  return decode_order(p, t, gridDim.x);
 }
 
 // One 32-column slab of a finished tile: row r of the tile, columns c0..c0+31.
@@ -567,3 +575,32 @@ int sm_count() {
 
 }  // namespace tc
 }  // namespace fm
+
+// Host-only test hook: the tiles of one launch in the order the persistent loop takes them.
+extern "C" int fmx_tile_order(int order, int mt_mod, int ntiles_n, int batch, int lower, int grid, int* out,
+                              int cap) {
+  using namespace fm::tc;
+  if (order < ORDER_RASTER || order > ORDER_HERM || mt_mod < 1 || ntiles_n < 1 || batch < 1 || grid < 1 ||
+      (order == ORDER_PAIRS_A && mt_mod % 2) || (order == ORDER_PAIRS_B && ntiles_n % 2) ||
+      (order == ORDER_HERM && ntiles_n != mt_mod))
+    return -1;
+  Params p;
+  memset(&p, 0, sizeof(p));
+  p.order = order;
+  p.mt_mod = mt_mod;
+  p.mtiles = 2 * mt_mod;
+  p.ntiles_n = ntiles_n;
+  p.kb_hi_mt = lower ? 4 : 0;
+  p.kb_lo_mt = lower ? 0 : 4;
+  const int64_t n = order == ORDER_HERM ? (int64_t)batch * mt_mod * (mt_mod + 1) : (int64_t)batch * 2 * mt_mod * ntiles_n;
+  if (n > cap || n > (1 << 30)) return -1;
+  p.ntiles = (int)n;
+  const int G = grid < p.ntiles ? grid : p.ntiles;     // as tc::launch clamps it
+  for (int t = 0; t < p.ntiles; ++t) {
+    const TileInfo ti = decode_order(p, t, G);
+    out[3 * t] = ti.mt;
+    out[3 * t + 1] = ti.nt;
+    out[3 * t + 2] = ti.b;
+  }
+  return p.ntiles;
+}
