@@ -580,7 +580,7 @@ int sm_count() {
 extern "C" int fmx_tile_order(int order, int mt_mod, int ntiles_n, int batch, int lower, int grid, int* out,
                               int cap) {
   using namespace fm::tc;
-  if (order < ORDER_RASTER || order > ORDER_HERM || mt_mod < 1 || ntiles_n < 1 || batch < 1 || grid < 1 ||
+  if (!out || order < ORDER_RASTER || order > ORDER_HERM || mt_mod < 1 || ntiles_n < 1 || batch < 1 || grid < 1 ||
       (order == ORDER_PAIRS_A && mt_mod % 2) || (order == ORDER_PAIRS_B && ntiles_n % 2) ||
       (order == ORDER_HERM && ntiles_n != mt_mod))
     return -1;

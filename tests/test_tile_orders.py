@@ -77,6 +77,7 @@ def test_invalid_arguments_are_refused(order):
     assert f(HERM, 4, 5, 1, 0, 8, buf.ctypes.data, 64) == -1         # not square
     assert f(7, 4, 4, 1, 0, 8, buf.ctypes.data, 64) == -1            # unknown order
     assert f(RASTER, 4, 4, 2, 0, 8, buf.ctypes.data, 63) == -1       # 64 tiles do not fit
+    assert f(RASTER, 4, 4, 1, 0, 8, None, 64) == -1                  # no output array
 
 
 def _imbalance(tiles, G, kind, lower, mt_mod):
