@@ -17,7 +17,21 @@ FM_PROJECTIVE, FM_HOMODYNE, FM_HOMODYNE_RK4, FM_PROJECTIVE_POISSON = 0, 1, 2, 3
 FM_FP64, FM_MIXED = 0, 1
 FM_PROP_DENSE, FM_PROP_BANDED = 0, 1
 FM_EE_FULL, FM_EE_SKETCH, FM_EE_AUTO = 0, 1, 2
+FM_TILE_BN_AUTO, FM_TILE_BN_128, FM_TILE_BN_256 = 0, 1, 2
+FM_TILE_CHOL_CHAINS = 1 << 7
+FM_NOALLOC_MAX_SITES, FM_NOALLOC_MAX_N = 1024, 512
+
+
+def FM_TILE_GROUP(g):
+    """Raster groups of 2^(g+1) row tiles (fm_params.tile_config bits 2-4)."""
+    return g << 2
+
+
+def FM_TILE_DRAIN(d):
+    """First-pass accumulators drained every 2^(d+1) K-blocks (fm_params.tile_config bits 5-6)."""
+    return d << 5
 PHASES = ("propagate", "measure", "gram", "cholesky", "trmm", "entropy")
+FM_NPHASES = len(PHASES)
 STATUS_NAMES = {0: "FM_OK", 1: "FM_EINVAL", 2: "FM_ENOMEM", 3: "FM_ECUDA", 4: "FM_ENUMERIC",
                 5: "FM_ETIMEOUT", 6: "FM_ESTATE"}
 

@@ -149,3 +149,27 @@ def test_test_hooks_reject_invalid_sizes_before_any_launch(fm):
     for n, ld, B in ((0, 1, 1), (129, 129, 1), (64, 63, 1), (64, 64, 0)):
         assert lib.fmx_chol_leaf(dummy, n, ld, B, dummy, dummy, dummy, None) == INVALID
     assert lib.fmx_chol_leaf(dummy, 64, 64, 1, dummy, dummy, None, None) == INVALID   # no status word
+
+
+def test_binding_constants_match_the_header(fm):
+    """Every integer constant of include/fm.h (enumerators and object-like #defines) has the same
+    value in the binding, and the function-like tile macros agree on a few arguments."""
+    src = open(os.path.join(ROOT, "include", "fm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"\b(FM_[A-Z0-9_]+)\s*=\s*([0-9]+)", body):
+            consts[name] = int(val)
+    for name, expr in re.findall(r"#define\s+(FM_[A-Z0-9_]+)\s+(\(?[0-9][0-9 <()]*\)?)\s*$", src, flags=re.M):
+        consts[name] = int(eval(expr))                    # plain integers and (1 << k)
+    assert {"FM_OK", "FM_MIXED", "FM_TILE_CHOL_CHAINS", "FM_NOALLOC_MAX_N"} <= set(consts)
+    for name, val in consts.items():
+        if name.startswith("FM_PH_"):
+            assert fm.PHASES[val] == name[6:].lower(), name
+            continue
+        assert getattr(fm, name) == val, name
+    for g in range(8):
+        assert fm.FM_TILE_GROUP(g) == g << 2
+    for d in range(3):
+        assert fm.FM_TILE_DRAIN(d) == d << 5
+
